@@ -1,0 +1,195 @@
+"""ctypes wrapper of the HWENO-I CPU oracle (``hweno_oracle.cpp``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` are its only users.  The product package never imports this module and this module
+never imports the product package.
+
+The oracle follows the paper (Xie, Tao, Jiao, Zhang, arXiv 2411.11229) step by step in FP64:
+Sec. 2.1 (HWENO interpolation and limiter), Sec. 2.2 (central Hermite D-terms), Eqs. (flux-1d),
+(flux-LF), (fully-hweno), Sec. 3 (2D, Eq. mixed) and the characteristic-decomposition remarks.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hweno_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ADVECTION, BURGERS, EULER = 0, 1, 2
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (-O2, no FMA contraction) into oracle/liboracle.so."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Cfg(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("system", ctypes.c_int32), ("nx", ctypes.c_int32),
+                ("ny", ctypes.c_int32), ("bc", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("gamma0", ctypes.c_double), ("d0", ctypes.c_double), ("eps", ctypes.c_double),
+                ("ax", ctypes.c_double), ("ay", ctypes.c_double)]
+
+
+def make_cfg(dim, system, nx, ny=1, dx=1.0, dy=1.0, gamma=1.4, bc=BC_PERIODIC, gamma0=None, d0=0.9,
+             eps=1e-10, ax=1.0, ay=1.0) -> Cfg:
+    """Scheme parameters; gamma0 defaults to 0.95 (1D) / 0.99 (2D) and d0 to 0.9 (Sec. 4)."""
+    if gamma0 is None:
+        gamma0 = 0.95 if dim == 1 else 0.99
+    return Cfg(dim, system, nx, ny if dim == 2 else 1, bc, 0, dx, dy if dim == 2 else dx, gamma,
+               gamma0, d0, eps, ax, ay)
+
+
+_P = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            CP = ctypes.POINTER(Cfg)
+            L.oracle_state_size.argtypes = [CP]
+            L.oracle_state_size.restype = ctypes.c_longlong
+            L.oracle_max_wavespeed.argtypes = [CP, _P, _P, _P]
+            L.oracle_rhs.argtypes = [CP, _P, _P, _P]
+            L.oracle_rhs_alpha.argtypes = [CP, _P, ctypes.c_double, ctypes.c_double, _P, _P]
+            L.oracle_steps.argtypes = [CP, _P, ctypes.c_double, ctypes.c_int]
+            L.oracle_cfl_dt.argtypes = [CP, _P, ctypes.c_double, ctypes.c_double]
+            L.oracle_cfl_dt.restype = ctypes.c_double
+            L.oracle_run.argtypes = [CP, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_longlong, _P]
+            L.oracle_run.restype = ctypes.c_longlong
+            L.oracle_stencil.argtypes = [_P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, _P]
+            L.oracle_dterms.argtypes = [_P, _P, ctypes.c_double, _P]
+            L.oracle_euler_flux.argtypes = [CP, ctypes.c_int, _P, _P]
+            L.oracle_euler_jacobian.argtypes = [CP, ctypes.c_int, _P, _P]
+            L.oracle_euler_eigen.argtypes = [CP, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_P)
+
+
+def _check(rc):
+    if rc != 0:
+        raise ValueError(f"oracle call failed ({rc})")
+
+
+def state_size(cfg: Cfg) -> int:
+    n = lib().oracle_state_size(ctypes.byref(cfg))
+    if n < 0:
+        raise ValueError("invalid configuration")
+    return int(n)
+
+
+def max_wavespeed(cfg: Cfg, S: np.ndarray):
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    ax, ay = np.zeros(1), np.zeros(1)
+    _check(lib().oracle_max_wavespeed(ctypes.byref(cfg), _ptr(S), _ptr(ax), _ptr(ay)))
+    return float(ax[0]), float(ay[0])
+
+
+def rhs(cfg: Cfg, S: np.ndarray, alpha=None):
+    """(L(S), M(S)) of one stage; M = (U, V~, W~).  Arrays have the state's shape."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    assert S.size == state_size(cfg)
+    L = np.zeros_like(S)
+    M = np.zeros_like(S)
+    if alpha is None:
+        _check(lib().oracle_rhs(ctypes.byref(cfg), _ptr(S), _ptr(L), _ptr(M)))
+    else:
+        _check(lib().oracle_rhs_alpha(ctypes.byref(cfg), _ptr(S), float(alpha[0]), float(alpha[1]),
+                                      _ptr(L), _ptr(M)))
+    return L, M
+
+
+def steps(cfg: Cfg, S: np.ndarray, dt: float, nsteps: int = 1) -> np.ndarray:
+    out = np.array(S, dtype=np.float64, copy=True, order="C")
+    _check(lib().oracle_steps(ctypes.byref(cfg), _ptr(out), float(dt), int(nsteps)))
+    return out
+
+
+def cfl_dt(cfg: Cfg, S: np.ndarray, cfl: float = 0.6, dx_pow: float = 1.0) -> float:
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    return float(lib().oracle_cfl_dt(ctypes.byref(cfg), _ptr(S), float(cfl), float(dx_pow)))
+
+
+def run(cfg: Cfg, S: np.ndarray, t_end: float, cfl: float = 0.6, dx_pow: float = 1.0,
+        max_steps: int = 0):
+    """CFL time stepping to t_end (last step clamped).  Returns (state, steps, t)."""
+    out = np.array(S, dtype=np.float64, copy=True, order="C")
+    t = np.zeros(1)
+    n = lib().oracle_run(ctypes.byref(cfg), _ptr(out), float(t_end), float(cfl), float(dx_pow),
+                         int(max_steps), _ptr(t))
+    if n < 0:
+        raise ValueError("oracle run failed")
+    return out, int(n), float(t[0])
+
+
+def stencil(u3, v2, dx, gamma0=0.95, d0=0.9, eps=1e-10) -> dict:
+    """All intermediates of one HWENO stencil (Sec. 2.1)."""
+    u3 = np.ascontiguousarray(u3, dtype=np.float64)
+    v2 = np.ascontiguousarray(v2, dtype=np.float64)
+    out = np.zeros(22)
+    _check(lib().oracle_stencil(_ptr(u3), _ptr(v2), float(dx), float(gamma0), float(d0), float(eps),
+                                _ptr(out)))
+    return {"p": out[0:3], "dp0_half": out[3], "dp_center": out[4:7], "beta": out[7:10],
+            "tau": out[10], "omega_g": out[11:14], "omega_d": out[14:17], "u_minus": out[17],
+            "v_minus": out[18], "v_mod": out[19], "u_plus": out[20], "v_plus": out[21]}
+
+
+def dterms(f4, h2, dx):
+    f4 = np.ascontiguousarray(f4, dtype=np.float64)
+    h2 = np.ascontiguousarray(h2, dtype=np.float64)
+    out = np.zeros(2)
+    _check(lib().oracle_dterms(_ptr(f4), _ptr(h2), float(dx), _ptr(out)))
+    return float(out[0]), float(out[1])
+
+
+def euler_flux(cfg: Cfg, direction: int, U):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    F = np.zeros_like(U)
+    _check(lib().oracle_euler_flux(ctypes.byref(cfg), int(direction), _ptr(U), _ptr(F)))
+    return F
+
+
+def euler_jacobian(cfg: Cfg, direction: int, U):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    m = U.size
+    A = np.zeros(m * m)
+    _check(lib().oracle_euler_jacobian(ctypes.byref(cfg), int(direction), _ptr(U), _ptr(A)))
+    return A.reshape(m, m)
+
+
+def euler_eigen(cfg: Cfg, direction: int, UL, UR=None):
+    """(R, L, (u, v, H, c)) at the Roe average of UL, UR, or at the cell state UL if UR is None."""
+    UL = np.ascontiguousarray(UL, dtype=np.float64)
+    which = 1 if UR is None else 0
+    UR = UL if UR is None else np.ascontiguousarray(UR, dtype=np.float64)
+    m = UL.size
+    Rm, Lm, st = np.zeros(m * m), np.zeros(m * m), np.zeros(4)
+    _check(lib().oracle_euler_eigen(ctypes.byref(cfg), int(direction), which, _ptr(UL), _ptr(UR),
+                                    _ptr(Rm), _ptr(Lm), _ptr(st)))
+    return Rm.reshape(m, m), Lm.reshape(m, m), st

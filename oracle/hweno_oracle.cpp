@@ -1,0 +1,809 @@
+// HWENO-I oracle: a plain, slow CPU implementation of the fifth-order finite-difference
+// interpolation-based Hermite WENO scheme (Xie, Tao, Jiao, Zhang, arXiv 2411.11229).
+//
+// TEST INFRASTRUCTURE ONLY.  The tests, the smoke check and the CPU-baseline leg of the
+// benchmark are the only callers.  Nothing in the product library links or calls this file,
+// and this file shares no code, header or constant table with the CUDA path.
+//
+// Everything is FP64 and is meant to be compiled with -ffp-contract=off.  Every formula is
+// written in the order and notation of the paper:
+//   Sec. 2, Eq. (EQ1)/(odeH)      augmented system and conservative semi-discretisation (1D)
+//   Sec. 2.1, Eqs. (HWEp0)-(limiter)  Hermite candidates, smoothness indicators, weights,
+//                                      interpolation and HWENO limiter
+//   Sec. 2.2, Eqs. (Pc),(Cd-1),(DfDh) central Hermite correction D(f), D(h)
+//   Eqs. (flux-1d),(flux-LF)      Lax-Friedrichs numerical fluxes
+//   Eq. (fully-hweno), (2Dfully-hweno)  SSP-RK3 with the modified derivative in the base
+//   Sec. 3, Eqs. (EQ3),(ode2H),(mixed)  2D system, dimension-by-dimension fluxes, mixed fluxes
+//   Remarks after Sec. 2.2 and Sec. 3: local characteristic decomposition for Euler
+//   Remarks (RBC-1d), (RBC-2d-x), (RBC-2d-y): reflective boundary tables
+//
+// Readings where the paper is silent (see the design notes of the repository):
+//   * p0 has five conditions and is therefore degree 4 (the paper calls it quintic).
+//   * u^+ at x_{i-1/2} is the mirror image of u^- at x_{i+1/2}: the same procedure applied to the
+//     data reflected about x_i (derivatives change sign).  With gamma1 = gamma2 the weights are
+//     then the same numbers as those of u^-.
+//   * v^+/- is the linear p0' value (Eq. interp); the weights are shared by u^+/- and v~.
+//   * alpha of the Lax-Friedrichs flux is one global maximum of |f'(u)| (Euler: |u|+c, |v|+c)
+//     over the cells of the stage input, per direction, recomputed at every stage.
+//   * Characteristic decomposition: at face i+1/2 the Roe average of U_i and U_{i+1} gives the
+//     eigenvectors; all stencil values (solution and derivative) are projected with them.  The
+//     modified derivative of cell i uses the eigenvectors of U_i.  D-terms, LF and mixed fluxes
+//     are componentwise.
+//   * Transmissive boundary: zero-order extrapolation of U and of its derivatives.
+//   * dt = CFL dx / alpha (1D), CFL / (alpha_x/dx + alpha_y/dy) (2D); optional power p on dx.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+
+namespace hwo {
+
+using std::fabs;
+using std::sqrt;
+
+enum { ADVECTION = 0, BURGERS = 1, EULER = 2 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
+
+struct Cfg {
+  int32_t dim, system, nx, ny, bc, pad_;
+  double dx, dy, gamma, gamma0, d0, eps, ax, ay;
+};
+
+inline int ncomp(const Cfg& c) { return c.system == EULER ? (c.dim == 1 ? 3 : 4) : 1; }
+inline int nfield(const Cfg& c) { return c.dim == 1 ? 2 : 3; }
+
+template <class R> inline R sq(const R& a) { return a * a; }
+
+// ---------------------------------------------------------------------------------------------
+// Sec. 2.1: one HWENO stencil T0 = {i-1,i,i+1} with T1 = {i-1,i}, T2 = {i,i+1}.
+// Inputs: u_{i-1}, u_i, u_{i+1}, v_{i-1}, v_{i+1}.  Outputs the value and derivative at x_{i+1/2}
+// (u^-_{i+1/2}, v^-_{i+1/2}, Eq. interp), the modified derivative at x_i (Eq. limiter), and
+// the intermediate quantities for the unit tests.
+template <class R>
+struct StencilOut {
+  R p[3];      // p_l(x_{i+1/2}), Eq. (Pxi)
+  R dp0;       // p0'(x_{i+1/2}), Eq. (P'xi)
+  R dpc[3];    // p_l'(x_i), Eq. (limiter-p)
+  R beta[3];   // smoothness indicators
+  R tau;
+  R wg[3];     // omega^gamma
+  R wd[3];     // omega^d
+  R u_half;    // u^-_{i+1/2}
+  R v_half;    // v^-_{i+1/2}
+  R v_mod;     // v~_i
+};
+
+template <class R>
+void hweno_stencil(const R& um, const R& u0, const R& up, const R& vm, const R& vp, double dx,
+                   const double g[3], const double d[3], double eps, StencilOut<R>& o) {
+  // Eq. (Pxi)
+  o.p[0] = -(1.0 / 8.0) * um + (9.0 / 16.0) * u0 + (9.0 / 16.0) * up - dx * ((3.0 / 64.0) * vm + (9.0 / 64.0) * vp);
+  o.p[1] = -(1.0 / 2.0) * um + (3.0 / 2.0) * u0;
+  o.p[2] = (1.0 / 2.0) * u0 + (1.0 / 2.0) * up;
+  // Eq. (P'xi)
+  o.dp0 = (1.0 / dx) * ((3.0 / 16.0) * um - (3.0 / 2.0) * u0 + (21.0 / 16.0) * up) + (1.0 / 16.0) * vm - (3.0 / 16.0) * vp;
+  // Eq. (limiter-p)
+  o.dpc[0] = (3.0 / (4.0 * dx)) * (up - um) - (1.0 / 4.0) * (vm + vp);
+  o.dpc[1] = (1.0 / dx) * (u0 - um);
+  o.dpc[2] = (1.0 / dx) * (up - u0);
+  // smoothness indicators, explicit form of Eq. (GHYZ)
+  R a1 = -(dx / 4.0) * (vm + vp) + (3.0 / 4.0) * (up - um);
+  R a2 = (dx / 4.0) * (vm - vp) + (um - 2.0 * u0 + up);
+  R a3 = (dx / 4.0) * (vm + vp) + (1.0 / 4.0) * (um - up);
+  R a4 = (dx / 4.0) * (vp - vm) - (1.0 / 2.0) * (um - 2.0 * u0 + up);
+  o.beta[0] = sq(a1 + (1.0 / 4.0) * a3) + (13.0 / 3.0) * sq(a2 + (63.0 / 130.0) * a4) + (781.0 / 20.0) * sq(a3) +
+              (1421461.0 / 2275.0) * sq(a4);
+  o.beta[1] = sq(u0 - um);
+  o.beta[2] = sq(u0 - up);
+  // Eq. (nonlinear)
+  o.tau = (1.0 / 4.0) * sq(fabs(o.beta[0] - o.beta[1]) + fabs(o.beta[0] - o.beta[2]));
+  R wbg[3], wbd[3];
+  for (int l = 0; l < 3; ++l) {
+    wbg[l] = g[l] * (1.0 + o.tau / (o.beta[l] + eps));
+    wbd[l] = d[l] * (1.0 + o.tau / (o.beta[l] + eps));
+  }
+  R sg = wbg[0] + wbg[1] + wbg[2];
+  R sd = wbd[0] + wbd[1] + wbd[2];
+  for (int l = 0; l < 3; ++l) {
+    o.wg[l] = wbg[l] / sg;
+    o.wd[l] = wbd[l] / sd;
+  }
+  // Eq. (interp)
+  o.u_half = o.wg[0] * ((1.0 / g[0]) * o.p[0] - (g[1] / g[0]) * o.p[1] - (g[2] / g[0]) * o.p[2]) + o.wg[1] * o.p[1] +
+             o.wg[2] * o.p[2];
+  o.v_half = o.dp0;
+  // Eq. (limiter)
+  o.v_mod = o.wd[0] * ((1.0 / d[0]) * o.dpc[0] - (d[1] / d[0]) * o.dpc[1] - (d[2] / d[0]) * o.dpc[2]) +
+            o.wd[1] * o.dpc[1] + o.wd[2] * o.dpc[2];
+}
+
+// u^-_{i+1/2}, v^-_{i+1/2} from the stencil of cell i (and v~_i as a by-product).
+template <class R>
+void interp_minus(const R& um, const R& u0, const R& up, const R& vm, const R& vp, double dx, const double g[3],
+                  const double d[3], double eps, R& u_half, R& v_half, R& v_mod) {
+  StencilOut<R> o;
+  hweno_stencil(um, u0, up, vm, vp, dx, g, d, eps, o);
+  u_half = o.u_half;
+  v_half = o.v_half;
+  v_mod = o.v_mod;
+}
+
+// u^+_{i-1/2}, v^+_{i-1/2} from the stencil of cell i: the mirror image of interp_minus.  The
+// data are reflected about x_i (x -> 2 x_i - x): values swap ends, derivatives change sign.
+template <class R>
+void interp_plus(const R& um, const R& u0, const R& up, const R& vm, const R& vp, double dx, const double g[3],
+                 const double d[3], double eps, R& u_half, R& v_half) {
+  StencilOut<R> o;
+  R nvp = -vp, nvm = -vm;
+  hweno_stencil(up, u0, um, nvp, nvm, dx, g, d, eps, o);
+  u_half = o.u_half;
+  v_half = -o.v_half;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Sec. 2.2, Eqs. (Cd-1) and (DfDh): from f_{i-1..i+2} and h_{i-1}, h_{i+2}.
+template <class R>
+void dterms(const R& fm, const R& f0, const R& f1, const R& f2, const R& hm, const R& h2, double dx, R& Df, R& Dh) {
+  R P2 = (9.0 / 8.0) * (fm - f0 - f1 + f2) + (5.0 / 12.0) * dx * (hm - h2);                 // dx^2 P''
+  R P3 = -(1.0 / dx) * ((101.0 / 36.0) * fm - (27.0 / 4.0) * f0 + (27.0 / 4.0) * f1 - (101.0 / 36.0) * f2) -
+         (5.0 / 6.0) * (hm + h2);                                                             // dx^2 P'''
+  R P4 = -3.0 * (fm - f0 - f1 + f2) - 2.0 * dx * (hm - h2);                                  // dx^4 P''''
+  R P5 = (1.0 / dx) * ((130.0 / 9.0) * fm - 30.0 * f0 + 30.0 * f1 - (130.0 / 9.0) * f2) +
+         (20.0 / 3.0) * (hm + h2);                                                            // dx^4 P^(5)
+  Df = -(1.0 / 24.0) * P2 + (7.0 / 5760.0) * P4;
+  Dh = -(1.0 / 24.0) * P3 + (7.0 / 5760.0) * P5;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Physical fluxes.  dir = 0 is x, dir = 1 is y.  Euler equations (euler1d)/(euler2d) with
+// E = P/(gamma-1) + rho |mu|^2 / 2.
+template <class R>
+struct Phys {
+  const Cfg& c;
+  explicit Phys(const Cfg& cc) : c(cc) {}
+
+  // f(u) or g(u): the physical flux of U in direction dir
+  void flux(int dir, const R* U, R* F) const {
+    if (c.system == ADVECTION) {
+      F[0] = (dir == 0 ? c.ax : c.ay) * U[0];
+    } else if (c.system == BURGERS) {
+      F[0] = 0.5 * U[0] * U[0];
+    } else if (c.dim == 1) {
+      R rho = U[0], mu = U[1] / rho, E = U[2];
+      R P = (c.gamma - 1.0) * (E - 0.5 * rho * mu * mu);
+      F[0] = rho * mu;
+      F[1] = rho * mu * mu + P;
+      F[2] = mu * (E + P);
+    } else {
+      R rho = U[0], mu = U[1] / rho, nu = U[2] / rho, E = U[3];
+      R P = (c.gamma - 1.0) * (E - 0.5 * rho * (mu * mu + nu * nu));
+      if (dir == 0) {
+        F[0] = rho * mu;
+        F[1] = rho * mu * mu + P;
+        F[2] = rho * mu * nu;
+        F[3] = mu * (E + P);
+      } else {
+        F[0] = rho * nu;
+        F[1] = rho * mu * nu;
+        F[2] = rho * nu * nu + P;
+        F[3] = nu * (E + P);
+      }
+    }
+  }
+
+  // Flux Jacobian dF_dir/dU as an explicit matrix (textbook form, H = (E+P)/rho).
+  void jacobian(int dir, const R* U, R* A /* m x m, row major */) const {
+    int m = ncomp(c);
+    if (c.system == ADVECTION) {
+      A[0] = R(dir == 0 ? c.ax : c.ay);
+      return;
+    }
+    if (c.system == BURGERS) {
+      A[0] = U[0];
+      return;
+    }
+    double gm = c.gamma - 1.0;
+    if (c.dim == 1) {
+      R rho = U[0], u = U[1] / rho, E = U[2];
+      R P = gm * (E - 0.5 * rho * u * u);
+      R H = (E + P) / rho;
+      R Arow[9] = {R(0.0), R(1.0), R(0.0),
+                   0.5 * (c.gamma - 3.0) * u * u, (3.0 - c.gamma) * u, R(gm),
+                   u * (0.5 * gm * u * u - H), H - gm * u * u, c.gamma * u};
+      for (int k = 0; k < 9; ++k) A[k] = Arow[k];
+      (void)m;
+      return;
+    }
+    R rho = U[0], u = U[1] / rho, v = U[2] / rho, E = U[3];
+    R q2 = u * u + v * v;
+    R P = gm * (E - 0.5 * rho * q2);
+    R H = (E + P) / rho;
+    if (dir == 0) {
+      R Arow[16] = {R(0.0), R(1.0), R(0.0), R(0.0),
+                    0.5 * gm * q2 - u * u, (3.0 - c.gamma) * u, -gm * v, R(gm),
+                    -u * v, v, u, R(0.0),
+                    u * (0.5 * gm * q2 - H), H - gm * u * u, -gm * u * v, c.gamma * u};
+      for (int k = 0; k < 16; ++k) A[k] = Arow[k];
+    } else {
+      R Arow[16] = {R(0.0), R(0.0), R(1.0), R(0.0),
+                    -u * v, v, u, R(0.0),
+                    0.5 * gm * q2 - v * v, -gm * u, (3.0 - c.gamma) * v, R(gm),
+                    v * (0.5 * gm * q2 - H), -gm * u * v, H - gm * v * v, c.gamma * v};
+      for (int k = 0; k < 16; ++k) A[k] = Arow[k];
+    }
+  }
+
+  // h = f'(u) v (Eq. EQ1) and its 2D relatives xi, eta, theta (Eq. EQ3): Jacobian times a
+  // derivative vector.
+  void jac_vec(int dir, const R* U, const R* V, R* out) const {
+    int m = ncomp(c);
+    R A[16];
+    jacobian(dir, U, A);
+    for (int r = 0; r < m; ++r) {
+      R s = A[r * m] * V[0];
+      for (int k = 1; k < m; ++k) s = s + A[r * m + k] * V[k];
+      out[r] = s;
+    }
+  }
+
+  // |f'(u)| (scalar) or the spectral radius |velocity| + c (Euler) at one cell
+  R wavespeed(int dir, const R* U) const {
+    if (c.system == ADVECTION) return R(fabs(dir == 0 ? c.ax : c.ay));
+    if (c.system == BURGERS) return fabs(U[0]);
+    if (c.dim == 1) {
+      R rho = U[0], u = U[1] / rho, E = U[2];
+      R P = (c.gamma - 1.0) * (E - 0.5 * rho * u * u);
+      return fabs(u) + sqrt(c.gamma * P / rho);
+    }
+    R rho = U[0], u = U[1] / rho, v = U[2] / rho, E = U[3];
+    R P = (c.gamma - 1.0) * (E - 0.5 * rho * (u * u + v * v));
+    return fabs(dir == 0 ? u : v) + sqrt(c.gamma * P / rho);
+  }
+};
+
+// ---------------------------------------------------------------------------------------------
+// Local characteristic decomposition (Euler).  The averaged state (u, v, H, c) and the textbook
+// right eigenvectors of the direction-dir Jacobian, ordered by eigenvalue (vel-c, vel, [shear],
+// vel+c).  L is the closed-form inverse of R.
+template <class R>
+struct EigenState {
+  R u, v, H, c;
+};
+
+template <class R>
+EigenState<R> roe_average(const Cfg& cf, const R* UL, const R* UR) {
+  double gm = cf.gamma - 1.0;
+  EigenState<R> s;
+  if (cf.dim == 1) {
+    R rl = UL[0], ul = UL[1] / rl, El = UL[2];
+    R rr = UR[0], ur = UR[1] / rr, Er = UR[2];
+    R Pl = gm * (El - 0.5 * rl * ul * ul), Pr = gm * (Er - 0.5 * rr * ur * ur);
+    R Hl = (El + Pl) / rl, Hr = (Er + Pr) / rr;
+    R sl = sqrt(rl), sr = sqrt(rr);
+    s.u = (sl * ul + sr * ur) / (sl + sr);
+    s.v = R(0.0);
+    s.H = (sl * Hl + sr * Hr) / (sl + sr);
+    s.c = sqrt(gm * (s.H - 0.5 * s.u * s.u));
+    return s;
+  }
+  R rl = UL[0], ul = UL[1] / rl, vl = UL[2] / rl, El = UL[3];
+  R rr = UR[0], ur = UR[1] / rr, vr = UR[2] / rr, Er = UR[3];
+  R Pl = gm * (El - 0.5 * rl * (ul * ul + vl * vl)), Pr = gm * (Er - 0.5 * rr * (ur * ur + vr * vr));
+  R Hl = (El + Pl) / rl, Hr = (Er + Pr) / rr;
+  R sl = sqrt(rl), sr = sqrt(rr);
+  s.u = (sl * ul + sr * ur) / (sl + sr);
+  s.v = (sl * vl + sr * vr) / (sl + sr);
+  s.H = (sl * Hl + sr * Hr) / (sl + sr);
+  s.c = sqrt(gm * (s.H - 0.5 * (s.u * s.u + s.v * s.v)));
+  return s;
+}
+
+// eigen-state of one cell: the local state itself
+template <class R>
+EigenState<R> cell_state(const Cfg& cf, const R* U) {
+  double gm = cf.gamma - 1.0;
+  EigenState<R> s;
+  if (cf.dim == 1) {
+    R rho = U[0], u = U[1] / rho, E = U[2];
+    R P = gm * (E - 0.5 * rho * u * u);
+    s.u = u;
+    s.v = R(0.0);
+    s.H = (E + P) / rho;
+    s.c = sqrt(cf.gamma * P / rho);
+    return s;
+  }
+  R rho = U[0], u = U[1] / rho, v = U[2] / rho, E = U[3];
+  R P = gm * (E - 0.5 * rho * (u * u + v * v));
+  s.u = u;
+  s.v = v;
+  s.H = (E + P) / rho;
+  s.c = sqrt(cf.gamma * P / rho);
+  return s;
+}
+
+// Right eigenvectors as the columns of Rm (row-major m x m).
+template <class R>
+void right_eigen(const Cfg& cf, int dir, const EigenState<R>& s, R* Rm) {
+  const R &u = s.u, &v = s.v, &H = s.H, &c = s.c;
+  if (cf.dim == 1) {
+    R K[3][3] = {{R(1.0), u - c, H - u * c}, {R(1.0), u, 0.5 * u * u}, {R(1.0), u + c, H + u * c}};
+    for (int r = 0; r < 3; ++r)
+      for (int k = 0; k < 3; ++k) Rm[r * 3 + k] = K[k][r];
+    return;
+  }
+  R q = 0.5 * (u * u + v * v);
+  if (dir == 0) {
+    R K[4][4] = {{R(1.0), u - c, v, H - u * c}, {R(1.0), u, v, q}, {R(0.0), R(0.0), R(1.0), v}, {R(1.0), u + c, v, H + u * c}};
+    for (int r = 0; r < 4; ++r)
+      for (int k = 0; k < 4; ++k) Rm[r * 4 + k] = K[k][r];
+  } else {
+    R K[4][4] = {{R(1.0), u, v - c, H - v * c}, {R(1.0), u, v, q}, {R(0.0), R(1.0), R(0.0), u}, {R(1.0), u, v + c, H + v * c}};
+    for (int r = 0; r < 4; ++r)
+      for (int k = 0; k < 4; ++k) Rm[r * 4 + k] = K[k][r];
+  }
+}
+
+// Left eigenvectors (rows of Lm), the inverse of right_eigen, with b1 = (gamma-1)/c^2 and
+// b2 = b1 |vel|^2 / 2.
+template <class R>
+void left_eigen(const Cfg& cf, int dir, const EigenState<R>& s, R* Lm) {
+  double gm = cf.gamma - 1.0;
+  const R &u = s.u, &v = s.v, &c = s.c;
+  R b1 = gm / (c * c);
+  if (cf.dim == 1) {
+    R b2 = 0.5 * b1 * u * u;
+    R L[9] = {0.5 * (b2 + u / c), -0.5 * (b1 * u + 1.0 / c), 0.5 * b1,
+              1.0 - b2, b1 * u, -b1,
+              0.5 * (b2 - u / c), -0.5 * (b1 * u - 1.0 / c), 0.5 * b1};
+    for (int k = 0; k < 9; ++k) Lm[k] = L[k];
+    return;
+  }
+  R b2 = 0.5 * b1 * (u * u + v * v);
+  if (dir == 0) {
+    R L[16] = {0.5 * (b2 + u / c), -0.5 * (b1 * u + 1.0 / c), -0.5 * b1 * v, 0.5 * b1,
+               1.0 - b2, b1 * u, b1 * v, -b1,
+               -v, R(0.0), R(1.0), R(0.0),
+               0.5 * (b2 - u / c), -0.5 * (b1 * u - 1.0 / c), -0.5 * b1 * v, 0.5 * b1};
+    for (int k = 0; k < 16; ++k) Lm[k] = L[k];
+  } else {
+    R L[16] = {0.5 * (b2 + v / c), -0.5 * b1 * u, -0.5 * (b1 * v + 1.0 / c), 0.5 * b1,
+               1.0 - b2, b1 * u, b1 * v, -b1,
+               -u, R(1.0), R(0.0), R(0.0),
+               0.5 * (b2 - v / c), -0.5 * b1 * u, -0.5 * (b1 * v - 1.0 / c), 0.5 * b1};
+    for (int k = 0; k < 16; ++k) Lm[k] = L[k];
+  }
+}
+
+template <class R>
+void matvec(int m, const R* M, const R* x, R* y) {
+  for (int r = 0; r < m; ++r) {
+    R s = M[r * m] * x[0];
+    for (int k = 1; k < m; ++k) s = s + M[r * m + k] * x[k];
+    y[r] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Ghost-padded copy of a state.  Layout of a state: [field][comp][ny][nx], x fastest.
+// Fields: 1D (U, V), 2D (U, V, W) with V = U_x and W = U_y.
+template <class R>
+struct Padded {
+  int nf, nc, nx, ny, gx, gy, px, py;
+  std::vector<R> a;
+  Padded(const Cfg& c)
+      : nf(nfield(c)), nc(ncomp(c)), nx(c.nx), ny(c.dim == 2 ? c.ny : 1), gx(2), gy(c.dim == 2 ? 2 : 0) {
+    px = nx + 2 * gx;
+    py = ny + 2 * gy;
+    a.assign((size_t)nf * nc * px * py, R(0.0));
+  }
+  R& at(int f, int k, int j, int i) { return a[(((size_t)f * nc + k) * py + (j + gy)) * px + (i + gx)]; }
+  const R& at(int f, int k, int j, int i) const { return a[(((size_t)f * nc + k) * py + (j + gy)) * px + (i + gx)]; }
+};
+
+// Sign of a reflected ghost value (Remarks RBC-1d, RBC-2d-x, RBC-2d-y): wall normal to dir.
+inline double reflect_sign(const Cfg& c, int dir, int field, int comp) {
+  if (c.dim == 1) {
+    static const double U[3] = {1, -1, 1}, V[3] = {-1, 1, -1};
+    return field == 0 ? U[comp] : V[comp];
+  }
+  // rows: U, V = U_x, W = U_y; columns: rho, rho mu, rho nu, E
+  static const double X[3][4] = {{1, -1, 1, 1}, {-1, 1, -1, -1}, {1, -1, 1, 1}};
+  static const double Y[3][4] = {{1, 1, -1, 1}, {1, 1, -1, 1}, {-1, -1, 1, -1}};
+  return dir == 0 ? X[field][comp] : Y[field][comp];
+}
+
+// index of the interior cell that supplies ghost/interior index i on an axis of n cells
+inline int bc_source(int bc, int i, int n, bool* flipped) {
+  *flipped = false;
+  if (i >= 0 && i < n) return i;
+  if (bc == BC_PERIODIC) return ((i % n) + n) % n;
+  if (bc == BC_TRANSMISSIVE) return i < 0 ? 0 : n - 1;
+  *flipped = true;  // reflective: mirror about the wall
+  return i < 0 ? -1 - i : 2 * n - 1 - i;
+}
+
+template <class R>
+void fill_padded(const Cfg& c, const R* S, Padded<R>& P) {
+  const size_t plane = (size_t)P.nx * P.ny;
+  for (int f = 0; f < P.nf; ++f)
+    for (int k = 0; k < P.nc; ++k)
+      for (int j = -P.gy; j < P.ny + P.gy; ++j)
+        for (int i = -P.gx; i < P.nx + P.gx; ++i) {
+          bool fx, fy;
+          int si = bc_source(c.bc, i, P.nx, &fx);
+          int sj = c.dim == 2 ? bc_source(c.bc, j, P.ny, &fy) : 0;
+          if (c.dim == 1) fy = false;
+          double sgn = 1.0;
+          if (fx) sgn *= reflect_sign(c, 0, f, k);
+          if (fy) sgn *= reflect_sign(c, 1, f, k);
+          R val = S[((size_t)f * P.nc + k) * plane + (size_t)sj * P.nx + si];
+          P.at(f, k, j, i) = sgn == 1.0 ? val : -val;
+        }
+}
+
+// ---------------------------------------------------------------------------------------------
+// The stage operator.  Given the stage input S, produce L(S) (Eq. odeH / ode2H, all fields) and
+// M(S) = (U, V~, W~): the solution and the modified derivatives (Eq. limiter) that enter the
+// SSP-RK3 update (Eq. fully-hweno / 2Dfully-hweno).  alpha_x, alpha_y: the LF coefficients.
+template <class R>
+struct Operator {
+  const Cfg& c;
+  Phys<R> ph;
+  int m, nf;
+  double g[3], d[3];
+  Operator(const Cfg& cc) : c(cc), ph(cc), m(ncomp(cc)), nf(nfield(cc)) {
+    g[0] = c.gamma0;
+    g[1] = g[2] = 0.5 * (1.0 - c.gamma0);
+    d[0] = c.d0;
+    d[1] = d[2] = 0.5 * (1.0 - c.d0);
+  }
+
+  // Step (1.1)/(2.1) for one face and direction: U and D (D = V for x, W for y) of the four
+  // cells k-1..k+2 around face k+1/2 -> U^-, D^-, U^+, D^+ at the face.
+  void face_states(int dir, R Uc[4][4], R Dc[4][4], R* Um, R* Dm, R* Up, R* Dp) const {
+    double h = dir == 0 ? c.dx : c.dy;
+    if (c.system != EULER) {
+      R vmod;
+      interp_minus(Uc[0][0], Uc[1][0], Uc[2][0], Dc[0][0], Dc[2][0], h, g, d, c.eps, Um[0], Dm[0], vmod);
+      interp_plus(Uc[1][0], Uc[2][0], Uc[3][0], Dc[1][0], Dc[3][0], h, g, d, c.eps, Up[0], Dp[0]);
+      return;
+    }
+    // local characteristic decomposition at the face
+    EigenState<R> s = roe_average(c, Uc[1], Uc[2]);
+    R Rm[16], Lm[16];
+    right_eigen(c, dir, s, Rm);
+    left_eigen(c, dir, s, Lm);
+    R W[4][4], Z[4][4];
+    for (int q = 0; q < 4; ++q) {
+      matvec(m, Lm, Uc[q], W[q]);
+      matvec(m, Lm, Dc[q], Z[q]);
+    }
+    R wm[4], zm[4], wp[4], zp[4];
+    for (int s2 = 0; s2 < m; ++s2) {
+      R vmod;
+      interp_minus(W[0][s2], W[1][s2], W[2][s2], Z[0][s2], Z[2][s2], h, g, d, c.eps, wm[s2], zm[s2], vmod);
+      interp_plus(W[1][s2], W[2][s2], W[3][s2], Z[1][s2], Z[3][s2], h, g, d, c.eps, wp[s2], zp[s2]);
+    }
+    matvec(m, Rm, wm, Um);
+    matvec(m, Rm, zm, Dm);
+    matvec(m, Rm, wp, Up);
+    matvec(m, Rm, zp, Dp);
+  }
+
+  // modified derivative of one cell from U, D of cells i-1, i, i+1 (Eq. limiter)
+  void modified_derivative(int dir, R Uc[3][4], R Dc[3][4], R* Dt) const {
+    double h = dir == 0 ? c.dx : c.dy;
+    if (c.system != EULER) {
+      R uh, vh;
+      interp_minus(Uc[0][0], Uc[1][0], Uc[2][0], Dc[0][0], Dc[2][0], h, g, d, c.eps, uh, vh, Dt[0]);
+      return;
+    }
+    EigenState<R> s = cell_state(c, Uc[1]);
+    R Rm[16], Lm[16];
+    right_eigen(c, dir, s, Rm);
+    left_eigen(c, dir, s, Lm);
+    R W[3][4], Z[3][4];
+    for (int q = 0; q < 3; ++q) {
+      matvec(m, Lm, Uc[q], W[q]);
+      matvec(m, Lm, Dc[q], Z[q]);
+    }
+    R zt[4];
+    for (int s2 = 0; s2 < m; ++s2) {
+      R uh, vh;
+      interp_minus(W[0][s2], W[1][s2], W[2][s2], Z[0][s2], Z[2][s2], h, g, d, c.eps, uh, vh, zt[s2]);
+    }
+    matvec(m, Rm, zt, Dt);
+  }
+
+  R max_wavespeed(int dir, const R* S) const {
+    const int ny = c.dim == 2 ? c.ny : 1;
+    const size_t plane = (size_t)c.nx * ny;
+    R a = R(0.0);
+    for (size_t p = 0; p < plane; ++p) {
+      R U[4];
+      for (int k = 0; k < m; ++k) U[k] = S[k * plane + p];
+      R w = ph.wavespeed(dir, U);
+      if (w > a) a = w;
+    }
+    return a;
+  }
+
+  // L and M of one stage.  alpha: the LF coefficients (x, y).
+  void rhs(const R* S, R* Lout, R* Mout, R alpha_x, R alpha_y) const {
+    Padded<R> P(c);
+    fill_padded(c, S, P);
+    const int nx = c.nx, ny = c.dim == 2 ? c.ny : 1;
+    const size_t plane = (size_t)nx * ny;
+    const int nfl = nf;  // fields
+    // face fluxes: x faces (nx+1 per row), y faces (ny+1 per column); [field][comp][...]
+    std::vector<R> FX((size_t)nfl * m * ny * (nx + 1), R(0.0));
+    std::vector<R> FY(c.dim == 2 ? (size_t)nfl * m * (ny + 1) * nx : 0, R(0.0));
+    auto fx = [&](int f, int k, int j, int i) -> R& { return FX[(((size_t)f * m + k) * ny + j) * (nx + 1) + i]; };
+    auto fy = [&](int f, int k, int j, int i) -> R& { return FY[(((size_t)f * m + k) * (ny + 1) + j) * nx + i]; };
+
+    for (int dir = 0; dir < c.dim; ++dir) {
+      const double h = dir == 0 ? c.dx : c.dy;
+      const R alpha = dir == 0 ? alpha_x : alpha_y;
+      const int own = dir == 0 ? 1 : 2;    // derivative field interpolated in this direction
+      const int other = dir == 0 ? 2 : 1;  // derivative field with the mixed flux (2D)
+      const int nlines = dir == 0 ? ny : nx;
+      const int nalong = dir == 0 ? nx : ny;
+      for (int line = 0; line < nlines; ++line) {
+        auto cellU = [&](int a, R* U) {
+          for (int k = 0; k < m; ++k) U[k] = dir == 0 ? P.at(0, k, line, a) : P.at(0, k, a, line);
+        };
+        auto cellF = [&](int f, int a, R* D) {
+          for (int k = 0; k < m; ++k) D[k] = dir == 0 ? P.at(f, k, line, a) : P.at(f, k, a, line);
+        };
+        // faces a+1/2, a = -1 .. nalong-1
+        for (int a = -1; a < nalong; ++a) {
+          R Uc[4][4], Dc[4][4], Oc[4][4];
+          for (int q = 0; q < 4; ++q) {
+            cellU(a - 1 + q, Uc[q]);
+            cellF(own, a - 1 + q, Dc[q]);
+            if (c.dim == 2) cellF(other, a - 1 + q, Oc[q]);
+          }
+          // Step 1.1: interface values
+          R Um[4], Dm[4], Up[4], Dp[4];
+          face_states(dir, Uc, Dc, Um, Dm, Up, Dp);
+          // nodal fluxes for the D-terms (Eq. Pc: f at k-1..k+2, h at k-1 and k+2)
+          R fn[4][4], hn[4][4], on[4][4];
+          for (int q = 0; q < 4; ++q) {
+            ph.flux(dir, Uc[q], fn[q]);
+            ph.jac_vec(dir, Uc[q], Dc[q], hn[q]);
+            if (c.dim == 2) ph.jac_vec(dir, Uc[q], Oc[q], on[q]);
+          }
+          // Step 1.3: Eqs. (flux-1d), (flux-LF)
+          R FUm[4], FUp[4], HDm[4], HDp[4];
+          ph.flux(dir, Um, FUm);
+          ph.flux(dir, Up, FUp);
+          ph.jac_vec(dir, Um, Dm, HDm);
+          ph.jac_vec(dir, Up, Dp, HDp);
+          for (int k = 0; k < m; ++k) {
+            R Df, Dh;
+            dterms(fn[0][k], fn[1][k], fn[2][k], fn[3][k], hn[0][k], hn[3][k], h, Df, Dh);
+            R fhat = 0.5 * (FUm[k] + FUp[k] - alpha * (Up[k] - Um[k])) + Df;
+            R hhat = 0.5 * (HDm[k] + HDp[k] - alpha * (Dp[k] - Dm[k])) + Dh;
+            if (dir == 0) {
+              fx(0, k, line, a + 1) = fhat;
+              fx(own, k, line, a + 1) = hhat;
+            } else {
+              fy(0, k, a + 1, line) = fhat;
+              fy(own, k, a + 1, line) = hhat;
+            }
+            if (c.dim == 2) {
+              // Eq. (mixed): linear fourth-order flux of the other derivative field
+              R mixed = -(1.0 / 12.0) * on[0][k] + (7.0 / 12.0) * on[1][k] + (7.0 / 12.0) * on[2][k] -
+                        (1.0 / 12.0) * on[3][k];
+              if (dir == 0)
+                fx(other, k, line, a + 1) = mixed;
+              else
+                fy(other, k, a + 1, line) = mixed;
+            }
+          }
+        }
+        // modified derivative of every cell on the line
+        for (int a = 0; a < nalong; ++a) {
+          R Uc[3][4], Dc[3][4], Dt[4];
+          for (int q = 0; q < 3; ++q) {
+            cellU(a - 1 + q, Uc[q]);
+            cellF(own, a - 1 + q, Dc[q]);
+          }
+          modified_derivative(dir, Uc, Dc, Dt);
+          for (int k = 0; k < m; ++k) {
+            size_t p = dir == 0 ? (size_t)line * nx + a : (size_t)a * nx + line;
+            Mout[((size_t)own * m + k) * plane + p] = Dt[k];
+          }
+        }
+      }
+    }
+    // Step 4: the conservative differences
+    for (int f = 0; f < nfl; ++f)
+      for (int k = 0; k < m; ++k)
+        for (int j = 0; j < ny; ++j)
+          for (int i = 0; i < nx; ++i) {
+            R val = -(1.0 / c.dx) * (fx(f, k, j, i + 1) - fx(f, k, j, i));
+            if (c.dim == 2) val = val - (1.0 / c.dy) * (fy(f, k, j + 1, i) - fy(f, k, j, i));
+            Lout[((size_t)f * m + k) * plane + (size_t)j * nx + i] = val;
+          }
+    for (int k = 0; k < m; ++k)
+      for (size_t p = 0; p < plane; ++p) Mout[(size_t)k * plane + p] = S[(size_t)k * plane + p];
+  }
+};
+
+// One SSP-RK3 step with the modified derivative in the base (Eq. fully-hweno / 2Dfully-hweno).
+// S is updated in place.  alpha per stage from the stage input.
+template <class R>
+void rk3_step(const Cfg& c, R* S, double dt) {
+  Operator<R> op(c);
+  const int ny = c.dim == 2 ? c.ny : 1;
+  const size_t n = (size_t)nfield(c) * ncomp(c) * c.nx * ny;
+  std::vector<R> L(n), M(n), B(n), S1(n);
+  static const double a_k[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0};
+  static const double b_k[3] = {1.0, 1.0 / 4.0, 2.0 / 3.0};
+  for (int st = 0; st < 3; ++st) {
+    R ax = op.max_wavespeed(0, S);
+    R ay = c.dim == 2 ? op.max_wavespeed(1, S) : R(0.0);
+    op.rhs(S, L.data(), M.data(), ax, ay);
+    if (st == 0) {
+      for (size_t p = 0; p < n; ++p) B[p] = M[p];  // (u^n, v~^n, w~^n)
+      for (size_t p = 0; p < n; ++p) S[p] = M[p] + dt * L[p];
+    } else {
+      for (size_t p = 0; p < n; ++p) S[p] = a_k[st] * B[p] + b_k[st] * (M[p] + dt * L[p]);
+    }
+  }
+}
+
+template <class R>
+double cfl_dt(const Cfg& c, const R* S, double cfl, double dx_pow) {
+  Operator<R> op(c);
+  double ax = (double)op.max_wavespeed(0, S);
+  if (c.dim == 1) return cfl * std::pow(c.dx, dx_pow) / ax;
+  double ay = (double)op.max_wavespeed(1, S);
+  return cfl / (ax / std::pow(c.dx, dx_pow) + ay / std::pow(c.dy, dx_pow));
+}
+
+}  // namespace hwo
+
+// =============================================================================================
+// C interface (doubles only).  Return 0 on success, -1 on invalid arguments.
+extern "C" {
+
+typedef hwo::Cfg oracle_cfg;
+
+static int check_cfg(const oracle_cfg* c) {
+  if (!c) return -1;
+  if (c->dim != 1 && c->dim != 2) return -1;
+  if (c->system < 0 || c->system > 2) return -1;
+  if (c->nx < 5 || (c->dim == 2 && c->ny < 5)) return -1;
+  if (!(c->dx > 0) || (c->dim == 2 && !(c->dy > 0))) return -1;
+  if (c->system == hwo::EULER && !(c->gamma > 1.0)) return -1;
+  if (c->bc < 0 || c->bc > 2) return -1;
+  if (c->bc == hwo::BC_REFLECTIVE && c->system != hwo::EULER) return -1;
+  if (!(c->gamma0 > 0 && c->gamma0 < 1) || !(c->d0 > 0 && c->d0 < 1) || !(c->eps > 0)) return -1;
+  return 0;
+}
+
+// number of doubles in one state
+long long oracle_state_size(const oracle_cfg* c) {
+  if (check_cfg(c)) return -1;
+  return (long long)hwo::nfield(*c) * hwo::ncomp(*c) * c->nx * (c->dim == 2 ? c->ny : 1);
+}
+
+int oracle_max_wavespeed(const oracle_cfg* c, const double* S, double* ax, double* ay) {
+  if (check_cfg(c)) return -1;
+  hwo::Operator<double> op(*c);
+  *ax = op.max_wavespeed(0, S);
+  *ay = c->dim == 2 ? op.max_wavespeed(1, S) : 0.0;
+  return 0;
+}
+
+// L(S) and M(S) = (U, V~, W~) with the LF coefficients taken from S
+int oracle_rhs(const oracle_cfg* c, const double* S, double* L, double* M) {
+  if (check_cfg(c)) return -1;
+  hwo::Operator<double> op(*c);
+  double ax = op.max_wavespeed(0, S);
+  double ay = c->dim == 2 ? op.max_wavespeed(1, S) : 0.0;
+  op.rhs(S, L, M, ax, ay);
+  return 0;
+}
+
+// same with given LF coefficients
+int oracle_rhs_alpha(const oracle_cfg* c, const double* S, double ax, double ay, double* L, double* M) {
+  if (check_cfg(c)) return -1;
+  hwo::Operator<double> op(*c);
+  op.rhs(S, L, M, ax, ay);
+  return 0;
+}
+
+// nsteps SSP-RK3 steps in place with a fixed dt
+int oracle_steps(const oracle_cfg* c, double* S, double dt, int nsteps) {
+  if (check_cfg(c) || nsteps < 0) return -1;
+  for (int s = 0; s < nsteps; ++s) hwo::rk3_step(*c, S, dt);
+  return 0;
+}
+
+// CFL dt of a state: cfl dx^p / alpha (1D) or cfl / (ax/dx^p + ay/dy^p) (2D)
+double oracle_cfl_dt(const oracle_cfg* c, const double* S, double cfl, double dx_pow) {
+  if (check_cfg(c)) return -1.0;
+  return hwo::cfl_dt(*c, S, cfl, dx_pow);
+}
+
+// Run to t_end with CFL steps (last step clamped), or at most max_steps steps when t_end <= 0.
+// Returns the number of steps taken, or -1.  *t_out = final time.
+long long oracle_run(const oracle_cfg* c, double* S, double t_end, double cfl, double dx_pow, long long max_steps,
+                     double* t_out) {
+  if (check_cfg(c)) return -1;
+  double t = 0.0;
+  long long n = 0;
+  while ((t_end <= 0.0 || t < t_end) && (max_steps <= 0 || n < max_steps)) {
+    double dt = hwo::cfl_dt(*c, S, cfl, dx_pow);
+    if (!(dt > 0) || !std::isfinite(dt)) return -1;
+    if (t_end > 0.0 && t + dt > t_end) dt = t_end - t;
+    hwo::rk3_step(*c, S, dt);
+    t += dt;
+    ++n;
+    if (t_end > 0.0 && t >= t_end) break;
+  }
+  if (t_out) *t_out = t;
+  return n;
+}
+
+// One HWENO stencil (Sec. 2.1) with all intermediates, for the unit tests.
+// out[0..2] p_l(x_{i+1/2}); out[3] p0'(x_{i+1/2}); out[4..6] p_l'(x_i); out[7..9] beta_l; out[10] tau;
+// out[11..13] omega^gamma; out[14..16] omega^d; out[17] u^-_{i+1/2}; out[18] v^-_{i+1/2};
+// out[19] v~_i; out[20] u^+_{i-1/2}; out[21] v^+_{i-1/2}.
+int oracle_stencil(const double* u3, const double* v2, double dx, double gamma0, double d0, double eps, double* out) {
+  double g[3] = {gamma0, 0.5 * (1.0 - gamma0), 0.5 * (1.0 - gamma0)};
+  double d[3] = {d0, 0.5 * (1.0 - d0), 0.5 * (1.0 - d0)};
+  hwo::StencilOut<double> o;
+  hwo::hweno_stencil(u3[0], u3[1], u3[2], v2[0], v2[1], dx, g, d, eps, o);
+  for (int l = 0; l < 3; ++l) out[l] = o.p[l];
+  out[3] = o.dp0;
+  for (int l = 0; l < 3; ++l) out[4 + l] = o.dpc[l];
+  for (int l = 0; l < 3; ++l) out[7 + l] = o.beta[l];
+  out[10] = o.tau;
+  for (int l = 0; l < 3; ++l) out[11 + l] = o.wg[l];
+  for (int l = 0; l < 3; ++l) out[14 + l] = o.wd[l];
+  out[17] = o.u_half;
+  out[18] = o.v_half;
+  out[19] = o.v_mod;
+  hwo::interp_plus(u3[0], u3[1], u3[2], v2[0], v2[1], dx, g, d, eps, out[20], out[21]);
+  return 0;
+}
+
+// D-terms of Eqs. (Cd-1), (DfDh): f4 = f_{i-1..i+2}, h2 = (h_{i-1}, h_{i+2}); out = (Df, Dh)
+int oracle_dterms(const double* f4, const double* h2, double dx, double* out) {
+  hwo::dterms(f4[0], f4[1], f4[2], f4[3], h2[0], h2[1], dx, out[0], out[1]);
+  return 0;
+}
+
+// Euler pieces for the unit tests: flux, Jacobian, eigenvectors at a state.
+int oracle_euler_flux(const oracle_cfg* c, int dir, const double* U, double* F) {
+  if (check_cfg(c)) return -1;
+  hwo::Phys<double>(*c).flux(dir, U, F);
+  return 0;
+}
+int oracle_euler_jacobian(const oracle_cfg* c, int dir, const double* U, double* A) {
+  if (check_cfg(c)) return -1;
+  hwo::Phys<double>(*c).jacobian(dir, U, A);
+  return 0;
+}
+// which = 0: Roe average of UL, UR; which = 1: the cell state UL.  R, L: m x m row major.
+int oracle_euler_eigen(const oracle_cfg* c, int dir, int which, const double* UL, const double* UR, double* Rm,
+                       double* Lm, double* state4) {
+  if (check_cfg(c) || c->system != hwo::EULER) return -1;
+  hwo::EigenState<double> s = which == 0 ? hwo::roe_average(*c, UL, UR) : hwo::cell_state(*c, UL);
+  hwo::right_eigen(*c, dir, s, Rm);
+  hwo::left_eigen(*c, dir, s, Lm);
+  if (state4) {
+    state4[0] = s.u;
+    state4[1] = s.v;
+    state4[2] = s.H;
+    state4[3] = s.c;
+  }
+  return 0;
+}
+
+}  // extern "C"
