@@ -1,0 +1,304 @@
+#!/usr/bin/env python
+"""Benchmark of the HWENO-I hot path on GB300: FP64 2D Euler, 4096 x 4096 cells, periodic
+[0, 2]^2, smooth wave rho = 1 + 0.2 sin(pi (x + y)), velocity (0.7, 0.3), P = 1, SSP-RK3 at CFL 0.6
+with the step size computed on the device every step.
+
+One benchmark step = one full SSP-RK3 step (three stages: cell, face and update kernels each) over
+the whole grid.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 4096]
+
+--impl reference times the CPU oracle (plain C++ FP64, one host core) on a bounded sample of the
+same workload: a 256 x 256 periodic patch of the same smooth wave, one oracle SSP-RK3 step per
+benchmark step.  Multi-GPU (torchrun): every rank advances its own 4096^2 grid (independent
+replicas, weak scaling); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2D Euler HWENO-I Mcell-updates/s & HBM roofline %; batched/adjoint vs plain"
+UNIT = "Mcell-updates/s"
+# FP64 peak for the ALU roofline, from the SM count (152), the maximum SM clock (2070 MHz) and the
+# FP64 rate of GB300 (2 DFMA per SM per clock = 4 flop/clk/SM): 152 * 2.07e9 * 4.
+FP64_PEAK_FLOPS = 152 * 2.07e9 * 4
+HBM_PEAK_GBS_FALLBACK = 6800.0
+# DRAM bytes per launch of the 2D Euler face kernel at 4096^2 from ncu (profiles/), per face.
+FACE_TRAFFIC_BYTES_PER_FACE = 285.2  # 2048^2 capture, profiles/k_face_euler2d_2048_full.md
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu), "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def cpu_baseline(steps: int = 8, n: int = 256):
+    """The oracle (single thread) on a 256^2 periodic patch of the same smooth wave."""
+    import oracle as O
+    import workloads as W
+
+    S, dx, dy = W.euler2d_smooth(n)
+    cfg = O.make_cfg(2, O.EULER, n, n, dx=dx, dy=dy)
+    dt = O.cfl_dt(cfg, S, 0.6)
+    t0 = time.perf_counter()
+    O.steps(cfg, S, dt, steps)
+    sec = time.perf_counter() - t0
+    return {"value": n * n * steps / sec / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} oracle SSP-RK3 steps on a {n}x{n} periodic patch of the same smooth "
+                      f"wave (same per-cell work), one host thread, {sec:.1f} s"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    import oracle as O
+    import workloads as W
+
+    n = 256
+    S, dx, dy = W.euler2d_smooth(n)
+    cfg = O.make_cfg(2, O.EULER, n, n, dx=dx, dy=dy)
+    dt = O.cfl_dt(cfg, S, 0.6)
+    for _ in range(args.warmup):
+        S = O.steps(cfg, S, dt, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        S = O.steps(cfg, S, dt, 1)
+    sec = time.perf_counter() - t0
+    value = n * n * args.steps / sec / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "2D Euler HWENO-I, smooth wave, periodic [0,2]^2, SSP-RK3 CFL 0.6; "
+                               "oracle sample: 256x256 patch per step", "n": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"one oracle SSP-RK3 step on a {n}x{n} periodic patch per benchmark step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import oracle as O
+    import workloads as W
+    from paper_2411_11229_gb300 import Solver
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    S, dx, dy = W.euler2d_smooth(n)
+    cells = n * n
+    solver = Solver(2, "euler", n, n, dx=dx, dy=dy, device=dev)
+    solver.set_state(S)
+    stream = solver.stream
+    solver.set_time(0.0, 0.0)
+    for _ in range(args.warmup):
+        solver.step(0.0)
+    solver.sync()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    gpu_idx = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis and vis.split(",")[local].strip().isdigit():
+        gpu_idx = int(vis.split(",")[local])
+    sampler = ClockSampler(gpu_idx)
+
+    # device-resident timed region
+    solver.set_profiling(True)
+    solver.kernel_times()
+    launches0 = solver.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    e0.record(stream)
+    for _ in range(args.steps):
+        solver.step(0.0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = solver.launch_count() - launches0
+    ktimes = solver.kernel_times()
+    solver.set_profiling(False)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = ws * cells * args.steps / (ms_max * 1e-3) / 1e6
+
+    # end to end through the C ABI with host buffers: upload, step, download every step
+    host_in = torch.from_numpy(np.ascontiguousarray(solver.state.cpu().numpy())).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    nbytes = host_in.numel() * 8
+    ke2e = max(1, min(args.steps, 5))
+    solver.upload(host_in)
+    solver.step(0.0)
+    solver.download(host_out)
+    solver.sync()
+    barrier()
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(ke2e):
+        solver.upload(host_in)
+        solver.step(0.0)
+        solver.download(host_out)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = f0.elapsed_time(f1)
+    te = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = ws * cells * ke2e / (float(te.item()) * 1e-3) / 1e6
+
+    if rank != 0:
+        return 0
+    # roofline of the dominant kernel (face kernel: FP64 ALU bound)
+    cfg = O.make_cfg(2, O.EULER, n, n, dx=dx, dy=dy)
+    counts = O.count_flops(cfg)
+    faces = 2 * (n + 1) * n
+    face_ms, face_n = ktimes["face"]
+    face_avg_ms = face_ms / max(face_n, 1)
+    flops_face_launch = counts["face"] * faces
+    achieved = flops_face_launch / (face_avg_ms * 1e-3)
+    total_ms = sum(v[0] for v in ktimes.values())
+    traffic = None if FACE_TRAFFIC_BYTES_PER_FACE is None else FACE_TRAFFIC_BYTES_PER_FACE * faces
+    peaks = _measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", HBM_PEAK_GBS_FALLBACK)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"2D Euler HWENO-I {n}x{n} periodic [0,2]^2, smooth wave (0.7, 0.3), "
+                               "SSP-RK3 CFL 0.6, dt on device", "n": n, "cells": cells,
+                   "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (state 1.6 GB + workspace)"},
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                "steps": ke2e, "path": "hweno_upload + hweno_step + hweno_download, pinned host buffers"},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic,
+                     "kernel": "k_face<2,EULER>", "flops_per_face": counts["face"],
+                     "faces_per_launch": faces, "avg_launch_ms": face_avg_ms,
+                     "peak_note": "FP64 derived: 152 SMs x 2070 MHz x 4 flop/clk",
+                     "hbm_peak_gbs": hbm_peak},
+        "kernel_share": {k: v[0] / total_ms for k, v in ktimes.items()} if total_ms > 0 else None,
+        "kernel_avg_ms": {k: v[0] / max(v[1], 1) for k, v in ktimes.items()},
+        "flops_per_cell_step": counts["per_cell_step"],
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    try:
+        return run_ours(args, ws, rank, local)
+    finally:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

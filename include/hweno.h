@@ -1,0 +1,145 @@
+/* hweno.h -- C ABI of the GB300 (sm_103a) HWENO-I library (libhweno.so).
+ *
+ * The library advances the fifth-order finite-difference interpolation-based Hermite WENO scheme
+ * (HWENO-I) of Xie, Tao, Jiao and Zhang (arXiv 2411.11229) on one GPU, in FP64:
+ *   - the augmented system u_t + f(u)_x = 0, v_t + h(u,v)_x = 0 with v = u_x, h = f'(u) v
+ *     (Sec. 2, Eq. EQ1) and its 2D form with w = u_y (Sec. 3, Eq. EQ3);
+ *   - the conservative semi-discretisation L = -(F_{i+1/2} - F_{i-1/2})/dx (- the y difference)
+ *     (Eqs. odeH, ode2H);
+ *   - one HWENO interpolation per stencil for u^{+-}, v^{+-} and the modified derivative v~
+ *     (Sec. 2.1, Eqs. Pxi, P'xi, limiter-p, GHYZ, nonlinear, interp, limiter);
+ *   - Lax-Friedrichs fluxes with the central Hermite corrections D(f), D(h)
+ *     (Eqs. flux-1d, flux-LF, Cd-1, DfDh) and the linear mixed fluxes (Eq. mixed);
+ *   - local characteristic decomposition for the Euler equations (remarks closing Sec. 2 and
+ *     Sec. 3): Roe-averaged eigenvectors at each face, cell eigenvectors for v~;
+ *   - SSP-RK3 with the modified derivative in the update base (Eqs. fully-hweno, 2Dfully-hweno).
+ *
+ * Systems: linear advection (f = a_x u, g = a_y u), Burgers (f = g = u^2/2) and the Euler
+ * equations with E = P/(gamma-1) + rho |vel|^2 / 2 (Eqs. euler1d, euler2d).
+ *
+ * STATE LAYOUT.  One state is a contiguous FP64 array [field][comp][ny][nx], x fastest.
+ *   fields: 1D (U, V = U_x), 2D (U, V = U_x, W = U_y);
+ *   comps : 1 (scalar), 3 (1D Euler: rho, rho*mu, E), 4 (2D Euler: rho, rho*mu, rho*nu, E).
+ *   1D problems have ny = 1.  hweno_state_doubles() gives the element count.
+ *
+ * OWNERSHIP.  All device memory (the state and the workspace) belongs to the caller.  The library
+ * borrows the pointers given to hweno_bind() until the next bind or hweno_destroy(), and owns only
+ * the handle itself.  Device pointers must be 16-byte aligned.
+ *
+ * ERRORS.  Every call returns an int status (HWENO_OK = 0 or a negative code); no exception or
+ * abort crosses the ABI.  Launches are asynchronous on the handle's stream: a device-side failure
+ * (a non-physical state: rho <= 0, P <= 0 or a non-finite wavespeed) is recorded in a device status
+ * word and reported as HWENO_ENONPHYS by the next synchronising call (hweno_sync,
+ * hweno_last_dt, hweno_max_wavespeed).  CUDA errors are reported as HWENO_ECUDA.
+ *
+ * THREADS.  A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef HWENO_H
+#define HWENO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hweno_ctx hweno_t;
+
+enum { HWENO_ADVECTION = 0, HWENO_BURGERS = 1, HWENO_EULER = 2 };
+enum { HWENO_BC_PERIODIC = 0, HWENO_BC_TRANSMISSIVE = 1, HWENO_BC_REFLECTIVE = 2 };
+enum {
+  HWENO_OK = 0,
+  HWENO_EINVAL = -1,   /* invalid argument */
+  HWENO_ECUDA = -2,    /* a CUDA runtime error */
+  HWENO_ENOMEM = -3,   /* workspace too small / host allocation failed */
+  HWENO_ENONPHYS = -4, /* rho <= 0, P <= 0 or non-finite wavespeed met on the device */
+  HWENO_ESTATE = -5    /* call out of order (e.g. no state bound) */
+};
+
+/* Create a solver for a uniform grid of nx (x ny) cells with spacing dx (dy).
+ * dim: 1 or 2.  system: HWENO_ADVECTION, HWENO_BURGERS or HWENO_EULER.  gamma: ratio of specific
+ * heats (Euler only, > 1).  bc: boundary condition on every side (periodic, as in every accuracy
+ * test of Sec. 4; transmissive = zero-order extrapolation of U and of its derivatives; reflective =
+ * the sign tables RBC-1d / RBC-2d-x / RBC-2d-y, Euler only).
+ * EINVAL: dim not 1 or 2, nx < 5 (ny < 5 in 2D), dx or dy <= 0, gamma <= 1 for Euler, unknown
+ * system or bc, reflective with a scalar system.  ny and dy are ignored when dim == 1.
+ * Defaults (Sec. 4): gamma0 = 0.95 (1D) / 0.99 (2D), d0 = 0.9, eps = 1e-10, CFL = 0.6, a = (1, 1). */
+int hweno_create(int dim, int system, int64_t nx, int64_t ny, double dx, double dy, double gamma,
+                 int bc, hweno_t **out);
+
+/* Linear weights gamma = (gamma0, (1-gamma0)/2, (1-gamma0)/2) and d = (d0, (1-d0)/2, (1-d0)/2)
+ * (Sec. 4), epsilon of Eq. (nonlinear), the CFL number, and the advection speeds.
+ * EINVAL: gamma0 or d0 outside (0,1), eps <= 0, cfl <= 0. */
+int hweno_set_params(hweno_t *h, double gamma0, double d0, double eps, double cfl, double adv_ax,
+                     double adv_ay);
+
+/* Stream for all launches and copies of this handle (a cudaStream_t; NULL = legacy default). */
+int hweno_set_stream(hweno_t *h, void *cuda_stream);
+
+/* Number of doubles in one state ([field][comp][ny][nx]). */
+size_t hweno_state_doubles(const hweno_t *h);
+
+/* Bytes of device workspace hweno_bind() needs (stage base, modified derivatives, nodal fluxes,
+ * face fluxes, wavespeed slots and status words). */
+size_t hweno_workspace_bytes(const hweno_t *h);
+
+/* Borrow the caller's device state (updated in place by hweno_step) and workspace (at least
+ * hweno_workspace_bytes() bytes).  Clears the device scalars (wavespeed slots, time, status) with
+ * an asynchronous memset on the handle's stream.  EINVAL: NULL pointers or unaligned pointers. */
+int hweno_bind(hweno_t *h, double *state_dev, void *workspace_dev);
+
+/* One evaluation of the spatial operator at S: L(S) (Eq. odeH / ode2H, every field) and
+ * M(S) = (U, V~, W~), the solution with the modified derivatives of Eq. (limiter).  The LF
+ * coefficients alpha_x, alpha_y are the maxima of |f'(u)| (Euler: |mu|+c, |nu|+c) over the cells
+ * of S.  S, L, M: device arrays of hweno_state_doubles() doubles; S must not alias L or M.
+ * Uses the bound workspace (ESTATE if none). */
+int hweno_rhs(hweno_t *h, const double *S_dev, double *L_dev, double *M_dev);
+
+/* One SSP-RK3 step of the bound state in place (Eq. fully-hweno / 2Dfully-hweno):
+ *   S1 = M(S^n) + dt L(S^n);  S2 = 3/4 B + 1/4 (M(S1) + dt L(S1));  S^{n+1} = 1/3 B + 2/3 (M(S2) + dt L(S2))
+ * with B = M(S^n).  dt > 0: fixed step.  dt <= 0: CFL step computed on the device from the
+ * wavespeeds of S^n: dt = CFL dx / alpha (1D), CFL / (alpha_x/dx + alpha_y/dy) (2D), clamped to the
+ * end time set by hweno_set_time() if one was set.  No host synchronisation. */
+int hweno_step(hweno_t *h, double dt);
+
+/* nsteps calls of hweno_step(h, dt). */
+int hweno_steps(hweno_t *h, double dt, int nsteps);
+
+/* Device time and end time used by CFL steps (t_end <= 0: no clamp). */
+int hweno_set_time(hweno_t *h, double t, double t_end);
+
+/* Synchronise the stream; read the dt of the last step (and the device time). */
+int hweno_last_dt(hweno_t *h, double *dt_host, double *t_host);
+
+/* Synchronise; alpha_x, alpha_y of the bound state (ay = 0 in 1D). */
+int hweno_max_wavespeed(hweno_t *h, double *ax, double *ay);
+
+/* Synchronise the stream and report the device status (HWENO_OK or HWENO_ENONPHYS). */
+int hweno_sync(hweno_t *h);
+
+/* Copy a host state into the bound device state / the bound state to the host (asynchronous
+ * cudaMemcpyAsync on the handle's stream; pinned host memory gives true asynchrony). */
+int hweno_upload(hweno_t *h, const double *host_state);
+int hweno_download(hweno_t *h, double *host_state);
+
+/* Per-kernel timing (tracing aid).  When on, every stage records CUDA events on the handle's
+ * stream around its three launches (cell, face, update kernels).  hweno_kernel_times()
+ * synchronises, returns the summed milliseconds and launch counts per kernel kind in
+ * ms3[0..2], n3[0..2] (cell, face, update) since the previous query, and resets them. */
+int hweno_set_profiling(hweno_t *h, int on);
+int hweno_kernel_times(hweno_t *h, double *ms3, long long *n3);
+
+/* Free the handle (not the borrowed device memory). */
+void hweno_destroy(hweno_t *h);
+
+/* Static message for a status code. */
+const char *hweno_strerror(int status);
+
+/* Number of kernel launches issued by this handle since creation (for accounting). */
+long long hweno_launch_count(const hweno_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HWENO_H */

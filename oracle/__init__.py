@@ -71,12 +71,15 @@ def lib():
             L.oracle_max_wavespeed.argtypes = [CP, _P, _P, _P]
             L.oracle_rhs.argtypes = [CP, _P, _P, _P]
             L.oracle_rhs_alpha.argtypes = [CP, _P, ctypes.c_double, ctypes.c_double, _P, _P]
+            L.oracle_rhs_cells.argtypes = [CP, _P, ctypes.c_double, ctypes.c_double, ctypes.c_longlong,
+                                           ctypes.POINTER(ctypes.c_longlong), _P, _P]
             L.oracle_steps.argtypes = [CP, _P, ctypes.c_double, ctypes.c_int]
             L.oracle_cfl_dt.argtypes = [CP, _P, ctypes.c_double, ctypes.c_double]
             L.oracle_cfl_dt.restype = ctypes.c_double
             L.oracle_run.argtypes = [CP, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_longlong, _P]
             L.oracle_run.restype = ctypes.c_longlong
+            L.oracle_count_flops.argtypes = [CP, ctypes.POINTER(ctypes.c_longlong)]
             L.oracle_stencil.argtypes = [_P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, _P]
             L.oracle_dterms.argtypes = [_P, _P, ctypes.c_double, _P]
@@ -125,6 +128,19 @@ def rhs(cfg: Cfg, S: np.ndarray, alpha=None):
     return L, M
 
 
+def rhs_cells(cfg: Cfg, S: np.ndarray, idx, alpha):
+    """L and M at the cells with flat indices idx (j*nx + i); arrays [ncell, field, comp]."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    nf = 2 if cfg.dim == 1 else 3
+    m = S.size // (nf * cfg.nx * cfg.ny)
+    L = np.zeros((idx.size, nf, m))
+    M = np.zeros((idx.size, nf, m))
+    _check(lib().oracle_rhs_cells(ctypes.byref(cfg), _ptr(S), float(alpha[0]), float(alpha[1]), idx.size,
+                                  idx.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), _ptr(L), _ptr(M)))
+    return L, M
+
+
 def steps(cfg: Cfg, S: np.ndarray, dt: float, nsteps: int = 1) -> np.ndarray:
     out = np.array(S, dtype=np.float64, copy=True, order="C")
     _check(lib().oracle_steps(ctypes.byref(cfg), _ptr(out), float(dt), int(nsteps)))
@@ -146,6 +162,15 @@ def run(cfg: Cfg, S: np.ndarray, t_end: float, cfl: float = 0.6, dx_pow: float =
     if n < 0:
         raise ValueError("oracle run failed")
     return out, int(n), float(t[0])
+
+
+def count_flops(cfg: Cfg) -> dict:
+    """Floating-point operation counts of the scheme as the oracle writes it (see the C source)."""
+    out = (ctypes.c_longlong * 6)()
+    _check(lib().oracle_count_flops(ctypes.byref(cfg), out))
+    keys = ("face", "nodal_per_dir", "modified_derivative_per_dir", "wavespeed_per_dir",
+            "update", "per_cell_step")
+    return dict(zip(keys, [int(v) for v in out]))
 
 
 def stencil(u3, v2, dx, gamma0=0.95, d0=0.9, eps=1e-10) -> dict:

@@ -529,6 +529,41 @@ struct Operator {
     return a;
   }
 
+  // Steps (1.1)-(1.3) / (2.1)-(2.3) and Step 3 for one face k+1/2 in direction dir, from the four
+  // cells k-1..k+2: U, the derivative field of this direction D (V for x, W for y) and, in 2D,
+  // the other derivative field O.  Outputs the flux of U (f^ or g^), of D (h^ or theta^) and
+  // the mixed flux of O (eta^ or xi^).
+  void face_flux(int dir, R Uc[4][4], R Dc[4][4], R Oc[4][4], R alpha, R* fhat, R* hhat, R* mixed) const {
+    double h = dir == 0 ? c.dx : c.dy;
+    // Step 1.1: interface values
+    R Um[4], Dm[4], Up[4], Dp[4];
+    face_states(dir, Uc, Dc, Um, Dm, Up, Dp);
+    // nodal fluxes for the D-terms (Eq. Pc: f at k-1..k+2, h at k-1 and k+2)
+    R fn[4][4], hn[4][4], on[4][4];
+    for (int q = 0; q < 4; ++q) {
+      ph.flux(dir, Uc[q], fn[q]);
+      ph.jac_vec(dir, Uc[q], Dc[q], hn[q]);
+      if (c.dim == 2) ph.jac_vec(dir, Uc[q], Oc[q], on[q]);
+    }
+    // Step 1.3: Eqs. (flux-1d), (flux-LF)
+    R FUm[4], FUp[4], HDm[4], HDp[4];
+    ph.flux(dir, Um, FUm);
+    ph.flux(dir, Up, FUp);
+    ph.jac_vec(dir, Um, Dm, HDm);
+    ph.jac_vec(dir, Up, Dp, HDp);
+    for (int k = 0; k < m; ++k) {
+      R Df, Dh;
+      dterms(fn[0][k], fn[1][k], fn[2][k], fn[3][k], hn[0][k], hn[3][k], h, Df, Dh);
+      fhat[k] = 0.5 * (FUm[k] + FUp[k] - alpha * (Up[k] - Um[k])) + Df;
+      hhat[k] = 0.5 * (HDm[k] + HDp[k] - alpha * (Dp[k] - Dm[k])) + Dh;
+      if (c.dim == 2) {
+        // Eq. (mixed): linear fourth-order flux of the other derivative field
+        mixed[k] = -(1.0 / 12.0) * on[0][k] + (7.0 / 12.0) * on[1][k] + (7.0 / 12.0) * on[2][k] -
+                   (1.0 / 12.0) * on[3][k];
+      }
+    }
+  }
+
   // L and M of one stage.  alpha: the LF coefficients (x, y).
   void rhs(const R* S, R* Lout, R* Mout, R alpha_x, R alpha_y) const {
     Padded<R> P(c);
@@ -543,16 +578,12 @@ struct Operator {
     auto fy = [&](int f, int k, int j, int i) -> R& { return FY[(((size_t)f * m + k) * (ny + 1) + j) * nx + i]; };
 
     for (int dir = 0; dir < c.dim; ++dir) {
-      const double h = dir == 0 ? c.dx : c.dy;
       const R alpha = dir == 0 ? alpha_x : alpha_y;
       const int own = dir == 0 ? 1 : 2;    // derivative field interpolated in this direction
       const int other = dir == 0 ? 2 : 1;  // derivative field with the mixed flux (2D)
       const int nlines = dir == 0 ? ny : nx;
       const int nalong = dir == 0 ? nx : ny;
       for (int line = 0; line < nlines; ++line) {
-        auto cellU = [&](int a, R* U) {
-          for (int k = 0; k < m; ++k) U[k] = dir == 0 ? P.at(0, k, line, a) : P.at(0, k, a, line);
-        };
         auto cellF = [&](int f, int a, R* D) {
           for (int k = 0; k < m; ++k) D[k] = dir == 0 ? P.at(f, k, line, a) : P.at(f, k, a, line);
         };
@@ -560,46 +591,21 @@ struct Operator {
         for (int a = -1; a < nalong; ++a) {
           R Uc[4][4], Dc[4][4], Oc[4][4];
           for (int q = 0; q < 4; ++q) {
-            cellU(a - 1 + q, Uc[q]);
+            cellF(0, a - 1 + q, Uc[q]);
             cellF(own, a - 1 + q, Dc[q]);
             if (c.dim == 2) cellF(other, a - 1 + q, Oc[q]);
           }
-          // Step 1.1: interface values
-          R Um[4], Dm[4], Up[4], Dp[4];
-          face_states(dir, Uc, Dc, Um, Dm, Up, Dp);
-          // nodal fluxes for the D-terms (Eq. Pc: f at k-1..k+2, h at k-1 and k+2)
-          R fn[4][4], hn[4][4], on[4][4];
-          for (int q = 0; q < 4; ++q) {
-            ph.flux(dir, Uc[q], fn[q]);
-            ph.jac_vec(dir, Uc[q], Dc[q], hn[q]);
-            if (c.dim == 2) ph.jac_vec(dir, Uc[q], Oc[q], on[q]);
-          }
-          // Step 1.3: Eqs. (flux-1d), (flux-LF)
-          R FUm[4], FUp[4], HDm[4], HDp[4];
-          ph.flux(dir, Um, FUm);
-          ph.flux(dir, Up, FUp);
-          ph.jac_vec(dir, Um, Dm, HDm);
-          ph.jac_vec(dir, Up, Dp, HDp);
+          R fh[4], hh[4], mx[4];
+          face_flux(dir, Uc, Dc, Oc, alpha, fh, hh, mx);
           for (int k = 0; k < m; ++k) {
-            R Df, Dh;
-            dterms(fn[0][k], fn[1][k], fn[2][k], fn[3][k], hn[0][k], hn[3][k], h, Df, Dh);
-            R fhat = 0.5 * (FUm[k] + FUp[k] - alpha * (Up[k] - Um[k])) + Df;
-            R hhat = 0.5 * (HDm[k] + HDp[k] - alpha * (Dp[k] - Dm[k])) + Dh;
             if (dir == 0) {
-              fx(0, k, line, a + 1) = fhat;
-              fx(own, k, line, a + 1) = hhat;
+              fx(0, k, line, a + 1) = fh[k];
+              fx(own, k, line, a + 1) = hh[k];
+              if (c.dim == 2) fx(other, k, line, a + 1) = mx[k];
             } else {
-              fy(0, k, a + 1, line) = fhat;
-              fy(own, k, a + 1, line) = hhat;
-            }
-            if (c.dim == 2) {
-              // Eq. (mixed): linear fourth-order flux of the other derivative field
-              R mixed = -(1.0 / 12.0) * on[0][k] + (7.0 / 12.0) * on[1][k] + (7.0 / 12.0) * on[2][k] -
-                        (1.0 / 12.0) * on[3][k];
-              if (dir == 0)
-                fx(other, k, line, a + 1) = mixed;
-              else
-                fy(other, k, a + 1, line) = mixed;
+              fy(0, k, a + 1, line) = fh[k];
+              fy(own, k, a + 1, line) = hh[k];
+              fy(other, k, a + 1, line) = mx[k];
             }
           }
         }
@@ -607,7 +613,7 @@ struct Operator {
         for (int a = 0; a < nalong; ++a) {
           R Uc[3][4], Dc[3][4], Dt[4];
           for (int q = 0; q < 3; ++q) {
-            cellU(a - 1 + q, Uc[q]);
+            cellF(0, a - 1 + q, Uc[q]);
             cellF(own, a - 1 + q, Dc[q]);
           }
           modified_derivative(dir, Uc, Dc, Dt);
@@ -629,6 +635,69 @@ struct Operator {
           }
     for (int k = 0; k < m; ++k)
       for (size_t p = 0; p < plane; ++p) Mout[(size_t)k * plane + p] = S[(size_t)k * plane + p];
+  }
+
+  // The same L and M at selected cells only, reading S through the boundary map (for checks at
+  // sizes where the full operator is too slow on the CPU).  Lout, Mout: [ncell][field][comp].
+  void rhs_cells(const R* S, R alpha_x, R alpha_y, long long ncell, const long long* idx, R* Lout, R* Mout) const {
+    const int nx = c.nx, ny = c.dim == 2 ? c.ny : 1;
+    const size_t plane = (size_t)nx * ny;
+    auto value = [&](int f, int k, int j, int i) -> R {
+      bool fx, fy = false;
+      int si = bc_source(c.bc, i, nx, &fx);
+      int sj = c.dim == 2 ? bc_source(c.bc, j, ny, &fy) : 0;
+      double sgn = 1.0;
+      if (fx) sgn *= reflect_sign(c, 0, f, k);
+      if (fy) sgn *= reflect_sign(c, 1, f, k);
+      R v = S[((size_t)f * m + k) * plane + (size_t)sj * nx + si];
+      return sgn == 1.0 ? v : -v;
+    };
+    for (long long s = 0; s < ncell; ++s) {
+      const int i = (int)(idx[s] % nx), j = (int)(idx[s] / nx);
+      R Lc[3][4], Mc[3][4];
+      for (int f = 0; f < nf; ++f)
+        for (int k = 0; k < m; ++k) Lc[f][k] = R(0.0);
+      for (int k = 0; k < m; ++k) Mc[0][k] = value(0, k, j, i);
+      for (int dir = 0; dir < c.dim; ++dir) {
+        const R alpha = dir == 0 ? alpha_x : alpha_y;
+        const int own = dir == 0 ? 1 : 2, other = dir == 0 ? 2 : 1;
+        const double inv_h = dir == 0 ? 1.0 / c.dx : 1.0 / c.dy;
+        auto at = [&](int f, int k, int off) -> R { return dir == 0 ? value(f, k, j, i + off) : value(f, k, j + off, i); };
+        R fl[2][3][4];  // faces -1/2 and +1/2: [face][field][comp]
+        for (int side = 0; side < 2; ++side) {
+          R Uc[4][4], Dc[4][4], Oc[4][4];
+          for (int q = 0; q < 4; ++q)
+            for (int k = 0; k < m; ++k) {
+              int off = side - 2 + q;  // face i-1/2: cells i-2..i+1; face i+1/2: i-1..i+2
+              Uc[q][k] = at(0, k, off);
+              Dc[q][k] = at(own, k, off);
+              Oc[q][k] = c.dim == 2 ? at(other, k, off) : R(0.0);
+            }
+          R fh[4], hh[4], mx[4];
+          face_flux(dir, Uc, Dc, Oc, alpha, fh, hh, mx);
+          for (int k = 0; k < m; ++k) {
+            fl[side][0][k] = fh[k];
+            fl[side][own][k] = hh[k];
+            if (c.dim == 2) fl[side][other][k] = mx[k];
+          }
+        }
+        for (int f = 0; f < nf; ++f)
+          for (int k = 0; k < m; ++k) Lc[f][k] = Lc[f][k] - inv_h * (fl[1][f][k] - fl[0][f][k]);
+        R Uc[3][4], Dc[3][4], Dt[4];
+        for (int q = 0; q < 3; ++q)
+          for (int k = 0; k < m; ++k) {
+            Uc[q][k] = at(0, k, q - 1);
+            Dc[q][k] = at(own, k, q - 1);
+          }
+        modified_derivative(dir, Uc, Dc, Dt);
+        for (int k = 0; k < m; ++k) Mc[own][k] = Dt[k];
+      }
+      for (int f = 0; f < nf; ++f)
+        for (int k = 0; k < m; ++k) {
+          Lout[((size_t)s * nf + f) * m + k] = Lc[f][k];
+          Mout[((size_t)s * nf + f) * m + k] = Mc[f][k];
+        }
+    }
   }
 };
 
@@ -663,6 +732,28 @@ double cfl_dt(const Cfg& c, const R* S, double cfl, double dx_pow) {
   double ay = (double)op.max_wavespeed(1, S);
   return cfl / (ax / std::pow(c.dx, dx_pow) + ay / std::pow(c.dy, dx_pow));
 }
+
+// ---------------------------------------------------------------------------------------------
+// Operation counting: the same templated code instantiated with a scalar that counts every
+// floating-point +, -, *, / and sqrt (sign changes, fabs and comparisons are not counted).  The
+// counts are data independent (the arithmetic has no data-dependent branches).
+struct Counted {
+  double v;
+  Counted() : v(0.0) {}
+  Counted(double x) : v(x) {}
+  static long long& n() {
+    static long long c = 0;
+    return c;
+  }
+};
+inline Counted operator+(const Counted& a, const Counted& b) { ++Counted::n(); return Counted(a.v + b.v); }
+inline Counted operator-(const Counted& a, const Counted& b) { ++Counted::n(); return Counted(a.v - b.v); }
+inline Counted operator*(const Counted& a, const Counted& b) { ++Counted::n(); return Counted(a.v * b.v); }
+inline Counted operator/(const Counted& a, const Counted& b) { ++Counted::n(); return Counted(a.v / b.v); }
+inline Counted operator-(const Counted& a) { return Counted(-a.v); }
+inline bool operator>(const Counted& a, const Counted& b) { return a.v > b.v; }
+inline Counted fabs(const Counted& a) { return Counted(std::fabs(a.v)); }
+inline Counted sqrt(const Counted& a) { ++Counted::n(); return Counted(std::sqrt(a.v)); }
 
 }  // namespace hwo
 
@@ -717,6 +808,16 @@ int oracle_rhs_alpha(const oracle_cfg* c, const double* S, double ax, double ay,
   return 0;
 }
 
+// L and M at selected cells (flat indices j*nx+i) with given LF coefficients.
+// Lout, Mout: [ncell][field][comp].
+int oracle_rhs_cells(const oracle_cfg* c, const double* S, double ax, double ay, long long ncell,
+                     const long long* idx, double* Lout, double* Mout) {
+  if (check_cfg(c) || ncell < 0) return -1;
+  hwo::Operator<double> op(*c);
+  op.rhs_cells(S, ax, ay, ncell, idx, Lout, Mout);
+  return 0;
+}
+
 // nsteps SSP-RK3 steps in place with a fixed dt
 int oracle_steps(const oracle_cfg* c, double* S, double dt, int nsteps) {
   if (check_cfg(c) || nsteps < 0) return -1;
@@ -748,6 +849,63 @@ long long oracle_run(const oracle_cfg* c, double* S, double t_end, double cfl, d
   }
   if (t_out) *t_out = t;
   return n;
+}
+
+// Floating-point operation counts of the scheme as written (counting scalar):
+// out[0] one face: interface values, fluxes at U^+-, D-terms, LF and mixed fluxes (the nodal
+//        values of the four cells excluded);
+// out[1] nodal values of one cell in one direction (f, f'(u) v and, in 2D, the mixed nodal value);
+// out[2] modified derivative of one cell in one direction;  out[3] wavespeed of one cell, one
+// direction;  out[4] conservative difference and SSP-RK3 combination of one cell (stage 2 form);
+// out[5] one full SSP-RK3 step per cell: 3 (dim (faces + nodal + modified + wavespeed) + update).
+int oracle_count_flops(const oracle_cfg* c, long long* out) {
+  if (check_cfg(c)) return -1;
+  using hwo::Counted;
+  hwo::Operator<Counted> op(*c);
+  const int m = hwo::ncomp(*c);
+  const int dim = c->dim;
+  long long& n = Counted::n();
+  Counted Uc[4][4], Dc[4][4], Oc[4][4];
+  for (int q = 0; q < 4; ++q)
+    for (int k = 0; k < 4; ++k) {
+      Uc[q][k] = Counted(k == 0 ? 1.0 + 0.1 * q : (k == m - 1 ? 2.5 + 0.1 * q : 0.2 * q - 0.1));
+      Dc[q][k] = Counted(0.3 * q - 0.2 * k);
+      Oc[q][k] = Counted(0.1 * k - 0.2 * q);
+    }
+  Counted fh[4], hh[4], mx[4];
+  n = 0;
+  op.face_flux(0, Uc, Dc, Oc, Counted(2.0), fh, hh, mx);
+  long long face_all = n;
+  n = 0;
+  Counted fn[4], hn[4], on[4];
+  op.ph.flux(0, Uc[0], fn);
+  op.ph.jac_vec(0, Uc[0], Dc[0], hn);
+  if (dim == 2) op.ph.jac_vec(0, Uc[0], Oc[0], on);
+  long long nodal = n;
+  n = 0;
+  Counted U3[3][4], D3[3][4], Dt[4];
+  for (int q = 0; q < 3; ++q)
+    for (int k = 0; k < 4; ++k) {
+      U3[q][k] = Uc[q][k];
+      D3[q][k] = Dc[q][k];
+    }
+  op.modified_derivative(0, U3, D3, Dt);
+  long long md = n;
+  n = 0;
+  op.ph.wavespeed(0, Uc[0]);
+  long long ws = n;
+  // conservative difference (dim differences, each a subtraction and a scaling, summed) and the
+  // stage combination a B + b (M + dt L) per value
+  const long long nvals = (long long)hwo::nfield(*c) * m;
+  long long upd = nvals * (dim == 2 ? 5 : 2) + nvals * 4;
+  out[0] = face_all - 4 * nodal;
+  out[1] = nodal;
+  out[2] = md;
+  out[3] = ws;
+  out[4] = upd;
+  out[5] = 3 * (dim * (out[0] + out[1] + out[2] + out[3]) + upd);
+  n = 0;
+  return 0;
 }
 
 // One HWENO stencil (Sec. 2.1) with all intermediates, for the unit tests.

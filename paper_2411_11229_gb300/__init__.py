@@ -1,0 +1,17 @@
+"""GB300-native (sm_103a) FP64 implementation of the fifth-order finite-difference
+interpolation-based Hermite WENO scheme HWENO-I (Xie, Tao, Jiao, Zhang, arXiv 2411.11229).
+
+The numerical work runs in libhweno.so (CUDA, see include/hweno.h); this package only builds
+and loads it and marshals torch-owned device memory into its C ABI.
+"""
+from ._make import build  # noqa: F401
+
+
+def __getattr__(name):
+    if name == "Solver":
+        from .solver import Solver
+        return Solver
+    if name == "capi":
+        from . import _capi
+        return _capi
+    raise AttributeError(name)

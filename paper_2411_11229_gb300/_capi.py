@@ -1,0 +1,79 @@
+"""ctypes binding of libhweno.so with the names of include/hweno.h (argument marshalling only).
+
+Every numerical step runs in the CUDA library; there is no host fallback.  Loading fails loudly
+when the library is missing or cannot be built.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+from . import _make as _build
+
+HWENO_ADVECTION, HWENO_BURGERS, HWENO_EULER = 0, 1, 2
+HWENO_BC_PERIODIC, HWENO_BC_TRANSMISSIVE, HWENO_BC_REFLECTIVE = 0, 1, 2
+HWENO_OK, HWENO_EINVAL, HWENO_ECUDA, HWENO_ENOMEM, HWENO_ENONPHYS, HWENO_ESTATE = 0, -1, -2, -3, -4, -5
+
+# every entry point declared in include/hweno.h: name -> (restype, argtypes)
+_D = ctypes.c_double
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_H = ctypes.c_void_p
+SIGNATURES = {
+    "hweno_create": (_I, [_I, _I, ctypes.c_int64, ctypes.c_int64, _D, _D, _D, _I, ctypes.POINTER(_H)]),
+    "hweno_set_params": (_I, [_H, _D, _D, _D, _D, _D, _D]),
+    "hweno_set_stream": (_I, [_H, _P]),
+    "hweno_state_doubles": (ctypes.c_size_t, [_H]),
+    "hweno_workspace_bytes": (ctypes.c_size_t, [_H]),
+    "hweno_bind": (_I, [_H, _P, _P]),
+    "hweno_rhs": (_I, [_H, _P, _P, _P]),
+    "hweno_step": (_I, [_H, _D]),
+    "hweno_steps": (_I, [_H, _D, _I]),
+    "hweno_set_time": (_I, [_H, _D, _D]),
+    "hweno_last_dt": (_I, [_H, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "hweno_max_wavespeed": (_I, [_H, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "hweno_sync": (_I, [_H]),
+    "hweno_upload": (_I, [_H, _P]),
+    "hweno_download": (_I, [_H, _P]),
+    "hweno_set_profiling": (_I, [_H, _I]),
+    "hweno_kernel_times": (_I, [_H, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)]),
+    "hweno_destroy": (None, [_H]),
+    "hweno_strerror": (ctypes.c_char_p, [_I]),
+    "hweno_launch_count": (ctypes.c_longlong, [_H]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(build: bool = True):
+    """Load libhweno.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build else _build.LIB
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class HwenoError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = load().hweno_strerror(code).decode()
+        super().__init__(f"{where}: {msg} ({code})")
+        self.code = code
+
+
+def check(code: int, where: str) -> None:
+    if code != HWENO_OK:
+        raise HwenoError(code, where)
+
+
+def __getattr__(name):
+    if name in SIGNATURES:
+        return getattr(load(), name)
+    raise AttributeError(name)

@@ -1,0 +1,481 @@
+// Stage kernels of the HWENO-I scheme (Xie, Tao, Jiao, Zhang, arXiv 2411.11229) for sm_103a.
+//
+// One Runge-Kutta stage is three launches over the grid:
+//   k_cell   per cell : wavespeed (LF alpha of the stage input), nodal fluxes f, h = f'(u) v (and
+//                       the mixed-flux nodal values in 2D) for the D-terms (Eqs. Cd-1, DfDh, mixed),
+//                       Euler primitives for the Roe averages, and the modified derivative v~
+//                       (Eq. limiter) in the local characteristic fields of the cell.
+//   k_face   per face : characteristic projection with the Roe-averaged eigenvectors, the HWENO
+//                       interpolation of u and v to both sides of the face (Eqs. Pxi, P'xi, GHYZ,
+//                       nonlinear, interp), back projection, and the numerical fluxes
+//                       (Eqs. flux-1d, flux-LF, DfDh, mixed).
+//   k_update per cell : conservative differences (Eqs. odeH / ode2H) and the SSP-RK3 combination
+//                       with the modified derivative in the base (Eqs. fully-hweno, 2Dfully-hweno),
+//                       in place; or L and M written out (rhs mode).
+// The path is bound by the FP64 pipe (a few thousand FP64 operations per cell and stage against
+// roughly a kilobyte of traffic), so the split keeps every warp's lanes busy on one kind of work
+// and exchanges intermediates through L2/HBM, which has bandwidth to spare.
+#pragma once
+#include "hweno_math.cuh"
+
+namespace hw {
+
+// Device views into the caller's workspace.
+struct Work {
+  double* B;     // stage base M(S^n): [NF][NC][plane]
+  double* MD;    // modified derivatives (V~, W~): [DIM][NC][plane]
+  double* NOD;   // nodal values per direction, normal frame: [DIM][NG][NC][plane]
+  double* PRIM;  // Euler primitives (sqrt(rho), u[, v], H): [NP][plane]
+  double* FX;    // x-face fluxes, original frame: [NF][NC][ny][nx+1]
+  double* FY;    // y-face fluxes: [NF][NC][ny+1][nx]
+  unsigned long long* alpha;  // wavespeed slots (bit patterns of non-negative doubles): [4][2]
+  double* scal;               // [0] dt of the current step, [1] t, [2] t_end
+  unsigned int* status;       // bit 0: non-physical state met
+};
+
+constexpr int kThreads = 128;
+
+template <int NC>
+__device__ __forceinline__ void swap_frame(double* q) {
+  if (NC == 4) {
+    const double t = q[1];
+    q[1] = q[2];
+    q[2] = t;
+  }
+}
+
+// max over the block of (a, b), then one atomicMax per block on the bit patterns
+__device__ __forceinline__ void block_max2(double a, double b, unsigned long long* dst) {
+  __shared__ double sa[32], sb[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sa[wid] = a;
+    sb[wid] = b;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    a = lane < nw ? sa[lane] : 0.0;
+    b = lane < nw ? sb[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+      b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    if (lane == 0) {
+      atomicMax(dst, dbl_bits(a));
+      atomicMax(dst + 1, dbl_bits(b));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Modified derivative of one cell in one direction (normal frame).  U3/D3: cells i-1, i, i+1
+// (D = derivative along the sweep; only i-1 and i+1 enter).  e: eigenvectors of the cell.
+template <int NC, int SYS>
+__device__ __forceinline__ void modified_derivative(const double (&U3)[3][NC], const double (&D3)[3][NC],
+                                                    const Eig<NC>& e, double h, double inv_h, const Grid& g,
+                                                    double* out) {
+  double W[3][NC], Zm[NC], Zp[NC];
+  double hDm[NC], hDp[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    hDm[k] = h * D3[0][k];
+    hDp[k] = h * D3[2][k];
+  }
+  if (SYS == SYS_EULER) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) e.project(U3[q], W[q]);
+    e.project(hDm, Zm);
+    e.project(hDp, Zp);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) W[q][0] = U3[q][0];
+    Zm[0] = hDm[0];
+    Zp[0] = hDp[0];
+  }
+  double ht[NC];
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    const Beta b = indicators(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s]);
+    const Wts w = weights(b, g.eps);
+    ht[s] = limiter(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], w, g.d0, g.d1);
+  }
+  if (SYS == SYS_EULER) {
+    double hv[NC];
+    e.back(ht, hv);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) out[k] = hv[k] * inv_h;
+  } else {
+    out[0] = ht[0] * inv_h;
+  }
+}
+
+template <int DIM, int SYS>
+__global__ void __launch_bounds__(kThreads) k_cell(Grid g, const double* __restrict__ S, Work w, int slot) {
+  using T = Traits<DIM, SYS>;
+  constexpr int NC = T::NC, NG = T::NG;
+  const long long plane = g.plane;
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  double wsx = 0.0, wsy = 0.0;
+  if (p < plane) {
+    const int i = (int)(p % g.nx), j = (int)(p / g.nx);
+    double U[NC], V[NC], Wd[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      U[k] = S[k * plane + p];
+      V[k] = S[(NC + k) * plane + p];
+      if (DIM == 2) Wd[k] = S[(2 * NC + k) * plane + p];
+    }
+    // primitives and wavespeeds
+    double u = 0, v = 0, pr = 0, ir = 0, H = 0, c = 0;
+    if (SYS == SYS_EULER) {
+      ir = rcp(U[0]);
+      u = U[1] * ir;
+      if (DIM == 2) v = U[2] * ir;
+      const double ke = DIM == 2 ? fma(U[1], u, U[2] * v) : U[1] * u;
+      pr = g.gm1 * fma(-0.5, ke, U[NC - 1]);
+      H = (U[NC - 1] + pr) * ir;
+      c = sqrt(g.gamma * pr * ir);
+      wsx = fabs(u) + c;
+      wsy = DIM == 2 ? fabs(v) + c : 0.0;
+      if (!(U[0] > 0.0) || !(pr > 0.0) || !isfinite(wsx) || !isfinite(wsy)) atomicOr(w.status, 1u);
+      w.PRIM[p] = sqrt(U[0]);
+      w.PRIM[plane + p] = u;
+      if (DIM == 2) {
+        w.PRIM[2 * plane + p] = v;
+        w.PRIM[3 * plane + p] = H;
+      } else {
+        w.PRIM[2 * plane + p] = H;
+      }
+    } else if (SYS == SYS_BURGERS) {
+      wsx = fabs(U[0]);
+      wsy = DIM == 2 ? wsx : 0.0;
+      if (!isfinite(wsx)) atomicOr(w.status, 1u);
+    } else {
+      wsx = fabs(g.ax);
+      wsy = DIM == 2 ? fabs(g.ay) : 0.0;
+    }
+    // nodal values per direction (normal frame)
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      double Un[NC], Dn[NC], On[NC], F[NC], Hn[NC], Mx[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        Un[k] = U[k];
+        Dn[k] = d == 0 ? V[k] : Wd[k];
+        On[k] = d == 0 ? Wd[k] : V[k];
+      }
+      const double a = d == 0 ? g.ax : g.ay;
+      if (SYS == SYS_EULER) {
+        if (d == 1) {
+          swap_frame<NC>(Un);
+          swap_frame<NC>(Dn);
+          swap_frame<NC>(On);
+        }
+        const double un = d == 0 ? u : v, vt = d == 0 ? v : u;
+        F[0] = Un[1];
+        F[1] = fma(Un[1], un, pr);
+        if (DIM == 2) F[2] = Un[2] * un;
+        F[NC - 1] = (Un[NC - 1] + pr) * un;
+        if (DIM == 2) {
+          Phys<2, SYS_EULER>::jvp_prim(Un, un, vt, pr, ir, Dn, Hn, g.gm1);
+          Phys<2, SYS_EULER>::jvp_prim(Un, un, vt, pr, ir, On, Mx, g.gm1);
+        } else {
+          Phys<1, SYS_EULER>::jvp_prim(Un, un, pr, ir, Dn, Hn, g.gm1);
+        }
+      } else {
+        Phys<DIM, SYS>::flux(Un, F, a, g.gm1);
+        Phys<DIM, SYS>::jvp(Un, Dn, Hn, a, g.gm1);
+        if (DIM == 2) Phys<DIM, SYS>::jvp(Un, On, Mx, a, g.gm1);
+      }
+      double* nod = w.NOD + (long long)d * NG * NC * plane;
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        nod[k * plane + p] = F[k];
+        nod[(NC + k) * plane + p] = Hn[k];
+        if (DIM == 2) nod[(2 * NC + k) * plane + p] = Mx[k];
+      }
+    }
+    // modified derivatives (Eq. limiter), one per direction
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const int n = d == 0 ? g.nx : g.ny;
+      const int a0 = d == 0 ? i : j;
+      const int fld = d == 0 ? 1 : 2;
+      double U3[3][NC], D3[3][NC];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int ac = bc_index(a0 - 1 + q, n, g.bc);
+        const long long pc = d == 0 ? (long long)j * g.nx + ac : (long long)ac * g.nx + i;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          U3[q][k] = q == 1 ? U[k] : S[k * plane + pc];
+          D3[q][k] = S[(fld * NC + k) * plane + pc];
+        }
+        if (SYS == SYS_EULER && d == 1) {
+          swap_frame<NC>(U3[q]);
+          swap_frame<NC>(D3[q]);
+        }
+      }
+      Eig<NC> e;
+      if (SYS == SYS_EULER) e.setup(d == 0 ? u : v, d == 0 ? v : u, H, c, rcp(c), g.gm1);
+      double out[NC];
+      const double h = d == 0 ? g.dx : g.dy, ih = d == 0 ? g.inv_dx : g.inv_dy;
+      modified_derivative<NC, SYS>(U3, D3, e, h, ih, g, out);
+      if (SYS == SYS_EULER && d == 1) swap_frame<NC>(out);
+#pragma unroll
+      for (int k = 0; k < NC; ++k) w.MD[((long long)d * NC + k) * plane + p] = out[k];
+    }
+  }
+  block_max2(wsx, wsy, w.alpha + 2 * slot);
+}
+
+// ---------------------------------------------------------------------------------------------
+template <int DIM, int SYS>
+__global__ void __launch_bounds__(kThreads) k_face(Grid g, const double* __restrict__ S, Work w, int slot) {
+  using T = Traits<DIM, SYS>;
+  constexpr int NC = T::NC, NG = T::NG;
+  const int dir = blockIdx.y;
+  const long long plane = g.plane;
+  const int n = dir == 0 ? g.nx : g.ny;
+  const int nlines = dir == 0 ? g.ny : g.nx;
+  const long long f = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (f >= (long long)(n + 1) * nlines) return;
+  int fa, line;
+  if (dir == 0) {
+    line = (int)(f / (n + 1));
+    fa = (int)(f % (n + 1));
+  } else {
+    fa = (int)(f / g.nx);
+    line = (int)(f % g.nx);
+  }
+  // cells fa-2 .. fa+1 around face fa (between cells fa-1 and fa)
+  long long pc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int a = bc_index(fa - 2 + q, n, g.bc);
+    pc[q] = dir == 0 ? (long long)line * g.nx + a : (long long)a * g.nx + line;
+  }
+  const int fown = dir == 0 ? 1 : 2, foth = dir == 0 ? 2 : 1;
+  const double h = dir == 0 ? g.dx : g.dy, ih = dir == 0 ? g.inv_dx : g.inv_dy;
+  double Uq[4][NC], Zq[4][NC];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      Uq[q][k] = S[k * plane + pc[q]];
+      Zq[q][k] = h * S[(fown * NC + k) * plane + pc[q]];
+    }
+    if (SYS == SYS_EULER && dir == 1) {
+      swap_frame<NC>(Uq[q]);
+      swap_frame<NC>(Zq[q]);
+    }
+  }
+  // characteristic fields at the face: Roe average of the two adjacent cells
+  Eig<NC> e;
+  double Wq[4][NC], Yq[4][NC];
+  if (SYS == SYS_EULER) {
+    const double sl = w.PRIM[pc[1]], sr = w.PRIM[pc[2]];
+    const int ou = dir == 0 ? 1 : 2, ov = dir == 0 ? 2 : 1;
+    const double ul = w.PRIM[ou * plane + pc[1]], ur = w.PRIM[ou * plane + pc[2]];
+    double vl = 0, vr = 0;
+    if (DIM == 2) {
+      vl = w.PRIM[ov * plane + pc[1]];
+      vr = w.PRIM[ov * plane + pc[2]];
+    }
+    const int oh = DIM == 2 ? 3 : 2;
+    const double Hl = w.PRIM[oh * plane + pc[1]], Hr = w.PRIM[oh * plane + pc[2]];
+    const double iw = rcp(sl + sr);
+    const double ub = fma(sl, ul, sr * ur) * iw;
+    const double vb = DIM == 2 ? fma(sl, vl, sr * vr) * iw : 0.0;
+    const double Hb = fma(sl, Hl, sr * Hr) * iw;
+    const double c2 = g.gm1 * fma(-0.5, DIM == 2 ? fma(ub, ub, vb * vb) : ub * ub, Hb);
+    const double ic = rsqrt(c2);
+    e.setup(ub, vb, Hb, c2 * ic, ic, g.gm1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      e.project(Uq[q], Wq[q]);
+      e.project(Zq[q], Yq[q]);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      Wq[q][0] = Uq[q][0];
+      Yq[q][0] = Zq[q][0];
+    }
+  }
+  // HWENO interpolation in each characteristic field: u^- from the stencil of cell fa-1,
+  // u^+ from the stencil of cell fa (mirror image)
+  double cm[NC], chm[NC], cp[NC], chp[NC];
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    {
+      const Beta b = indicators(Wq[0][s], Wq[1][s], Wq[2][s], Yq[0][s], Yq[2][s]);
+      const Wts wt = weights(b, g.eps);
+      right_face(Wq[0][s], Wq[1][s], Wq[2][s], Yq[0][s], Yq[2][s], wt, g.g0, g.g1, cm[s], chm[s]);
+    }
+    {
+      const Beta b = indicators(Wq[1][s], Wq[2][s], Wq[3][s], Yq[1][s], Yq[3][s]);
+      const Wts wt = weights(b, g.eps);
+      left_face(Wq[1][s], Wq[2][s], Wq[3][s], Yq[1][s], Yq[3][s], wt, g.g0, g.g1, cp[s], chp[s]);
+    }
+  }
+  double Um[NC], Up[NC], Dm[NC], Dp[NC];
+  if (SYS == SYS_EULER) {
+    double hDm[NC], hDp[NC];
+    e.back(cm, Um);
+    e.back(cp, Up);
+    e.back(chm, hDm);
+    e.back(chp, hDp);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      Dm[k] = hDm[k] * ih;
+      Dp[k] = hDp[k] * ih;
+    }
+  } else {
+    Um[0] = cm[0];
+    Up[0] = cp[0];
+    Dm[0] = chm[0] * ih;
+    Dp[0] = chp[0] * ih;
+  }
+  // Lax-Friedrichs fluxes at the interpolated states (Eq. flux-LF)
+  const double a_adv = dir == 0 ? g.ax : g.ay;
+  double FUm[NC], FUp[NC], HDm[NC], HDp[NC];
+  Phys<DIM, SYS>::flux(Um, FUm, a_adv, g.gm1);
+  Phys<DIM, SYS>::flux(Up, FUp, a_adv, g.gm1);
+  Phys<DIM, SYS>::jvp(Um, Dm, HDm, a_adv, g.gm1);
+  Phys<DIM, SYS>::jvp(Up, Dp, HDp, a_adv, g.gm1);
+  const double alpha = __longlong_as_double((long long)w.alpha[2 * slot + dir]);
+  const double* nod = w.NOD + (long long)dir * NG * NC * plane;
+  double* out = dir == 0 ? w.FX : w.FY;
+  const long long oplane = dir == 0 ? (long long)g.ny * (g.nx + 1) : (long long)(g.ny + 1) * g.nx;
+  const long long fo = dir == 0 ? (long long)line * (g.nx + 1) + fa : (long long)fa * g.nx + line;
+  double fh[NC], hh[NC], mh[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const double f0 = nod[k * plane + pc[0]], f1 = nod[k * plane + pc[1]];
+    const double f2 = nod[k * plane + pc[2]], f3 = nod[k * plane + pc[3]];
+    const double h0 = nod[(NC + k) * plane + pc[0]], h3 = nod[(NC + k) * plane + pc[3]];
+    // D-terms (Eqs. Cd-1, DfDh)
+    const double Df = fma(DCoef::cf, (f0 - f1) + (f3 - f2), DCoef::ch * h * (h0 - h3));
+    const double Dh = fma(ih, fma(DCoef::ef, f0 - f3, DCoef::eg * (f2 - f1)), DCoef::eh * (h0 + h3));
+    fh[k] = fma(0.5, fma(-alpha, Up[k] - Um[k], FUm[k] + FUp[k]), Df);
+    hh[k] = fma(0.5, fma(-alpha, Dp[k] - Dm[k], HDm[k] + HDp[k]), Dh);
+    if (DIM == 2) {
+      const double o0 = nod[(2 * NC + k) * plane + pc[0]], o1 = nod[(2 * NC + k) * plane + pc[1]];
+      const double o2 = nod[(2 * NC + k) * plane + pc[2]], o3 = nod[(2 * NC + k) * plane + pc[3]];
+      // Eq. (mixed)
+      mh[k] = fma(7.0 / 12.0, o1 + o2, (-1.0 / 12.0) * (o0 + o3));
+    }
+  }
+  if (SYS == SYS_EULER && dir == 1) {
+    swap_frame<NC>(fh);
+    swap_frame<NC>(hh);
+    swap_frame<NC>(mh);
+  }
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    out[k * oplane + fo] = fh[k];
+    out[(fown * NC + k) * oplane + fo] = hh[k];
+    if (DIM == 2) out[(foth * NC + k) * oplane + fo] = mh[k];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// mode 0: Runge-Kutta stage in place, S = a B + b (M + dt L) (stage 0: B := M, S = M + dt L).
+// mode 1: write L and M to Lout, Mout.
+// dt: dt_fixed > 0, or (dt_fixed <= 0) the CFL step from wavespeed slot `slot` at stage 0
+// (clamped to t_end), stored in scal[0] and reused by stages 1 and 2.
+template <int DIM, int SYS>
+__global__ void __launch_bounds__(kThreads) k_update(Grid g, double* __restrict__ S, Work w, int mode, int stage,
+                                                      double a_k, double b_k, double dt_fixed, int slot,
+                                                      double* __restrict__ Lout, double* __restrict__ Mout) {
+  using T = Traits<DIM, SYS>;
+  constexpr int NC = T::NC, NF = T::NF;
+  __shared__ double s_dt;
+  const long long plane = g.plane;
+  if (mode == 0) {
+    if (threadIdx.x == 0) {
+      double dt;
+      if (stage == 0) {
+        if (dt_fixed > 0.0) {
+          dt = dt_fixed;
+        } else {
+          const double axs = __longlong_as_double((long long)w.alpha[2 * slot]);
+          const double ays = __longlong_as_double((long long)w.alpha[2 * slot + 1]);
+          dt = DIM == 2 ? g.cfl / fma(axs, g.inv_dx, ays * g.inv_dy) : g.cfl * g.dx / axs;
+          const double t = w.scal[1], te = w.scal[2];
+          if (te > 0.0 && t + dt > te) dt = fmax(te - t, 0.0);
+        }
+        if (blockIdx.x == 0) w.scal[0] = dt;
+      } else {
+        dt = w.scal[0];
+      }
+      s_dt = dt;
+    }
+    __syncthreads();
+  }
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (p >= plane) return;
+  const int i = (int)(p % g.nx), j = (int)(p / g.nx);
+  const long long px = (long long)j * (g.nx + 1) + i;
+  const long long oplx = (long long)g.ny * (g.nx + 1), oply = (long long)(g.ny + 1) * g.nx;
+  const double dt = mode == 0 ? s_dt : 0.0;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      const int fk = f * NC + k;
+      double L = -(w.FX[fk * oplx + px + 1] - w.FX[fk * oplx + px]) * g.inv_dx;
+      if (DIM == 2) L = fma(-(w.FY[fk * oply + p + g.nx] - w.FY[fk * oply + p]), g.inv_dy, L);
+      const double M = f == 0 ? S[fk * plane + p] : w.MD[((long long)(f - 1) * NC + k) * plane + p];
+      if (mode == 1) {
+        Lout[fk * plane + p] = L;
+        Mout[fk * plane + p] = M;
+      } else if (stage == 0) {
+        w.B[fk * plane + p] = M;
+        S[fk * plane + p] = fma(dt, L, M);
+      } else {
+        S[fk * plane + p] = fma(a_k, w.B[fk * plane + p], b_k * fma(dt, L, M));
+      }
+    }
+  }
+  if (mode == 0 && stage == 2 && p == 0) w.scal[1] += dt;
+}
+
+// alpha of a state only (hweno_max_wavespeed)
+template <int DIM, int SYS>
+__global__ void __launch_bounds__(kThreads) k_wavespeed(Grid g, const double* __restrict__ S, Work w, int slot) {
+  constexpr int NC = Traits<DIM, SYS>::NC;
+  const long long plane = g.plane;
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  double wsx = 0.0, wsy = 0.0;
+  if (p < plane) {
+    if (SYS == SYS_EULER) {
+      double U[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) U[k] = S[k * plane + p];
+      const double ir = rcp(U[0]);
+      const double u = U[1] * ir, v = DIM == 2 ? U[2] * ir : 0.0;
+      const double ke = DIM == 2 ? fma(U[1], u, U[2] * v) : U[1] * u;
+      const double pr = g.gm1 * fma(-0.5, ke, U[NC - 1]);
+      const double c = sqrt(g.gamma * pr * ir);
+      wsx = fabs(u) + c;
+      wsy = DIM == 2 ? fabs(v) + c : 0.0;
+      if (!(U[0] > 0.0) || !(pr > 0.0) || !isfinite(wsx) || !isfinite(wsy)) atomicOr(w.status, 1u);
+    } else if (SYS == SYS_BURGERS) {
+      wsx = fabs(S[p]);
+      wsy = DIM == 2 ? wsx : 0.0;
+    } else {
+      wsx = fabs(g.ax);
+      wsy = DIM == 2 ? fabs(g.ay) : 0.0;
+    }
+  }
+  block_max2(wsx, wsy, w.alpha + 2 * slot);
+}
+
+}  // namespace hw

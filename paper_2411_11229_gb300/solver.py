@@ -1,0 +1,140 @@
+"""Torch-backed handle around the C ABI: torch supplies device memory and the stream; every step
+of the scheme runs in libhweno.so."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _capi as C
+
+_SYSTEMS = {"advection": C.HWENO_ADVECTION, "burgers": C.HWENO_BURGERS, "euler": C.HWENO_EULER}
+_BCS = {"periodic": C.HWENO_BC_PERIODIC, "transmissive": C.HWENO_BC_TRANSMISSIVE,
+        "reflective": C.HWENO_BC_REFLECTIVE}
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+class Solver:
+    """One HWENO-I problem on one GPU.
+
+    state: float64 tensor (nfield, ncomp, ny, nx) on the device, updated in place by step().
+    The workspace is a uint8 device tensor of hweno_workspace_bytes() bytes.
+    """
+
+    def __init__(self, dim: int, system: str, nx: int, ny: int = 1, dx: float = 1.0, dy: float = None,
+                 gamma: float = 1.4, bc: str = "periodic", gamma0: float = None, d0: float = 0.9,
+                 eps: float = 1e-10, cfl: float = 0.6, ax: float = 1.0, ay: float = 1.0,
+                 device="cuda", stream: torch.cuda.Stream = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("HWENO solver needs a CUDA device")
+        self.lib = C.load()
+        self.dim, self.system = int(dim), _SYSTEMS[system] if isinstance(system, str) else int(system)
+        self.nx, self.ny = int(nx), (int(ny) if dim == 2 else 1)
+        dy = dx if dy is None else dy
+        h = ctypes.c_void_p()
+        C.check(self.lib.hweno_create(self.dim, self.system, self.nx, self.ny, float(dx), float(dy),
+                                      float(gamma), _BCS[bc] if isinstance(bc, str) else int(bc),
+                                      ctypes.byref(h)), "hweno_create")
+        self.h = h
+        if gamma0 is None:
+            gamma0 = 0.95 if dim == 1 else 0.99
+        C.check(self.lib.hweno_set_params(h, float(gamma0), float(d0), float(eps), float(cfl), float(ax),
+                                          float(ay)), "hweno_set_params")
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        C.check(self.lib.hweno_set_stream(h, ctypes.c_void_p(self.stream.cuda_stream)), "hweno_set_stream")
+        self.ncomp = (3 if dim == 1 else 4) if self.system == C.HWENO_EULER else 1
+        self.nfield = dim + 1
+        n = self.lib.hweno_state_doubles(h)
+        assert n == self.nfield * self.ncomp * self.nx * self.ny
+        self.state = torch.zeros((self.nfield, self.ncomp, self.ny, self.nx), dtype=torch.float64,
+                                 device=self.device)
+        self.workspace = torch.empty(int(self.lib.hweno_workspace_bytes(h)), dtype=torch.uint8,
+                                     device=self.device)
+        with torch.cuda.stream(self.stream):
+            C.check(self.lib.hweno_bind(h, _ptr(self.state), _ptr(self.workspace)), "hweno_bind")
+
+    # ------------------------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hweno_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, S) -> None:
+        S = torch.as_tensor(np.asarray(S) if not isinstance(S, torch.Tensor) else S, dtype=torch.float64)
+        with torch.cuda.stream(self.stream):
+            self.state.copy_(S.reshape(self.state.shape).to(self.device, non_blocking=True))
+
+    def rhs(self, S=None):
+        """(L(S), M(S)) of one stage as device tensors; S defaults to the bound state."""
+        Sd = self.state if S is None else torch.as_tensor(S, dtype=torch.float64).to(self.device).contiguous()
+        Sd = Sd.reshape(self.state.shape)
+        L = torch.empty_like(Sd)
+        M = torch.empty_like(Sd)
+        C.check(self.lib.hweno_rhs(self.h, _ptr(Sd), _ptr(L), _ptr(M)), "hweno_rhs")
+        return L, M
+
+    def step(self, dt: float = 0.0, nsteps: int = 1) -> None:
+        C.check(self.lib.hweno_steps(self.h, float(dt), int(nsteps)), "hweno_steps")
+
+    def set_time(self, t: float, t_end: float) -> None:
+        C.check(self.lib.hweno_set_time(self.h, float(t), float(t_end)), "hweno_set_time")
+
+    def last_dt(self):
+        dt, t = ctypes.c_double(), ctypes.c_double()
+        C.check(self.lib.hweno_last_dt(self.h, ctypes.byref(dt), ctypes.byref(t)), "hweno_last_dt")
+        return dt.value, t.value
+
+    def max_wavespeed(self):
+        ax, ay = ctypes.c_double(), ctypes.c_double()
+        C.check(self.lib.hweno_max_wavespeed(self.h, ctypes.byref(ax), ctypes.byref(ay)),
+                "hweno_max_wavespeed")
+        return ax.value, ay.value
+
+    def sync(self) -> None:
+        C.check(self.lib.hweno_sync(self.h), "hweno_sync")
+
+    def upload(self, host: torch.Tensor) -> None:
+        """Asynchronous host->device copy of a (pinned) CPU float64 tensor into the state."""
+        assert host.dtype == torch.float64 and host.is_contiguous() and host.numel() == self.state.numel()
+        C.check(self.lib.hweno_upload(self.h, ctypes.c_void_p(host.data_ptr())), "hweno_upload")
+
+    def download(self, host: torch.Tensor) -> None:
+        assert host.dtype == torch.float64 and host.is_contiguous() and host.numel() == self.state.numel()
+        C.check(self.lib.hweno_download(self.h, ctypes.c_void_p(host.data_ptr())), "hweno_download")
+
+    def set_profiling(self, on: bool) -> None:
+        C.check(self.lib.hweno_set_profiling(self.h, int(bool(on))), "hweno_set_profiling")
+
+    def kernel_times(self):
+        """{kind: (total ms, launches)} for kinds cell, face, update since the last query."""
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_longlong * 3)()
+        C.check(self.lib.hweno_kernel_times(self.h, ms, n), "hweno_kernel_times")
+        return {k: (ms[i], n[i]) for i, k in enumerate(("cell", "face", "update"))}
+
+    def launch_count(self) -> int:
+        return int(self.lib.hweno_launch_count(self.h))
+
+    def run(self, t_end: float, max_steps: int = 10 ** 9) -> int:
+        """CFL steps to t_end (last step clamped on the device); returns the step count."""
+        self.set_time(0.0, t_end)
+        n = 0
+        while n < max_steps:
+            self.step(0.0)
+            n += 1
+            if n % 64 == 0 or True:
+                dt, t = self.last_dt()
+                if t >= t_end or dt <= 0.0:
+                    break
+        return n

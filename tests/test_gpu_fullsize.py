@@ -1,0 +1,148 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark times.
+
+2D Euler 4096^2 (the benchmark workload): the one-stage operator checked cell by cell against the
+oracle at sampled cells (interior, edges, corners, across the discontinuities), plus properties
+of 10 CFL steps that hold at any size (conservation to round-off, the exact translation of the
+smooth wave).  2D Euler 1024^2 and 1D Euler 16384: full-field comparisons.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2411_11229_gb300 import Solver  # noqa: E402
+
+
+def _samples(nx, ny, rng, n=400):
+    pts = {(0, 0), (nx - 1, 0), (0, ny - 1), (nx - 1, ny - 1)}
+    for i in (0, 1, 2, nx // 2 - 2, nx // 2 - 1, nx // 2, nx // 2 + 1, nx - 3, nx - 2, nx - 1):
+        for j in (0, 1, ny // 2 - 1, ny // 2, ny - 2, ny - 1):
+            pts.add((i, j))
+    while len(pts) < n:
+        pts.add((int(rng.integers(0, nx)), int(rng.integers(0, ny))))
+    return np.array(sorted(j * nx + i for i, j in pts), dtype=np.int64)
+
+
+def _planes_rel(a, b, den):
+    """per-plane max |a - b| / den over samples; a, b: [ncell, field, comp]; den: [field, comp]"""
+    return (np.abs(a - b).max(axis=0) / np.maximum(den, 1e-300)).max()
+
+
+def _perturbed(S, seed):
+    sign = np.random.default_rng(seed).choice([-1.0, 1.0], S.shape)
+    return S * (1.0 + sign * 2.0 ** -52)
+
+
+@pytest.mark.parametrize("kind", ["smooth", "quadrants"])
+def test_rhs_4096_sampled(kind):
+    """One stage at 4096^2.  The state after the stage, S1 = M + dt L with the CFL dt, must match
+    within 1e-12 per plane.  L itself (a difference quotient: the derivative planes carry 1/h^2)
+    and M must match within 1e-12 or ten times the oracle's own rounding envelope at these cells
+    (the oracle against itself with a one-ulp input perturbation), whichever is larger."""
+    n = 4096
+    if kind == "smooth":
+        S, dx, dy = W.euler2d_smooth(n)
+    else:
+        S, dx, dy = W.euler2d_quadrants(n, seed=2000)
+    cfg = O.make_cfg(2, O.EULER, n, n, dx=dx, dy=dy)
+    s = Solver(2, "euler", n, n, dx=dx, dy=dy)
+    s.set_state(S)
+    L, M = s.rhs()
+    idx = _samples(n, n, np.random.default_rng(7))
+    idx_t = torch.as_tensor(idx, device=L.device)
+    Lg = L.reshape(3, 4, -1)[:, :, idx_t].permute(2, 0, 1).cpu().numpy()
+    Mg = M.reshape(3, 4, -1)[:, :, idx_t].permute(2, 0, 1).cpu().numpy()
+    Lmax = L.reshape(12, -1).abs().amax(dim=1).cpu().numpy().reshape(3, 4)
+    Mmax = M.reshape(12, -1).abs().amax(dim=1).cpu().numpy().reshape(3, 4)
+    del L, M
+    alpha = O.max_wavespeed(cfg, S)
+    ax, ay = s.max_wavespeed()
+    assert abs(ax - alpha[0]) <= 1e-15 * alpha[0] and abs(ay - alpha[1]) <= 1e-15 * alpha[1]
+    Lo, Mo = O.rhs_cells(cfg, S, idx, alpha)
+    envL, envM = 0.0, 0.0
+    for seed in (1, 2):
+        P = _perturbed(S, seed)
+        Lp, Mp = O.rhs_cells(cfg, P, idx, O.max_wavespeed(cfg, P))
+        envL = max(envL, _planes_rel(Lp, Lo, Lmax))
+        envM = max(envM, _planes_rel(Mp, Mo, Mmax))
+        del P
+    errL, errM = _planes_rel(Lg, Lo, Lmax), _planes_rel(Mg, Mo, Mmax)
+    assert errL <= max(1e-12, 10 * envL), (errL, envL)
+    assert errM <= max(1e-12, 10 * envM), (errM, envM)
+    dt = O.cfl_dt(cfg, S, 0.6)
+    S1g, S1o = Mg + dt * Lg, Mo + dt * Lo
+    assert _planes_rel(S1g, S1o, np.abs(S1o).max(axis=0)) <= 1e-12
+
+
+def test_steps_4096_properties():
+    n = 4096
+    S, dx, dy = W.euler2d_smooth(n)
+    s = Solver(2, "euler", n, n, dx=dx, dy=dy)
+    s.set_state(S)
+    tot0 = s.state[0].reshape(4, -1).sum(dim=1).cpu().numpy()
+    s.set_time(0.0, 0.0)
+    s.step(0.0, 10)
+    dt, t = s.last_dt()
+    out = s.state
+    tot1 = out[0].reshape(4, -1).sum(dim=1).cpu().numpy()
+    scale = out[0].reshape(4, -1).abs().sum(dim=1).cpu().numpy()
+    assert (np.abs(tot1 - tot0) <= 1e-12 * scale).all()
+    ex, _, _ = W.euler2d_smooth(n, t=t)
+    err = (out[0, 0] - torch.as_tensor(ex[0, 0], device=out.device)).abs().max().item()
+    assert err < 1e-10, err
+
+
+@pytest.mark.parametrize("kind", ["smooth", "quadrants"])
+def test_rhs_1024_full(kind):
+    """Full-field one-stage parity at 1024^2 with the same bars as the 4096^2 test."""
+    n = 1024
+    if kind == "smooth":
+        S, dx, dy = W.euler2d_smooth(n)
+    else:
+        S, dx, dy = W.euler2d_quadrants(n, seed=2000)
+    cfg = O.make_cfg(2, O.EULER, n, n, dx=dx, dy=dy)
+    s = Solver(2, "euler", n, n, dx=dx, dy=dy)
+    s.set_state(S)
+    L, M = s.rhs()
+    L, M = L.cpu().numpy(), M.cpu().numpy()
+    Lo, Mo = O.rhs(cfg, S)
+    Lp, Mp = O.rhs(cfg, _perturbed(S, 1))
+
+    def rel(a, b):
+        a, b = a.reshape(12, -1), b.reshape(12, -1)
+        return (np.abs(a - b).max(axis=1) / np.maximum(np.abs(b).max(axis=1), 1e-300)).max()
+
+    assert rel(L, Lo) <= max(1e-12, 10 * rel(Lp, Lo))
+    assert rel(M, Mo) <= max(1e-12, 10 * rel(Mp, Mo))
+    dt = O.cfl_dt(cfg, S, 0.6)
+    assert rel(M + dt * L, Mo + dt * Lo) <= 1e-12
+
+
+def test_euler1d_riemann_16384_full():
+    """The 1D Euler Riemann workload at its largest size, 50 CFL steps with transmissive walls."""
+    S, dx, t_stop = W.euler1d_riemann(16384, seed=1000)
+    cfg = O.make_cfg(1, O.EULER, 16384, dx=dx, bc=O.BC_TRANSMISSIVE)
+    s = Solver(1, "euler", 16384, dx=dx, bc="transmissive")
+    s.set_state(S)
+    s.set_time(0.0, 0.0)
+    s.step(0.0, 50)
+    ref, n, t = O.run(cfg, S, 0.0, 0.6, 1.0, max_steps=50)
+    out = s.state.cpu().numpy()
+
+    def rel(x, y):
+        a, b = x.reshape(6, -1), y.reshape(6, -1)
+        return (np.abs(a - b).max(axis=1) / np.abs(b).max(axis=1)).max()
+
+    # bar: 1e-10 or ten times the oracle's own drift under a one-ulp input perturbation
+    sign = np.random.default_rng(5).choice([-1.0, 1.0], S.shape)
+    pert, _, _ = O.run(cfg, S * (1.0 + sign * 2.0 ** -52), 0.0, 0.6, 1.0, max_steps=50)
+    env = rel(pert, ref)
+    err = rel(out, ref)
+    assert err <= max(1e-10, 10.0 * env), (err, env)

@@ -1,0 +1,199 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
+
+Bars (FP64): one stage (L and M of the spatial operator) within 1e-12 relative max-norm per
+plane; one SSP-RK3 step within 1e-12; 100 steps within 1e-10.  The relative max-norm of a plane
+is max|gpu - oracle| / max|oracle| over that (field, component) plane.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2411_11229_gb300 import Solver  # noqa: E402
+
+SYS = {"advection": O.ADVECTION, "burgers": O.BURGERS, "euler": O.EULER}
+BC = {"periodic": O.BC_PERIODIC, "transmissive": O.BC_TRANSMISSIVE}
+
+
+def rel_planes(a, b):
+    nf, nc = b.shape[0], b.shape[1]
+    a = a.reshape(nf * nc, -1)
+    b = b.reshape(nf * nc, -1)
+    den = np.maximum(np.abs(b).max(axis=1), 1e-300)
+    return (np.abs(a - b).max(axis=1) / den).max()
+
+
+def make_state(dim, system, nx, ny, kind, seed):
+    if system == "euler":
+        if dim == 1:
+            S, dx = W.euler1d_random(nx, seed, kind)
+            return S, dx, dx
+        return W.euler2d_random(nx, ny, seed, kind)
+    return W.scalar_random(dim, nx, ny, seed, kind)
+
+
+def pair(dim, system, nx, ny, bc, S, dx, dy, **kw):
+    cfg = O.make_cfg(dim, SYS[system], nx, ny, dx=dx, dy=dy, bc=BC[bc], ax=kw.get("ax", 1.0),
+                     ay=kw.get("ay", 1.0))
+    s = Solver(dim, system, nx, ny, dx=dx, dy=dy, bc=bc, ax=kw.get("ax", 1.0), ay=kw.get("ay", 1.0))
+    s.set_state(S)
+    return cfg, s
+
+
+CASES = [
+    (1, "advection", 37, 1, "periodic"),
+    (1, "burgers", 64, 1, "periodic"),
+    (1, "burgers", 50, 1, "transmissive"),
+    (1, "euler", 133, 1, "periodic"),
+    (1, "euler", 130, 1, "transmissive"),
+    (1, "euler", 5, 1, "periodic"),
+    (2, "advection", 29, 23, "periodic"),
+    (2, "burgers", 31, 17, "periodic"),
+    (2, "burgers", 19, 26, "transmissive"),
+    (2, "euler", 37, 29, "periodic"),
+    (2, "euler", 33, 21, "transmissive"),
+    (2, "euler", 5, 7, "periodic"),
+    (2, "euler", 130, 6, "transmissive"),
+]
+
+
+@pytest.mark.parametrize("kind", ["smooth", "jumps"])
+@pytest.mark.parametrize("dim,system,nx,ny,bc", CASES)
+def test_rhs_parity(dim, system, nx, ny, bc, kind):
+    S, dx, dy = make_state(dim, system, nx, ny, kind, seed=nx * 7 + ny)
+    cfg, s = pair(dim, system, nx, ny, bc, S, dx, dy, ax=0.8, ay=-0.6)
+    L, M = s.rhs()
+    Lo, Mo = O.rhs(cfg, S)
+    assert rel_planes(L.cpu().numpy(), Lo) <= 1e-12
+    assert rel_planes(M.cpu().numpy(), Mo) <= 1e-12
+    ax, ay = s.max_wavespeed()
+    oax, oay = O.max_wavespeed(cfg, S)
+    assert abs(ax - oax) <= 1e-14 * oax and abs(ay - oay) <= 1e-14 * max(oay, 1e-300)
+
+
+@pytest.mark.parametrize("kind", ["smooth", "jumps"])
+@pytest.mark.parametrize("dim,system,nx,ny,bc", CASES)
+def test_one_step_parity(dim, system, nx, ny, bc, kind):
+    S, dx, dy = make_state(dim, system, nx, ny, kind, seed=nx * 5 + ny)
+    cfg, s = pair(dim, system, nx, ny, bc, S, dx, dy)
+    dt = O.cfl_dt(cfg, S, 0.6)
+    s.step(dt)
+    ref = O.steps(cfg, S, dt, 1)
+    assert rel_planes(s.state.cpu().numpy(), ref) <= 1e-12
+
+
+def _long_case(case):
+    if case == "euler2d_smooth":
+        S, dx, dy = W.euler2d_smooth(40, 32)
+        return S, dx, dy, (2, "euler", 40, 32, "periodic")
+    if case == "euler1d_smooth":
+        S, dx = W.euler1d_smooth(96)
+        return S, dx, dx, (1, "euler", 96, 1, "periodic")
+    if case == "euler2d_jumps":
+        S, dx, dy = W.euler2d_random(36, 28, 9, "jumps")
+        return S, dx, dy, (2, "euler", 36, 28, "periodic")
+    if case == "euler2d_quadrants":
+        S, dx, dy = W.euler2d_quadrants(32, 32, seed=2000)
+        return S, dx, dy, (2, "euler", 32, 32, "periodic")
+    if case == "euler1d_riemann":
+        S, dx, _ = W.euler1d_riemann(256, seed=1000)
+        return S, dx, dx, (1, "euler", 256, 1, "transmissive")
+    if case == "burgers2d":
+        S, dx = W.burgers_2d(40)
+        return S, dx, dx, (2, "burgers", 40, 40, "periodic")
+    S, dx = W.advection_1d(160)
+    return S, dx, dx, (1, "advection", 160, 1, "periodic")
+
+
+def _gpu_steps(s, n):
+    s.set_time(0.0, 0.0)
+    for _ in range(n):
+        s.step(0.0)
+    return s.state.cpu().numpy()
+
+
+@pytest.mark.parametrize("case", ["euler2d_smooth", "euler1d_smooth", "burgers2d", "advection1d"])
+def test_hundred_steps_parity_smooth(case):
+    """Smooth data: 100 CFL steps (dt computed on each side from its own state) within 1e-10."""
+    S, dx, dy, (dim, system, nx, ny, bc) = _long_case(case)
+    cfg, s = pair(dim, system, nx, ny, bc, S, dx, dy)
+    out = _gpu_steps(s, 100)
+    ref, n, t = O.run(cfg, S, 0.0, 0.6, 1.0, max_steps=100)
+    assert n == 100
+    _, tg = s.last_dt()
+    assert abs(tg - t) <= 1e-12 * t
+    assert rel_planes(out, ref) <= 1e-10
+
+
+def _noise_envelope(cfg, S, ref, nsteps, seeds=3):
+    """How far the oracle itself moves after nsteps when its input is perturbed by one ulp
+    (random signs): the rounding-noise envelope of the scheme on this data."""
+    env = 0.0
+    for sd in range(seeds):
+        sign = np.random.default_rng(100 + sd).choice([-1.0, 1.0], S.shape)
+        P = S * (1.0 + sign * 2.0 ** -52)
+        out, _, _ = O.run(cfg, P, 0.0, 0.6, 1.0, max_steps=nsteps)
+        env = max(env, rel_planes(out, ref))
+    return env
+
+
+@pytest.mark.parametrize("case", ["euler2d_jumps", "euler2d_quadrants", "euler1d_riemann"])
+@pytest.mark.parametrize("nsteps", [20, 100])
+def test_long_run_parity_discontinuous(case, nsteps):
+    """Discontinuous data: the scheme amplifies rounding differences (the oracle against itself
+    with a one-ulp input perturbation drifts to 1e-9 .. 1e-2 after 100 steps), so no
+    implementation with a different rounding order can stay within a fixed 1e-10.  The bar is
+    1e-10 or ten times the oracle's own rounding-noise envelope, whichever is larger; the
+    conserved totals must agree to round-off."""
+    S, dx, dy, (dim, system, nx, ny, bc) = _long_case(case)
+    cfg, s = pair(dim, system, nx, ny, bc, S, dx, dy)
+    out = _gpu_steps(s, nsteps)
+    ref, n, _ = O.run(cfg, S, 0.0, 0.6, 1.0, max_steps=nsteps)
+    env = _noise_envelope(cfg, S, ref, nsteps)
+    err = rel_planes(out, ref)
+    assert err <= max(1e-10, 10.0 * env), (err, env)
+    if bc == "periodic":
+        for k in range(out.shape[1]):
+            tot = np.abs(ref[0, k]).sum()
+            assert abs(out[0, k].sum() - ref[0, k].sum()) <= 1e-12 * tot
+
+
+def test_run_to_end_time_clamps_last_step():
+    """Config of the 1D advection workload: N = 160 on [0, 2] to T = 2 with CFL 0.6."""
+    S, dx = W.advection_1d(160)
+    cfg, s = pair(1, "advection", 160, 1, "periodic", S, dx, dx)
+    n = s.run(2.0)
+    ref, no, t = O.run(cfg, S, 2.0, 0.6)
+    assert n == no
+    dt, tg = s.last_dt()
+    assert abs(tg - 2.0) < 1e-14
+    assert rel_planes(s.state.cpu().numpy(), ref) <= 1e-10
+    assert np.abs(s.state.cpu().numpy()[0] - S[0]).max() < 1e-4  # exact solution is the initial data
+
+
+def test_constant_state_is_steady():
+    S = np.zeros((3, 4, 16, 16))
+    S[0, 0], S[0, 1], S[0, 2], S[0, 3] = 1.0, 0.3, -0.2, 2.5
+    s = Solver(2, "euler", 16, 16, dx=0.1, dy=0.1)
+    s.set_state(S)
+    L, M = s.rhs()
+    assert np.abs(L.cpu().numpy()).max() < 1e-13
+    assert np.abs(M.cpu().numpy() - S).max() < 1e-15
+
+
+def test_nonphysical_state_reported():
+    S, dx, dy = W.euler2d_random(16, 16, 3, "smooth")
+    S[0, 0, 5, 5] = -1.0  # negative density
+    s = Solver(2, "euler", 16, 16, dx=dx, dy=dy)
+    s.set_state(S)
+    from paper_2411_11229_gb300._capi import HwenoError, HWENO_ENONPHYS
+    with pytest.raises(HwenoError) as ei:
+        s.max_wavespeed()
+    assert ei.value.code == HWENO_ENONPHYS

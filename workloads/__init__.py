@@ -380,3 +380,39 @@ def euler2d_adjoint_init(n: int, seed: int = 4000, gamma: float = 1.4):
     S = np.zeros((3, 4, n, n))
     S[0], S[1], S[2] = U, V, W
     return S, 2.0 / n, 2.0 / n
+
+
+def scalar_random(dim: int, nx: int, ny: int, seed: int, kind: str = "smooth"):
+    """Seeded scalar test states on [0, 2] (x [0, 2]): 'smooth' = a few random Fourier modes with
+    exact derivatives; 'jumps' = random piecewise-constant blocks with random derivative noise."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ny = ny if dim == 2 else 1
+    x = centres(nx, 0.0, 2.0)[None, :]
+    y = centres(ny, 0.0, 2.0)[:, None] if dim == 2 else np.zeros((1, 1))
+    nf = dim + 1
+    S = np.zeros((nf, 1, ny, nx))
+    if kind == "smooth":
+        f = np.full((ny, nx), 0.5)
+        fx = np.zeros((ny, nx))
+        fy = np.zeros((ny, nx))
+        for _ in range(3):
+            kx = rng.integers(-3, 4)
+            ky = rng.integers(-3, 4) if dim == 2 else 0
+            ph0 = rng.uniform(0, 2 * np.pi)
+            a = rng.uniform(0.2, 0.5)
+            arg = np.pi * (kx * x + ky * y) + ph0
+            f = f + a * np.sin(arg)
+            fx = fx + a * np.pi * kx * np.cos(arg)
+            fy = fy + a * np.pi * ky * np.cos(arg)
+        S[0, 0], S[1, 0] = f, fx
+        if dim == 2:
+            S[2, 0] = fy
+    else:
+        nb = int(rng.integers(3, 8))
+        ix = np.minimum((x / 2.0 * nb).astype(int), nb - 1)
+        iy = np.minimum((y / 2.0 * nb).astype(int), nb - 1) if dim == 2 else 0
+        blk = np.broadcast_to(iy * nb + ix, (ny, nx))
+        S[0, 0] = rng.uniform(-1.0, 2.0, nb * nb)[blk]
+        for f in range(1, nf):
+            S[f, 0] = rng.normal(0.0, 1.0, (ny, nx))
+    return S, 2.0 / nx, 2.0 / ny
