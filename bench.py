@@ -34,7 +34,7 @@ UNIT = "Mcell-updates/s"
 FP64_PEAK_FLOPS = 152 * 2.07e9 * 4
 HBM_PEAK_GBS_FALLBACK = 6800.0
 # DRAM bytes per launch of the 2D Euler face kernel at 4096^2 from ncu (profiles/), per face.
-FACE_TRAFFIC_BYTES_PER_FACE = 285.2  # 2048^2 capture, profiles/k_face_euler2d_2048_full.md
+FACE_TRAFFIC_BYTES_PER_FACE = 285.0  # 2048^2 capture of the current kernel, profiles/k_face_euler2d_2048_full.md
 
 
 def _dist():

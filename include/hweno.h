@@ -139,6 +139,11 @@ const char *hweno_strerror(int status);
 /* Number of kernel launches issued by this handle since creation (for accounting). */
 long long hweno_launch_count(const hweno_t *h);
 
+/* Self-test of the library's FP64 reciprocal (the hardware approximation refined by two
+ * Newton-Raphson steps; used for every normalisation of the nonlinear weights and every 1/rho):
+ * r_dev[i] = 1/x_dev[i] for i < n, launched on `stream`.  Device arrays; EINVAL on NULL/n < 0. */
+int hweno_selftest_rcp(const double *x_dev, double *r_dev, int64_t n, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

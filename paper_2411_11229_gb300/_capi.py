@@ -37,6 +37,7 @@ SIGNATURES = {
     "hweno_download": (_I, [_H, _P]),
     "hweno_set_profiling": (_I, [_H, _I]),
     "hweno_kernel_times": (_I, [_H, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)]),
+    "hweno_selftest_rcp": (_I, [_P, _P, ctypes.c_int64, _P]),
     "hweno_destroy": (None, [_H]),
     "hweno_strerror": (ctypes.c_char_p, [_I]),
     "hweno_launch_count": (ctypes.c_longlong, [_H]),

@@ -10,6 +10,14 @@
 #include "../../include/hweno.h"
 #include "hweno_kernels.cuh"
 
+namespace hw {
+// applies the library's FP64 reciprocal to n values (accuracy self-test)
+__global__ void k_rcp_check(const double* __restrict__ x, double* __restrict__ r, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = rcp(x[i]);
+}
+}  // namespace hw
+
 namespace {
 
 using hw::Grid;
@@ -121,6 +129,29 @@ Grid grid_of(const hweno_ctx* h) {
   g.d1 = 0.5 * (1.0 - h->d0);
   g.eps = h->eps;
   g.cfl = h->cfl;
+  // folded constants (see hw::Grid)
+  const double g1 = g.g1;
+  const double cr[5] = {(-0.125 + 0.5 * g1) / g1, (0.5625 - 2.0 * g1) / g1, (0.5625 - 0.5 * g1) / g1,
+                        -0.046875 / g1, -0.140625 / g1};
+  const double cl[5] = {(0.5625 - 0.5 * g1) / g1, (0.5625 - 2.0 * g1) / g1, (-0.125 + 0.5 * g1) / g1,
+                        0.140625 / g1, 0.046875 / g1};
+  for (int k = 0; k < 5; ++k) {
+    g.cr[k] = cr[k];
+    g.cl[k] = cl[k];
+  }
+  g.G = g.g0 / g1;
+  g.cdu = (0.75 - g.d1) / g.d1;
+  g.csv = 0.25 / g.d1;
+  g.Gd = g.d0 / g.d1;
+  const double hs[2] = {h->dx, h->dy};
+  for (int d = 0; d < 2; ++d) {
+    g.h[d] = hs[d];
+    g.ih[d] = 1.0 / hs[d];
+    g.chh[d] = hw::DCoef::ch * hs[d];
+    g.efih[d] = hw::DCoef::ef / hs[d];
+    g.egih[d] = hw::DCoef::eg / hs[d];
+    g.hih[d] = 0.5 / hs[d];
+  }
   return g;
 }
 
@@ -413,5 +444,12 @@ const char* hweno_strerror(int s) {
 }
 
 long long hweno_launch_count(const hweno_t* h) { return h ? h->launches : -1; }
+
+int hweno_selftest_rcp(const double* x_dev, double* r_dev, int64_t n, void* stream) {
+  if (!x_dev || !r_dev || n < 0) return HWENO_EINVAL;
+  if (n == 0) return HWENO_OK;
+  hw::k_rcp_check<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(x_dev, r_dev, n);
+  return cuda_status();
+}
 
 }  // extern "C"

@@ -77,8 +77,8 @@ __device__ __forceinline__ void block_max2(double a, double b, unsigned long lon
 // (D = derivative along the sweep; only i-1 and i+1 enter).  e: eigenvectors of the cell.
 template <int NC, int SYS>
 __device__ __forceinline__ void modified_derivative(const double (&U3)[3][NC], const double (&D3)[3][NC],
-                                                    const Eig<NC>& e, double h, double inv_h, const Grid& g,
-                                                    double* out) {
+                                                    const Eig<NC>& e, int dir, const Grid& g, double* out) {
+  const double h = g.h[dir], ih = g.ih[dir];
   double W[3][NC], Zm[NC], Zp[NC];
   double hDm[NC], hDp[NC];
 #pragma unroll
@@ -99,18 +99,11 @@ __device__ __forceinline__ void modified_derivative(const double (&U3)[3][NC], c
   }
   double ht[NC];
 #pragma unroll
-  for (int s = 0; s < NC; ++s) {
-    const Beta b = indicators(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s]);
-    const Wts w = weights(b, g.eps);
-    ht[s] = limiter(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], w, g.d0, g.d1);
-  }
+  for (int s = 0; s < NC; ++s) ht[s] = cell_field(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], g) * ih;
   if (SYS == SYS_EULER) {
-    double hv[NC];
-    e.back(ht, hv);
-#pragma unroll
-    for (int k = 0; k < NC; ++k) out[k] = hv[k] * inv_h;
+    e.back(ht, out);
   } else {
-    out[0] = ht[0] * inv_h;
+    out[0] = ht[0];
   }
 }
 
@@ -131,7 +124,7 @@ __global__ void __launch_bounds__(kThreads) k_cell(Grid g, const double* __restr
       if (DIM == 2) Wd[k] = S[(2 * NC + k) * plane + p];
     }
     // primitives and wavespeeds
-    double u = 0, v = 0, pr = 0, ir = 0, H = 0, c = 0;
+    double u = 0, v = 0, pr = 0, ir = 0, H = 0, c = 0, ic = 0;
     if (SYS == SYS_EULER) {
       ir = rcp(U[0]);
       u = U[1] * ir;
@@ -139,7 +132,9 @@ __global__ void __launch_bounds__(kThreads) k_cell(Grid g, const double* __restr
       const double ke = DIM == 2 ? fma(U[1], u, U[2] * v) : U[1] * u;
       pr = g.gm1 * fma(-0.5, ke, U[NC - 1]);
       H = (U[NC - 1] + pr) * ir;
-      c = sqrt(g.gamma * pr * ir);
+      const double c2 = g.gamma * pr * ir;
+      ic = rsqrt(c2);
+      c = c2 * ic;
       wsx = fabs(u) + c;
       wsy = DIM == 2 ? fabs(v) + c : 0.0;
       if (!(U[0] > 0.0) || !(pr > 0.0) || !isfinite(wsx) || !isfinite(wsy)) atomicOr(w.status, 1u);
@@ -222,10 +217,9 @@ __global__ void __launch_bounds__(kThreads) k_cell(Grid g, const double* __restr
         }
       }
       Eig<NC> e;
-      if (SYS == SYS_EULER) e.setup(d == 0 ? u : v, d == 0 ? v : u, H, c, rcp(c), g.gm1);
+      if (SYS == SYS_EULER) e.setup(d == 0 ? u : v, d == 0 ? v : u, H, c, ic, g.gm1);
       double out[NC];
-      const double h = d == 0 ? g.dx : g.dy, ih = d == 0 ? g.inv_dx : g.inv_dy;
-      modified_derivative<NC, SYS>(U3, D3, e, h, ih, g, out);
+      modified_derivative<NC, SYS>(U3, D3, e, d, g, out);
       if (SYS == SYS_EULER && d == 1) swap_frame<NC>(out);
 #pragma unroll
       for (int k = 0; k < NC; ++k) w.MD[((long long)d * NC + k) * plane + p] = out[k];
@@ -261,7 +255,7 @@ __global__ void __launch_bounds__(kThreads) k_face(Grid g, const double* __restr
     pc[q] = dir == 0 ? (long long)line * g.nx + a : (long long)a * g.nx + line;
   }
   const int fown = dir == 0 ? 1 : 2, foth = dir == 0 ? 2 : 1;
-  const double h = dir == 0 ? g.dx : g.dy, ih = dir == 0 ? g.inv_dx : g.inv_dy;
+  const double h = g.h[dir];
   double Uq[4][NC], Zq[4][NC];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -312,35 +306,21 @@ __global__ void __launch_bounds__(kThreads) k_face(Grid g, const double* __restr
   // u^+ from the stencil of cell fa (mirror image)
   double cm[NC], chm[NC], cp[NC], chp[NC];
 #pragma unroll
-  for (int s = 0; s < NC; ++s) {
-    {
-      const Beta b = indicators(Wq[0][s], Wq[1][s], Wq[2][s], Yq[0][s], Yq[2][s]);
-      const Wts wt = weights(b, g.eps);
-      right_face(Wq[0][s], Wq[1][s], Wq[2][s], Yq[0][s], Yq[2][s], wt, g.g0, g.g1, cm[s], chm[s]);
-    }
-    {
-      const Beta b = indicators(Wq[1][s], Wq[2][s], Wq[3][s], Yq[1][s], Yq[3][s]);
-      const Wts wt = weights(b, g.eps);
-      left_face(Wq[1][s], Wq[2][s], Wq[3][s], Yq[1][s], Yq[3][s], wt, g.g0, g.g1, cp[s], chp[s]);
-    }
-  }
+  for (int s = 0; s < NC; ++s)
+    face_field(Wq[0][s], Wq[1][s], Wq[2][s], Wq[3][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, cm[s], chm[s],
+               cp[s], chp[s]);
+  // back to conserved variables; the derivatives stay scaled by h
   double Um[NC], Up[NC], Dm[NC], Dp[NC];
   if (SYS == SYS_EULER) {
-    double hDm[NC], hDp[NC];
     e.back(cm, Um);
     e.back(cp, Up);
-    e.back(chm, hDm);
-    e.back(chp, hDp);
-#pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      Dm[k] = hDm[k] * ih;
-      Dp[k] = hDp[k] * ih;
-    }
+    e.back(chm, Dm);
+    e.back(chp, Dp);
   } else {
     Um[0] = cm[0];
     Up[0] = cp[0];
-    Dm[0] = chm[0] * ih;
-    Dp[0] = chp[0] * ih;
+    Dm[0] = chm[0];
+    Dp[0] = chp[0];
   }
   // Lax-Friedrichs fluxes at the interpolated states (Eq. flux-LF)
   const double a_adv = dir == 0 ? g.ax : g.ay;
@@ -361,10 +341,11 @@ __global__ void __launch_bounds__(kThreads) k_face(Grid g, const double* __restr
     const double f2 = nod[k * plane + pc[2]], f3 = nod[k * plane + pc[3]];
     const double h0 = nod[(NC + k) * plane + pc[0]], h3 = nod[(NC + k) * plane + pc[3]];
     // D-terms (Eqs. Cd-1, DfDh)
-    const double Df = fma(DCoef::cf, (f0 - f1) + (f3 - f2), DCoef::ch * h * (h0 - h3));
-    const double Dh = fma(ih, fma(DCoef::ef, f0 - f3, DCoef::eg * (f2 - f1)), DCoef::eh * (h0 + h3));
+    const double Df = fma(DCoef::cf, (f0 - f1) + (f3 - f2), g.chh[dir] * (h0 - h3));
+    const double Dh = fma(g.efih[dir], f0 - f3, fma(g.egih[dir], f2 - f1, DCoef::eh * (h0 + h3)));
     fh[k] = fma(0.5, fma(-alpha, Up[k] - Um[k], FUm[k] + FUp[k]), Df);
-    hh[k] = fma(0.5, fma(-alpha, Dp[k] - Dm[k], HDm[k] + HDp[k]), Dh);
+    // Dm, Dp and the Jacobian products carry the factor h: 1/(2h) restores both
+    hh[k] = fma(g.hih[dir], fma(-alpha, Dp[k] - Dm[k], HDm[k] + HDp[k]), Dh);
     if (DIM == 2) {
       const double o0 = nod[(2 * NC + k) * plane + pc[0]], o1 = nod[(2 * NC + k) * plane + pc[1]];
       const double o2 = nod[(2 * NC + k) * plane + pc[2]], o3 = nod[(2 * NC + k) * plane + pc[3]];

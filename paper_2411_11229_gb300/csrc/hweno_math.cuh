@@ -37,88 +37,118 @@ struct Grid {
   double d0, d1;    // limiter weights d0, d1 = d2 (Eq. limiter)
   double eps;       // epsilon of Eq. (nonlinear)
   double cfl;
+  // Folded constants (computed on the host from the linear weights and the spacings):
+  //   cr, cl: coefficients of (p0 - gamma1 (p1 + p2)) / gamma1 on (um, u0, up, hvm, hvp) at the
+  //           right face x_{i+1/2} and, mirrored, at the left face x_{i-1/2};
+  //   G = gamma0 / gamma1;  limiter: cdu = (3/4 - d1)/d1, csv = (1/4)/d1, Gd = d0 / d1;
+  //   per direction: h, 1/h, ch*h, ef/h, eg/h (D-terms), 1/(2h).
+  double cr[5], cl[5], G;
+  double cdu, csv, Gd;
+  double h[2], ih[2], chh[2], efih[2], egih[2], hih[2];
 };
 
-__device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+// 1/x for normal, finite x: the hardware approximation (rcp.approx.ftz.f64) refined by two
+// Newton-Raphson steps r <- r + r (1 - x r), each of which squares the relative error.
+__device__ __forceinline__ double rcp(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
 __device__ __forceinline__ double sqr(double x) { return x * x; }
 
 // ---------------------------------------------------------------------------------------------
-// Smoothness indicators (Eq. GHYZ, explicit forms) of the stencil {i-1, i, i+1} with values
-// um, u0, up and scaled derivatives hvm = h v_{i-1}, hvp = h v_{i+1}.  beta0 is the paper's sum of
-// four weighted squares, with a1..a4 regrouped as below.
-struct Beta {
-  double b0, b1, b2;
-};
-
-__device__ __forceinline__ Beta indicators(double um, double u0, double up, double hvm, double hvp) {
-  const double sv = hvm + hvp, dv = hvm - hvp, du = up - um;
-  const double d2 = fma(-2.0, u0, um + up);
-  // a1 + a3/4 = -3/16 sv + 11/16 du;  a2 + 63/130 a4 = 67/520 dv + 197/260 d2;
-  // a3 = (sv - du)/4;  a4 = -(dv/4 + d2/2)
+// Smoothness indicators (Eq. GHYZ, explicit forms) of the stencil {i-1, i, i+1} from the cell
+// differences dm = u_i - u_{i-1}, dp = u_{i+1} - u_i and the scaled derivatives hvm = h v_{i-1},
+// hvp = h v_{i+1}:  with du = dm + dp, d2 = dp - dm, sv = hvm + hvp, dv = hvm - hvp,
+//   a1 + a3/4 = -3/16 sv + 11/16 du,  a2 + 63/130 a4 = 67/520 dv + 197/260 d2,
+//   a3 = (sv - du)/4,  a4 = -(dv + 2 d2)/4,
+// beta0 = (a1 + a3/4)^2 + 13/3 (a2 + 63/130 a4)^2 + 781/20 a3^2 + 1421461/2275 a4^2,
+// beta1 = dm^2, beta2 = dp^2 (passed in: neighbouring stencils share them).
+__device__ __forceinline__ double beta0(double dm, double dp, double hvm, double hvp, double& du_out,
+                                        double& sv_out) {
+  const double du = dm + dp, d2 = dp - dm;
+  const double sv = hvm + hvp, dv = hvm - hvp;
   const double A = fma(-0.1875, sv, 0.6875 * du);
   const double B = fma(67.0 / 520.0, dv, (197.0 / 260.0) * d2);
-  const double C = 0.25 * (sv - du);
-  const double D = fma(0.25, dv, 0.5 * d2);
-  Beta b;
-  b.b0 = fma((1421461.0 / 2275.0) * D, D, fma((781.0 / 20.0) * C, C, fma((13.0 / 3.0) * B, B, A * A)));
-  b.b1 = sqr(u0 - um);
-  b.b2 = sqr(u0 - up);
-  return b;
+  const double C = sv - du;
+  const double D = fma(2.0, d2, dv);
+  du_out = du;
+  sv_out = sv;
+  return fma((1421461.0 / 2275.0 / 16.0) * D, D, fma((781.0 / 20.0 / 16.0) * C, C, fma((13.0 / 3.0) * B, B, A * A)));
 }
 
-// Un-normalised nonlinear weights of Eq. (nonlinear) over the common denominator b0 b1 b2:
-// omega_l is proportional to lin_l * W_l with W_l = (b_l + tau) * prod_{k != l} b_k, b = beta + eps.
+// Nonlinear weights of Eq. (nonlinear) up to a common factor: with e_l = beta_l + eps,
+// omega_l is proportional to lin_l (1 + tau/e_l), i.e. to lin_l W_l with
+// W_l = e0 e1 e2 + tau * prod_{k != l} e_k.  One reciprocal normalises them later.
 struct Wts {
   double W0, W1, W2;
 };
 
-__device__ __forceinline__ Wts weights(const Beta& b, double eps) {
-  const double tau_s = fabs(b.b0 - b.b1) + fabs(b.b0 - b.b2);
-  const double tau = 0.25 * (tau_s * tau_s);
-  const double e0 = b.b0 + eps, e1 = b.b1 + eps, e2 = b.b2 + eps;
+__device__ __forceinline__ Wts weights(double b0, double b1, double b2, double e1, double e2, double eps) {
+  const double ts = fabs(b0 - b1) + fabs(b0 - b2);
+  const double tau = (0.25 * ts) * ts;
+  const double e0 = b0 + eps;
+  const double Q0 = e1 * e2, Q1 = e0 * e2, Q2 = e0 * e1;
+  const double P = Q0 * e0;
   Wts w;
-  w.W0 = (e0 + tau) * (e1 * e2);
-  w.W1 = (e1 + tau) * (e0 * e2);
-  w.W2 = (e2 + tau) * (e0 * e1);
+  w.W0 = fma(tau, Q0, P);
+  w.W1 = fma(tau, Q1, P);
+  w.W2 = fma(tau, Q2, P);
   return w;
 }
 
-// u^-_{i+1/2} (Eqs. Pxi, interp) and h v^-_{i+1/2} = h p0'(x_{i+1/2}) (Eq. P'xi).
-__device__ __forceinline__ void right_face(double um, double u0, double up, double hvm, double hvp, const Wts& w,
-                                           double g0, double g1, double& u_out, double& hv_out) {
-  const double p0 = fma(-0.125, um, fma(0.5625, u0 + up, fma(-0.046875, hvm, -0.140625 * hvp)));
-  const double p1 = fma(-0.5, um, 1.5 * u0);
-  const double p2 = 0.5 * (u0 + up);
-  const double r = fma(-g1, p1 + p2, p0);
-  const double num = fma(w.W0, r, g1 * fma(w.W1, p1, w.W2 * p2));
-  const double den = fma(g0, w.W0, g1 * (w.W1 + w.W2));
-  u_out = num * rcp(den);
-  hv_out = fma(0.1875, um, fma(-1.5, u0, fma(1.3125, up, fma(0.0625, hvm, -0.1875 * hvp))));
+// One characteristic field at one face k+1/2 from the four cells k-1..k+2 (values w0..w3,
+// scaled derivatives y0..y3):  u^- and h v^- from the stencil of cell k (Eqs. Pxi, P'xi,
+// interp), u^+ and h v^+ from the stencil of cell k+1 evaluated at its left face (the mirror
+// image about x_{k+1}).  gamma1 = gamma2; both weight sets normalise with one reciprocal each.
+__device__ __forceinline__ void face_field(double w0, double w1, double w2, double w3, double y0, double y1,
+                                           double y2, double y3, const Grid& g, double& um, double& hvm,
+                                           double& up, double& hvp) {
+  const double d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2;
+  const double b01 = d01 * d01, b12 = d12 * d12, b23 = d23 * d23;
+  const double e01 = b01 + g.eps, e12 = b12 + g.eps, e23 = b23 + g.eps;
+  const double pmid = 0.5 * (w1 + w2);  // linear candidate on {k, k+1}, shared by both stencils
+  double du, sv;
+  {
+    // stencil of cell k: u_{i-1..i+1} = w0, w1, w2
+    const double b0 = beta0(d01, d12, y0, y2, du, sv);
+    const Wts wt = weights(b0, b01, b12, e01, e12, g.eps);
+    const double r = fma(g.cr[0], w0, fma(g.cr[1], w1, fma(g.cr[2], w2, fma(g.cr[3], y0, g.cr[4] * y2))));
+    const double p1 = fma(-0.5, w0, 1.5 * w1);
+    const double num = fma(wt.W0, r, fma(wt.W1, p1, wt.W2 * pmid));
+    const double den = fma(g.G, wt.W0, wt.W1 + wt.W2);
+    um = num * rcp(den);
+    hvm = fma(0.1875, w0, fma(-1.5, w1, fma(1.3125, w2, fma(0.0625, y0, -0.1875 * y2))));
+  }
+  {
+    // stencil of cell k+1: u_{i-1..i+1} = w1, w2, w3; its candidate on {i, i+1} carries beta2,
+    // the one on {i-1, i} (pmid) carries beta1 (mirror image)
+    const double b0 = beta0(d12, d23, y1, y3, du, sv);
+    const Wts wt = weights(b0, b12, b23, e12, e23, g.eps);
+    const double r = fma(g.cl[0], w1, fma(g.cl[1], w2, fma(g.cl[2], w3, fma(g.cl[3], y1, g.cl[4] * y3))));
+    const double q1 = fma(-0.5, w3, 1.5 * w2);
+    const double num = fma(wt.W0, r, fma(wt.W2, q1, wt.W1 * pmid));
+    const double den = fma(g.G, wt.W0, wt.W1 + wt.W2);
+    up = num * rcp(den);
+    hvp = fma(-1.3125, w1, fma(1.5, w2, fma(-0.1875, w3, fma(-0.1875, y1, 0.0625 * y3))));
+  }
 }
 
-// u^+_{i-1/2} and h v^+_{i-1/2}: the mirror image about x_i.  The linear candidate on {i, i+1}
-// carries beta2 (W2) and the one on {i-1, i} carries beta1 (W1); gamma1 = gamma2.
-__device__ __forceinline__ void left_face(double um, double u0, double up, double hvm, double hvp, const Wts& w,
-                                          double g0, double g1, double& u_out, double& hv_out) {
-  const double q0 = fma(0.5625, um + u0, fma(-0.125, up, fma(0.140625, hvm, 0.046875 * hvp)));
-  const double q1 = fma(-0.5, up, 1.5 * u0);  // linear on {i, i+1}
-  const double q2 = 0.5 * (um + u0);          // linear on {i-1, i}
-  const double r = fma(-g1, q1 + q2, q0);
-  const double num = fma(w.W0, r, g1 * fma(w.W2, q1, w.W1 * q2));
-  const double den = fma(g0, w.W0, g1 * (w.W1 + w.W2));
-  u_out = num * rcp(den);
-  hv_out = fma(-1.3125, um, fma(1.5, u0, fma(-0.1875, up, fma(-0.1875, hvm, 0.0625 * hvp))));
-}
-
-// h v~_i (Eq. limiter with the derivatives of Eq. limiter-p) from the same W and the limiter's
-// linear weights d0, d1 = d2.
-__device__ __forceinline__ double limiter(double um, double u0, double up, double hvm, double hvp, const Wts& w,
-                                          double d0, double d1) {
-  const double du = up - um;
-  const double hp0 = fma(0.75, du, -0.25 * (hvm + hvp));
-  const double hp1 = u0 - um, hp2 = up - u0;
-  const double num = fma(w.W0, fma(-d1, du, hp0), d1 * fma(w.W1, hp1, w.W2 * hp2));
-  const double den = fma(d0, w.W0, d1 * (w.W1 + w.W2));
+// h v~_i of one characteristic field (Eq. limiter with the derivatives of Eq. limiter-p) from
+// w0..w2 = u_{i-1..i+1} and y0, y2 = h v_{i-1}, h v_{i+1}.
+__device__ __forceinline__ double cell_field(double w0, double w1, double w2, double y0, double y2, const Grid& g) {
+  const double d01 = w1 - w0, d12 = w2 - w1;
+  const double b1 = d01 * d01, b2 = d12 * d12;
+  double du, sv;
+  const double b0 = beta0(d01, d12, y0, y2, du, sv);
+  const Wts wt = weights(b0, b1, b2, b1 + g.eps, b2 + g.eps, g.eps);
+  // (h p0'(x_i) - d1 (h p1' + h p2')) / d1 = cdu du - csv sv;  h p1' = d01, h p2' = d12
+  const double t = fma(g.cdu, du, -g.csv * sv);
+  const double num = fma(wt.W0, t, fma(wt.W1, d01, wt.W2 * d12));
+  const double den = fma(g.Gd, wt.W0, wt.W1 + wt.W2);
   return num * rcp(den);
 }
 

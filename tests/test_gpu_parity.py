@@ -197,3 +197,21 @@ def test_nonphysical_state_reported():
     with pytest.raises(HwenoError) as ei:
         s.max_wavespeed()
     assert ei.value.code == HWENO_ENONPHYS
+
+
+def test_reciprocal_accuracy():
+    """The library's reciprocal (hardware approximation + two Newton-Raphson steps) against the
+    correctly rounded 1/x: at most one unit in the last place over twenty decades."""
+    import ctypes
+    from paper_2411_11229_gb300 import _capi as C
+    rng = np.random.default_rng(17)
+    x = (rng.uniform(1.0, 2.0, 200000) * 10.0 ** rng.integers(-30, 30, 200000)) * rng.choice([-1, 1], 200000)
+    xd = torch.as_tensor(x, device="cuda")
+    rd = torch.empty_like(xd)
+    C.check(C.load().hweno_selftest_rcp(ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(rd.data_ptr()),
+                                        x.size, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+            "hweno_selftest_rcp")
+    r = rd.cpu().numpy()
+    exact = 1.0 / x
+    ulps = np.abs(r - exact) / np.spacing(np.abs(exact))
+    assert ulps.max() <= 1.0, ulps.max()
