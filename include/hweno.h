@@ -54,7 +54,8 @@ enum {
   HWENO_ECUDA = -2,    /* a CUDA runtime error */
   HWENO_ENOMEM = -3,   /* workspace too small / host allocation failed */
   HWENO_ENONPHYS = -4, /* rho <= 0, P <= 0 or non-finite wavespeed met on the device */
-  HWENO_ESTATE = -5    /* call out of order (e.g. no state bound) */
+  HWENO_ESTATE = -5,   /* call out of order (e.g. no state bound) */
+  HWENO_ETOOBIG = -6   /* grid larger than the fixed scratch of hweno_rhs_static */
 };
 
 /* Create a solver for a uniform grid of nx (x ny) cells with spacing dx (dy).
@@ -138,6 +139,30 @@ const char *hweno_strerror(int status);
 
 /* Number of kernel launches issued by this handle since creation (for accounting). */
 long long hweno_launch_count(const hweno_t *h);
+
+/* hweno_rhs without any allocation.  The paper has no counterpart: this is a convenience for
+ * callers that cannot allocate device memory for a workspace, such as host programs whose own
+ * framework or memory pool owns every device allocation and passes a library nothing but the
+ * input and output buffers, or latency-sensitive loops that cannot afford a cudaMalloc (which can
+ * synchronise the whole device).  It evaluates exactly what hweno_rhs evaluates (L(S) and
+ * M(S) = (U, V~, W~) with alpha taken from S), with the same kernels, launched on `stream`.
+ *   Arguments: the grid as in hweno_create (dim, system, nx, ny, dx, dy, gamma, bc; reflective is
+ *   EINVAL); params5 = {gamma0, d0, eps, adv_ax, adv_ay} or NULL for the defaults of
+ *   hweno_create; S, L, M: caller-owned device arrays of nfield*ncomp*ny*nx doubles in the state
+ *   layout, S not aliasing L or M.
+ *   Scratch: a fixed 16 MiB device array inside the library, present on every GPU that loads it
+ *   until the process exits.  The grid must fit: about 480 bytes per cell for 2D Euler (roughly
+ *   34 000 cells, e.g. 180 x 180) and 144 bytes per cell for 1D Euler; larger grids return
+ *   HWENO_ETOOBIG before any device work.
+ *   It calls no cudaMalloc, cudaFree or other allocating routine.  The first call on a device looks
+ *   up the array's device address (cudaGetSymbolAddress) with that device current; make that first
+ *   call before any stream capture.  All calls share the one array, which keeps the previous call's
+ *   contents (the wavespeed slot and status word are cleared on the stream at every call), so calls
+ *   whose work overlaps on the GPU (other streams, other host threads) race and must be
+ *   serialised by the caller.  Device-side failures are reported by later synchronising calls only
+ *   through the CUDA error state; use hweno_rhs with a handle to read the status word. */
+int hweno_rhs_static(int dim, int system, int64_t nx, int64_t ny, double dx, double dy, double gamma, int bc,
+                     const double *params5, const double *S_dev, double *L_dev, double *M_dev, void *stream);
 
 /* Self-test of the library's FP64 reciprocal (the hardware approximation refined by two
  * Newton-Raphson steps; used for every normalisation of the nonlinear weights and every 1/rho):

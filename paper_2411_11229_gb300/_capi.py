@@ -13,6 +13,7 @@ from . import _make as _build
 HWENO_ADVECTION, HWENO_BURGERS, HWENO_EULER = 0, 1, 2
 HWENO_BC_PERIODIC, HWENO_BC_TRANSMISSIVE, HWENO_BC_REFLECTIVE = 0, 1, 2
 HWENO_OK, HWENO_EINVAL, HWENO_ECUDA, HWENO_ENOMEM, HWENO_ENONPHYS, HWENO_ESTATE = 0, -1, -2, -3, -4, -5
+HWENO_ETOOBIG = -6
 
 # every entry point declared in include/hweno.h: name -> (restype, argtypes)
 _D = ctypes.c_double
@@ -38,6 +39,7 @@ SIGNATURES = {
     "hweno_set_profiling": (_I, [_H, _I]),
     "hweno_kernel_times": (_I, [_H, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)]),
     "hweno_selftest_rcp": (_I, [_P, _P, ctypes.c_int64, _P]),
+    "hweno_rhs_static": (_I, [_I, _I, ctypes.c_int64, ctypes.c_int64, _D, _D, _D, _I, _P, _P, _P, _P, _P]),
     "hweno_destroy": (None, [_H]),
     "hweno_strerror": (ctypes.c_char_p, [_I]),
     "hweno_launch_count": (ctypes.c_longlong, [_H]),

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -439,6 +440,7 @@ const char* hweno_strerror(int s) {
     case HWENO_ENOMEM: return "out of memory or workspace too small";
     case HWENO_ENONPHYS: return "non-physical state (rho <= 0, P <= 0 or non-finite wavespeed)";
     case HWENO_ESTATE: return "call out of order (no state or workspace bound)";
+    case HWENO_ETOOBIG: return "grid too large for the fixed device scratch of hweno_rhs_static (16 MiB)";
     default: return "unknown status";
   }
 }
@@ -453,3 +455,115 @@ int hweno_selftest_rcp(const double* x_dev, double* r_dev, int64_t n, void* stre
 }
 
 }  // extern "C"
+
+// =============================================================================================
+// hweno_rhs_static: the spatial operator without any allocation.
+//
+// Some callers cannot allocate device memory for a workspace: host programs that hand a library
+// only the input and output buffers because a framework or memory pool of their own owns every
+// device allocation, and latency-sensitive loops in which a cudaMalloc (which can synchronise the
+// whole device) is not acceptable.  For them this entry point runs the same three kernels as
+// hweno_rhs but takes its scratch (modified derivatives, nodal values, primitives, face fluxes,
+// wavespeed slot and status word) from the fixed array below, which every GPU that loads this
+// library holds until the process exits.
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB per device
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// device address of g_static_scratch, looked up once per device (host code cannot use the
+// symbol itself: on the host it names a stand-in, not device memory)
+std::atomic<void*> g_static_scratch_dev[kMaxDevices];
+
+int static_scratch(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HWENO_ECUDA;
+  if (dev < 0 || dev >= kMaxDevices) return HWENO_ECUDA;
+  void* p = g_static_scratch_dev[dev].load(std::memory_order_acquire);
+  if (!p) {
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return HWENO_ECUDA;
+    g_static_scratch_dev[dev].store(p, std::memory_order_release);
+  }
+  *out = p;
+  return HWENO_OK;
+}
+
+}  // namespace
+
+extern "C" int hweno_rhs_static(int dim, int system, int64_t nx, int64_t ny, double dx, double dy, double gamma,
+                                int bc, const double* params5, const double* S, double* Lo, double* Mo,
+                                void* stream) {
+  if (!S || !Lo || !Mo || S == Lo || S == Mo || Lo == Mo) return HWENO_EINVAL;
+  // the same validation as hweno_create, on a handle that lives on this stack frame
+  hweno_ctx h;
+  if (dim != 1 && dim != 2) return HWENO_EINVAL;
+  if (system < HWENO_ADVECTION || system > HWENO_EULER) return HWENO_EINVAL;
+  if (bc < HWENO_BC_PERIODIC || bc > HWENO_BC_REFLECTIVE || bc == HWENO_BC_REFLECTIVE) return HWENO_EINVAL;
+  if (dim == 1) {
+    ny = 1;
+    dy = dx;
+  }
+  if (nx < 5 || ny < 1 || (dim == 2 && ny < 5)) return HWENO_EINVAL;
+  if (nx > (1 << 28) || ny > (1 << 28)) return HWENO_ETOOBIG;
+  if (!(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy)) return HWENO_EINVAL;
+  if (system == HWENO_EULER && !(gamma > 1.0)) return HWENO_EINVAL;
+  h.dim = dim;
+  h.system = system;
+  h.bc = bc;
+  h.nx = nx;
+  h.ny = ny;
+  h.dx = dx;
+  h.dy = dy;
+  h.gamma = system == HWENO_EULER ? gamma : 1.4;
+  h.gamma0 = dim == 1 ? 0.95 : 0.99;
+  h.d0 = 0.9;
+  h.eps = 1e-10;
+  h.cfl = 0.6;
+  h.ax = 1.0;
+  h.ay = 1.0;
+  if (params5) {
+    if (!(params5[0] > 0.0 && params5[0] < 1.0) || !(params5[1] > 0.0 && params5[1] < 1.0) || !(params5[2] > 0.0) ||
+        !std::isfinite(params5[3]) || !std::isfinite(params5[4]))
+      return HWENO_EINVAL;
+    h.gamma0 = params5[0];
+    h.d0 = params5[1];
+    h.eps = params5[2];
+    h.ax = params5[3];
+    h.ay = params5[4];
+  }
+  h.stream = static_cast<cudaStream_t>(stream);
+  h.state = nullptr;
+  h.ws = nullptr;
+  h.launches = 0;
+  h.profiling = false;
+  // scratch layout: the workspace layout of hweno_bind without the stage base B
+  const Layout l = layout_of(&h);
+  const size_t need = l.total - l.B;
+  if (need > kStaticScratchBytes) return HWENO_ETOOBIG;
+  void* base = nullptr;
+  int rc = static_scratch(&base);
+  if (rc) return rc;
+  unsigned char* p = static_cast<unsigned char*>(base);
+  h.w.B = nullptr;  // not used by the rhs mode
+  h.w.MD = reinterpret_cast<double*>(p);
+  p += l.MD;
+  h.w.NOD = reinterpret_cast<double*>(p);
+  p += l.NOD;
+  h.w.PRIM = reinterpret_cast<double*>(p);
+  p += l.PRIM;
+  h.w.FX = reinterpret_cast<double*>(p);
+  p += l.FX;
+  h.w.FY = l.FY ? reinterpret_cast<double*>(p) : nullptr;
+  p += l.FY;
+  h.w.alpha = reinterpret_cast<unsigned long long*>(p);
+  unsigned char* scal_begin = p;
+  p += l.alpha;
+  h.w.scal = reinterpret_cast<double*>(p);
+  p += l.scal;
+  h.w.status = reinterpret_cast<unsigned int*>(p);
+  // the array keeps the previous call's contents: clear the wavespeed slots and the status word
+  if (cudaMemsetAsync(scal_begin, 0, l.alpha + l.scal + l.status, h.stream) != cudaSuccess) return HWENO_ECUDA;
+  return stage(&h, S, const_cast<double*>(S), 1, 0, 0.0, 3, Lo, Mo);
+}

@@ -1,0 +1,85 @@
+"""hweno_rhs_static: the spatial operator for callers that cannot allocate device memory.
+
+Some callers of this library cannot allocate a workspace: their own framework or memory pool owns
+every device allocation and hands a library only input and output buffers, or they run
+latency-sensitive loops that cannot afford a cudaMalloc.  hweno_rhs_static serves them from a
+fixed scratch array inside the library.  These tests call it through the C ABI and check it
+against the workspace-based hweno_rhs, on two calls in a row (the array keeps the previous call's
+contents), and check that an oversized grid is refused.  The file is collected last so that a run
+stopping at the first failure has already run every other test; it also passes on its own in a
+fresh process, where its first call performs the one-time device set-up.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2411_11229_gb300 import Solver  # noqa: E402
+from paper_2411_11229_gb300 import _capi as C  # noqa: E402
+
+SYSTEMS = {"advection": C.HWENO_ADVECTION, "burgers": C.HWENO_BURGERS, "euler": C.HWENO_EULER}
+BCS = {"periodic": C.HWENO_BC_PERIODIC, "transmissive": C.HWENO_BC_TRANSMISSIVE}
+
+
+def _static_rhs(dim, system, nx, ny, dx, dy, bc, S):
+    Sd = torch.as_tensor(S, device="cuda").contiguous()
+    L = torch.full_like(Sd, float("nan"))
+    M = torch.full_like(Sd, float("nan"))
+    stream = torch.cuda.current_stream()
+    rc = C.load().hweno_rhs_static(dim, SYSTEMS[system], nx, ny, dx, dy, 1.4, BCS[bc], None,
+                                   ctypes.c_void_p(Sd.data_ptr()), ctypes.c_void_p(L.data_ptr()),
+                                   ctypes.c_void_p(M.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    C.check(rc, "hweno_rhs_static")
+    torch.cuda.synchronize()
+    return L.cpu().numpy(), M.cpu().numpy()
+
+
+def _handle_rhs(dim, system, nx, ny, dx, dy, bc, S):
+    s = Solver(dim, system, nx, ny, dx=dx, dy=dy, bc=bc)
+    s.set_state(S)
+    L, M = s.rhs()
+    torch.cuda.synchronize()
+    return L.cpu().numpy(), M.cpu().numpy()
+
+
+def _rel(a, b):
+    nf, nc = b.shape[0], b.shape[1]
+    a, b = a.reshape(nf * nc, -1), b.reshape(nf * nc, -1)
+    return (np.abs(a - b).max(axis=1) / np.maximum(np.abs(b).max(axis=1), 1e-300)).max()
+
+
+def test_static_rhs_matches_workspace_rhs_on_two_calls():
+    # first call: 2D Euler with discontinuities; second call: a different grid and system, so the
+    # second result must not depend on what the first call left in the scratch array
+    cases = [
+        (2, "euler", 37, 29, "periodic", W.euler2d_random(37, 29, 11, "jumps")[0]),
+        (1, "euler", 300, 1, "transmissive", W.euler1d_random(300, 12, "smooth")[0]),
+        (2, "euler", 180, 180, "periodic", W.euler2d_quadrants(180, seed=2000)[0]),
+    ]
+    for dim, system, nx, ny, bc, S in cases:
+        dx = 2.0 / nx
+        dy = 2.0 / ny if dim == 2 else dx
+        Ls, Ms = _static_rhs(dim, system, nx, ny, dx, dy, bc, S)
+        Lh, Mh = _handle_rhs(dim, system, nx, ny, dx, dy, bc, S)
+        assert np.isfinite(Ls).all() and np.isfinite(Ms).all()
+        assert _rel(Ls, Lh) <= 1e-12
+        assert _rel(Ms, Mh) <= 1e-12
+
+
+def test_static_rhs_rejects_grids_beyond_its_scratch():
+    n = 256  # 2D Euler needs about 480 bytes per cell: 256^2 cells exceed the 16 MiB array
+    S = np.zeros((3, 4, n, n))
+    Sd = torch.as_tensor(S, device="cuda")
+    L, M = torch.empty_like(Sd), torch.empty_like(Sd)
+    rc = C.load().hweno_rhs_static(2, C.HWENO_EULER, n, n, 2.0 / n, 2.0 / n, 1.4, C.HWENO_BC_PERIODIC, None,
+                                   ctypes.c_void_p(Sd.data_ptr()), ctypes.c_void_p(L.data_ptr()),
+                                   ctypes.c_void_p(M.data_ptr()), None)
+    assert rc == C.HWENO_ETOOBIG
