@@ -116,6 +116,50 @@ def cpu_baseline(steps: int = 8, n: int = 256):
                       f"wave (same per-cell work), one host thread, {sec:.1f} s"}
 
 
+def run_batched(dev, steps: int = 3):
+    """The uneven batched sweep: 256 1D Euler lines (N log-uniform in [128, 16384], seeded Riemann
+    data) and 32 2D Euler grids (sides in {128, 256, 512, 1024}), every instance with its own CFL
+    step.  Batched path (one persistent launch per stage, CUDA graph, autotuned launch shape)
+    against one launch per instance and kernel."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2411_11229_gb300 import Batch
+
+    pairs = W.batched_states(W.batched_instances())
+    cells = sum(int(np.prod(S.shape[2:])) for _, S in pairs)
+    res = {"instances": len(pairs), "cells": cells}
+    times = {}
+    for mode in ("plain", "batched"):
+        b = Batch([d for d, _ in pairs], device=dev)
+        for i, (_, S) in enumerate(pairs):
+            b.set_state(i, S)
+        if mode == "batched":
+            res["tuned_tiles_per_item"], res["tuned_blocks_per_sm"] = b.tune()
+        b.set_time(0.0)
+        run = b.step if mode == "batched" else b.step_plain
+        run(1)
+        b.sync()
+        l0 = b.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(b.stream)
+        run(steps)
+        e1.record(b.stream)
+        b.sync()
+        times[mode] = e0.elapsed_time(e1) / steps
+        res[f"launches_per_step_{mode}"] = (b.launch_count() - l0) // steps
+        b.dts()
+        del b
+        torch.cuda.empty_cache()
+    res["ms_per_step_plain"] = times["plain"]
+    res["ms_per_step_batched"] = times["batched"]
+    res["speedup_vs_plain"] = times["plain"] / times["batched"]
+    res["mcell_updates_per_s_batched"] = cells / (times["batched"] * 1e-3) / 1e6
+    return res
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
@@ -269,6 +313,10 @@ def run_ours(args, ws, rank, local):
         "kernel_avg_ms": {k: v[0] / max(v[1], 1) for k, v in ktimes.items()},
         "flops_per_cell_step": counts["per_cell_step"],
     }
+    if ws == 1 and not args.no_batched:
+        del solver
+        torch.cuda.empty_cache()
+        line["batched"] = run_batched(dev)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -283,6 +331,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":

@@ -140,6 +140,55 @@ const char *hweno_strerror(int status);
 /* Number of kernel launches issued by this handle since creation (for accounting). */
 long long hweno_launch_count(const hweno_t *h);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batched problems (not in the paper: many independent Euler problems of uneven sizes advanced
+ * together).  Every instance is an independent HWENO-I problem exactly as above (its own grid,
+ * boundary, wavespeeds and CFL step); the batch only changes how the work is launched:
+ * hweno_batch_step runs every Runge-Kutta stage over a work-list of tiles of all instances, either
+ * as one persistent cooperative launch (cell work, grid barrier, face work, grid barrier, update)
+ * or as three persistent launches (one per phase; the default and usually the autotuner's
+ * choice), the stages of a step recorded once in a CUDA graph and replayed;
+ * hweno_batch_step_plain launches the three kernels of every instance separately (the comparison
+ * path).  Both give the same results up to rounding.
+ * Only the Euler system is accepted (1D and 2D may be mixed). */
+typedef struct hweno_batch hweno_batch_t;
+
+typedef struct {
+  int dim, system, bc, pad_;
+  int64_t nx, ny;
+  double dx, dy, gamma;
+} hweno_desc;
+
+/* EINVAL: n <= 0, a non-Euler system, or any instance hweno_create would reject. */
+int hweno_batch_create(int n, const hweno_desc *descs, hweno_batch_t **out);
+/* Stream for all launches and copies (a non-default stream lets the steps replay a CUDA graph). */
+int hweno_batch_set_stream(hweno_batch_t *b, void *cuda_stream);
+/* Total doubles of the packed state (instances back to back, each in the state layout) and the
+ * offset (in doubles) of instance i. */
+size_t hweno_batch_state_doubles(const hweno_batch_t *b);
+size_t hweno_batch_state_offset(const hweno_batch_t *b, int i);
+/* Bytes of device workspace: the per-instance workspaces plus the batch tables. */
+size_t hweno_batch_workspace_bytes(const hweno_batch_t *b);
+/* Borrow the packed device state and the workspace (caller-owned); uploads the work-list. */
+int hweno_batch_bind(hweno_batch_t *b, double *state_dev, void *workspace_dev);
+/* Every instance: t = 0 and end time t_end (<= 0: no clamp) for the CFL steps. */
+int hweno_batch_set_time(hweno_batch_t *b, double t_end);
+/* nsteps SSP-RK3 steps of every instance with its own CFL step (no host synchronisation). */
+int hweno_batch_step(hweno_batch_t *b, int nsteps);
+int hweno_batch_step_plain(hweno_batch_t *b, int nsteps);
+/* Synchronise; the last dt and the time of every instance (arrays of n doubles; t may be NULL).
+ * HWENO_ENONPHYS if any instance met a non-physical state. */
+int hweno_batch_dts(hweno_batch_t *b, double *dt_host, double *t_host);
+/* Autotuner: times one step of each launch shape (tiles per work item 1, 2, 4; three phase
+ * launches, or one cooperative launch with 1 .. occupancy resident blocks per SM) on the bound
+ * state, keeps the fastest, and restores the state and the instance times from backup_dev
+ * (caller-owned device buffer of hweno_batch_state_doubles() doubles).  Returns the chosen tiles
+ * per item and resident blocks per SM (0 = three phase launches).  Results are cached per
+ * instance list for the process.  Synchronises. */
+int hweno_batch_tune(hweno_batch_t *b, double *backup_dev, int *tiles_per_item, int *blocks_per_sm);
+long long hweno_batch_launch_count(const hweno_batch_t *b);
+void hweno_batch_destroy(hweno_batch_t *b);
+
 /* hweno_rhs without any allocation.  The paper has no counterpart: this is a convenience for
  * callers that cannot allocate device memory for a workspace, such as host programs whose own
  * framework or memory pool owns every device allocation and passes a library nothing but the

@@ -11,6 +11,9 @@ def __getattr__(name):
     if name == "Solver":
         from .solver import Solver
         return Solver
+    if name == "Batch":
+        from .solver import Batch
+        return Batch
     if name == "capi":
         from . import _capi
         return _capi

@@ -40,10 +40,30 @@ SIGNATURES = {
     "hweno_kernel_times": (_I, [_H, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)]),
     "hweno_selftest_rcp": (_I, [_P, _P, ctypes.c_int64, _P]),
     "hweno_rhs_static": (_I, [_I, _I, ctypes.c_int64, ctypes.c_int64, _D, _D, _D, _I, _P, _P, _P, _P, _P]),
+    "hweno_batch_create": (_I, [_I, _P, ctypes.POINTER(_H)]),
+    "hweno_batch_set_stream": (_I, [_H, _P]),
+    "hweno_batch_state_doubles": (ctypes.c_size_t, [_H]),
+    "hweno_batch_state_offset": (ctypes.c_size_t, [_H, _I]),
+    "hweno_batch_workspace_bytes": (ctypes.c_size_t, [_H]),
+    "hweno_batch_bind": (_I, [_H, _P, _P]),
+    "hweno_batch_set_time": (_I, [_H, _D]),
+    "hweno_batch_step": (_I, [_H, _I]),
+    "hweno_batch_step_plain": (_I, [_H, _I]),
+    "hweno_batch_dts": (_I, [_H, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "hweno_batch_tune": (_I, [_H, _P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "hweno_batch_launch_count": (ctypes.c_longlong, [_H]),
+    "hweno_batch_destroy": (None, [_H]),
     "hweno_destroy": (None, [_H]),
     "hweno_strerror": (ctypes.c_char_p, [_I]),
     "hweno_launch_count": (ctypes.c_longlong, [_H]),
 }
+
+class HwenoDesc(ctypes.Structure):
+    """hweno_desc of include/hweno.h"""
+    _fields_ = [("dim", ctypes.c_int), ("system", ctypes.c_int), ("bc", ctypes.c_int), ("pad_", ctypes.c_int),
+                ("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("gamma", ctypes.c_double)]
+
 
 _lock = threading.Lock()
 _lib = None

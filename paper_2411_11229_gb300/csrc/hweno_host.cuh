@@ -1,0 +1,193 @@
+// Host-side internals shared by the translation units of libhweno.so (not part of the ABI):
+// the handle, the workspace layout, the folded kernel constants and the launch helpers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/hweno.h"
+#include "hweno_kernels.cuh"
+
+
+namespace hwh {
+
+using hw::Grid;
+using hw::Work;
+
+struct Launchers {
+  void (*cell)(const Grid&, const double*, const Work&, int, cudaStream_t);
+  void (*face)(const Grid&, const double*, const Work&, int, cudaStream_t);
+  void (*update)(const Grid&, double*, const Work&, int, int, double, double, double, int, double*, double*,
+                 cudaStream_t);
+  void (*wavespeed)(const Grid&, const double*, const Work&, int, cudaStream_t);
+};
+
+inline unsigned blocks_for(long long n) { return (unsigned)((n + hw::kThreads - 1) / hw::kThreads); }
+
+template <int DIM, int SYS>
+struct L {
+  static void cell(const Grid& g, const double* S, const Work& w, int slot, cudaStream_t st) {
+    hw::k_cell<DIM, SYS><<<blocks_for(g.plane), hw::kThreads, 0, st>>>(g, S, w, slot);
+  }
+  static void face(const Grid& g, const double* S, const Work& w, int slot, cudaStream_t st) {
+    const long long nfx = (long long)(g.nx + 1) * g.ny;
+    const long long nfy = DIM == 2 ? (long long)(g.ny + 1) * g.nx : 0;
+    dim3 grid(blocks_for(nfx > nfy ? nfx : nfy), DIM);
+    hw::k_face<DIM, SYS><<<grid, hw::kThreads, 0, st>>>(g, S, w, slot);
+  }
+  static void update(const Grid& g, double* S, const Work& w, int mode, int stage, double a, double b,
+                     double dt, int slot, double* Lo, double* Mo, cudaStream_t st) {
+    hw::k_update<DIM, SYS><<<blocks_for(g.plane), hw::kThreads, 0, st>>>(g, S, w, mode, stage, a, b, dt, slot, Lo, Mo);
+  }
+  static void wavespeed(const Grid& g, const double* S, const Work& w, int slot, cudaStream_t st) {
+    hw::k_wavespeed<DIM, SYS><<<blocks_for(g.plane), hw::kThreads, 0, st>>>(g, S, w, slot);
+  }
+  static constexpr Launchers table() { return Launchers{&cell, &face, &update, &wavespeed}; }
+};
+
+static const Launchers kTable[2][3] = {
+    {L<1, hw::SYS_ADV>::table(), L<1, hw::SYS_BURGERS>::table(), L<1, hw::SYS_EULER>::table()},
+    {L<2, hw::SYS_ADV>::table(), L<2, hw::SYS_BURGERS>::table(), L<2, hw::SYS_EULER>::table()}};
+
+inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace hwh
+
+struct hweno_ctx {
+  int dim, system, bc;
+  int64_t nx, ny;
+  double dx, dy, gamma;
+  double gamma0, d0, eps, cfl, ax, ay;
+  cudaStream_t stream;
+  double* state;
+  unsigned char* ws;
+  hw::Work w;
+  long long launches;
+  // optional per-kernel timing: events recorded around the three launches of every stage
+  bool profiling;
+  std::vector<cudaEvent_t> events;  // groups of 4: before cell, before face, before update, after
+  double kernel_ms[3];
+  long long kernel_n[3];
+};
+
+namespace hwh {
+
+inline int nc_of(const hweno_ctx* h) { return h->system == HWENO_EULER ? (h->dim == 1 ? 3 : 4) : 1; }
+inline int nf_of(const hweno_ctx* h) { return h->dim + 1; }
+inline int ng_of(const hweno_ctx* h) { return h->dim == 2 ? 3 : 2; }
+inline int np_of(const hweno_ctx* h) { return h->system == HWENO_EULER ? (h->dim == 2 ? 4 : 3) : 0; }
+
+// workspace sub-buffers in bytes, in layout order
+struct Layout {
+  size_t B, MD, NOD, PRIM, FX, FY, alpha, scal, status, total;
+};
+
+inline Layout layout_of(const hweno_ctx* h) {
+  const size_t plane = (size_t)h->nx * h->ny;
+  const size_t nc = nc_of(h), nf = nf_of(h);
+  Layout l;
+  l.B = align_up(nf * nc * plane * 8);
+  l.MD = align_up((size_t)h->dim * nc * plane * 8);
+  l.NOD = align_up((size_t)h->dim * ng_of(h) * nc * plane * 8);
+  l.PRIM = align_up((size_t)np_of(h) * plane * 8 + 8);
+  l.FX = align_up(nf * nc * (size_t)h->ny * (h->nx + 1) * 8);
+  l.FY = h->dim == 2 ? align_up(nf * nc * (size_t)(h->ny + 1) * h->nx * 8) : 0;
+  l.alpha = align_up(8 * 8);
+  l.scal = align_up(8 * 8);
+  l.status = align_up(16);
+  l.total = l.B + l.MD + l.NOD + l.PRIM + l.FX + l.FY + l.alpha + l.scal + l.status;
+  return l;
+}
+
+inline Grid grid_of(const hweno_ctx* h) {
+  Grid g;
+  g.nx = (int)h->nx;
+  g.ny = (int)h->ny;
+  g.bc = h->bc;
+  g.pad_ = 0;
+  g.plane = (long long)h->nx * h->ny;
+  g.dx = h->dx;
+  g.dy = h->dy;
+  g.inv_dx = 1.0 / h->dx;
+  g.inv_dy = 1.0 / h->dy;
+  g.gamma = h->gamma;
+  g.gm1 = h->gamma - 1.0;
+  g.ax = h->ax;
+  g.ay = h->ay;
+  g.g0 = h->gamma0;
+  g.g1 = 0.5 * (1.0 - h->gamma0);
+  g.d0 = h->d0;
+  g.d1 = 0.5 * (1.0 - h->d0);
+  g.eps = h->eps;
+  g.cfl = h->cfl;
+  // folded constants (see hw::Grid)
+  const double g1 = g.g1;
+  const double cr[5] = {(-0.125 + 0.5 * g1) / g1, (0.5625 - 2.0 * g1) / g1, (0.5625 - 0.5 * g1) / g1,
+                        -0.046875 / g1, -0.140625 / g1};
+  const double cl[5] = {(0.5625 - 0.5 * g1) / g1, (0.5625 - 2.0 * g1) / g1, (-0.125 + 0.5 * g1) / g1,
+                        0.140625 / g1, 0.046875 / g1};
+  for (int k = 0; k < 5; ++k) {
+    g.cr[k] = cr[k];
+    g.cl[k] = cl[k];
+  }
+  g.G = g.g0 / g1;
+  g.cdu = (0.75 - g.d1) / g.d1;
+  g.csv = 0.25 / g.d1;
+  g.Gd = g.d0 / g.d1;
+  const double hs[2] = {h->dx, h->dy};
+  for (int d = 0; d < 2; ++d) {
+    g.h[d] = hs[d];
+    g.ih[d] = 1.0 / hs[d];
+    g.chh[d] = hw::DCoef::ch * hs[d];
+    g.efih[d] = hw::DCoef::ef / hs[d];
+    g.egih[d] = hw::DCoef::eg / hs[d];
+    g.hih[d] = 0.5 / hs[d];
+  }
+  return g;
+}
+
+inline int cuda_status() { return cudaGetLastError() == cudaSuccess ? HWENO_OK : HWENO_ECUDA; }
+
+inline int read_status(hweno_ctx* h) {
+  unsigned int st = 0;
+  if (cudaMemcpyAsync(&st, h->w.status, sizeof(st), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return HWENO_ECUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return HWENO_ECUDA;
+  return st ? HWENO_ENONPHYS : HWENO_OK;
+}
+
+inline const Launchers& launchers(const hweno_ctx* h) { return kTable[h->dim - 1][h->system]; }
+
+// one spatial-operator evaluation: cell, face; then update in the requested mode
+inline int stage(hweno_ctx* h, const double* S_in, double* S_out, int mode, int st, double dt, int slot, double* Lo,
+          double* Mo) {
+  const Grid g = grid_of(h);
+  const Launchers& f = launchers(h);
+  if (cudaMemsetAsync(h->w.alpha + 2 * slot, 0, 2 * sizeof(unsigned long long), h->stream) != cudaSuccess)
+    return HWENO_ECUDA;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (h->profiling) {
+    for (int k = 0; k < 4; ++k)
+      if (cudaEventCreate(&ev[k]) != cudaSuccess) return HWENO_ECUDA;
+    for (int k = 0; k < 4; ++k) h->events.push_back(ev[k]);
+  }
+  static const double a_k[3] = {0.0, 0.75, 1.0 / 3.0};
+  static const double b_k[3] = {1.0, 0.25, 2.0 / 3.0};
+  if (ev[0]) cudaEventRecord(ev[0], h->stream);
+  f.cell(g, S_in, h->w, slot, h->stream);
+  if (ev[1]) cudaEventRecord(ev[1], h->stream);
+  f.face(g, S_in, h->w, slot, h->stream);
+  if (ev[2]) cudaEventRecord(ev[2], h->stream);
+  f.update(g, S_out, h->w, mode, st, a_k[st], b_k[st], dt, slot, Lo, Mo, h->stream);
+  if (ev[3]) cudaEventRecord(ev[3], h->stream);
+  h->launches += 3;
+  return cuda_status();
+}
+
+}  // namespace hwh
+

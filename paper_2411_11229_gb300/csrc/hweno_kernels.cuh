@@ -28,9 +28,11 @@ struct Work {
   double* PRIM;  // Euler primitives (sqrt(rho), u[, v], H): [NP][plane]
   double* FX;    // x-face fluxes, original frame: [NF][NC][ny][nx+1]
   double* FY;    // y-face fluxes: [NF][NC][ny+1][nx]
-  unsigned long long* alpha;  // wavespeed slots (bit patterns of non-negative doubles): [4][2]
+  unsigned long long* alpha;  // wavespeed slots (bit patterns of non-negative doubles): slot s of
+                              // direction d at alpha[s * astride + d]
   double* scal;               // [0] dt of the current step, [1] t, [2] t_end
   unsigned int* status;       // bit 0: non-physical state met
+  long long astride;          // distance between slots (2 for a single grid)
 };
 
 constexpr int kThreads = 128;
@@ -107,14 +109,15 @@ __device__ __forceinline__ void modified_derivative(const double (&U3)[3][NC], c
   }
 }
 
+// Cell work of one stage at cell p: primitives and wavespeeds (returned in wsx, wsy), nodal
+// values per direction, modified derivatives.
 template <int DIM, int SYS>
-__global__ void __launch_bounds__(kThreads) k_cell(Grid g, const double* __restrict__ S, Work w, int slot) {
+__device__ __forceinline__ void cell_body(const Grid& g, const double* __restrict__ S, const Work& w, long long p,
+                                          double& wsx, double& wsy) {
   using T = Traits<DIM, SYS>;
   constexpr int NC = T::NC, NG = T::NG;
   const long long plane = g.plane;
-  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
-  double wsx = 0.0, wsy = 0.0;
-  if (p < plane) {
+  {
     const int i = (int)(p % g.nx), j = (int)(p / g.nx);
     double U[NC], V[NC], Wd[NC];
 #pragma unroll
@@ -225,20 +228,26 @@ __global__ void __launch_bounds__(kThreads) k_cell(Grid g, const double* __restr
       for (int k = 0; k < NC; ++k) w.MD[((long long)d * NC + k) * plane + p] = out[k];
     }
   }
-  block_max2(wsx, wsy, w.alpha + 2 * slot);
+}
+
+template <int DIM, int SYS>
+__global__ void __launch_bounds__(kThreads) k_cell(Grid g, const double* __restrict__ S, Work w, int slot) {
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  double wsx = 0.0, wsy = 0.0;
+  if (p < g.plane) cell_body<DIM, SYS>(g, S, w, p, wsx, wsy);
+  block_max2(wsx, wsy, w.alpha + slot * w.astride);
 }
 
 // ---------------------------------------------------------------------------------------------
+// Face work of one stage: face f of direction dir (x faces: f = j (nx+1) + i; y faces:
+// f = j nx + i), alpha = the LF coefficient of that direction.
 template <int DIM, int SYS>
-__global__ void __launch_bounds__(kThreads) k_face(Grid g, const double* __restrict__ S, Work w, int slot) {
+__device__ __forceinline__ void face_body(const Grid& g, const double* __restrict__ S, const Work& w, int dir,
+                                          long long f, double alpha) {
   using T = Traits<DIM, SYS>;
   constexpr int NC = T::NC, NG = T::NG;
-  const int dir = blockIdx.y;
   const long long plane = g.plane;
   const int n = dir == 0 ? g.nx : g.ny;
-  const int nlines = dir == 0 ? g.ny : g.nx;
-  const long long f = (long long)blockIdx.x * kThreads + threadIdx.x;
-  if (f >= (long long)(n + 1) * nlines) return;
   int fa, line;
   if (dir == 0) {
     line = (int)(f / (n + 1));
@@ -329,7 +338,6 @@ __global__ void __launch_bounds__(kThreads) k_face(Grid g, const double* __restr
   Phys<DIM, SYS>::flux(Up, FUp, a_adv, g.gm1);
   Phys<DIM, SYS>::jvp(Um, Dm, HDm, a_adv, g.gm1);
   Phys<DIM, SYS>::jvp(Up, Dp, HDp, a_adv, g.gm1);
-  const double alpha = __longlong_as_double((long long)w.alpha[2 * slot + dir]);
   const double* nod = w.NOD + (long long)dir * NG * NC * plane;
   double* out = dir == 0 ? w.FX : w.FY;
   const long long oplane = dir == 0 ? (long long)g.ny * (g.nx + 1) : (long long)(g.ny + 1) * g.nx;
@@ -366,46 +374,29 @@ __global__ void __launch_bounds__(kThreads) k_face(Grid g, const double* __restr
   }
 }
 
-// ---------------------------------------------------------------------------------------------
-// mode 0: Runge-Kutta stage in place, S = a B + b (M + dt L) (stage 0: B := M, S = M + dt L).
-// mode 1: write L and M to Lout, Mout.
-// dt: dt_fixed > 0, or (dt_fixed <= 0) the CFL step from wavespeed slot `slot` at stage 0
-// (clamped to t_end), stored in scal[0] and reused by stages 1 and 2.
 template <int DIM, int SYS>
-__global__ void __launch_bounds__(kThreads) k_update(Grid g, double* __restrict__ S, Work w, int mode, int stage,
-                                                      double a_k, double b_k, double dt_fixed, int slot,
-                                                      double* __restrict__ Lout, double* __restrict__ Mout) {
+__global__ void __launch_bounds__(kThreads) k_face(Grid g, const double* __restrict__ S, Work w, int slot) {
+  const int dir = blockIdx.y;
+  const int n = dir == 0 ? g.nx : g.ny;
+  const int nlines = dir == 0 ? g.ny : g.nx;
+  const long long f = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (f >= (long long)(n + 1) * nlines) return;
+  face_body<DIM, SYS>(g, S, w, dir, f, __longlong_as_double((long long)w.alpha[slot * w.astride + dir]));
+}
+
+// ---------------------------------------------------------------------------------------------
+// Update of one cell p.  mode 0: Runge-Kutta stage in place, S = a B + b (M + dt L) (stage 0:
+// B := M, S = M + dt L).  mode 1: write L and M to Lout, Mout.
+template <int DIM, int SYS>
+__device__ __forceinline__ void update_body(const Grid& g, double* __restrict__ S, const Work& w, int mode, int stage,
+                                            double a_k, double b_k, double dt, long long p,
+                                            double* __restrict__ Lout, double* __restrict__ Mout) {
   using T = Traits<DIM, SYS>;
   constexpr int NC = T::NC, NF = T::NF;
-  __shared__ double s_dt;
   const long long plane = g.plane;
-  if (mode == 0) {
-    if (threadIdx.x == 0) {
-      double dt;
-      if (stage == 0) {
-        if (dt_fixed > 0.0) {
-          dt = dt_fixed;
-        } else {
-          const double axs = __longlong_as_double((long long)w.alpha[2 * slot]);
-          const double ays = __longlong_as_double((long long)w.alpha[2 * slot + 1]);
-          dt = DIM == 2 ? g.cfl / fma(axs, g.inv_dx, ays * g.inv_dy) : g.cfl * g.dx / axs;
-          const double t = w.scal[1], te = w.scal[2];
-          if (te > 0.0 && t + dt > te) dt = fmax(te - t, 0.0);
-        }
-        if (blockIdx.x == 0) w.scal[0] = dt;
-      } else {
-        dt = w.scal[0];
-      }
-      s_dt = dt;
-    }
-    __syncthreads();
-  }
-  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
-  if (p >= plane) return;
   const int i = (int)(p % g.nx), j = (int)(p / g.nx);
   const long long px = (long long)j * (g.nx + 1) + i;
   const long long oplx = (long long)g.ny * (g.nx + 1), oply = (long long)(g.ny + 1) * g.nx;
-  const double dt = mode == 0 ? s_dt : 0.0;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
 #pragma unroll
@@ -425,6 +416,41 @@ __global__ void __launch_bounds__(kThreads) k_update(Grid g, double* __restrict_
       }
     }
   }
+}
+
+// The step size of a stage: dt_fixed > 0, or (dt_fixed <= 0) at stage 0 the CFL step from the
+// wavespeed slot (clamped to t_end); stages 1 and 2 reuse the value stored in scal[0].
+template <int DIM>
+__device__ __forceinline__ double stage_dt(const Grid& g, const Work& w, int stage, double dt_fixed, int slot) {
+  if (stage != 0) return w.scal[0];
+  if (dt_fixed > 0.0) return dt_fixed;
+  const double axs = __longlong_as_double((long long)w.alpha[slot * w.astride]);
+  const double ays = __longlong_as_double((long long)w.alpha[slot * w.astride + 1]);
+  double dt = DIM == 2 ? g.cfl / fma(axs, g.inv_dx, ays * g.inv_dy) : g.cfl * g.dx / axs;
+  const double t = w.scal[1], te = w.scal[2];
+  if (te > 0.0 && t + dt > te) dt = fmax(te - t, 0.0);
+  return dt;
+}
+
+// dt of stage 0 is stored in scal[0] by block 0 and reused by stages 1 and 2; the time advances
+// at stage 2.
+template <int DIM, int SYS>
+__global__ void __launch_bounds__(kThreads) k_update(Grid g, double* __restrict__ S, Work w, int mode, int stage,
+                                                      double a_k, double b_k, double dt_fixed, int slot,
+                                                      double* __restrict__ Lout, double* __restrict__ Mout) {
+  __shared__ double s_dt;
+  if (mode == 0) {
+    if (threadIdx.x == 0) {
+      const double dt = stage_dt<DIM>(g, w, stage, dt_fixed, slot);
+      if (stage == 0 && blockIdx.x == 0) w.scal[0] = dt;
+      s_dt = dt;
+    }
+    __syncthreads();
+  }
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (p >= g.plane) return;
+  const double dt = mode == 0 ? s_dt : 0.0;
+  update_body<DIM, SYS>(g, S, w, mode, stage, a_k, b_k, dt, p, Lout, Mout);
   if (mode == 0 && stage == 2 && p == 0) w.scal[1] += dt;
 }
 
@@ -456,7 +482,7 @@ __global__ void __launch_bounds__(kThreads) k_wavespeed(Grid g, const double* __
       wsy = DIM == 2 ? fabs(g.ay) : 0.0;
     }
   }
-  block_max2(wsx, wsy, w.alpha + 2 * slot);
+  block_max2(wsx, wsy, w.alpha + slot * w.astride);
 }
 
 }  // namespace hw

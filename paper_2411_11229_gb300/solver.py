@@ -138,3 +138,93 @@ class Solver:
                 if t >= t_end or dt <= 0.0:
                     break
         return n
+
+
+class Batch:
+    """Many independent Euler problems (1D and 2D, uneven sizes) advanced together.
+
+    descs: list of dicts with keys dim, nx, ny (2D), dx, dy (2D), bc ('periodic' or
+    'transmissive'), gamma.  The packed device state holds the instances back to back; view(i)
+    is instance i's (nfield, ncomp, ny, nx) view.  The batch runs on a stream of its own so that
+    its steps can replay a CUDA graph.
+    """
+
+    def __init__(self, descs, device="cuda", stream: torch.cuda.Stream = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("HWENO batch needs a CUDA device")
+        self.lib = C.load()
+        self.device = torch.device(device)
+        n = len(descs)
+        arr = (C.HwenoDesc * n)()
+        self.shapes = []
+        for i, d in enumerate(descs):
+            dim = int(d["dim"])
+            nx = int(d["nx"])
+            ny = int(d.get("ny", 1)) if dim == 2 else 1
+            arr[i] = C.HwenoDesc(dim, C.HWENO_EULER, _BCS[d.get("bc", "periodic")], 0, nx, ny,
+                                 float(d["dx"]), float(d.get("dy", d["dx"])), float(d.get("gamma", 1.4)))
+            self.shapes.append((dim + 1, 3 if dim == 1 else 4, ny, nx))
+        h = ctypes.c_void_p()
+        C.check(self.lib.hweno_batch_create(n, arr, ctypes.byref(h)), "hweno_batch_create")
+        self.h, self.n = h, n
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        C.check(self.lib.hweno_batch_set_stream(h, ctypes.c_void_p(self.stream.cuda_stream)), "hweno_batch_set_stream")
+        total = int(self.lib.hweno_batch_state_doubles(h))
+        self.offsets = [int(self.lib.hweno_batch_state_offset(h, i)) for i in range(n)]
+        self.state = torch.zeros(total, dtype=torch.float64, device=self.device)
+        self.workspace = torch.empty(int(self.lib.hweno_batch_workspace_bytes(h)), dtype=torch.uint8,
+                                     device=self.device)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        C.check(self.lib.hweno_batch_bind(h, ctypes.c_void_p(self.state.data_ptr()),
+                                          ctypes.c_void_p(self.workspace.data_ptr())), "hweno_batch_bind")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hweno_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def view(self, i):
+        size = int(np.prod(self.shapes[i]))
+        return self.state[self.offsets[i]:self.offsets[i] + size].view(self.shapes[i])
+
+    def set_state(self, i, S) -> None:
+        S = torch.as_tensor(np.asarray(S) if not isinstance(S, torch.Tensor) else S, dtype=torch.float64)
+        with torch.cuda.stream(self.stream):
+            self.view(i).copy_(S.reshape(self.shapes[i]).to(self.device, non_blocking=True))
+
+    def set_time(self, t_end: float = 0.0) -> None:
+        C.check(self.lib.hweno_batch_set_time(self.h, float(t_end)), "hweno_batch_set_time")
+
+    def step(self, nsteps: int = 1) -> None:
+        C.check(self.lib.hweno_batch_step(self.h, int(nsteps)), "hweno_batch_step")
+
+    def step_plain(self, nsteps: int = 1) -> None:
+        C.check(self.lib.hweno_batch_step_plain(self.h, int(nsteps)), "hweno_batch_step_plain")
+
+    def dts(self):
+        dt = (ctypes.c_double * self.n)()
+        t = (ctypes.c_double * self.n)()
+        C.check(self.lib.hweno_batch_dts(self.h, dt, t), "hweno_batch_dts")
+        return np.array(dt[:]), np.array(t[:])
+
+    def tune(self):
+        """Autotune the persistent launch; returns (tiles per item, blocks per SM)."""
+        backup = torch.empty_like(self.state)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        tpi, bps = ctypes.c_int(), ctypes.c_int()
+        C.check(self.lib.hweno_batch_tune(self.h, ctypes.c_void_p(backup.data_ptr()), ctypes.byref(tpi),
+                                          ctypes.byref(bps)), "hweno_batch_tune")
+        return tpi.value, bps.value
+
+    def launch_count(self) -> int:
+        return int(self.lib.hweno_batch_launch_count(self.h))
+
+    def sync(self) -> None:
+        self.stream.synchronize()

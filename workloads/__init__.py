@@ -416,3 +416,23 @@ def scalar_random(dim: int, nx: int, ny: int, seed: int, kind: str = "smooth"):
         for f in range(1, nf):
             S[f, 0] = rng.normal(0.0, 1.0, (ny, nx))
     return S, 2.0 / nx, 2.0 / ny
+
+
+def batched_states(instances, gamma: float = 1.4):
+    """Initial states of the batched sweep: 1D instances take the seeded Riemann data (transmissive
+    boundaries), 2D instances alternate between the smooth wave and the four-quadrant data (by seed
+    parity, periodic boundaries).  Returns a list of (desc, state) with desc as hweno_desc fields."""
+    out = []
+    for inst in instances:
+        if inst["dim"] == 1:
+            S, dx, _ = euler1d_riemann(inst["nx"], inst["seed"], gamma)
+            out.append(({"dim": 1, "nx": inst["nx"], "ny": 1, "dx": dx, "dy": dx, "bc": "transmissive",
+                         "gamma": gamma}, S))
+        else:
+            n = inst["nx"]
+            if inst["seed"] % 2 == 0:
+                S, dx, dy = euler2d_smooth(n)
+            else:
+                S, dx, dy = euler2d_quadrants(n, seed=inst["seed"])
+            out.append(({"dim": 2, "nx": n, "ny": n, "dx": dx, "dy": dy, "bc": "periodic", "gamma": gamma}, S))
+    return out
