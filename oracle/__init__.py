@@ -80,6 +80,11 @@ def lib():
                                      ctypes.c_longlong, _P]
             L.oracle_run.restype = ctypes.c_longlong
             L.oracle_count_flops.argtypes = [CP, ctypes.POINTER(ctypes.c_longlong)]
+            L.oracle_stage_vjp.argtypes = [CP, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P]
+            L.oracle_stage_jvp.argtypes = [CP, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P]
+            L.oracle_steps_record.argtypes = [CP, _P, ctypes.c_int, ctypes.c_double, _P, _P]
+            L.oracle_steps_replay.argtypes = [CP, _P, ctypes.c_int, _P, _P]
+            L.oracle_adjoint_step.argtypes = [CP, _P, ctypes.c_double, _P, _P, _P]
             L.oracle_stencil.argtypes = [_P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, _P]
             L.oracle_dterms.argtypes = [_P, _P, ctypes.c_double, _P]
@@ -171,6 +176,53 @@ def count_flops(cfg: Cfg) -> dict:
     keys = ("face", "nodal_per_dir", "modified_derivative_per_dir", "wavespeed_per_dir",
             "update", "per_cell_step")
     return dict(zip(keys, [int(v) for v in out]))
+
+
+def stage_vjp(cfg: Cfg, S, alpha, muM, muL):
+    """(dM/dS)^T muM + (dL/dS)^T muL at S with the LF coefficients alpha = (ax, ay) held fixed."""
+    S, muM, muL = (np.ascontiguousarray(a, dtype=np.float64) for a in (S, muM, muL))
+    lam = np.zeros_like(S)
+    _check(lib().oracle_stage_vjp(ctypes.byref(cfg), _ptr(S), float(alpha[0]), float(alpha[1]), _ptr(muM),
+                                  _ptr(muL), _ptr(lam)))
+    return lam
+
+
+def stage_jvp(cfg: Cfg, S, alpha, delta):
+    """(dM/dS delta, dL/dS delta) at S with alpha held fixed (forward-mode derivatives)."""
+    S, delta = (np.ascontiguousarray(a, dtype=np.float64) for a in (S, delta))
+    jM, jL = np.zeros_like(S), np.zeros_like(S)
+    _check(lib().oracle_stage_jvp(ctypes.byref(cfg), _ptr(S), float(alpha[0]), float(alpha[1]), _ptr(delta),
+                                  _ptr(jM), _ptr(jL)))
+    return jM, jL
+
+
+def steps_record(cfg: Cfg, S, nsteps: int, cfl: float = 0.6):
+    """nsteps CFL steps; returns (state, dts[nsteps], alphas[nsteps, 6])."""
+    out = np.array(S, dtype=np.float64, copy=True, order="C")
+    dts = np.zeros(nsteps)
+    alphas = np.zeros((nsteps, 6))
+    _check(lib().oracle_steps_record(ctypes.byref(cfg), _ptr(out), int(nsteps), float(cfl), _ptr(dts),
+                                     _ptr(alphas)))
+    return out, dts, alphas
+
+
+def steps_replay(cfg: Cfg, S, dts, alphas):
+    """Steps with the given step sizes and per-stage LF coefficients."""
+    out = np.array(S, dtype=np.float64, copy=True, order="C")
+    dts = np.ascontiguousarray(dts, dtype=np.float64)
+    alphas = np.ascontiguousarray(alphas, dtype=np.float64)
+    _check(lib().oracle_steps_replay(ctypes.byref(cfg), _ptr(out), int(dts.size), _ptr(dts), _ptr(alphas)))
+    return out
+
+
+def adjoint_step(cfg: Cfg, Sn, dt: float, alpha6, lam_in):
+    """(dS^{n+1}/dS^n)^T lam_in for one SSP-RK3 step with fixed dt and per-stage alpha."""
+    Sn, lam_in = (np.ascontiguousarray(a, dtype=np.float64) for a in (Sn, lam_in))
+    alpha6 = np.ascontiguousarray(alpha6, dtype=np.float64)
+    lam = np.zeros_like(Sn)
+    _check(lib().oracle_adjoint_step(ctypes.byref(cfg), _ptr(Sn), float(dt), _ptr(alpha6), _ptr(lam_in),
+                                     _ptr(lam)))
+    return lam
 
 
 def stencil(u3, v2, dx, gamma0=0.95, d0=0.9, eps=1e-10) -> dict:

@@ -755,6 +755,279 @@ inline bool operator>(const Counted& a, const Counted& b) { return a.v > b.v; }
 inline Counted fabs(const Counted& a) { return Counted(std::fabs(a.v)); }
 inline Counted sqrt(const Counted& a) { ++Counted::n(); return Counted(std::sqrt(a.v)); }
 
+// ---------------------------------------------------------------------------------------------
+// Derivatives of the scheme for the adjoint (conventions: the step sizes and the LF coefficients
+// alpha of every stage are held fixed at recorded values; d|x|/dx = sign(x) with sign(0) = 0).
+//
+// Reverse mode: `Adj` records every operation on a tape (two parents with their partial
+// derivatives); one reverse sweep gives the gradient of a weighted sum of outputs.  The tape is
+// kept per face or per cell (the operator is local), so its size stays small.
+// Forward mode: `Dual` carries one directional derivative through the same code.
+struct Tape {
+  std::vector<int> a, b;
+  std::vector<double> da, db;
+  void clear() {
+    a.clear();
+    b.clear();
+    da.clear();
+    db.clear();
+  }
+  int push(int ia, double pa, int ib, double pb) {
+    a.push_back(ia);
+    b.push_back(ib);
+    da.push_back(pa);
+    db.push_back(pb);
+    return (int)a.size() - 1;
+  }
+  size_t size() const { return a.size(); }
+};
+inline Tape& tape() {
+  static thread_local Tape t;
+  return t;
+}
+
+struct Adj {
+  double v;
+  int id;  // tape index, -1 for a constant
+  Adj() : v(0.0), id(-1) {}
+  Adj(double x) : v(x), id(-1) {}
+  Adj(double x, int i) : v(x), id(i) {}
+};
+inline Adj adj_var(double x) { return Adj(x, tape().push(-1, 0.0, -1, 0.0)); }
+inline Adj adj_node(double v, int ia, double pa, int ib, double pb) {
+  if (ia < 0 && ib < 0) return Adj(v);
+  return Adj(v, tape().push(ia, pa, ib, pb));
+}
+inline Adj operator+(const Adj& x, const Adj& y) { return adj_node(x.v + y.v, x.id, 1.0, y.id, 1.0); }
+inline Adj operator-(const Adj& x, const Adj& y) { return adj_node(x.v - y.v, x.id, 1.0, y.id, -1.0); }
+inline Adj operator*(const Adj& x, const Adj& y) { return adj_node(x.v * y.v, x.id, y.v, y.id, x.v); }
+inline Adj operator/(const Adj& x, const Adj& y) {
+  const double q = x.v / y.v;
+  return adj_node(q, x.id, 1.0 / y.v, y.id, -q / y.v);
+}
+inline Adj operator-(const Adj& x) { return adj_node(-x.v, x.id, -1.0, -1, 0.0); }
+inline bool operator>(const Adj& x, const Adj& y) { return x.v > y.v; }
+inline Adj fabs(const Adj& x) { return adj_node(std::fabs(x.v), x.id, x.v > 0 ? 1.0 : (x.v < 0 ? -1.0 : 0.0), -1, 0.0); }
+inline Adj sqrt(const Adj& x) {
+  const double r = std::sqrt(x.v);
+  return adj_node(r, x.id, 0.5 / r, -1, 0.0);
+}
+
+// reverse sweep: adjoint of every tape entry from the seeds already placed in g
+inline void adj_sweep(std::vector<double>& g) {
+  const Tape& t = tape();
+  for (int i = (int)t.size() - 1; i >= 0; --i) {
+    const double gi = g[i];
+    if (gi == 0.0) continue;
+    if (t.a[i] >= 0) g[t.a[i]] += t.da[i] * gi;
+    if (t.b[i] >= 0) g[t.b[i]] += t.db[i] * gi;
+  }
+}
+
+struct Dual {
+  double v, d;
+  Dual() : v(0.0), d(0.0) {}
+  Dual(double x) : v(x), d(0.0) {}
+  Dual(double x, double y) : v(x), d(y) {}
+};
+inline Dual operator+(const Dual& x, const Dual& y) { return Dual(x.v + y.v, x.d + y.d); }
+inline Dual operator-(const Dual& x, const Dual& y) { return Dual(x.v - y.v, x.d - y.d); }
+inline Dual operator*(const Dual& x, const Dual& y) { return Dual(x.v * y.v, x.d * y.v + x.v * y.d); }
+inline Dual operator/(const Dual& x, const Dual& y) {
+  const double q = x.v / y.v;
+  return Dual(q, (x.d - q * y.d) / y.v);
+}
+inline Dual operator-(const Dual& x) { return Dual(-x.v, -x.d); }
+inline bool operator>(const Dual& x, const Dual& y) { return x.v > y.v; }
+inline Dual fabs(const Dual& x) { return Dual(std::fabs(x.v), x.v > 0 ? x.d : (x.v < 0 ? -x.d : 0.0)); }
+inline Dual sqrt(const Dual& x) {
+  const double r = std::sqrt(x.v);
+  return Dual(r, 0.5 * x.d / r);
+}
+
+// Vector-Jacobian product of one stage operator at S with alpha fixed:
+// lam = (dM/dS)^T muM + (dL/dS)^T muL (all arrays in the state layout).
+inline void stage_vjp(const Cfg& c, const double* S, double ax, double ay, const double* muM, const double* muL,
+                      double* lam) {
+  Operator<Adj> op(c);
+  const int m = ncomp(c), nf = nfield(c);
+  const int nx = c.nx, ny = c.dim == 2 ? c.ny : 1;
+  const size_t plane = (size_t)nx * ny;
+  const size_t n = (size_t)nf * m * plane;
+  for (size_t p = 0; p < n; ++p) lam[p] = 0.0;
+  for (int k = 0; k < m; ++k)
+    for (size_t p = 0; p < plane; ++p) lam[k * plane + p] += muM[k * plane + p];  // M = (U, ...)
+  // boundary map of a cell (f, k, j, i) to its source cell and sign
+  auto source = [&](int f, int k, int j, int i, size_t* idx) -> double {
+    bool fx, fy = false;
+    int si = bc_source(c.bc, i, nx, &fx);
+    int sj = c.dim == 2 ? bc_source(c.bc, j, ny, &fy) : 0;
+    double sgn = 1.0;
+    if (fx) sgn *= reflect_sign(c, 0, f, k);
+    if (fy) sgn *= reflect_sign(c, 1, f, k);
+    *idx = ((size_t)f * m + k) * plane + (size_t)sj * nx + si;
+    return sgn;
+  };
+  std::vector<double> g;
+  for (int dir = 0; dir < c.dim; ++dir) {
+    const double h = dir == 0 ? c.dx : c.dy;
+    const double alpha = dir == 0 ? ax : ay;
+    const int own = dir == 0 ? 1 : 2, other = dir == 0 ? 2 : 1;
+    const int nlines = dir == 0 ? ny : nx, nalong = dir == 0 ? nx : ny;
+    for (int line = 0; line < nlines; ++line) {
+      auto cell = [&](int a, int* jj, int* ii) {
+        *jj = dir == 0 ? line : a;
+        *ii = dir == 0 ? a : line;
+      };
+      auto mu_at = [&](const double* mu, int f, int k, int a) -> double {
+        if (a < 0 || a >= nalong) return 0.0;
+        int jj, ii;
+        cell(a, &jj, &ii);
+        return mu[((size_t)f * m + k) * plane + (size_t)jj * nx + ii];
+      };
+      // faces a+1/2: the fluxes enter L of cells a (-1/h) and a+1 (+1/h)
+      for (int a = -1; a < nalong; ++a) {
+        tape().clear();
+        Adj Uc[4][4], Dc[4][4], Oc[4][4];
+        size_t iu[4][4], id[4][4], io[4][4];
+        double su[4][4], sd[4][4], so[4][4];
+        for (int q = 0; q < 4; ++q) {
+          int jj, ii;
+          cell(a - 1 + q, &jj, &ii);
+          for (int k = 0; k < m; ++k) {
+            su[q][k] = source(0, k, jj, ii, &iu[q][k]);
+            sd[q][k] = source(own, k, jj, ii, &id[q][k]);
+            Uc[q][k] = adj_var(su[q][k] * S[iu[q][k]]);
+            Dc[q][k] = adj_var(sd[q][k] * S[id[q][k]]);
+            if (c.dim == 2) {
+              so[q][k] = source(other, k, jj, ii, &io[q][k]);
+              Oc[q][k] = adj_var(so[q][k] * S[io[q][k]]);
+            }
+          }
+        }
+        Adj fh[4], hh[4], mx[4];
+        op.face_flux(dir, Uc, Dc, Oc, Adj(alpha), fh, hh, mx);
+        g.assign(tape().size(), 0.0);
+        for (int k = 0; k < m; ++k) {
+          auto nu = [&](int f) { return (mu_at(muL, f, k, a + 1) - mu_at(muL, f, k, a)) / h; };
+          if (fh[k].id >= 0) g[fh[k].id] += nu(0);
+          if (hh[k].id >= 0) g[hh[k].id] += nu(own);
+          if (c.dim == 2 && mx[k].id >= 0) g[mx[k].id] += nu(other);
+        }
+        adj_sweep(g);
+        for (int q = 0; q < 4; ++q)
+          for (int k = 0; k < m; ++k) {
+            lam[iu[q][k]] += su[q][k] * g[Uc[q][k].id];
+            lam[id[q][k]] += sd[q][k] * g[Dc[q][k].id];
+            if (c.dim == 2) lam[io[q][k]] += so[q][k] * g[Oc[q][k].id];
+          }
+      }
+      // modified derivative of every cell on the line
+      for (int a = 0; a < nalong; ++a) {
+        tape().clear();
+        Adj Uc[3][4], Dc[3][4], Dt[4];
+        size_t iu[3][4], id[3][4];
+        double su[3][4], sd[3][4];
+        for (int q = 0; q < 3; ++q) {
+          int jj, ii;
+          cell(a - 1 + q, &jj, &ii);
+          for (int k = 0; k < m; ++k) {
+            su[q][k] = source(0, k, jj, ii, &iu[q][k]);
+            sd[q][k] = source(own, k, jj, ii, &id[q][k]);
+            Uc[q][k] = adj_var(su[q][k] * S[iu[q][k]]);
+            Dc[q][k] = adj_var(sd[q][k] * S[id[q][k]]);
+          }
+        }
+        op.modified_derivative(dir, Uc, Dc, Dt);
+        g.assign(tape().size(), 0.0);
+        for (int k = 0; k < m; ++k)
+          if (Dt[k].id >= 0) g[Dt[k].id] += mu_at(muM, own, k, a);
+        adj_sweep(g);
+        for (int q = 0; q < 3; ++q)
+          for (int k = 0; k < m; ++k) {
+            lam[iu[q][k]] += su[q][k] * g[Uc[q][k].id];
+            lam[id[q][k]] += sd[q][k] * g[Dc[q][k].id];
+          }
+      }
+    }
+  }
+  tape().clear();
+}
+
+// Jacobian-vector products of one stage operator at S along delta with alpha fixed.
+inline void stage_jvp(const Cfg& c, const double* S, double ax, double ay, const double* delta, double* jM,
+                      double* jL) {
+  Operator<Dual> op(c);
+  const int ny = c.dim == 2 ? c.ny : 1;
+  const size_t n = (size_t)nfield(c) * ncomp(c) * c.nx * ny;
+  std::vector<Dual> Sd(n), L(n), M(n);
+  for (size_t p = 0; p < n; ++p) Sd[p] = Dual(S[p], delta[p]);
+  op.rhs(Sd.data(), L.data(), M.data(), Dual(ax), Dual(ay));
+  for (size_t p = 0; p < n; ++p) {
+    jM[p] = M[p].d;
+    jL[p] = L[p].d;
+  }
+}
+
+// One SSP-RK3 step with given step size and given LF coefficients per stage
+// (alpha6 = {ax, ay} of stages 1, 2, 3).
+template <class R>
+void rk3_step_alpha(const Cfg& c, R* S, double dt, const double* alpha6) {
+  Operator<R> op(c);
+  const int ny = c.dim == 2 ? c.ny : 1;
+  const size_t n = (size_t)nfield(c) * ncomp(c) * c.nx * ny;
+  std::vector<R> L(n), M(n), B(n);
+  static const double a_k[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0};
+  static const double b_k[3] = {1.0, 1.0 / 4.0, 2.0 / 3.0};
+  for (int st = 0; st < 3; ++st) {
+    op.rhs(S, L.data(), M.data(), R(alpha6[2 * st]), R(alpha6[2 * st + 1]));
+    if (st == 0) {
+      for (size_t p = 0; p < n; ++p) B[p] = M[p];
+      for (size_t p = 0; p < n; ++p) S[p] = M[p] + dt * L[p];
+    } else {
+      for (size_t p = 0; p < n; ++p) S[p] = a_k[st] * B[p] + b_k[st] * (M[p] + dt * L[p]);
+    }
+  }
+}
+
+// Adjoint of one SSP-RK3 step (fixed dt, alpha6 as above): lam_out = (dS^{n+1}/dS^n)^T lam_in.
+inline void adjoint_step(const Cfg& c, const double* Sn, double dt, const double* alpha6, const double* lam_in,
+                         double* lam_out) {
+  Operator<double> op(c);
+  const int ny = c.dim == 2 ? c.ny : 1;
+  const size_t n = (size_t)nfield(c) * ncomp(c) * c.nx * ny;
+  std::vector<double> L(n), M(n), B(n), S1(n), S2(n);
+  // forward stages, keeping the stage inputs
+  op.rhs(Sn, L.data(), M.data(), alpha6[0], alpha6[1]);
+  for (size_t p = 0; p < n; ++p) {
+    B[p] = M[p];
+    S1[p] = M[p] + dt * L[p];
+  }
+  op.rhs(S1.data(), L.data(), M.data(), alpha6[2], alpha6[3]);
+  for (size_t p = 0; p < n; ++p) S2[p] = (3.0 / 4.0) * B[p] + (1.0 / 4.0) * (M[p] + dt * L[p]);
+  // S^{n+1} = 1/3 B + 2/3 (M(S2) + dt L(S2))
+  std::vector<double> muM(n), muL(n), lam2(n), lam1(n), lamB(n);
+  for (size_t p = 0; p < n; ++p) {
+    muM[p] = (2.0 / 3.0) * lam_in[p];
+    muL[p] = (2.0 / 3.0) * dt * lam_in[p];
+    lamB[p] = (1.0 / 3.0) * lam_in[p];
+  }
+  stage_vjp(c, S2.data(), alpha6[4], alpha6[5], muM.data(), muL.data(), lam2.data());
+  // S2 = 3/4 B + 1/4 (M(S1) + dt L(S1))
+  for (size_t p = 0; p < n; ++p) {
+    muM[p] = (1.0 / 4.0) * lam2[p];
+    muL[p] = (1.0 / 4.0) * dt * lam2[p];
+    lamB[p] += (3.0 / 4.0) * lam2[p];
+  }
+  stage_vjp(c, S1.data(), alpha6[2], alpha6[3], muM.data(), muL.data(), lam1.data());
+  // S1 = M(S^n) + dt L(S^n), B = M(S^n)
+  for (size_t p = 0; p < n; ++p) {
+    muM[p] = lam1[p] + lamB[p];
+    muL[p] = dt * lam1[p];
+  }
+  stage_vjp(c, Sn, alpha6[0], alpha6[1], muM.data(), muL.data(), lam_out);
+}
+
 }  // namespace hwo
 
 // =============================================================================================
@@ -905,6 +1178,65 @@ int oracle_count_flops(const oracle_cfg* c, long long* out) {
   out[4] = upd;
   out[5] = 3 * (dim * (out[0] + out[1] + out[2] + out[3]) + upd);
   n = 0;
+  return 0;
+}
+
+// ---- derivatives (adjoint conventions: fixed dt and alpha per stage) ----
+
+int oracle_stage_vjp(const oracle_cfg* c, const double* S, double ax, double ay, const double* muM,
+                     const double* muL, double* lam) {
+  if (check_cfg(c)) return -1;
+  hwo::stage_vjp(*c, S, ax, ay, muM, muL, lam);
+  return 0;
+}
+
+int oracle_stage_jvp(const oracle_cfg* c, const double* S, double ax, double ay, const double* delta, double* jM,
+                     double* jL) {
+  if (check_cfg(c)) return -1;
+  hwo::stage_jvp(*c, S, ax, ay, delta, jM, jL);
+  return 0;
+}
+
+// nsteps CFL steps recording dt (dts[nsteps]) and alpha of every stage (alphas[nsteps][6])
+int oracle_steps_record(const oracle_cfg* c, double* S, int nsteps, double cfl, double* dts, double* alphas) {
+  if (check_cfg(c) || nsteps < 0) return -1;
+  hwo::Operator<double> op(*c);
+  const int ny = c->dim == 2 ? c->ny : 1;
+  const size_t n = (size_t)hwo::nfield(*c) * hwo::ncomp(*c) * c->nx * ny;
+  std::vector<double> L(n), M(n), B(n);
+  static const double a_k[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0};
+  static const double b_k[3] = {1.0, 1.0 / 4.0, 2.0 / 3.0};
+  for (int s = 0; s < nsteps; ++s) {
+    const double dt = hwo::cfl_dt(*c, S, cfl, 1.0);
+    dts[s] = dt;
+    for (int st = 0; st < 3; ++st) {
+      const double ax = op.max_wavespeed(0, S);
+      const double ay = c->dim == 2 ? op.max_wavespeed(1, S) : 0.0;
+      alphas[6 * s + 2 * st] = ax;
+      alphas[6 * s + 2 * st + 1] = ay;
+      op.rhs(S, L.data(), M.data(), ax, ay);
+      if (st == 0) {
+        for (size_t p = 0; p < n; ++p) B[p] = M[p];
+        for (size_t p = 0; p < n; ++p) S[p] = M[p] + dt * L[p];
+      } else {
+        for (size_t p = 0; p < n; ++p) S[p] = a_k[st] * B[p] + b_k[st] * (M[p] + dt * L[p]);
+      }
+    }
+  }
+  return 0;
+}
+
+// nsteps steps with the recorded dts and alphas
+int oracle_steps_replay(const oracle_cfg* c, double* S, int nsteps, const double* dts, const double* alphas) {
+  if (check_cfg(c) || nsteps < 0) return -1;
+  for (int s = 0; s < nsteps; ++s) hwo::rk3_step_alpha(*c, S, dts[s], alphas + 6 * s);
+  return 0;
+}
+
+int oracle_adjoint_step(const oracle_cfg* c, const double* Sn, double dt, const double* alpha6, const double* lam_in,
+                        double* lam_out) {
+  if (check_cfg(c)) return -1;
+  hwo::adjoint_step(*c, Sn, dt, alpha6, lam_in, lam_out);
   return 0;
 }
 
