@@ -141,6 +141,41 @@ const char *hweno_strerror(int status);
 long long hweno_launch_count(const hweno_t *h);
 
 /* ---------------------------------------------------------------------------------------------
+ * Adjoint (Euler, 1D and 2D; periodic or transmissive).  Not in the paper: derivatives of the
+ * scheme above for gradient-based use.  Conventions: the step size and the LF coefficient alpha
+ * of every stage are held at the values recorded in the forward pass (the derivative of the
+ * CFL rule and of the wavespeed maximum is not taken); d|x|/dx = sign(x) with sign(0) = 0 in the
+ * nonlinear weights (Eq. nonlinear).  Everything else -- smoothness indicators, weights, the
+ * characteristic projections with their Roe-averaged eigenvectors, fluxes, D-terms, mixed
+ * fluxes, modified derivatives -- is differentiated exactly.  All arrays are device arrays in
+ * the state layout unless stated; alpha arrays hold {alpha_x, alpha_y} per stage. */
+
+/* Device workspace of the adjoint entry points (7 states, per-face and per-cell contributions). */
+size_t hweno_adjoint_workspace_bytes(const hweno_t *h);
+
+/* Record of the last hweno_step: rec7_dev[0] = dt, rec7_dev[1..6] = alpha of stages 1, 2, 3
+ * (device to device copy on the stream; no synchronisation). */
+int hweno_step_record(hweno_t *h, double *rec7_dev);
+
+/* One SSP-RK3 step of the bound state with the given dt (> 0) and per-stage alpha6_dev instead of
+ * the wavespeeds of the stage inputs (replay of a recorded step, as the adjoint assumes). */
+int hweno_step_replay(hweno_t *h, double dt, const double *alpha6_dev);
+
+/* lam_out = (dS^{n+1} / dS^n)^T lam_in for one SSP-RK3 step from S_n_dev with dt and alpha6_dev
+ * (Eqs. fully-hweno / 2Dfully-hweno transposed: the three stage operators' vector-Jacobian
+ * products in reverse order, the stage inputs recomputed from S^n).  Uses the bound workspace as
+ * scratch (its stage base and wavespeed slots are overwritten; the bound state and time are not)
+ * and adj_ws_dev (hweno_adjoint_workspace_bytes, 256-byte aligned).  S_n, lam_in and lam_out must
+ * not alias each other.  EINVAL for scalar systems, reflective walls or dt <= 0. */
+int hweno_adjoint_step(hweno_t *h, const double *S_n_dev, double dt, const double *alpha6_dev,
+                       const double *lam_in_dev, double *lam_out_dev, void *adj_ws_dev);
+
+/* lam = (dM/dS)^T muM + (dL/dS)^T muL at S with alpha2_dev held fixed: the transpose of one
+ * evaluation of hweno_rhs (the building block of hweno_adjoint_step). */
+int hweno_stage_vjp(hweno_t *h, const double *S_dev, const double *alpha2_dev, const double *muM_dev,
+                    const double *muL_dev, double *lam_dev, void *adj_ws_dev);
+
+/* ---------------------------------------------------------------------------------------------
  * Batched problems (not in the paper: many independent Euler problems of uneven sizes advanced
  * together).  Every instance is an independent HWENO-I problem exactly as above (its own grid,
  * boundary, wavespeeds and CFL step); the batch only changes how the work is launched:

@@ -40,6 +40,11 @@ SIGNATURES = {
     "hweno_kernel_times": (_I, [_H, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)]),
     "hweno_selftest_rcp": (_I, [_P, _P, ctypes.c_int64, _P]),
     "hweno_rhs_static": (_I, [_I, _I, ctypes.c_int64, ctypes.c_int64, _D, _D, _D, _I, _P, _P, _P, _P, _P]),
+    "hweno_adjoint_workspace_bytes": (ctypes.c_size_t, [_H]),
+    "hweno_step_record": (_I, [_H, _P]),
+    "hweno_step_replay": (_I, [_H, _D, _P]),
+    "hweno_adjoint_step": (_I, [_H, _P, _D, _P, _P, _P, _P]),
+    "hweno_stage_vjp": (_I, [_H, _P, _P, _P, _P, _P, _P]),
     "hweno_batch_create": (_I, [_I, _P, ctypes.POINTER(_H)]),
     "hweno_batch_set_stream": (_I, [_H, _P]),
     "hweno_batch_state_doubles": (ctypes.c_size_t, [_H]),

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libhweno.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
-SOURCES = ["hweno_api.cu", "hweno_batch.cu"]
+SOURCES = ["hweno_api.cu", "hweno_batch.cu", "hweno_adjoint.cu"]
 
 
 def _nvcc() -> str:

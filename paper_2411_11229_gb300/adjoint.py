@@ -1,0 +1,68 @@
+"""Differentiable time stepping: a torch.autograd.Function around the C ABI.
+
+The forward pass advances the state with CFL steps (dt on the device) and records dt and the LF
+coefficients of every stage; the backward pass applies the hand-written adjoint step
+(hweno_adjoint_step) in reverse, with the derivative taken at the recorded dt and alphas.
+States are checkpointed every `every` steps in device memory; within a segment the states are
+recomputed from its checkpoint by replaying the recorded steps.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from .solver import Solver
+
+
+class Rollout(torch.autograd.Function):
+    """S0 -> state after nsteps steps.  Arguments: S0 (device tensor in the state layout), the
+    Solver, nsteps, checkpoint interval."""
+
+    @staticmethod
+    def forward(ctx, S0: torch.Tensor, solver: Solver, nsteps: int, every: int):
+        every = max(1, int(every))
+        with torch.cuda.stream(solver.stream):
+            solver.state.copy_(S0.reshape(solver.state.shape))
+        solver.set_time(0.0, 0.0)
+        rec = torch.empty((nsteps, 7), dtype=torch.float64, device=solver.device)
+        checkpoints = []
+        for s in range(nsteps):
+            if s % every == 0:
+                checkpoints.append(solver.state.clone())
+            solver.step(0.0)
+            solver.record(rec[s])
+        solver.sync()
+        ctx.solver, ctx.rec, ctx.checkpoints, ctx.every, ctx.nsteps = solver, rec, checkpoints, every, nsteps
+        ctx.dts = rec[:, 0].cpu().numpy()
+        return solver.state.clone().reshape(S0.shape)
+
+    @staticmethod
+    def backward(ctx, lam_T: torch.Tensor):
+        solver, rec, every, nsteps, dts = ctx.solver, ctx.rec, ctx.every, ctx.nsteps, ctx.dts
+        lam = lam_T.contiguous().reshape(solver.state.shape).clone()
+        nseg = (nsteps + every - 1) // every
+        for seg in range(nseg - 1, -1, -1):
+            s0, s1 = seg * every, min((seg + 1) * every, nsteps)
+            states = [ctx.checkpoints[seg]]
+            with torch.cuda.stream(solver.stream):
+                solver.state.copy_(states[0])
+            for s in range(s0, s1 - 1):
+                solver.step_replay(float(dts[s]), rec[s, 1:])
+                states.append(solver.state.clone())
+            for s in range(s1 - 1, s0 - 1, -1):
+                lam = solver.adjoint_step(states[s - s0], float(dts[s]), rec[s, 1:].contiguous(), lam)
+        return lam.reshape(lam_T.shape), None, None, None
+
+
+def rollout(S0: torch.Tensor, solver: Solver, nsteps: int, every: int = 20) -> torch.Tensor:
+    return Rollout.apply(S0, solver, nsteps, every)
+
+
+def replay(S0: torch.Tensor, solver: Solver, dts: np.ndarray, rec: torch.Tensor) -> torch.Tensor:
+    """The forward pass again with the recorded dts and alphas (no gradient)."""
+    with torch.cuda.stream(solver.stream):
+        solver.state.copy_(S0.reshape(solver.state.shape))
+    for s in range(len(dts)):
+        solver.step_replay(float(dts[s]), rec[s, 1:])
+    solver.sync()
+    return solver.state.clone()

@@ -1,0 +1,612 @@
+// Adjoint of one SSP-RK3 step of the Euler equations (1D and 2D), hand-written: see
+// include/hweno.h (hweno_adjoint_step) for the contract.
+//
+// The vector-Jacobian product of one stage operator, lam = (dM/dS)^T muM + (dL/dS)^T muL at a
+// stage input S with alpha fixed, is the transpose of the forward kernels:
+//   k_adj_cell   per cell and direction: backward of the modified derivative (Eq. limiter in the
+//                cell's characteristic fields): contributions to U of cells i-1..i+1 and to the
+//                derivative of cells i-1, i+1;
+//   k_adj_face   per face: recomputes the face and back-propagates the flux adjoint
+//                nu = (muL[right cell] - muL[left cell]) / h through the LF fluxes at U^+-, the
+//                back projection, the HWENO weights and smoothness indicators, the projections,
+//                the eigenvectors and the Roe average: contributions to U and to the derivative
+//                of the four cells of the face;
+//   k_adj_gather per cell: collects those contributions, applies the transposes of the (linear)
+//                D-terms and mixed fluxes to the flux adjoints and the nodal flux VJPs, and adds
+//                the identity part of M.
+// Contributions are stored per face / per cell and gathered (no atomics: deterministic).
+#include "hweno_adjoint.cuh"
+#include "hweno_host.cuh"
+
+using namespace hwh;
+
+namespace hw {
+
+struct AdjWork {
+  double* CU;  // face contributions to U: [dir][face][4 cells][NC] (original frame)
+  double* CD;  // face contributions to the own-direction derivative, same layout
+  double* CM;  // modified-derivative contributions: [dir][cell][3 U + 2 D][NC] (original frame)
+};
+
+template <int DIM>
+__device__ __forceinline__ long long nfaces_dir(const Grid& g, int dir) {
+  return dir == 0 ? (long long)(g.nx + 1) * g.ny : (long long)(g.ny + 1) * g.nx;
+}
+
+// -------------------------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __restrict__ S, const double* __restrict__ muM,
+                                                       AdjWork aw) {
+  constexpr int NC = DIM == 1 ? 3 : 4;
+  const int d = blockIdx.y;
+  const long long plane = g.plane;
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (p >= plane) return;
+  const int i = (int)(p % g.nx), j = (int)(p / g.nx);
+  const int n = d == 0 ? g.nx : g.ny;
+  const int a0 = d == 0 ? i : j;
+  const int fld = d == 0 ? 1 : 2;
+  const double h = g.h[d], ih = g.ih[d];
+  double U3[3][NC], hD3[3][NC];
+  long long pc[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int ac = bc_index(a0 - 1 + q, n, g.bc);
+    pc[q] = d == 0 ? (long long)j * g.nx + ac : (long long)ac * g.nx + i;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      U3[q][k] = S[k * plane + pc[q]];
+      hD3[q][k] = h * S[(fld * NC + k) * plane + pc[q]];
+    }
+    if (d == 1) {
+      swap_frame<NC>(U3[q]);
+      swap_frame<NC>(hD3[q]);
+    }
+  }
+  // forward: eigenvectors of the cell's own state
+  const Prim<NC> pr = prim_of<NC>(U3[1], g.gm1);
+  const double H = (U3[1][NC - 1] + pr.p) * pr.ir;
+  const double c2 = g.gamma * pr.p * pr.ir;
+  const double ic = rsqrt(c2);
+  const double c = c2 * ic;
+  Eig<NC> e;
+  e.setup(pr.u, pr.v, H, c, ic, g.gm1);
+  double W[3][NC], Zm[NC], Zp[NC], ht[NC];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) e.project(U3[q], W[q]);
+  e.project(hD3[0], Zm);
+  e.project(hD3[2], Zp);
+#pragma unroll
+  for (int s = 0; s < NC; ++s) ht[s] = cell_field(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], g) * ih;
+  // backward from the adjoint of the modified derivative of this cell
+  double ob[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) ob[k] = muM[(fld * NC + k) * plane + p];
+  if (d == 1) swap_frame<NC>(ob);
+  EigBar eb = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double hq2b = 0.0, ucb = 0.0, hb1b = 0.0, hb2b = 0.0, hicb = 0.0;
+  double htb[NC];
+#pragma unroll
+  for (int s = 0; s < NC; ++s) htb[s] = 0.0;
+  back_bwd<NC>(e, ht, ob, htb, hq2b, ucb, eb);
+  double Wb[3][NC], Zmb[NC], Zpb[NC];
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    Wb[0][s] = Wb[1][s] = Wb[2][s] = 0.0;
+    Zmb[s] = Zpb[s] = 0.0;
+  }
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    double wb[3] = {0.0, 0.0, 0.0};
+    cell_field_bwd(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], g, htb[s] * ih, wb, Zmb[s], Zpb[s]);
+    Wb[0][s] = wb[0];
+    Wb[1][s] = wb[1];
+    Wb[2][s] = wb[2];
+  }
+  double Ub[3][NC], hDmb[NC], hDpb[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    Ub[0][k] = Ub[1][k] = Ub[2][k] = 0.0;
+    hDmb[k] = hDpb[k] = 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) project_bwd<NC>(e, U3[q], Wb[q], Ub[q], hb1b, hb2b, hicb, eb);
+  project_bwd<NC>(e, hD3[0], Zmb, hDmb, hb1b, hb2b, hicb, eb);
+  project_bwd<NC>(e, hD3[2], Zpb, hDpb, hb1b, hb2b, hicb, eb);
+  setup_bwd<NC>(e, g.gm1, ic, hb1b, hb2b, hicb, hq2b, ucb, eb);
+  // c = sqrt(c2), ic = 1/sqrt(c2), c2 = gamma p ir, H = (E + p) ir
+  const double c2b = 0.5 * ic * (eb.c - eb.ic * ic * ic);
+  double pb = c2b * g.gamma * pr.ir + eb.H * pr.ir;
+  double irb = c2b * g.gamma * pr.p + eb.H * (U3[1][NC - 1] + pr.p);
+  Ub[1][NC - 1] += eb.H * pr.ir;
+  prim_bwd<NC>(U3[1], pr, g.gm1, irb, eb.u, eb.v, pb, Ub[1]);
+  // store (original frame): 3 U contributions, then h * (derivative adjoints) of cells i-1, i+1
+  double* out = aw.CM + ((long long)d * plane + p) * 5 * NC;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (d == 1) swap_frame<NC>(Ub[q]);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) out[q * NC + k] = Ub[q][k];
+  }
+  if (d == 1) {
+    swap_frame<NC>(hDmb);
+    swap_frame<NC>(hDpb);
+  }
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    out[3 * NC + k] = h * hDmb[k];
+    out[4 * NC + k] = h * hDpb[k];
+  }
+}
+
+// -------------------------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __restrict__ S, const double* __restrict__ muL,
+                                                       AdjWork aw, const double* __restrict__ alpha2) {
+  constexpr int NC = DIM == 1 ? 3 : 4;
+  const int dir = blockIdx.y;
+  const long long plane = g.plane;
+  const int n = dir == 0 ? g.nx : g.ny;
+  const int nlines = dir == 0 ? g.ny : g.nx;
+  const long long f = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (f >= (long long)(n + 1) * nlines) return;
+  int fa, line;
+  if (dir == 0) {
+    line = (int)(f / (n + 1));
+    fa = (int)(f % (n + 1));
+  } else {
+    fa = (int)(f / g.nx);
+    line = (int)(f % g.nx);
+  }
+  long long pc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int a = bc_index(fa - 2 + q, n, g.bc);
+    pc[q] = dir == 0 ? (long long)line * g.nx + a : (long long)a * g.nx + line;
+  }
+  const int fown = dir == 0 ? 1 : 2;
+  const double h = g.h[dir], ih = g.ih[dir];
+  const double alpha = alpha2[dir];
+  double Uq[4][NC], Zq[4][NC];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      Uq[q][k] = S[k * plane + pc[q]];
+      Zq[q][k] = h * S[(fown * NC + k) * plane + pc[q]];
+    }
+    if (dir == 1) {
+      swap_frame<NC>(Uq[q]);
+      swap_frame<NC>(Zq[q]);
+    }
+  }
+  // adjoints of the face fluxes of U and of the own derivative (normal frame)
+  double nuf[NC], nuh[NC];
+  {
+    const bool hasL = fa - 1 >= 0, hasR = fa <= n - 1;
+    const long long cL = dir == 0 ? (long long)line * g.nx + (fa - 1) : (long long)(fa - 1) * g.nx + line;
+    const long long cR = dir == 0 ? (long long)line * g.nx + fa : (long long)fa * g.nx + line;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      const double rf = hasR ? muL[k * plane + cR] : 0.0, lf = hasL ? muL[k * plane + cL] : 0.0;
+      const double rh = hasR ? muL[(fown * NC + k) * plane + cR] : 0.0;
+      const double lh = hasL ? muL[(fown * NC + k) * plane + cL] : 0.0;
+      nuf[k] = (rf - lf) * ih;
+      nuh[k] = (rh - lh) * ih;
+    }
+    if (dir == 1) {
+      swap_frame<NC>(nuf);
+      swap_frame<NC>(nuh);
+    }
+  }
+  // ---- forward recomputation
+  const Prim<NC> pl = prim_of<NC>(Uq[1], g.gm1), prr = prim_of<NC>(Uq[2], g.gm1);
+  const double sl = sqrt(Uq[1][0]), sr = sqrt(Uq[2][0]);
+  const double Hl = (Uq[1][NC - 1] + pl.p) * pl.ir, Hr = (Uq[2][NC - 1] + prr.p) * prr.ir;
+  const double iw = rcp(sl + sr);
+  const double ub = fma(sl, pl.u, sr * prr.u) * iw;
+  const double vb = NC == 4 ? fma(sl, pl.v, sr * prr.v) * iw : 0.0;
+  const double Hb = fma(sl, Hl, sr * Hr) * iw;
+  const double c2 = g.gm1 * fma(-0.5, NC == 4 ? fma(ub, ub, vb * vb) : ub * ub, Hb);
+  const double ic = rsqrt(c2);
+  Eig<NC> e;
+  e.setup(ub, vb, Hb, c2 * ic, ic, g.gm1);
+  double Wq[4][NC], Yq[4][NC];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    e.project(Uq[q], Wq[q]);
+    e.project(Zq[q], Yq[q]);
+  }
+  double cm[NC], chm[NC], cp[NC], chp[NC];
+#pragma unroll
+  for (int s = 0; s < NC; ++s)
+    face_field(Wq[0][s], Wq[1][s], Wq[2][s], Wq[3][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, cm[s], chm[s],
+               cp[s], chp[s]);
+  double Um[NC], Up[NC], Dm[NC], Dp[NC];
+  e.back(cm, Um);
+  e.back(cp, Up);
+  e.back(chm, Dm);
+  e.back(chp, Dp);
+  // ---- backward: fh = (FUm + FUp - alpha (Up - Um)) / 2 + Df, hh = hih (HDm + HDp - alpha (Dp - Dm)) + Dh
+  double Umb[NC], Upb[NC], Dmb[NC], Dpb[NC], Fb[NC], Hb2[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    Umb[k] = 0.5 * alpha * nuf[k];
+    Upb[k] = -0.5 * alpha * nuf[k];
+    Dmb[k] = g.hih[dir] * alpha * nuh[k];
+    Dpb[k] = -g.hih[dir] * alpha * nuh[k];
+    Fb[k] = 0.5 * nuf[k];
+    Hb2[k] = g.hih[dir] * nuh[k];
+  }
+  flux_bwd<NC>(Um, g.gm1, Fb, Umb);
+  flux_bwd<NC>(Up, g.gm1, Fb, Upb);
+  jvp_bwd<NC>(Um, Dm, g.gm1, Hb2, Umb, Dmb);
+  jvp_bwd<NC>(Up, Dp, g.gm1, Hb2, Upb, Dpb);
+  EigBar eb = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double hq2b = 0.0, ucb = 0.0, hb1b = 0.0, hb2b = 0.0, hicb = 0.0;
+  double cmb[NC], cpb[NC], chmb[NC], chpb[NC];
+#pragma unroll
+  for (int s = 0; s < NC; ++s) cmb[s] = cpb[s] = chmb[s] = chpb[s] = 0.0;
+  back_bwd<NC>(e, cm, Umb, cmb, hq2b, ucb, eb);
+  back_bwd<NC>(e, cp, Upb, cpb, hq2b, ucb, eb);
+  back_bwd<NC>(e, chm, Dmb, chmb, hq2b, ucb, eb);
+  back_bwd<NC>(e, chp, Dpb, chpb, hq2b, ucb, eb);
+  double Wb[4][NC], Yb[4][NC];
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    double wb[4] = {0.0, 0.0, 0.0, 0.0}, yb[4] = {0.0, 0.0, 0.0, 0.0};
+    face_field_bwd(Wq[0][s], Wq[1][s], Wq[2][s], Wq[3][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, cmb[s],
+                   chmb[s], cpb[s], chpb[s], wb, yb);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      Wb[q][s] = wb[q];
+      Yb[q][s] = yb[q];
+    }
+  }
+  double Uqb[4][NC], Zqb[4][NC];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) Uqb[q][k] = Zqb[q][k] = 0.0;
+    project_bwd<NC>(e, Uq[q], Wb[q], Uqb[q], hb1b, hb2b, hicb, eb);
+    project_bwd<NC>(e, Zq[q], Yb[q], Zqb[q], hb1b, hb2b, hicb, eb);
+  }
+  setup_bwd<NC>(e, g.gm1, ic, hb1b, hb2b, hicb, hq2b, ucb, eb);
+  // c = sqrt(c2), ic = 1/sqrt(c2); c2 = gm1 (Hb - (ub^2 + vb^2)/2)
+  const double c2b = 0.5 * ic * (eb.c - eb.ic * ic * ic);
+  const double Hbb = eb.H + g.gm1 * c2b;
+  const double ubb = eb.u - g.gm1 * ub * c2b;
+  const double vbb = eb.v - g.gm1 * vb * c2b;
+  // Roe average: x_b = (sl x_l + sr x_r) iw for x in (u, v, H)
+  const double iwb = ubb * fma(sl, pl.u, sr * prr.u) + (NC == 4 ? vbb * fma(sl, pl.v, sr * prr.v) : 0.0) +
+                     Hbb * fma(sl, Hl, sr * Hr);
+  const double slb = iw * (ubb * pl.u + (NC == 4 ? vbb * pl.v : 0.0) + Hbb * Hl) - iwb * iw * iw;
+  const double srb = iw * (ubb * prr.u + (NC == 4 ? vbb * prr.v : 0.0) + Hbb * Hr) - iwb * iw * iw;
+  // cells 1 and 2: sqrt(rho), u, v, H = (E + p) ir
+  {
+    const double Hlb = Hbb * sl * iw;
+    Uqb[1][0] += slb * 0.5 / sl;
+    Uqb[1][NC - 1] += Hlb * pl.ir;
+    prim_bwd<NC>(Uq[1], pl, g.gm1, Hlb * (Uq[1][NC - 1] + pl.p), ubb * sl * iw, vbb * sl * iw, Hlb * pl.ir, Uqb[1]);
+    const double Hrb = Hbb * sr * iw;
+    Uqb[2][0] += srb * 0.5 / sr;
+    Uqb[2][NC - 1] += Hrb * prr.ir;
+    prim_bwd<NC>(Uq[2], prr, g.gm1, Hrb * (Uq[2][NC - 1] + prr.p), ubb * sr * iw, vbb * sr * iw, Hrb * prr.ir,
+                 Uqb[2]);
+  }
+  // store (original frame); the derivative contributions carry the factor h of Z = h D
+  const long long fo = dir == 0 ? (long long)line * (g.nx + 1) + fa : (long long)fa * g.nx + line;
+  const long long base = ((dir == 0 ? 0 : (long long)(g.nx + 1) * g.ny) + fo) * 4 * NC;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (dir == 1) {
+      swap_frame<NC>(Uqb[q]);
+      swap_frame<NC>(Zqb[q]);
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      aw.CU[base + q * NC + k] = Uqb[q][k];
+      aw.CD[base + q * NC + k] = h * Zqb[q][k];
+    }
+  }
+}
+
+// -------------------------------------------------------------------------------------------
+// aliases of cell a (0 <= a < n) among the unmapped indices -2 .. n+1 of the stencils
+__device__ __forceinline__ int aliases(int a, int n, int bc, int* x) {
+  int k = 0;
+  x[k++] = a;
+  if (bc == BC_PERIODIC) {
+    if (a + n <= n + 1) x[k++] = a + n;
+    if (a - n >= -2) x[k++] = a - n;
+  } else {
+    if (a == 0) {
+      x[k++] = -1;
+      x[k++] = -2;
+    }
+    if (a == n - 1) {
+      x[k++] = n;
+      x[k++] = n + 1;
+    }
+  }
+  return k;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_adj_gather(Grid g, const double* __restrict__ S,
+                                                         const double* __restrict__ muM, const double* __restrict__ muL,
+                                                         AdjWork aw, double* __restrict__ lam) {
+  constexpr int NC = DIM == 1 ? 3 : 4;
+  constexpr int NF = DIM + 1;
+  const long long plane = g.plane;
+  const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (p >= plane) return;
+  const int i = (int)(p % g.nx), j = (int)(p / g.nx);
+  double lb[NF][NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    lb[0][k] = muM[k * plane + p];  // M = (U, ...): identity part
+#pragma unroll
+    for (int f = 1; f < NF; ++f) lb[f][k] = 0.0;
+  }
+  double U[NC], V[NF - 1][NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    U[k] = S[k * plane + p];
+#pragma unroll
+    for (int f = 1; f < NF; ++f) V[f - 1][k] = S[(f * NC + k) * plane + p];
+  }
+  const long long oplx = (long long)g.ny * (g.nx + 1);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int n = d == 0 ? g.nx : g.ny;
+    const int a0 = d == 0 ? i : j;
+    const int fown = d == 0 ? 1 : 2, foth = d == 0 ? 2 : 1;
+    const double ih = g.ih[d];
+    int xs[3];
+    const int nx_ = aliases(a0, n, g.bc, xs);
+    double nf[NC], nh[NC], no[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) nf[k] = nh[k] = no[k] = 0.0;
+    for (int t = 0; t < nx_; ++t) {
+      const int x = xs[t];
+      // faces fa = x + 2 - q hold this cell at position q
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int fa = x + 2 - q;
+        if (fa < 0 || fa > n) continue;
+        const int line = d == 0 ? j : i;
+        const long long fo = d == 0 ? (long long)line * (g.nx + 1) + fa : (long long)fa * g.nx + line;
+        const long long base = ((d == 0 ? 0 : oplx) + fo) * 4 * NC + q * NC;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          lb[0][k] += aw.CU[base + k];
+          lb[fown][k] += aw.CD[base + k];
+        }
+        // flux adjoints of this face, for the nodal values (D-terms, mixed flux)
+        const bool hasL = fa - 1 >= 0, hasR = fa <= n - 1;
+        const long long cL = d == 0 ? (long long)line * g.nx + (fa - 1) : (long long)(fa - 1) * g.nx + line;
+        const long long cR = d == 0 ? (long long)line * g.nx + fa : (long long)fa * g.nx + line;
+        const double s1 = (q == 0 || q == 3) ? DCoef::cf : -DCoef::cf;
+        const double sdh = q == 0 ? g.efih[d] : (q == 1 ? -g.egih[d] : (q == 2 ? g.egih[d] : -g.efih[d]));
+        const double th = q == 0 ? g.chh[d] : (q == 3 ? -g.chh[d] : 0.0);
+        const double th2 = (q == 0 || q == 3) ? DCoef::eh : 0.0;
+        const double mq = (q == 1 || q == 2) ? 7.0 / 12.0 : -1.0 / 12.0;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          auto nu = [&](int fld) {
+            const double r = hasR ? muL[(fld * NC + k) * plane + cR] : 0.0;
+            const double l = hasL ? muL[(fld * NC + k) * plane + cL] : 0.0;
+            return (r - l) * ih;
+          };
+          const double nfh = nu(0), nhh = nu(fown);
+          nf[k] = fma(s1, nfh, fma(sdh, nhh, nf[k]));
+          nh[k] = fma(th, nfh, fma(th2, nhh, nh[k]));
+          if (DIM == 2) no[k] = fma(mq, nu(foth), no[k]);
+        }
+      }
+      // modified derivatives of cells c = x + 1 - q hold this cell at stencil position q
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int c = x + 1 - q;
+        if (c < 0 || c > n - 1) continue;
+        const long long pcl = d == 0 ? (long long)j * g.nx + c : (long long)c * g.nx + i;
+        const double* cm = aw.CM + ((long long)d * plane + pcl) * 5 * NC;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) lb[0][k] += cm[q * NC + k];
+        if (q == 0) {
+#pragma unroll
+          for (int k = 0; k < NC; ++k) lb[fown][k] += cm[3 * NC + k];
+        } else if (q == 2) {
+#pragma unroll
+          for (int k = 0; k < NC; ++k) lb[fown][k] += cm[4 * NC + k];
+        }
+      }
+    }
+    // nodal VJPs at this cell (normal frame): f(U), A(U) D_own, A(U) D_other
+    double Un[NC], Dn[NC], On[NC], Ub[NC], Db[NC], Ob[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      Un[k] = U[k];
+      Dn[k] = V[fown - 1][k];
+      On[k] = DIM == 2 ? V[foth - 1][k] : 0.0;
+      Ub[k] = Db[k] = Ob[k] = 0.0;
+    }
+    if (d == 1) {
+      swap_frame<NC>(Un);
+      swap_frame<NC>(Dn);
+      swap_frame<NC>(On);
+      swap_frame<NC>(nf);
+      swap_frame<NC>(nh);
+      swap_frame<NC>(no);
+    }
+    flux_bwd<NC>(Un, g.gm1, nf, Ub);
+    jvp_bwd<NC>(Un, Dn, g.gm1, nh, Ub, Db);
+    if (DIM == 2) jvp_bwd<NC>(Un, On, g.gm1, no, Ub, Ob);
+    if (d == 1) {
+      swap_frame<NC>(Ub);
+      swap_frame<NC>(Db);
+      swap_frame<NC>(Ob);
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      lb[0][k] += Ub[k];
+      lb[fown][k] += Db[k];
+      if (DIM == 2) lb[foth][k] += Ob[k];
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) lam[(f * NC + k) * plane + p] = lb[f][k];
+}
+
+// out = c1 x1 + c2 x2 + c3 x3 (x2, x3 may be null)
+__global__ void k_lincomb(long long n, double* __restrict__ out, double c1, const double* __restrict__ x1, double c2,
+                          const double* __restrict__ x2, double c3, const double* __restrict__ x3) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = c1 * x1[i];
+  if (x2) v = fma(c2, x2[i], v);
+  if (x3) v = fma(c3, x3[i], v);
+  out[i] = v;
+}
+
+}  // namespace hw
+
+namespace {
+
+struct AdjLayout {
+  size_t S1, S2, lam2, lam1, lamB, muM, muL, CU, CD, CM, total;
+};
+
+AdjLayout adj_layout(const hweno_ctx* h) {
+  const size_t nst = hweno_state_doubles(h) * 8;
+  const size_t nc = nc_of(h);
+  const size_t nfx = (size_t)(h->nx + 1) * h->ny, nfy = h->dim == 2 ? (size_t)(h->ny + 1) * h->nx : 0;
+  AdjLayout l;
+  l.S1 = l.S2 = l.lam2 = l.lam1 = l.lamB = l.muM = l.muL = align_up(nst);
+  l.CU = l.CD = align_up((nfx + nfy) * 4 * nc * 8);
+  l.CM = align_up((size_t)h->dim * h->nx * h->ny * 5 * nc * 8);
+  l.total = 7 * l.S1 + l.CU + l.CD + l.CM;
+  return l;
+}
+
+struct AdjPtrs {
+  double *S1, *S2, *lam2, *lam1, *lamB, *muM, *muL;
+  hw::AdjWork aw;
+};
+
+AdjPtrs adj_ptrs(const hweno_ctx* h, void* ws) {
+  const AdjLayout l = adj_layout(h);
+  unsigned char* p = static_cast<unsigned char*>(ws);
+  AdjPtrs a;
+  double** arr[7] = {&a.S1, &a.S2, &a.lam2, &a.lam1, &a.lamB, &a.muM, &a.muL};
+  for (int k = 0; k < 7; ++k) {
+    *arr[k] = reinterpret_cast<double*>(p);
+    p += l.S1;
+  }
+  a.aw.CU = reinterpret_cast<double*>(p);
+  p += l.CU;
+  a.aw.CD = reinterpret_cast<double*>(p);
+  p += l.CD;
+  a.aw.CM = reinterpret_cast<double*>(p);
+  return a;
+}
+
+template <int DIM>
+int stage_vjp(const hweno_ctx* h, const Grid& g, const double* S, const double* alpha2, const double* muM,
+              const double* muL, const hw::AdjWork& aw, double* lam) {
+  const cudaStream_t st = h->stream;
+  const unsigned bc = blocks_for(g.plane);
+  hw::k_adj_cell<DIM><<<dim3(bc, DIM), hw::kThreads, 0, st>>>(g, S, muM, aw);
+  const long long nfx = (long long)(g.nx + 1) * g.ny;
+  const long long nfy = DIM == 2 ? (long long)(g.ny + 1) * g.nx : 0;
+  hw::k_adj_face<DIM><<<dim3(blocks_for(nfx > nfy ? nfx : nfy), DIM), hw::kThreads, 0, st>>>(g, S, muL, aw, alpha2);
+  hw::k_adj_gather<DIM><<<bc, hw::kThreads, 0, st>>>(g, S, muM, muL, aw, lam);
+  return cudaGetLastError() == cudaSuccess ? HWENO_OK : HWENO_ECUDA;
+}
+
+int lincomb(const hweno_ctx* h, double* out, double c1, const double* x1, double c2, const double* x2, double c3,
+            const double* x3) {
+  const long long n = (long long)hweno_state_doubles(h);
+  hw::k_lincomb<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(n, out, c1, x1, c2, x2, c3, x3);
+  return cudaGetLastError() == cudaSuccess ? HWENO_OK : HWENO_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t hweno_adjoint_workspace_bytes(const hweno_t* h) { return h ? adj_layout(h).total : 0; }
+
+int hweno_adjoint_step(hweno_t* h, const double* Sn, double dt, const double* alpha6, const double* lam_in,
+                       double* lam_out, void* adj_ws) {
+  if (!h || !Sn || !alpha6 || !lam_in || !lam_out || !adj_ws) return HWENO_EINVAL;
+  if (h->system != HWENO_EULER || h->bc == HWENO_BC_REFLECTIVE) return HWENO_EINVAL;
+  if (!(dt > 0.0) || ((uintptr_t)adj_ws & 255)) return HWENO_EINVAL;
+  if (!h->ws) return HWENO_ESTATE;
+  const AdjPtrs a = adj_ptrs(h, adj_ws);
+  const size_t bytes = hweno_state_doubles(h) * 8;
+  const Grid g = grid_of(h);
+  // forward stages 1 and 2 from S^n with the recorded alphas (the forward workspace is scratch)
+  if (cudaMemcpyAsync(a.S1, Sn, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess) return HWENO_ECUDA;
+  int rc = stage_replay(h, a.S1, 0, dt, alpha6);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(a.S2, a.S1, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess) return HWENO_ECUDA;
+  rc = stage_replay(h, a.S2, 1, dt, alpha6 + 2);
+  if (rc) return rc;
+  auto vjp = [&](const double* S, int st, const double* muM, const double* muL, double* lam) {
+    return h->dim == 1 ? stage_vjp<1>(h, g, S, alpha6 + 2 * st, muM, muL, a.aw, lam)
+                       : stage_vjp<2>(h, g, S, alpha6 + 2 * st, muM, muL, a.aw, lam);
+  };
+  // S^{n+1} = 1/3 B + 2/3 (M(S2) + dt L(S2))
+  if ((rc = lincomb(h, a.muM, 2.0 / 3.0, lam_in, 0.0, nullptr, 0.0, nullptr))) return rc;
+  if ((rc = lincomb(h, a.muL, 2.0 / 3.0 * dt, lam_in, 0.0, nullptr, 0.0, nullptr))) return rc;
+  if ((rc = vjp(a.S2, 2, a.muM, a.muL, a.lam2))) return rc;
+  // S2 = 3/4 B + 1/4 (M(S1) + dt L(S1));  lamB = 1/3 lam_in + 3/4 lam2
+  if ((rc = lincomb(h, a.lamB, 1.0 / 3.0, lam_in, 0.75, a.lam2, 0.0, nullptr))) return rc;
+  if ((rc = lincomb(h, a.muM, 0.25, a.lam2, 0.0, nullptr, 0.0, nullptr))) return rc;
+  if ((rc = lincomb(h, a.muL, 0.25 * dt, a.lam2, 0.0, nullptr, 0.0, nullptr))) return rc;
+  if ((rc = vjp(a.S1, 1, a.muM, a.muL, a.lam1))) return rc;
+  // S1 = M(S^n) + dt L(S^n), B = M(S^n)
+  if ((rc = lincomb(h, a.muM, 1.0, a.lam1, 1.0, a.lamB, 0.0, nullptr))) return rc;
+  if ((rc = lincomb(h, a.muL, dt, a.lam1, 0.0, nullptr, 0.0, nullptr))) return rc;
+  if ((rc = vjp(Sn, 0, a.muM, a.muL, lam_out))) return rc;
+  h->launches += 9 + 8;
+  return HWENO_OK;
+}
+
+int hweno_step_replay(hweno_t* h, double dt, const double* alpha6) {
+  if (!h || !alpha6 || !(dt > 0.0)) return HWENO_EINVAL;
+  if (!h->ws || !h->state) return HWENO_ESTATE;
+  for (int st = 0; st < 3; ++st) {
+    int rc = stage(h, h->state, h->state, 0, st, dt, st, nullptr, nullptr, alpha6 + 2 * st);
+    if (rc) return rc;
+  }
+  return HWENO_OK;
+}
+
+int hweno_step_record(hweno_t* h, double* rec7) {
+  if (!h || !rec7) return HWENO_EINVAL;
+  if (!h->ws) return HWENO_ESTATE;
+  // dt of the last step, then the wavespeed slots of its three stages (bit patterns of doubles)
+  if (cudaMemcpyAsync(rec7, h->w.scal, sizeof(double), cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(rec7 + 1, h->w.alpha, 6 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+    return HWENO_ECUDA;
+  return HWENO_OK;
+}
+
+int hweno_stage_vjp(hweno_t* h, const double* S, const double* alpha2, const double* muM, const double* muL,
+                    double* lam, void* adj_ws) {
+  if (!h || !S || !alpha2 || !muM || !muL || !lam || !adj_ws) return HWENO_EINVAL;
+  if (h->system != HWENO_EULER || h->bc == HWENO_BC_REFLECTIVE) return HWENO_EINVAL;
+  if ((uintptr_t)adj_ws & 255) return HWENO_EINVAL;
+  const AdjPtrs a = adj_ptrs(h, adj_ws);
+  const Grid g = grid_of(h);
+  h->launches += 3;
+  return h->dim == 1 ? stage_vjp<1>(h, g, S, alpha2, muM, muL, a.aw, lam)
+                     : stage_vjp<2>(h, g, S, alpha2, muM, muL, a.aw, lam);
+}
+
+}  // extern "C"

@@ -1,0 +1,391 @@
+// Reverse-mode derivatives (hand-written) of the device arithmetic in hweno_math.cuh, for the
+// adjoint of one Runge-Kutta stage.  Conventions: the LF coefficient alpha of every stage and the
+// step size are held fixed; d|x|/dx = sign(x) with sign(0) = 0.  Every backward routine
+// recomputes the forward values it needs from the same inputs and ADDS the adjoints of its
+// inputs to the bar arrays.
+#pragma once
+#include "hweno_kernels.cuh"
+
+namespace hw {
+
+__device__ __forceinline__ double sgn0(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
+
+// beta0 and its inputs: adds to dmb, dpb, ymb, ypb given b0b (adjoint of beta0)
+__device__ __forceinline__ void beta0_bwd(double dm, double dp, double ym, double yp, double b0b, double& dmb,
+                                          double& dpb, double& ymb, double& ypb) {
+  const double du = dm + dp, d2 = dp - dm;
+  const double sv = ym + yp, dv = ym - yp;
+  const double A = fma(-0.1875, sv, 0.6875 * du);
+  const double B = fma(67.0 / 520.0, dv, (197.0 / 260.0) * d2);
+  const double C = sv - du;
+  const double D = fma(2.0, d2, dv);
+  const double Ab = 2.0 * A * b0b;
+  const double Bb = 2.0 * (13.0 / 3.0) * B * b0b;
+  const double Cb = 2.0 * (781.0 / 20.0 / 16.0) * C * b0b;
+  const double Db = 2.0 * (1421461.0 / 2275.0 / 16.0) * D * b0b;
+  const double svb = -0.1875 * Ab + Cb;
+  const double dub = 0.6875 * Ab - Cb;
+  const double dvb = (67.0 / 520.0) * Bb + Db;
+  const double d2b = (197.0 / 260.0) * Bb + 2.0 * Db;
+  dmb += dub - d2b;
+  dpb += dub + d2b;
+  ymb += svb + dvb;
+  ypb += svb - dvb;
+}
+
+// weights: W_l = P + tau Q_l.  Given Wb, adds b0b, b1b, b2b (through tau and e0) and e1b, e2b.
+__device__ __forceinline__ void weights_bwd(double b0, double b1, double b2, double e1, double e2, double eps,
+                                            double W0b, double W1b, double W2b, double& b0b, double& b1b,
+                                            double& b2b, double& e1b, double& e2b) {
+  const double ts = fabs(b0 - b1) + fabs(b0 - b2);
+  const double tau = (0.25 * ts) * ts;
+  const double e0 = b0 + eps;
+  const double Q0 = e1 * e2, Q1 = e0 * e2, Q2 = e0 * e1;
+  const double Pb = W0b + W1b + W2b;
+  const double taub = fma(W0b, Q0, fma(W1b, Q1, W2b * Q2));
+  const double Q0b = fma(W0b, tau, Pb * e0), Q1b = W1b * tau, Q2b = W2b * tau;
+  const double e0b = fma(Pb, Q0, fma(Q1b, e2, Q2b * e1));
+  e1b += fma(Q0b, e2, Q2b * e0);
+  e2b += fma(Q0b, e1, Q1b * e0);
+  const double tsb = 0.5 * ts * taub;
+  const double s1 = sgn0(b0 - b1), s2 = sgn0(b0 - b2);
+  b0b += e0b + tsb * (s1 + s2);
+  b1b -= tsb * s1;
+  b2b -= tsb * s2;
+}
+
+// Backward of face_field: given the adjoints of um, hvm, up, hvp, adds those of w0..w3, y0..y3.
+__device__ __forceinline__ void face_field_bwd(double w0, double w1, double w2, double w3, double y0, double y1,
+                                               double y2, double y3, const Grid& g, double umb, double hvmb,
+                                               double upb, double hvpb, double* wb, double* yb) {
+  const double d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2;
+  const double b01 = d01 * d01, b12 = d12 * d12, b23 = d23 * d23;
+  const double e01 = b01 + g.eps, e12 = b12 + g.eps, e23 = b23 + g.eps;
+  const double pmid = 0.5 * (w1 + w2);
+  double d01b = 0.0, d12b = 0.0, d23b = 0.0, b01b = 0.0, b12b = 0.0, b23b = 0.0, pmidb = 0.0;
+  double e01b = 0.0, e12b = 0.0, e23b = 0.0;
+  double du, sv;
+  {
+    // stencil of cell k (w0, w1, w2)
+    const double b0 = beta0(d01, d12, y0, y2, du, sv);
+    const Wts wt = weights(b0, b01, b12, e01, e12, g.eps);
+    const double r = fma(g.cr[0], w0, fma(g.cr[1], w1, fma(g.cr[2], w2, fma(g.cr[3], y0, g.cr[4] * y2))));
+    const double p1 = fma(-0.5, w0, 1.5 * w1);
+    const double num = fma(wt.W0, r, fma(wt.W1, p1, wt.W2 * pmid));
+    const double den = fma(g.G, wt.W0, wt.W1 + wt.W2);
+    const double inv = rcp(den);
+    const double numb = umb * inv;
+    const double denb = -umb * num * inv * inv;
+    const double W0b = fma(numb, r, denb * g.G), W1b = fma(numb, p1, denb), W2b = fma(numb, pmid, denb);
+    const double rb = numb * wt.W0, p1b = numb * wt.W1;
+    pmidb += numb * wt.W2;
+    double b0b = 0.0;
+    weights_bwd(b0, b01, b12, e01, e12, g.eps, W0b, W1b, W2b, b0b, b01b, b12b, e01b, e12b);
+    beta0_bwd(d01, d12, y0, y2, b0b, d01b, d12b, yb[0], yb[2]);
+    wb[0] += fma(g.cr[0], rb, -0.5 * p1b) + 0.1875 * hvmb;
+    wb[1] += fma(g.cr[1], rb, 1.5 * p1b) - 1.5 * hvmb;
+    wb[2] += g.cr[2] * rb + 1.3125 * hvmb;
+    yb[0] += g.cr[3] * rb + 0.0625 * hvmb;
+    yb[2] += g.cr[4] * rb - 0.1875 * hvmb;
+  }
+  {
+    // stencil of cell k+1 (w1, w2, w3), evaluated at its left face
+    const double b0 = beta0(d12, d23, y1, y3, du, sv);
+    const Wts wt = weights(b0, b12, b23, e12, e23, g.eps);
+    const double r = fma(g.cl[0], w1, fma(g.cl[1], w2, fma(g.cl[2], w3, fma(g.cl[3], y1, g.cl[4] * y3))));
+    const double q1 = fma(-0.5, w3, 1.5 * w2);
+    const double num = fma(wt.W0, r, fma(wt.W2, q1, wt.W1 * pmid));
+    const double den = fma(g.G, wt.W0, wt.W1 + wt.W2);
+    const double inv = rcp(den);
+    const double numb = upb * inv;
+    const double denb = -upb * num * inv * inv;
+    const double W0b = fma(numb, r, denb * g.G), W1b = fma(numb, pmid, denb), W2b = fma(numb, q1, denb);
+    const double rb = numb * wt.W0, q1b = numb * wt.W2;
+    pmidb += numb * wt.W1;
+    double b0b = 0.0;
+    weights_bwd(b0, b12, b23, e12, e23, g.eps, W0b, W1b, W2b, b0b, b12b, b23b, e12b, e23b);
+    beta0_bwd(d12, d23, y1, y3, b0b, d12b, d23b, yb[1], yb[3]);
+    wb[1] += g.cl[0] * rb - 1.3125 * hvpb;
+    wb[2] += fma(g.cl[1], rb, 1.5 * q1b) + 1.5 * hvpb;
+    wb[3] += fma(g.cl[2], rb, -0.5 * q1b) - 0.1875 * hvpb;
+    yb[1] += g.cl[3] * rb - 0.1875 * hvpb;
+    yb[3] += g.cl[4] * rb + 0.0625 * hvpb;
+  }
+  b01b += e01b;
+  b12b += e12b;
+  b23b += e23b;
+  d01b += 2.0 * d01 * b01b;
+  d12b += 2.0 * d12 * b12b;
+  d23b += 2.0 * d23 * b23b;
+  wb[0] -= d01b;
+  wb[1] += d01b - d12b + 0.5 * pmidb;
+  wb[2] += d12b - d23b + 0.5 * pmidb;
+  wb[3] += d23b;
+}
+
+// Backward of cell_field (the limiter): given the adjoint of its output, adds those of
+// w0..w2, y0, y2.
+__device__ __forceinline__ void cell_field_bwd(double w0, double w1, double w2, double y0, double y2, const Grid& g,
+                                               double outb, double* wb, double& y0b, double& y2b) {
+  const double d01 = w1 - w0, d12 = w2 - w1;
+  const double b1 = d01 * d01, b2 = d12 * d12;
+  double du, sv;
+  const double b0 = beta0(d01, d12, y0, y2, du, sv);
+  const double e1 = b1 + g.eps, e2 = b2 + g.eps;
+  const Wts wt = weights(b0, b1, b2, e1, e2, g.eps);
+  const double t = fma(g.cdu, du, -g.csv * sv);
+  const double num = fma(wt.W0, t, fma(wt.W1, d01, wt.W2 * d12));
+  const double den = fma(g.Gd, wt.W0, wt.W1 + wt.W2);
+  const double inv = rcp(den);
+  const double numb = outb * inv;
+  const double denb = -outb * num * inv * inv;
+  const double W0b = fma(numb, t, denb * g.Gd), W1b = fma(numb, d01, denb), W2b = fma(numb, d12, denb);
+  const double tb = numb * wt.W0;
+  double d01b = numb * wt.W1, d12b = numb * wt.W2;
+  // t = cdu (d01 + d12) - csv (y0 + y2)
+  d01b += g.cdu * tb;
+  d12b += g.cdu * tb;
+  y0b -= g.csv * tb;
+  y2b -= g.csv * tb;
+  double b0b = 0.0, b1b = 0.0, b2b = 0.0, e1b = 0.0, e2b = 0.0;
+  weights_bwd(b0, b1, b2, e1, e2, g.eps, W0b, W1b, W2b, b0b, b1b, b2b, e1b, e2b);
+  beta0_bwd(d01, d12, y0, y2, b0b, d01b, d12b, y0b, y2b);
+  b1b += e1b;
+  b2b += e2b;
+  d01b += 2.0 * d01 * b1b;
+  d12b += 2.0 * d12 * b2b;
+  wb[0] -= d01b;
+  wb[1] += d01b - d12b;
+  wb[2] += d12b;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Eigenvector products.  EigBar accumulates the adjoints of the eigen-state variables.
+struct EigBar {
+  double u, v, H, c, ic;
+};
+
+template <int NC>
+__device__ __forceinline__ void project_bwd(const Eig<NC>& e, const double* q, const double* wbar, double* qbar,
+                                            double& hb1b, double& hb2b, double& hicb, EigBar& eb) {
+  // forward: k, th = hb2 q0 - hb1 k, sh = (u q0 - q1) hic
+  const double k = NC == 4 ? fma(e.v, q[2], e.u * q[1]) - q[3] : fma(e.u, q[1], -q[NC - 1]);
+  const double m = fma(e.u, q[0], -q[1]);
+  const double wr = NC == 4 ? wbar[3] : wbar[2];
+  const double thb = wbar[0] - 2.0 * wbar[1] + wr;
+  const double shb = wbar[0] - wr;
+  qbar[0] += wbar[1];
+  if (NC == 4) {
+    qbar[0] -= e.v * wbar[2];
+    qbar[2] += wbar[2];
+    eb.v -= wbar[2] * q[0];
+  }
+  // th
+  hb2b += thb * q[0];
+  qbar[0] += thb * e.hb2;
+  hb1b -= thb * k;
+  const double kb = -thb * e.hb1;
+  // sh
+  const double mb = shb * e.hic;
+  hicb += shb * m;
+  eb.u += mb * q[0];
+  qbar[0] += mb * e.u;
+  qbar[1] -= mb;
+  // k
+  eb.u += kb * q[1];
+  qbar[1] += kb * e.u;
+  if (NC == 4) {
+    eb.v += kb * q[2];
+    qbar[2] += kb * e.v;
+    qbar[3] -= kb;
+  } else {
+    qbar[NC - 1] -= kb;
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ void back_bwd(const Eig<NC>& e, const double* w, const double* qbar, double* wbar,
+                                         double& hq2b, double& ucb, EigBar& eb) {
+  const double wl = w[0], wr = NC == 4 ? w[3] : w[2];
+  const double sg = wl + wr, dl = wr - wl;
+  const double q0 = sg + w[1];
+  double sgb = 0.0, dlb = 0.0, q0b = qbar[0];
+  if (NC == 4) {
+    // q3 = H sg + hq2 w1 + v w2 + uc dl
+    eb.H += qbar[3] * sg;
+    sgb += qbar[3] * e.H;
+    hq2b += qbar[3] * w[1];
+    wbar[1] += qbar[3] * e.hq2;
+    eb.v += qbar[3] * w[2];
+    wbar[2] += qbar[3] * e.v;
+    ucb += qbar[3] * dl;
+    dlb += qbar[3] * e.uc;
+    // q2 = v q0 + w2
+    eb.v += qbar[2] * q0;
+    q0b += qbar[2] * e.v;
+    wbar[2] += qbar[2];
+  } else {
+    // q2 = H sg + hq2 w1 + uc dl
+    eb.H += qbar[2] * sg;
+    sgb += qbar[2] * e.H;
+    hq2b += qbar[2] * w[1];
+    wbar[1] += qbar[2] * e.hq2;
+    ucb += qbar[2] * dl;
+    dlb += qbar[2] * e.uc;
+  }
+  // q1 = u q0 + c dl
+  eb.u += qbar[1] * q0;
+  q0b += qbar[1] * e.u;
+  eb.c += qbar[1] * dl;
+  dlb += qbar[1] * e.c;
+  // q0 = sg + w1
+  sgb += q0b;
+  wbar[1] += q0b;
+  wbar[0] += sgb - dlb;
+  if (NC == 4)
+    wbar[3] += sgb + dlb;
+  else
+    wbar[2] += sgb + dlb;
+}
+
+// adjoints of the derived eigen quantities (hb1, hb2, hic, hq2, uc) into (u, v, c, ic)
+template <int NC>
+__device__ __forceinline__ void setup_bwd(const Eig<NC>& e, double gm1, double ic, double hb1b, double hb2b,
+                                          double hicb, double hq2b, double ucb, EigBar& eb) {
+  // hb2 = hb1 hq2
+  hb1b += hb2b * e.hq2;
+  hq2b += hb2b * e.hb1;
+  // hb1 = gm1 ic^2 / 2
+  eb.ic += hb1b * gm1 * ic;
+  // hic = ic / 2
+  eb.ic += 0.5 * hicb;
+  // hq2 = (u^2 + v^2) / 2
+  eb.u += hq2b * e.u;
+  if (NC == 4) eb.v += hq2b * e.v;
+  // uc = u c
+  eb.u += ucb * e.c;
+  eb.c += ucb * e.u;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Euler primitives of one cell in the normal frame, for the backward routines.
+template <int NC>
+struct Prim {
+  double ir, u, v, p;
+};
+
+template <int NC>
+__device__ __forceinline__ Prim<NC> prim_of(const double* U, double gm1) {
+  Prim<NC> q;
+  q.ir = rcp(U[0]);
+  q.u = U[1] * q.ir;
+  q.v = NC == 4 ? U[2] * q.ir : 0.0;
+  const double ke = NC == 4 ? fma(U[1], q.u, U[2] * q.v) : U[1] * q.u;
+  q.p = gm1 * fma(-0.5, ke, U[NC - 1]);
+  return q;
+}
+
+// Given the adjoints of (ir, u, v, p) of a cell, adds those of U.
+template <int NC>
+__device__ __forceinline__ void prim_bwd(const double* U, const Prim<NC>& q, double gm1, double irb, double ub,
+                                         double vb, double pb, double* Ub) {
+  // p = gm1 (E - (m u + n v)/2)
+  Ub[NC - 1] += gm1 * pb;
+  const double keb = -0.5 * gm1 * pb;
+  Ub[1] += keb * q.u;
+  ub += keb * U[1];
+  if (NC == 4) {
+    Ub[2] += keb * q.v;
+    vb += keb * U[2];
+  }
+  // u = m ir, v = n ir
+  Ub[1] += ub * q.ir;
+  irb += ub * U[1];
+  if (NC == 4) {
+    Ub[2] += vb * q.ir;
+    irb += vb * U[2];
+  }
+  // ir = 1/rho
+  Ub[0] -= irb * q.ir * q.ir;
+}
+
+// Flux F(U) in the normal frame: given Fb, adds Ub.
+template <int NC>
+__device__ __forceinline__ void flux_bwd(const double* U, double gm1, const double* Fb, double* Ub) {
+  const Prim<NC> q = prim_of<NC>(U, gm1);
+  double ub = 0.0, vb = 0.0, pb = 0.0;
+  // F = (m, m u + p, [n u,] (E + p) u)
+  Ub[1] += Fb[0] + Fb[1] * q.u;
+  ub += Fb[1] * U[1];
+  pb += Fb[1];
+  if (NC == 4) {
+    Ub[2] += Fb[2] * q.u;
+    ub += Fb[2] * U[2];
+  }
+  Ub[NC - 1] += Fb[NC - 1] * q.u;
+  pb += Fb[NC - 1] * q.u;
+  ub += Fb[NC - 1] * (U[NC - 1] + q.p);
+  prim_bwd<NC>(U, q, gm1, 0.0, ub, vb, pb, Ub);
+}
+
+// Jacobian product A(U) D in the normal frame: given ob, adds Ub and Db.
+template <int NC>
+__device__ __forceinline__ void jvp_bwd(const double* U, const double* D, double gm1, const double* ob, double* Ub,
+                                        double* Db) {
+  const Prim<NC> q = prim_of<NC>(U, gm1);
+  const double du = fma(-q.u, D[0], D[1]) * q.ir;
+  const double dv = NC == 4 ? fma(-q.v, D[0], D[2]) * q.ir : 0.0;
+  const double dk = NC == 4 ? fma(D[1], q.u, fma(U[1], du, fma(D[2], q.v, U[2] * dv))) : fma(D[1], q.u, U[1] * du);
+  const double dp = gm1 * fma(-0.5, dk, D[NC - 1]);
+  double ub = 0.0, vb = 0.0, pb = 0.0, irb = 0.0, dub = 0.0, dvb = 0.0, dpb = 0.0;
+  // out0 = D1
+  Db[1] += ob[0];
+  // out1 = D1 u + m du + dp
+  Db[1] += ob[1] * q.u;
+  ub += ob[1] * D[1];
+  Ub[1] += ob[1] * du;
+  dub += ob[1] * U[1];
+  dpb += ob[1];
+  if (NC == 4) {
+    // out2 = D2 u + n du
+    Db[2] += ob[2] * q.u;
+    ub += ob[2] * D[2];
+    Ub[2] += ob[2] * du;
+    dub += ob[2] * U[2];
+  }
+  // out_last = (D_E + dp) u + (E + p) du
+  Db[NC - 1] += ob[NC - 1] * q.u;
+  dpb += ob[NC - 1] * q.u;
+  ub += ob[NC - 1] * (D[NC - 1] + dp);
+  Ub[NC - 1] += ob[NC - 1] * du;
+  pb += ob[NC - 1] * du;
+  dub += ob[NC - 1] * (U[NC - 1] + q.p);
+  // dp = gm1 (D_E - dk/2)
+  Db[NC - 1] += gm1 * dpb;
+  const double dkb = -0.5 * gm1 * dpb;
+  // dk = D1 u + m du [+ D2 v + n dv]
+  Db[1] += dkb * q.u;
+  ub += dkb * D[1];
+  Ub[1] += dkb * du;
+  dub += dkb * U[1];
+  if (NC == 4) {
+    Db[2] += dkb * q.v;
+    vb += dkb * D[2];
+    Ub[2] += dkb * dv;
+    dvb += dkb * U[2];
+  }
+  // du = (D1 - u D0) ir, dv = (D2 - v D0) ir
+  Db[1] += dub * q.ir;
+  ub -= dub * D[0] * q.ir;
+  Db[0] -= dub * q.u * q.ir;
+  irb += dub * fma(-q.u, D[0], D[1]);
+  if (NC == 4) {
+    Db[2] += dvb * q.ir;
+    vb -= dvb * D[0] * q.ir;
+    Db[0] -= dvb * q.v * q.ir;
+    irb += dvb * fma(-q.v, D[0], D[2]);
+  }
+  prim_bwd<NC>(U, q, gm1, irb, ub, vb, pb, Ub);
+}
+
+}  // namespace hw

@@ -164,8 +164,10 @@ inline int read_status(hweno_ctx* h) {
 inline const Launchers& launchers(const hweno_ctx* h) { return kTable[h->dim - 1][h->system]; }
 
 // one spatial-operator evaluation: cell, face; then update in the requested mode
+// alpha_override (device, 2 doubles, may be null): LF coefficients to use instead of the
+// wavespeeds of S_in (the recorded alphas of an adjoint replay)
 inline int stage(hweno_ctx* h, const double* S_in, double* S_out, int mode, int st, double dt, int slot, double* Lo,
-          double* Mo) {
+          double* Mo, const double* alpha_override = nullptr) {
   const Grid g = grid_of(h);
   const Launchers& f = launchers(h);
   if (cudaMemsetAsync(h->w.alpha + 2 * slot, 0, 2 * sizeof(unsigned long long), h->stream) != cudaSuccess)
@@ -180,6 +182,10 @@ inline int stage(hweno_ctx* h, const double* S_in, double* S_out, int mode, int 
   static const double b_k[3] = {1.0, 0.25, 2.0 / 3.0};
   if (ev[0]) cudaEventRecord(ev[0], h->stream);
   f.cell(g, S_in, h->w, slot, h->stream);
+  if (alpha_override &&
+      cudaMemcpyAsync(h->w.alpha + slot * h->w.astride, alpha_override, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                      h->stream) != cudaSuccess)
+    return HWENO_ECUDA;
   if (ev[1]) cudaEventRecord(ev[1], h->stream);
   f.face(g, S_in, h->w, slot, h->stream);
   if (ev[2]) cudaEventRecord(ev[2], h->stream);
@@ -189,5 +195,9 @@ inline int stage(hweno_ctx* h, const double* S_in, double* S_out, int mode, int 
   return cuda_status();
 }
 
-}  // namespace hwh
+// one forward stage in place with fixed dt and the given LF coefficients
+inline int stage_replay(hweno_ctx* h, double* S, int st, double dt, const double* alpha2_dev) {
+  return stage(h, S, S, 0, st, dt, st, nullptr, nullptr, alpha2_dev);
+}
 
+}  // namespace hwh

@@ -126,6 +126,30 @@ class Solver:
     def launch_count(self) -> int:
         return int(self.lib.hweno_launch_count(self.h))
 
+    # ---- adjoint support (fixed dt and per-stage LF coefficients) ----------------------------
+    def _adj_ws(self):
+        if getattr(self, "adj_workspace", None) is None:
+            self.adj_workspace = torch.empty(int(self.lib.hweno_adjoint_workspace_bytes(self.h)), dtype=torch.uint8,
+                                             device=self.device)
+        return self.adj_workspace
+
+    def record(self, out7: torch.Tensor) -> None:
+        """Copy dt and the three stage alphas of the last step into a device tensor of 7 doubles."""
+        C.check(self.lib.hweno_step_record(self.h, ctypes.c_void_p(out7.data_ptr())), "hweno_step_record")
+
+    def step_replay(self, dt: float, alpha6: torch.Tensor) -> None:
+        C.check(self.lib.hweno_step_replay(self.h, float(dt), ctypes.c_void_p(alpha6.data_ptr())),
+                "hweno_step_replay")
+
+    def adjoint_step(self, Sn: torch.Tensor, dt: float, alpha6: torch.Tensor, lam_in: torch.Tensor) -> torch.Tensor:
+        """(dS^{n+1}/dS^n)^T lam_in for the step from Sn with dt and alpha6 (device tensors)."""
+        lam_out = torch.empty_like(lam_in)
+        C.check(self.lib.hweno_adjoint_step(self.h, ctypes.c_void_p(Sn.data_ptr()), float(dt),
+                                            ctypes.c_void_p(alpha6.data_ptr()), ctypes.c_void_p(lam_in.data_ptr()),
+                                            ctypes.c_void_p(lam_out.data_ptr()), ctypes.c_void_p(self._adj_ws().data_ptr())),
+                "hweno_adjoint_step")
+        return lam_out
+
     def run(self, t_end: float, max_steps: int = 10 ** 9) -> int:
         """CFL steps to t_end (last step clamped on the device); returns the step count."""
         self.set_time(0.0, t_end)
