@@ -160,6 +160,69 @@ def run_batched(dev, steps: int = 3):
     return res
 
 
+def run_adjoint(dev, nsteps: int = 200, every: int = 20):
+    """The adjoint workload: 2D Euler 1024^2, smooth wave plus 8 seeded Fourier modes, J = 1/2 sum
+    rho(T)^2 dx dy after 200 SSP-RK3 steps, gradient through the checkpointed rollout (checkpoints
+    every 20 steps).  Reports the cost of one adjoint step relative to one forward step."""
+    import torch
+
+    import workloads as W
+    from paper_2411_11229_gb300 import Solver
+    from paper_2411_11229_gb300.adjoint import Rollout
+
+    n = 1024
+    S0n, dx, dy = W.euler2d_adjoint_init(n, seed=4000)
+    s = Solver(2, "euler", n, n, dx=dx, dy=dy, device=dev)
+    s.set_state(S0n)
+    s.set_time(0.0, 0.0)
+    rec = torch.empty(7, dtype=torch.float64, device=dev)
+    s.step(0.0, 3)
+    s.record(rec)
+    s.sync()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    e0, e1 = ev(), ev()
+    e0.record(s.stream)
+    s.step(0.0, 10)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    fwd = e0.elapsed_time(e1) / 10
+    Sn = s.state.clone()
+    S1, S2 = torch.empty_like(Sn), torch.empty_like(Sn)
+    lam = torch.randn_like(Sn)
+    dt, al = float(rec[0].item()), rec[1:].contiguous()
+    s.step_replay_stages(dt, al, S1, S2)
+    lam = s.adjoint_step_stages(Sn, S1, S2, dt, al, lam)
+    lam = s.adjoint_step(Sn, dt, al, lam)
+    torch.cuda.synchronize()
+    res = {"workload": "2D Euler 1024^2 periodic, smooth wave + 8 seeded modes, J = 1/2 sum rho^2 dx dy",
+           "ms_forward_step": fwd}
+    for name, fn in (("from_stages", lambda l: s.adjoint_step_stages(Sn, S1, S2, dt, al, l)),
+                     ("self_contained", lambda l: s.adjoint_step(Sn, dt, al, l))):
+        e0.record(s.stream)
+        for _ in range(5):
+            lam = fn(lam)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        res[f"ms_adjoint_step_{name}"] = ms
+        res[f"cost_ratio_{name}"] = ms / fwd
+    S0 = torch.as_tensor(S0n, device=dev).requires_grad_(True)
+    (0.5 * (S0.detach()[0, 0] ** 2).sum()).item()  # first use of these torch kernels loads them
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ST = Rollout.apply(S0, s, nsteps, every)
+    J = 0.5 * (ST[0, 0] ** 2).sum() * dx * dy
+    J.item()
+    t1 = time.perf_counter()
+    J.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    res.update({"rollout_steps": nsteps, "checkpoint_every": every, "rollout_forward_s": t1 - t0,
+                "rollout_backward_s": t2 - t1, "backward_over_forward": (t2 - t1) / (t1 - t0), "J": J.item(),
+                "convention": "fixed recorded dt and per-stage alpha"})
+    return res
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
@@ -317,6 +380,9 @@ def run_ours(args, ws, rank, local):
         del solver
         torch.cuda.empty_cache()
         line["batched"] = run_batched(dev)
+    if ws == 1 and not args.no_adjoint:
+        torch.cuda.empty_cache()
+        line["adjoint"] = run_adjoint(dev)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -332,6 +398,7 @@ def main():
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":

@@ -170,6 +170,17 @@ int hweno_step_replay(hweno_t *h, double dt, const double *alpha6_dev);
 int hweno_adjoint_step(hweno_t *h, const double *S_n_dev, double dt, const double *alpha6_dev,
                        const double *lam_in_dev, double *lam_out_dev, void *adj_ws_dev);
 
+/* The same adjoint step when the caller already holds the stage inputs S1, S2 of the step (as
+ * hweno_step_replay_stages leaves them): no forward recomputation. */
+int hweno_adjoint_step_stages(hweno_t *h, const double *S_n_dev, const double *S1_dev, const double *S2_dev,
+                              double dt, const double *alpha6_dev, const double *lam_in_dev,
+                              double *lam_out_dev, void *adj_ws_dev);
+
+/* hweno_step_replay that also copies the stage inputs S1 (after stage 1) and S2 (after stage 2)
+ * of the step to S1_out_dev and S2_out_dev. */
+int hweno_step_replay_stages(hweno_t *h, double dt, const double *alpha6_dev, double *S1_out_dev,
+                             double *S2_out_dev);
+
 /* lam = (dM/dS)^T muM + (dL/dS)^T muL at S with alpha2_dev held fixed: the transpose of one
  * evaluation of hweno_rhs (the building block of hweno_adjoint_step). */
 int hweno_stage_vjp(hweno_t *h, const double *S_dev, const double *alpha2_dev, const double *muM_dev,

@@ -3,8 +3,9 @@
 The forward pass advances the state with CFL steps (dt on the device) and records dt and the LF
 coefficients of every stage; the backward pass applies the hand-written adjoint step
 (hweno_adjoint_step) in reverse, with the derivative taken at the recorded dt and alphas.
-States are checkpointed every `every` steps in device memory; within a segment the states are
-recomputed from its checkpoint by replaying the recorded steps.
+States are checkpointed every `every` steps in device memory; within a segment the states (and
+the two stage inputs of every step) are recomputed from its checkpoint by replaying the recorded
+steps, so the adjoint steps need no further forward work.
 """
 from __future__ import annotations
 
@@ -43,14 +44,18 @@ class Rollout(torch.autograd.Function):
         nseg = (nsteps + every - 1) // every
         for seg in range(nseg - 1, -1, -1):
             s0, s1 = seg * every, min((seg + 1) * every, nsteps)
-            states = [ctx.checkpoints[seg]]
+            # replay the segment from its checkpoint, keeping every step's input and stage inputs
+            states = [(ctx.checkpoints[seg], torch.empty_like(solver.state), torch.empty_like(solver.state))]
             with torch.cuda.stream(solver.stream):
-                solver.state.copy_(states[0])
-            for s in range(s0, s1 - 1):
-                solver.step_replay(float(dts[s]), rec[s, 1:])
-                states.append(solver.state.clone())
+                solver.state.copy_(states[0][0])
+            for s in range(s0, s1):
+                Sn, S1, S2 = states[-1]
+                solver.step_replay_stages(float(dts[s]), rec[s, 1:], S1, S2)
+                if s < s1 - 1:
+                    states.append((solver.state.clone(), torch.empty_like(solver.state), torch.empty_like(solver.state)))
             for s in range(s1 - 1, s0 - 1, -1):
-                lam = solver.adjoint_step(states[s - s0], float(dts[s]), rec[s, 1:].contiguous(), lam)
+                Sn, S1, S2 = states[s - s0]
+                lam = solver.adjoint_step_stages(Sn, S1, S2, float(dts[s]), rec[s, 1:].contiguous(), lam)
         return lam.reshape(lam_T.shape), None, None, None
 
 

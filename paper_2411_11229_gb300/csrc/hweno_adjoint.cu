@@ -536,9 +536,39 @@ int lincomb(const hweno_ctx* h, double* out, double c1, const double* x1, double
 
 }  // namespace
 
-extern "C" {
+extern "C" size_t hweno_adjoint_workspace_bytes(const hweno_t* h) { return h ? adj_layout(h).total : 0; }
 
-size_t hweno_adjoint_workspace_bytes(const hweno_t* h) { return h ? adj_layout(h).total : 0; }
+namespace {
+
+// the three stage VJPs of one step, given the stage inputs S^n, S1, S2
+int adjoint_from_stages(hweno_t* h, const AdjPtrs& a, const double* Sn, const double* S1, const double* S2, double dt,
+                        const double* alpha6, const double* lam_in, double* lam_out) {
+  const Grid g = grid_of(h);
+  int rc;
+  auto vjp = [&](const double* S, int st, const double* muM, const double* muL, double* lam) {
+    return h->dim == 1 ? stage_vjp<1>(h, g, S, alpha6 + 2 * st, muM, muL, a.aw, lam)
+                       : stage_vjp<2>(h, g, S, alpha6 + 2 * st, muM, muL, a.aw, lam);
+  };
+  // S^{n+1} = 1/3 B + 2/3 (M(S2) + dt L(S2))
+  if ((rc = lincomb(h, a.muM, 2.0 / 3.0, lam_in, 0.0, nullptr, 0.0, nullptr))) return rc;
+  if ((rc = lincomb(h, a.muL, 2.0 / 3.0 * dt, lam_in, 0.0, nullptr, 0.0, nullptr))) return rc;
+  if ((rc = vjp(S2, 2, a.muM, a.muL, a.lam2))) return rc;
+  // S2 = 3/4 B + 1/4 (M(S1) + dt L(S1));  lamB = 1/3 lam_in + 3/4 lam2
+  if ((rc = lincomb(h, a.lamB, 1.0 / 3.0, lam_in, 0.75, a.lam2, 0.0, nullptr))) return rc;
+  if ((rc = lincomb(h, a.muM, 0.25, a.lam2, 0.0, nullptr, 0.0, nullptr))) return rc;
+  if ((rc = lincomb(h, a.muL, 0.25 * dt, a.lam2, 0.0, nullptr, 0.0, nullptr))) return rc;
+  if ((rc = vjp(S1, 1, a.muM, a.muL, a.lam1))) return rc;
+  // S1 = M(S^n) + dt L(S^n), B = M(S^n)
+  if ((rc = lincomb(h, a.muM, 1.0, a.lam1, 1.0, a.lamB, 0.0, nullptr))) return rc;
+  if ((rc = lincomb(h, a.muL, dt, a.lam1, 0.0, nullptr, 0.0, nullptr))) return rc;
+  if ((rc = vjp(Sn, 0, a.muM, a.muL, lam_out))) return rc;
+  h->launches += 9 + 8;
+  return HWENO_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 int hweno_adjoint_step(hweno_t* h, const double* Sn, double dt, const double* alpha6, const double* lam_in,
                        double* lam_out, void* adj_ws) {
@@ -548,7 +578,6 @@ int hweno_adjoint_step(hweno_t* h, const double* Sn, double dt, const double* al
   if (!h->ws) return HWENO_ESTATE;
   const AdjPtrs a = adj_ptrs(h, adj_ws);
   const size_t bytes = hweno_state_doubles(h) * 8;
-  const Grid g = grid_of(h);
   // forward stages 1 and 2 from S^n with the recorded alphas (the forward workspace is scratch)
   if (cudaMemcpyAsync(a.S1, Sn, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess) return HWENO_ECUDA;
   int rc = stage_replay(h, a.S1, 0, dt, alpha6);
@@ -556,24 +585,28 @@ int hweno_adjoint_step(hweno_t* h, const double* Sn, double dt, const double* al
   if (cudaMemcpyAsync(a.S2, a.S1, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess) return HWENO_ECUDA;
   rc = stage_replay(h, a.S2, 1, dt, alpha6 + 2);
   if (rc) return rc;
-  auto vjp = [&](const double* S, int st, const double* muM, const double* muL, double* lam) {
-    return h->dim == 1 ? stage_vjp<1>(h, g, S, alpha6 + 2 * st, muM, muL, a.aw, lam)
-                       : stage_vjp<2>(h, g, S, alpha6 + 2 * st, muM, muL, a.aw, lam);
-  };
-  // S^{n+1} = 1/3 B + 2/3 (M(S2) + dt L(S2))
-  if ((rc = lincomb(h, a.muM, 2.0 / 3.0, lam_in, 0.0, nullptr, 0.0, nullptr))) return rc;
-  if ((rc = lincomb(h, a.muL, 2.0 / 3.0 * dt, lam_in, 0.0, nullptr, 0.0, nullptr))) return rc;
-  if ((rc = vjp(a.S2, 2, a.muM, a.muL, a.lam2))) return rc;
-  // S2 = 3/4 B + 1/4 (M(S1) + dt L(S1));  lamB = 1/3 lam_in + 3/4 lam2
-  if ((rc = lincomb(h, a.lamB, 1.0 / 3.0, lam_in, 0.75, a.lam2, 0.0, nullptr))) return rc;
-  if ((rc = lincomb(h, a.muM, 0.25, a.lam2, 0.0, nullptr, 0.0, nullptr))) return rc;
-  if ((rc = lincomb(h, a.muL, 0.25 * dt, a.lam2, 0.0, nullptr, 0.0, nullptr))) return rc;
-  if ((rc = vjp(a.S1, 1, a.muM, a.muL, a.lam1))) return rc;
-  // S1 = M(S^n) + dt L(S^n), B = M(S^n)
-  if ((rc = lincomb(h, a.muM, 1.0, a.lam1, 1.0, a.lamB, 0.0, nullptr))) return rc;
-  if ((rc = lincomb(h, a.muL, dt, a.lam1, 0.0, nullptr, 0.0, nullptr))) return rc;
-  if ((rc = vjp(Sn, 0, a.muM, a.muL, lam_out))) return rc;
-  h->launches += 9 + 8;
+  return adjoint_from_stages(h, a, Sn, a.S1, a.S2, dt, alpha6, lam_in, lam_out);
+}
+
+int hweno_adjoint_step_stages(hweno_t* h, const double* Sn, const double* S1, const double* S2, double dt,
+                              const double* alpha6, const double* lam_in, double* lam_out, void* adj_ws) {
+  if (!h || !Sn || !S1 || !S2 || !alpha6 || !lam_in || !lam_out || !adj_ws) return HWENO_EINVAL;
+  if (h->system != HWENO_EULER || h->bc == HWENO_BC_REFLECTIVE) return HWENO_EINVAL;
+  if (!(dt > 0.0) || ((uintptr_t)adj_ws & 255)) return HWENO_EINVAL;
+  return adjoint_from_stages(h, adj_ptrs(h, adj_ws), Sn, S1, S2, dt, alpha6, lam_in, lam_out);
+}
+
+int hweno_step_replay_stages(hweno_t* h, double dt, const double* alpha6, double* S1_out, double* S2_out) {
+  if (!h || !alpha6 || !S1_out || !S2_out || !(dt > 0.0)) return HWENO_EINVAL;
+  if (!h->ws || !h->state) return HWENO_ESTATE;
+  const size_t bytes = hweno_state_doubles(h) * 8;
+  for (int st = 0; st < 3; ++st) {
+    int rc = stage(h, h->state, h->state, 0, st, dt, st, nullptr, nullptr, alpha6 + 2 * st);
+    if (rc) return rc;
+    if (st < 2 && cudaMemcpyAsync(st == 0 ? S1_out : S2_out, h->state, bytes, cudaMemcpyDeviceToDevice,
+                                  h->stream) != cudaSuccess)
+      return HWENO_ECUDA;
+  }
   return HWENO_OK;
 }
 

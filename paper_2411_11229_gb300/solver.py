@@ -150,6 +150,20 @@ class Solver:
                 "hweno_adjoint_step")
         return lam_out
 
+    def step_replay_stages(self, dt: float, alpha6: torch.Tensor, S1: torch.Tensor, S2: torch.Tensor) -> None:
+        """Replay a recorded step, copying its stage inputs S1 and S2 out."""
+        C.check(self.lib.hweno_step_replay_stages(self.h, float(dt), ctypes.c_void_p(alpha6.data_ptr()),
+                                                  ctypes.c_void_p(S1.data_ptr()), ctypes.c_void_p(S2.data_ptr())),
+                "hweno_step_replay_stages")
+
+    def adjoint_step_stages(self, Sn, S1, S2, dt: float, alpha6: torch.Tensor, lam_in: torch.Tensor) -> torch.Tensor:
+        lam_out = torch.empty_like(lam_in)
+        C.check(self.lib.hweno_adjoint_step_stages(
+            self.h, ctypes.c_void_p(Sn.data_ptr()), ctypes.c_void_p(S1.data_ptr()), ctypes.c_void_p(S2.data_ptr()),
+            float(dt), ctypes.c_void_p(alpha6.data_ptr()), ctypes.c_void_p(lam_in.data_ptr()),
+            ctypes.c_void_p(lam_out.data_ptr()), ctypes.c_void_p(self._adj_ws().data_ptr())), "hweno_adjoint_step_stages")
+        return lam_out
+
     def run(self, t_end: float, max_steps: int = 10 ** 9) -> int:
         """CFL steps to t_end (last step clamped on the device); returns the step count."""
         self.set_time(0.0, t_end)
