@@ -62,7 +62,9 @@ enum {
  * dim: 1 or 2.  system: HWENO_ADVECTION, HWENO_BURGERS or HWENO_EULER.  gamma: ratio of specific
  * heats (Euler only, > 1).  bc: boundary condition on every side (periodic, as in every accuracy
  * test of Sec. 4; transmissive = zero-order extrapolation of U and of its derivatives; reflective =
- * the sign tables RBC-1d / RBC-2d-x / RBC-2d-y, Euler only).
+ * a wall at each end: ghost cell -1-k mirrors cell k with the sign tables of the reflective-boundary
+ * remarks closing Sec. 2 (1D) and Sec. 3 (2D) (normal velocity odd; the normal derivative of every other
+ * primitive odd, of the normal velocity even), Euler only).
  * EINVAL: dim not 1 or 2, nx < 5 (ny < 5 in 2D), dx or dy <= 0, gamma <= 1 for Euler, unknown
  * system or bc, reflective with a scalar system.  ny and dy are ignored when dim == 1.
  * Defaults (Sec. 4): gamma0 = 0.95 (1D) / 0.99 (2D), d0 = 0.9, eps = 1e-10, CFL = 0.6, a = (1, 1). */
@@ -241,8 +243,8 @@ void hweno_batch_destroy(hweno_batch_t *b);
  * input and output buffers, or latency-sensitive loops that cannot afford a cudaMalloc (which can
  * synchronise the whole device).  It evaluates exactly what hweno_rhs evaluates (L(S) and
  * M(S) = (U, V~, W~) with alpha taken from S), with the same kernels, launched on `stream`.
- *   Arguments: the grid as in hweno_create (dim, system, nx, ny, dx, dy, gamma, bc; reflective is
- *   EINVAL); params5 = {gamma0, d0, eps, adv_ax, adv_ay} or NULL for the defaults of
+ *   Arguments: the grid as in hweno_create (dim, system, nx, ny, dx, dy, gamma, bc; the same
+ *   EINVAL rules); params5 = {gamma0, d0, eps, adv_ax, adv_ay} or NULL for the defaults of
  *   hweno_create; S, L, M: caller-owned device arrays of nfield*ncomp*ny*nx doubles in the state
  *   layout, S not aliasing L or M.
  *   Scratch: a fixed 16 MiB device array inside the library, present on every GPU that loads it

@@ -20,7 +20,7 @@ int hweno_create(int dim, int system, int64_t nx, int64_t ny, double dx, double 
   if (dim != 1 && dim != 2) return HWENO_EINVAL;
   if (system < HWENO_ADVECTION || system > HWENO_EULER) return HWENO_EINVAL;
   if (bc < HWENO_BC_PERIODIC || bc > HWENO_BC_REFLECTIVE) return HWENO_EINVAL;
-  if (bc == HWENO_BC_REFLECTIVE) return HWENO_EINVAL;  // reflective walls: not in this build
+  if (bc == HWENO_BC_REFLECTIVE && system != HWENO_EULER) return HWENO_EINVAL;  // sign tables: Euler only
   if (dim == 1) {
     ny = 1;
     dy = dx;
@@ -316,7 +316,8 @@ extern "C" int hweno_rhs_static(int dim, int system, int64_t nx, int64_t ny, dou
   hweno_ctx h;
   if (dim != 1 && dim != 2) return HWENO_EINVAL;
   if (system < HWENO_ADVECTION || system > HWENO_EULER) return HWENO_EINVAL;
-  if (bc < HWENO_BC_PERIODIC || bc > HWENO_BC_REFLECTIVE || bc == HWENO_BC_REFLECTIVE) return HWENO_EINVAL;
+  if (bc < HWENO_BC_PERIODIC || bc > HWENO_BC_REFLECTIVE) return HWENO_EINVAL;
+  if (bc == HWENO_BC_REFLECTIVE && system != HWENO_EULER) return HWENO_EINVAL;
   if (dim == 1) {
     ny = 1;
     dy = dx;

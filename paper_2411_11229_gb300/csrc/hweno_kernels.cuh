@@ -207,7 +207,8 @@ __device__ __forceinline__ void cell_body(const Grid& g, const double* __restric
       double U3[3][NC], D3[3][NC];
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const int ac = bc_index(a0 - 1 + q, n, g.bc);
+        bool refl;
+        const int ac = bc_map(a0 - 1 + q, n, g.bc, refl);
         const long long pc = d == 0 ? (long long)j * g.nx + ac : (long long)ac * g.nx + i;
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
@@ -217,6 +218,10 @@ __device__ __forceinline__ void cell_body(const Grid& g, const double* __restric
         if (SYS == SYS_EULER && d == 1) {
           swap_frame<NC>(U3[q]);
           swap_frame<NC>(D3[q]);
+        }
+        if (SYS == SYS_EULER && refl) {
+          mirror_U<NC>(U3[q]);
+          mirror_D<NC>(D3[q]);
         }
       }
       Eig<NC> e;
@@ -258,9 +263,10 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
   }
   // cells fa-2 .. fa+1 around face fa (between cells fa-1 and fa)
   long long pc[4];
+  bool refl[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const int a = bc_index(fa - 2 + q, n, g.bc);
+    const int a = bc_map(fa - 2 + q, n, g.bc, refl[q]);
     pc[q] = dir == 0 ? (long long)line * g.nx + a : (long long)a * g.nx + line;
   }
   const int fown = dir == 0 ? 1 : 2, foth = dir == 0 ? 2 : 1;
@@ -277,6 +283,10 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
       swap_frame<NC>(Uq[q]);
       swap_frame<NC>(Zq[q]);
     }
+    if (SYS == SYS_EULER && refl[q]) {
+      mirror_U<NC>(Uq[q]);
+      mirror_D<NC>(Zq[q]);
+    }
   }
   // characteristic fields at the face: Roe average of the two adjacent cells
   Eig<NC> e;
@@ -284,7 +294,9 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
   if (SYS == SYS_EULER) {
     const double sl = w.PRIM[pc[1]], sr = w.PRIM[pc[2]];
     const int ou = dir == 0 ? 1 : 2, ov = dir == 0 ? 2 : 1;
-    const double ul = w.PRIM[ou * plane + pc[1]], ur = w.PRIM[ou * plane + pc[2]];
+    // a mirrored neighbour has the opposite normal velocity
+    const double ul = refl[1] ? -w.PRIM[ou * plane + pc[1]] : w.PRIM[ou * plane + pc[1]];
+    const double ur = refl[2] ? -w.PRIM[ou * plane + pc[2]] : w.PRIM[ou * plane + pc[2]];
     double vl = 0, vr = 0;
     if (DIM == 2) {
       vl = w.PRIM[ov * plane + pc[1]];
@@ -345,9 +357,15 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
   double fh[NC], hh[NC], mh[NC];
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
-    const double f0 = nod[k * plane + pc[0]], f1 = nod[k * plane + pc[1]];
-    const double f2 = nod[k * plane + pc[2]], f3 = nod[k * plane + pc[3]];
-    const double h0 = nod[(NC + k) * plane + pc[0]], h3 = nod[(NC + k) * plane + pc[3]];
+    // nodal values of mirrored neighbours (normal frame): f and the mixed value take -sU, the
+    // normal-derivative flux takes sU, with sU = -1 for the normal momentum and +1 otherwise
+    const double sU = k == 1 ? -1.0 : 1.0;
+    const double sf0 = refl[0] ? -sU : 1.0, sf1 = refl[1] ? -sU : 1.0;
+    const double sf2 = refl[2] ? -sU : 1.0, sf3 = refl[3] ? -sU : 1.0;
+    const double f0 = sf0 * nod[k * plane + pc[0]], f1 = sf1 * nod[k * plane + pc[1]];
+    const double f2 = sf2 * nod[k * plane + pc[2]], f3 = sf3 * nod[k * plane + pc[3]];
+    const double h0 = (refl[0] ? sU : 1.0) * nod[(NC + k) * plane + pc[0]];
+    const double h3 = (refl[3] ? sU : 1.0) * nod[(NC + k) * plane + pc[3]];
     // D-terms (Eqs. Cd-1, DfDh)
     const double Df = fma(DCoef::cf, (f0 - f1) + (f3 - f2), g.chh[dir] * (h0 - h3));
     const double Dh = fma(g.efih[dir], f0 - f3, fma(g.egih[dir], f2 - f1, DCoef::eh * (h0 + h3)));
@@ -355,8 +373,8 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
     // Dm, Dp and the Jacobian products carry the factor h: 1/(2h) restores both
     hh[k] = fma(g.hih[dir], fma(-alpha, Dp[k] - Dm[k], HDm[k] + HDp[k]), Dh);
     if (DIM == 2) {
-      const double o0 = nod[(2 * NC + k) * plane + pc[0]], o1 = nod[(2 * NC + k) * plane + pc[1]];
-      const double o2 = nod[(2 * NC + k) * plane + pc[2]], o3 = nod[(2 * NC + k) * plane + pc[3]];
+      const double o0 = sf0 * nod[(2 * NC + k) * plane + pc[0]], o1 = sf1 * nod[(2 * NC + k) * plane + pc[1]];
+      const double o2 = sf2 * nod[(2 * NC + k) * plane + pc[2]], o3 = sf3 * nod[(2 * NC + k) * plane + pc[3]];
       // Eq. (mixed)
       mh[k] = fma(7.0 / 12.0, o1 + o2, (-1.0 / 12.0) * (o0 + o3));
     }

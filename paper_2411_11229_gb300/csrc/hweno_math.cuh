@@ -300,13 +300,35 @@ struct Eig {
 };
 
 // ---------------------------------------------------------------------------------------------
-// Boundary index maps.  Periodic wraps, transmissive clamps (zero-order extrapolation).
+// Boundary index maps.  Periodic wraps, transmissive clamps (zero-order extrapolation),
+// reflective mirrors about the wall (cell -1-k for k < 0, 2n-1-k for k >= n) and sets refl.
+__device__ __forceinline__ int bc_map(int k, int n, int bc, bool& refl) {
+  refl = false;
+  if (k >= 0 && k < n) return k;
+  if (bc == BC_PERIODIC) return k < 0 ? k + n : k - n;
+  if (bc == BC_TRANSMISSIVE) return k < 0 ? 0 : n - 1;
+  refl = true;
+  return k < 0 ? -1 - k : 2 * n - 1 - k;
+}
+
 __device__ __forceinline__ int bc_index(int k, int n, int bc) {
-  if (bc == BC_PERIODIC) {
-    k = k < 0 ? k + n : k;
-    return k >= n ? k - n : k;
-  }
-  return k < 0 ? 0 : (k >= n ? n - 1 : k);
+  bool refl;
+  return bc_map(k, n, bc, refl);
+}
+
+// A mirrored cell in the normal frame (Remarks RBC-1d, RBC-2d-x, RBC-2d-y): in U and in the
+// tangential derivative the normal momentum changes sign; in the normal derivative every
+// component except that of the normal momentum changes sign.  Its nodal values then follow
+// exactly: f -> -sU f, f'(u) v (normal derivative) -> sU (f'(u) v), mixed value -> -sU (...).
+template <int NC>
+__device__ __forceinline__ void mirror_U(double* q) {
+  q[1] = -q[1];
+}
+template <int NC>
+__device__ __forceinline__ void mirror_D(double* q) {
+#pragma unroll
+  for (int k = 0; k < NC; ++k)
+    if (k != 1) q[k] = -q[k];
 }
 
 __device__ __forceinline__ unsigned long long dbl_bits(double x) {

@@ -30,7 +30,15 @@ def _small_batch():
     for (nx, ny), seed in (((19, 23), 4), ((40, 32), 5), ((64, 7), 6)):
         S, dx, dy = W.euler2d_random(nx, ny, seed, "jumps" if seed % 2 else "smooth")
         items.append(({"dim": 2, "nx": nx, "ny": ny, "dx": dx, "dy": dy, "bc": "periodic"}, S))
+    # reflective walls in the same launch
+    S, dx = W.blast_wave_1d(90, p_mid=1.0)
+    items.append(({"dim": 1, "nx": 90, "dx": dx, "bc": "reflective"}, S))
+    S, dx, dy = W.euler2d_quadrants(26, 21, seed=2002)
+    items.append(({"dim": 2, "nx": 26, "ny": 21, "dx": dx, "dy": dy, "bc": "reflective"}, S))
     return items
+
+
+_OBC = {"periodic": O.BC_PERIODIC, "transmissive": O.BC_TRANSMISSIVE, "reflective": O.BC_REFLECTIVE}
 
 
 def test_batch_matches_single_grids_and_oracle():
@@ -52,7 +60,7 @@ def test_batch_matches_single_grids_and_oracle():
         dt, t = s.last_dt()
         assert abs(dts[i] - dt) <= 1e-15 * dt and abs(ts[i] - t) <= 1e-14 * t
         cfg = O.make_cfg(d["dim"], O.EULER, d["nx"], d.get("ny", 1), dx=d["dx"], dy=d.get("dy", d["dx"]),
-                         bc=O.BC_TRANSMISSIVE if d["bc"] == "transmissive" else O.BC_PERIODIC)
+                         bc=_OBC[d["bc"]])
         oref, _, _ = O.run(cfg, S, 0.0, 0.6, 1.0, max_steps=3)
         assert _rel(got, oref) <= 1e-12
 

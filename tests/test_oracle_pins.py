@@ -311,3 +311,95 @@ def test_invalid_configuration_rejected():
         O.state_size(O.make_cfg(1, O.EULER, 4))
     with pytest.raises(ValueError):
         O.state_size(O.make_cfg(1, O.BURGERS, 16, bc=O.BC_REFLECTIVE))
+
+
+# ------------------------------------------------------------------------------------------------
+# reflective walls (Remarks RBC-1d, RBC-2d-x, RBC-2d-y)
+
+def _mirror_1d(S):
+    """[0, L] -> [-L, L]: cell -1-i is the mirror of cell i (U: (+, -, +), V: (-, +, -))."""
+    sU = np.array([1, -1, 1])[:, None, None]
+    sV = np.array([-1, 1, -1])[:, None, None]
+    D = np.concatenate([S[..., ::-1], S], axis=-1)
+    n = S.shape[-1]
+    D[0, :, :, :n] *= sU
+    D[1, :, :, :n] *= sV
+    return D
+
+
+def test_reflective_wall_equals_mirrored_periodic_1d():
+    n = 40
+    S, dx = W.euler1d_random(n, 31, "smooth")
+    cfg = O.make_cfg(1, O.EULER, n, dx=dx, bc=O.BC_REFLECTIVE)
+    cfgp = O.make_cfg(1, O.EULER, 2 * n, dx=dx, bc=O.BC_PERIODIC)
+    L, M = O.rhs(cfg, S)
+    Lp, Mp = O.rhs(cfgp, _mirror_1d(S))
+    assert np.abs(L - Lp[..., n:]).max() <= 1e-12 * np.abs(L).max()
+    assert np.abs(M - Mp[..., n:]).max() <= 1e-12 * np.abs(M).max()
+    dt = O.cfl_dt(cfg, S, 0.6)
+    out = O.steps(cfg, S, dt, 3)
+    outp = O.steps(cfgp, _mirror_1d(S), dt, 3)
+    assert np.abs(out - outp[..., n:]).max() <= 1e-12 * np.abs(out).max()
+
+
+def _mirror_2d(S):
+    """[0, Lx] x [0, Ly] -> [-Lx, Lx] x [-Ly, Ly] with the x-wall and y-wall sign tables."""
+    X = np.array([[1, -1, 1, 1], [-1, 1, -1, -1], [1, -1, 1, 1]])[:, :, None, None]
+    Y = np.array([[1, 1, -1, 1], [1, 1, -1, 1], [-1, -1, 1, -1]])[:, :, None, None]
+    ny, nx = S.shape[2], S.shape[3]
+    right = S
+    left = S[..., ::-1] * X
+    top = np.concatenate([left, right], axis=-1)
+    bottom = top[..., ::-1, :] * Y
+    return np.concatenate([bottom, top], axis=-2)
+
+
+def test_reflective_walls_equal_mirrored_periodic_2d():
+    nx, ny = 14, 12
+    S, dx, dy = W.euler2d_random(nx, ny, 32, "smooth")
+    cfg = O.make_cfg(2, O.EULER, nx, ny, dx=dx, dy=dy, bc=O.BC_REFLECTIVE)
+    cfgp = O.make_cfg(2, O.EULER, 2 * nx, 2 * ny, dx=dx, dy=dy, bc=O.BC_PERIODIC)
+    D = _mirror_2d(S)
+    L, M = O.rhs(cfg, S)
+    Lp, Mp = O.rhs(cfgp, D)
+    sl = (Ellipsis, slice(ny, None), slice(nx, None))
+    assert np.abs(L - Lp[sl]).max() <= 1e-12 * np.abs(L).max()
+    assert np.abs(M - Mp[sl]).max() <= 1e-12 * np.abs(M).max()
+
+
+def test_reflective_walls_conserve_mass_and_energy():
+    """The wall faces carry no mass or energy flux: the mirror makes the normal momentum odd and
+    everything else even, so the central flux, the LF jump and both D-terms vanish there."""
+    S, dx = W.blast_wave_1d(200, p_mid=1.0)
+    cfg = O.make_cfg(1, O.EULER, 200, dx=dx, bc=O.BC_REFLECTIVE)
+    out, n, _ = O.run(cfg, S, 0.0, 0.6, 1.0, max_steps=30)
+    assert n == 30
+    S2, dx2, dy2 = W.euler2d_quadrants(20, 18, seed=2001)
+    cfg2 = O.make_cfg(2, O.EULER, 20, 18, dx=dx2, dy=dy2, bc=O.BC_REFLECTIVE)
+    out2, _, _ = O.run(cfg2, S2, 0.0, 0.6, 1.0, max_steps=10)
+    for a, b in ((S, out), (S2, out2)):
+        for k in (0, a.shape[1] - 1):
+            assert abs(b[0, k].sum() - a[0, k].sum()) <= 1e-13 * np.abs(a[0, k]).sum()
+        # the momenta are not conserved: the walls push back
+        assert abs(b[0, 1].sum() - a[0, 1].sum()) > 1e-6 * np.abs(b[0, 1]).sum()
+
+
+def test_blast_wave_first_stage_momentum_is_the_central_d_term():
+    """Example 4.4 as printed (P = 1000 | 0.01 at x = 0.1, u = 0, zero derivatives).  At rest the
+    momentum flux is P, and the face interpolations on the flat side pick the flat sub-stencil, so
+    the one node whose face stencil reaches across the jump (the second node on the low side) gets
+    its momentum rate from the central D-term alone (Eqs. Cd-1, DfDh):
+    L = D(f)/dx with D(f) = -(1/24)(9/8) dP - (7/5760) 3 dP, dP = 1000 - 0.01.  That moves the node
+    at -0.81 after the first stage, a kinetic energy above P/(gamma-1) = 0.025, so the pressure goes
+    negative and the printed problem cannot be run without a positivity safeguard."""
+    n = 400
+    S, dx = W.blast_wave_1d(n)
+    cfg = O.make_cfg(1, O.EULER, n, dx=dx, bc=O.BC_REFLECTIVE)
+    L, _ = O.rhs(cfg, S)
+    dP = 1000.0 - 0.01
+    D = -(9.0 / 8.0 / 24.0) * dP - (7.0 / 5760.0) * 3.0 * dP
+    assert abs(L[0, 1, 0, 41] - D / dx) <= 1e-9 * abs(D / dx)
+    dt = O.cfl_dt(cfg, S, 0.6)
+    m = S[0, 1, 0, 41] + dt * L[0, 1, 0, 41]
+    E = S[0, 2, 0, 41] + dt * L[0, 2, 0, 41]
+    assert 0.4 * (E - 0.5 * m * m / S[0, 0, 0, 41]) < 0.0

@@ -436,3 +436,21 @@ def batched_states(instances, gamma: float = 1.4):
                 S, dx, dy = euler2d_quadrants(n, seed=inst["seed"])
             out.append(({"dim": 2, "nx": n, "ny": n, "dx": dx, "dy": dy, "bc": "periodic", "gamma": gamma}, S))
     return out
+
+
+def blast_wave_1d(n: int, gamma: float = 1.4, p_mid: float = 0.01):
+    """Woodward-Colella blast wave on [0, 1] (Example 4.4): rho = 1, u = 0, P = 1000 / p_mid / 100 on
+    [0, 0.1), [0.1, 0.9), [0.9, 1]; derivatives zero.  Reflective walls at both ends.
+
+    p_mid = 0.01 is the printed problem.  The scheme without a positivity safeguard loses it in
+    the first stage: the central D-term of the momentum flux at the face next to the 1e5
+    pressure jump moves the first low-pressure node with a kinetic energy above its internal
+    energy.  p_mid = 1 keeps the geometry, the wall reflections and the interaction of the two
+    blasts, with a pressure ratio of 1e3."""
+    x = centres(n, 0.0, 1.0)
+    p = np.where(x < 0.1, 1000.0, np.where(x < 0.9, p_mid, 100.0))
+    one, zero = np.ones(n), np.zeros(n)
+    U, _ = euler_from_primitive_1d(one, zero, p, zero, zero, zero, gamma)
+    S = np.zeros((2, 3, 1, n))
+    S[0, :, 0] = U
+    return S, 1.0 / n
