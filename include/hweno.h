@@ -62,8 +62,8 @@ enum {
  * dim: 1 or 2.  system: HWENO_ADVECTION, HWENO_BURGERS or HWENO_EULER.  gamma: ratio of specific
  * heats (Euler only, > 1).  bc: boundary condition on every side (periodic, as in every accuracy
  * test of Sec. 4; transmissive = zero-order extrapolation of U and of its derivatives; reflective =
- * a wall at each end: ghost cell -1-k mirrors cell k with the sign tables of the reflective-boundary
- * remarks closing Sec. 2 (1D) and Sec. 3 (2D) (normal velocity odd; the normal derivative of every other
+ * a wall at each end: ghost cell -1-k mirrors cell k with the sign tables of Eqs. RBC-1d, RBC-2d-x,
+ * RBC-2d-y (normal velocity odd; the normal derivative of every other
  * primitive odd, of the normal velocity even), Euler only).
  * EINVAL: dim not 1 or 2, nx < 5 (ny < 5 in 2D), dx or dy <= 0, gamma <= 1 for Euler, unknown
  * system or bc, reflective with a scalar system.  ny and dy are ignored when dim == 1.

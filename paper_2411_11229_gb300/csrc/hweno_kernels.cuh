@@ -219,9 +219,9 @@ __device__ __forceinline__ void cell_body(const Grid& g, const double* __restric
           swap_frame<NC>(U3[q]);
           swap_frame<NC>(D3[q]);
         }
-        if (SYS == SYS_EULER && refl) {
-          mirror_U<NC>(U3[q]);
-          mirror_D<NC>(D3[q]);
+        if (SYS == SYS_EULER) {
+          mirror_U<NC>(U3[q], refl);
+          mirror_D<NC>(D3[q], refl);
         }
       }
       Eig<NC> e;
@@ -283,9 +283,9 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
       swap_frame<NC>(Uq[q]);
       swap_frame<NC>(Zq[q]);
     }
-    if (SYS == SYS_EULER && refl[q]) {
-      mirror_U<NC>(Uq[q]);
-      mirror_D<NC>(Zq[q]);
+    if (SYS == SYS_EULER) {
+      mirror_U<NC>(Uq[q], refl[q]);
+      mirror_D<NC>(Zq[q], refl[q]);
     }
   }
   // characteristic fields at the face: Roe average of the two adjacent cells
@@ -295,8 +295,8 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
     const double sl = w.PRIM[pc[1]], sr = w.PRIM[pc[2]];
     const int ou = dir == 0 ? 1 : 2, ov = dir == 0 ? 2 : 1;
     // a mirrored neighbour has the opposite normal velocity
-    const double ul = refl[1] ? -w.PRIM[ou * plane + pc[1]] : w.PRIM[ou * plane + pc[1]];
-    const double ur = refl[2] ? -w.PRIM[ou * plane + pc[2]] : w.PRIM[ou * plane + pc[2]];
+    const double ul = neg_if(w.PRIM[ou * plane + pc[1]], refl[1]);
+    const double ur = neg_if(w.PRIM[ou * plane + pc[2]], refl[2]);
     double vl = 0, vr = 0;
     if (DIM == 2) {
       vl = w.PRIM[ov * plane + pc[1]];
@@ -357,15 +357,14 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
   double fh[NC], hh[NC], mh[NC];
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
-    // nodal values of mirrored neighbours (normal frame): f and the mixed value take -sU, the
-    // normal-derivative flux takes sU, with sU = -1 for the normal momentum and +1 otherwise
-    const double sU = k == 1 ? -1.0 : 1.0;
-    const double sf0 = refl[0] ? -sU : 1.0, sf1 = refl[1] ? -sU : 1.0;
-    const double sf2 = refl[2] ? -sU : 1.0, sf3 = refl[3] ? -sU : 1.0;
-    const double f0 = sf0 * nod[k * plane + pc[0]], f1 = sf1 * nod[k * plane + pc[1]];
-    const double f2 = sf2 * nod[k * plane + pc[2]], f3 = sf3 * nod[k * plane + pc[3]];
-    const double h0 = (refl[0] ? sU : 1.0) * nod[(NC + k) * plane + pc[0]];
-    const double h3 = (refl[3] ? sU : 1.0) * nod[(NC + k) * plane + pc[3]];
+    // nodal values of mirrored neighbours (normal frame): f and the mixed value change sign except
+    // for the normal momentum, the normal-derivative flux changes sign only for the normal momentum
+    const bool nm = k == 1;
+    const bool s0 = refl[0] && !nm, s1 = refl[1] && !nm, s2 = refl[2] && !nm, s3 = refl[3] && !nm;
+    const double f0 = neg_if(nod[k * plane + pc[0]], s0), f1 = neg_if(nod[k * plane + pc[1]], s1);
+    const double f2 = neg_if(nod[k * plane + pc[2]], s2), f3 = neg_if(nod[k * plane + pc[3]], s3);
+    const double h0 = neg_if(nod[(NC + k) * plane + pc[0]], refl[0] && nm);
+    const double h3 = neg_if(nod[(NC + k) * plane + pc[3]], refl[3] && nm);
     // D-terms (Eqs. Cd-1, DfDh)
     const double Df = fma(DCoef::cf, (f0 - f1) + (f3 - f2), g.chh[dir] * (h0 - h3));
     const double Dh = fma(g.efih[dir], f0 - f3, fma(g.egih[dir], f2 - f1, DCoef::eh * (h0 + h3)));
@@ -373,8 +372,10 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
     // Dm, Dp and the Jacobian products carry the factor h: 1/(2h) restores both
     hh[k] = fma(g.hih[dir], fma(-alpha, Dp[k] - Dm[k], HDm[k] + HDp[k]), Dh);
     if (DIM == 2) {
-      const double o0 = sf0 * nod[(2 * NC + k) * plane + pc[0]], o1 = sf1 * nod[(2 * NC + k) * plane + pc[1]];
-      const double o2 = sf2 * nod[(2 * NC + k) * plane + pc[2]], o3 = sf3 * nod[(2 * NC + k) * plane + pc[3]];
+      const double o0 = neg_if(nod[(2 * NC + k) * plane + pc[0]], s0);
+      const double o1 = neg_if(nod[(2 * NC + k) * plane + pc[1]], s1);
+      const double o2 = neg_if(nod[(2 * NC + k) * plane + pc[2]], s2);
+      const double o3 = neg_if(nod[(2 * NC + k) * plane + pc[3]], s3);
       // Eq. (mixed)
       mh[k] = fma(7.0 / 12.0, o1 + o2, (-1.0 / 12.0) * (o0 + o3));
     }

@@ -316,19 +316,26 @@ __device__ __forceinline__ int bc_index(int k, int n, int bc) {
   return bc_map(k, n, bc, refl);
 }
 
-// A mirrored cell in the normal frame (Remarks RBC-1d, RBC-2d-x, RBC-2d-y): in U and in the
-// tangential derivative the normal momentum changes sign; in the normal derivative every
-// component except that of the normal momentum changes sign.  Its nodal values then follow
-// exactly: f -> -sU f, f'(u) v (normal derivative) -> sU (f'(u) v), mixed value -> -sU (...).
+// -x when b, else x: a flip of the sign bit in the integer pipe, so that a data-dependent sign
+// costs no FP64 instruction
+__device__ __forceinline__ double neg_if(double x, bool b) {
+  return __hiloint2double(__double2hiint(x) ^ (b ? (int)0x80000000 : 0), __double2loint(x));
+}
+
+// A mirrored cell in the normal frame (Eqs. RBC-1d, RBC-2d-x, RBC-2d-y):
+// in U and in the tangential derivative the normal momentum changes sign; in the normal derivative
+// every component except that of the normal momentum changes sign.  Its nodal values then follow
+// exactly: f -> -sU f, f'(u) v (normal derivative) -> sU (f'(u) v), mixed value -> -sU (...),
+// with sU = -1 for the normal momentum and +1 otherwise.
 template <int NC>
-__device__ __forceinline__ void mirror_U(double* q) {
-  q[1] = -q[1];
+__device__ __forceinline__ void mirror_U(double* q, bool b) {
+  q[1] = neg_if(q[1], b);
 }
 template <int NC>
-__device__ __forceinline__ void mirror_D(double* q) {
+__device__ __forceinline__ void mirror_D(double* q, bool b) {
 #pragma unroll
   for (int k = 0; k < NC; ++k)
-    if (k != 1) q[k] = -q[k];
+    if (k != 1) q[k] = neg_if(q[k], b);
 }
 
 __device__ __forceinline__ unsigned long long dbl_bits(double x) {
