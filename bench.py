@@ -33,8 +33,9 @@ UNIT = "Mcell-updates/s"
 # FP64 rate of GB300 (2 DFMA per SM per clock = 4 flop/clk/SM): 152 * 2.07e9 * 4.
 FP64_PEAK_FLOPS = 152 * 2.07e9 * 4
 HBM_PEAK_GBS_FALLBACK = 6800.0
-# DRAM bytes per launch of the 2D Euler face kernel at 4096^2 from ncu (profiles/), per face.
-FACE_TRAFFIC_BYTES_PER_FACE = 285.0  # 2048^2 capture of the current kernel, profiles/k_face_euler2d_2048_full.md
+# DRAM bytes per face of the 2D Euler face kernel from an ncu capture at 2048^2 (profiles/); the
+# traffic grows in proportion to the faces, so a 4096^2 launch moves this times its faces.
+FACE_TRAFFIC_BYTES_PER_FACE = 285.4  # ncu dram bytes per face, 2048^2 capture of the current face kernel
 
 
 def _dist():
@@ -160,17 +161,17 @@ def run_batched(dev, steps: int = 3):
     return res
 
 
-def run_adjoint(dev, nsteps: int = 200, every: int = 20):
+def run_adjoint(dev, n: int = 1024, nsteps: int = 200, every: int = 20):
     """The adjoint workload: 2D Euler 1024^2, smooth wave plus 8 seeded Fourier modes, J = 1/2 sum
     rho(T)^2 dx dy after 200 SSP-RK3 steps, gradient through the checkpointed rollout (checkpoints
-    every 20 steps).  Reports the cost of one adjoint step relative to one forward step."""
+    every 20 steps).  Reports the cost of one adjoint step relative to one forward step.  n and
+    nsteps only shrink it for a profiler capture."""
     import torch
 
     import workloads as W
     from paper_2411_11229_gb300 import Solver
     from paper_2411_11229_gb300.adjoint import Rollout
 
-    n = 1024
     S0n, dx, dy = W.euler2d_adjoint_init(n, seed=4000)
     s = Solver(2, "euler", n, n, dx=dx, dy=dy, device=dev)
     s.set_state(S0n)
@@ -194,7 +195,7 @@ def run_adjoint(dev, nsteps: int = 200, every: int = 20):
     lam = s.adjoint_step_stages(Sn, S1, S2, dt, al, lam)
     lam = s.adjoint_step(Sn, dt, al, lam)
     torch.cuda.synchronize()
-    res = {"workload": "2D Euler 1024^2 periodic, smooth wave + 8 seeded modes, J = 1/2 sum rho^2 dx dy",
+    res = {"workload": f"2D Euler {n}^2 periodic, smooth wave + 8 seeded modes, J = 1/2 sum rho^2 dx dy",
            "ms_forward_step": fwd}
     for name, fn in (("from_stages", lambda l: s.adjoint_step_stages(Sn, S1, S2, dt, al, l)),
                      ("self_contained", lambda l: s.adjoint_step(Sn, dt, al, l))):
@@ -382,7 +383,7 @@ def run_ours(args, ws, rank, local):
         line["batched"] = run_batched(dev)
     if ws == 1 and not args.no_adjoint:
         torch.cuda.empty_cache()
-        line["adjoint"] = run_adjoint(dev)
+        line["adjoint"] = run_adjoint(dev, args.adjoint_n, args.adjoint_steps, min(20, args.adjoint_steps))
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -399,6 +400,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-n", type=int, default=1024)
+    ap.add_argument("--adjoint-steps", type=int, default=200)
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
