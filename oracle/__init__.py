@@ -24,7 +24,10 @@ _lock = threading.Lock()
 _lib = None
 
 ADVECTION, BURGERS, EULER = 0, 1, 2
-BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_FIXED = 0, 1, 2, 3
+# scheme variants: v^+/- with the nonlinear weights, D-terms of Eq. (Cd-2), characteristic
+# decomposition with the eigenvectors of each side's centre cell
+FLAG_V_WEIGHTED, FLAG_CD2, FLAG_R2 = 1, 2, 4
 
 
 def build(force: bool = False) -> str:
@@ -41,19 +44,30 @@ def build(force: bool = False) -> str:
 
 class Cfg(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("system", ctypes.c_int32), ("nx", ctypes.c_int32),
-                ("ny", ctypes.c_int32), ("bc", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("ny", ctypes.c_int32), ("bc", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("gamma0", ctypes.c_double), ("d0", ctypes.c_double), ("eps", ctypes.c_double),
-                ("ax", ctypes.c_double), ("ay", ctypes.c_double)]
+                ("ax", ctypes.c_double), ("ay", ctypes.c_double), ("grav", ctypes.c_double),
+                ("side", ctypes.c_int32 * 4), ("fixed", (ctypes.c_double * 4) * 4)]
 
 
 def make_cfg(dim, system, nx, ny=1, dx=1.0, dy=1.0, gamma=1.4, bc=BC_PERIODIC, gamma0=None, d0=0.9,
-             eps=1e-10, ax=1.0, ay=1.0) -> Cfg:
-    """Scheme parameters; gamma0 defaults to 0.95 (1D) / 0.99 (2D) and d0 to 0.9 (Sec. 4)."""
+             eps=1e-10, ax=1.0, ay=1.0, flags=0, grav=0.0, sides=None, fixed=None) -> Cfg:
+    """Scheme parameters; gamma0 defaults to 0.95 (1D) / 0.99 (2D) and d0 to 0.9 (Sec. 4).
+
+    bc applies to every side unless ``sides`` gives the four types (x-low, x-high, y-low, y-high);
+    ``fixed`` maps a side index to the conserved state held in its ghost cells (BC_FIXED).
+    grav: g of the gravity source of Eq. (euler2d-s) (2D Euler)."""
     if gamma0 is None:
         gamma0 = 0.95 if dim == 1 else 0.99
-    return Cfg(dim, system, nx, ny if dim == 2 else 1, bc, 0, dx, dy if dim == 2 else dx, gamma,
-               gamma0, d0, eps, ax, ay)
+    c = Cfg(dim, system, nx, ny if dim == 2 else 1, bc, flags, dx, dy if dim == 2 else dx, gamma,
+            gamma0, d0, eps, ax, ay, grav)
+    for k, t in enumerate(sides if sides is not None else (bc,) * 4):
+        c.side[k] = t
+    for k, U in (fixed or {}).items():
+        for j, u in enumerate(U):
+            c.fixed[k][j] = float(u)
+    return c
 
 
 _P = ctypes.POINTER(ctypes.c_double)
@@ -86,8 +100,9 @@ def lib():
             L.oracle_steps_replay.argtypes = [CP, _P, ctypes.c_int, _P, _P]
             L.oracle_adjoint_step.argtypes = [CP, _P, ctypes.c_double, _P, _P, _P]
             L.oracle_stencil.argtypes = [_P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                         ctypes.c_double, _P]
+                                         ctypes.c_double, ctypes.c_int, _P]
             L.oracle_dterms.argtypes = [_P, _P, ctypes.c_double, _P]
+            L.oracle_dterms2.argtypes = [_P, _P, ctypes.c_double, _P]
             L.oracle_euler_flux.argtypes = [CP, ctypes.c_int, _P, _P]
             L.oracle_euler_jacobian.argtypes = [CP, ctypes.c_int, _P, _P]
             L.oracle_euler_eigen.argtypes = [CP, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]
@@ -225,23 +240,27 @@ def adjoint_step(cfg: Cfg, Sn, dt: float, alpha6, lam_in):
     return lam
 
 
-def stencil(u3, v2, dx, gamma0=0.95, d0=0.9, eps=1e-10) -> dict:
-    """All intermediates of one HWENO stencil (Sec. 2.1)."""
+def stencil(u3, v2, dx, gamma0=0.95, d0=0.9, eps=1e-10, v_weighted=False) -> dict:
+    """All intermediates of one HWENO stencil (Sec. 2.1); v_weighted: the FLAG_V_WEIGHTED variant
+    of v^+/-."""
     u3 = np.ascontiguousarray(u3, dtype=np.float64)
     v2 = np.ascontiguousarray(v2, dtype=np.float64)
     out = np.zeros(22)
     _check(lib().oracle_stencil(_ptr(u3), _ptr(v2), float(dx), float(gamma0), float(d0), float(eps),
-                                _ptr(out)))
+                                int(bool(v_weighted)), _ptr(out)))
     return {"p": out[0:3], "dp0_half": out[3], "dp_center": out[4:7], "beta": out[7:10],
             "tau": out[10], "omega_g": out[11:14], "omega_d": out[14:17], "u_minus": out[17],
             "v_minus": out[18], "v_mod": out[19], "u_plus": out[20], "v_plus": out[21]}
 
 
-def dterms(f4, h2, dx):
+def dterms(f4, h2, dx, form: int = 1):
+    """(D(f), D(h)) of Eq. (DfDh) from f_{i-1..i+2} and, for form 1 (Eq. Cd-1), h_{i-1}, h_{i+2};
+    for form 2 (Eq. Cd-2), h_i, h_{i+1}."""
     f4 = np.ascontiguousarray(f4, dtype=np.float64)
     h2 = np.ascontiguousarray(h2, dtype=np.float64)
     out = np.zeros(2)
-    _check(lib().oracle_dterms(_ptr(f4), _ptr(h2), float(dx), _ptr(out)))
+    fn = lib().oracle_dterms if form == 1 else lib().oracle_dterms2
+    _check(fn(_ptr(f4), _ptr(h2), float(dx), _ptr(out)))
     return float(out[0]), float(out[1])
 
 

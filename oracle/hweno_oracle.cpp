@@ -30,7 +30,21 @@
 //     modified derivative of cell i uses the eigenvectors of U_i.  D-terms, LF and mixed fluxes
 //     are componentwise.
 //   * Transmissive boundary: zero-order extrapolation of U and of its derivatives.
+//   * Fixed-state side (the top and bottom of Example 4.11): the ghost cells hold the given state
+//     with zero derivatives.
+//   * Gravity source (Eq. euler2d-s, 2D Euler): L_U gains (0, 0, g rho, g rho nu); the derivative
+//     equations gain its derivatives, g (0, 0, V_rho, V_rhonu) and g (0, 0, W_rho, W_rhonu), taken
+//     from the stage input's own derivative fields (the semi-discrete operator; the modified
+//     derivative enters only the base of the time step).
 //   * dt = CFL dx / alpha (1D), CFL / (alpha_x/dx + alpha_y/dy) (2D); optional power p on dx.
+//
+// Variants (flags; the default is the scheme above):
+//   FLAG_V_WEIGHTED  v^+/- combined with the nonlinear weights of u^+/- (the abstract's wording)
+//                    instead of the linear p0' value.
+//   FLAG_CD2         D-terms from Eq. (Cd-2) (h at the two inner nodes) instead of Eq. (Cd-1).
+//   FLAG_R2          characteristic decomposition with the eigenvectors of the stencil's own
+//                    centre cell (U_i for u^-_{i+1/2}, U_{i+1} for u^+_{i+1/2}) instead of the
+//                    Roe average at the face.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -43,11 +57,15 @@ using std::fabs;
 using std::sqrt;
 
 enum { ADVECTION = 0, BURGERS = 1, EULER = 2 };
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2, BC_FIXED = 3 };
+enum { FLAG_V_WEIGHTED = 1, FLAG_CD2 = 2, FLAG_R2 = 4 };
 
 struct Cfg {
-  int32_t dim, system, nx, ny, bc, pad_;
+  int32_t dim, system, nx, ny, bc, flags;
   double dx, dy, gamma, gamma0, d0, eps, ax, ay;
+  double grav;         // g of Eq. (euler2d-s); 0 = no source
+  int32_t side[4];     // boundary type of the sides x-low, x-high, y-low, y-high
+  double fixed[4][4];  // conserved state in the ghost cells of a BC_FIXED side
 };
 
 inline int ncomp(const Cfg& c) { return c.system == EULER ? (c.dim == 1 ? 3 : 4) : 1; }
@@ -76,7 +94,7 @@ struct StencilOut {
 
 template <class R>
 void hweno_stencil(const R& um, const R& u0, const R& up, const R& vm, const R& vp, double dx,
-                   const double g[3], const double d[3], double eps, StencilOut<R>& o) {
+                   const double g[3], const double d[3], double eps, StencilOut<R>& o, bool v_weighted = false) {
   // Eq. (Pxi)
   o.p[0] = -(1.0 / 8.0) * um + (9.0 / 16.0) * u0 + (9.0 / 16.0) * up - dx * ((3.0 / 64.0) * vm + (9.0 / 64.0) * vp);
   o.p[1] = -(1.0 / 2.0) * um + (3.0 / 2.0) * u0;
@@ -113,6 +131,12 @@ void hweno_stencil(const R& um, const R& u0, const R& up, const R& vm, const R& 
   o.u_half = o.wg[0] * ((1.0 / g[0]) * o.p[0] - (g[1] / g[0]) * o.p[1] - (g[2] / g[0]) * o.p[2]) + o.wg[1] * o.p[1] +
              o.wg[2] * o.p[2];
   o.v_half = o.dp0;
+  if (v_weighted) {
+    // the same combination applied to the derivatives at x_{i+1/2}; p1 and p2 are linear, so
+    // their derivatives there are their slopes
+    o.v_half = o.wg[0] * ((1.0 / g[0]) * o.dp0 - (g[1] / g[0]) * o.dpc[1] - (g[2] / g[0]) * o.dpc[2]) +
+               o.wg[1] * o.dpc[1] + o.wg[2] * o.dpc[2];
+  }
   // Eq. (limiter)
   o.v_mod = o.wd[0] * ((1.0 / d[0]) * o.dpc[0] - (d[1] / d[0]) * o.dpc[1] - (d[2] / d[0]) * o.dpc[2]) +
             o.wd[1] * o.dpc[1] + o.wd[2] * o.dpc[2];
@@ -121,9 +145,9 @@ void hweno_stencil(const R& um, const R& u0, const R& up, const R& vm, const R& 
 // u^-_{i+1/2}, v^-_{i+1/2} from the stencil of cell i (and v~_i as a by-product).
 template <class R>
 void interp_minus(const R& um, const R& u0, const R& up, const R& vm, const R& vp, double dx, const double g[3],
-                  const double d[3], double eps, R& u_half, R& v_half, R& v_mod) {
+                  const double d[3], double eps, R& u_half, R& v_half, R& v_mod, bool vw = false) {
   StencilOut<R> o;
-  hweno_stencil(um, u0, up, vm, vp, dx, g, d, eps, o);
+  hweno_stencil(um, u0, up, vm, vp, dx, g, d, eps, o, vw);
   u_half = o.u_half;
   v_half = o.v_half;
   v_mod = o.v_mod;
@@ -133,10 +157,10 @@ void interp_minus(const R& um, const R& u0, const R& up, const R& vm, const R& v
 // data are reflected about x_i (x -> 2 x_i - x): values swap ends, derivatives change sign.
 template <class R>
 void interp_plus(const R& um, const R& u0, const R& up, const R& vm, const R& vp, double dx, const double g[3],
-                 const double d[3], double eps, R& u_half, R& v_half) {
+                 const double d[3], double eps, R& u_half, R& v_half, bool vw = false) {
   StencilOut<R> o;
   R nvp = -vp, nvm = -vm;
-  hweno_stencil(up, u0, um, nvp, nvm, dx, g, d, eps, o);
+  hweno_stencil(up, u0, um, nvp, nvm, dx, g, d, eps, o, vw);
   u_half = o.u_half;
   v_half = -o.v_half;
 }
@@ -151,6 +175,18 @@ void dterms(const R& fm, const R& f0, const R& f1, const R& f2, const R& hm, con
   R P4 = -3.0 * (fm - f0 - f1 + f2) - 2.0 * dx * (hm - h2);                                  // dx^4 P''''
   R P5 = (1.0 / dx) * ((130.0 / 9.0) * fm - 30.0 * f0 + 30.0 * f1 - (130.0 / 9.0) * f2) +
          (20.0 / 3.0) * (hm + h2);                                                            // dx^4 P^(5)
+  Df = -(1.0 / 24.0) * P2 + (7.0 / 5760.0) * P4;
+  Dh = -(1.0 / 24.0) * P3 + (7.0 / 5760.0) * P5;
+}
+
+// The alternative of the remark after Eq. (D6): Eq. (Cd-2), from the Hermite interpolant (Pc2)
+// of f_{i-1..i+2} and h_i, h_{i+1}, combined by Eq. (DfDh) as before.
+template <class R>
+void dterms2(const R& fm, const R& f0, const R& f1, const R& f2, const R& h0, const R& h1, double dx, R& Df, R& Dh) {
+  R P2 = -(1.0 / 8.0) * (fm - f0 - f1 + f2) - (5.0 / 4.0) * dx * (h0 - h1);                  // dx^2 P''
+  R P3 = (1.0 / (4.0 * dx)) * (fm + 57.0 * f0 - 57.0 * f1 - f2) + (15.0 / 2.0) * (h0 + h1);  // dx^2 P'''
+  R P4 = 3.0 * (fm - f0 - f1 + f2) + 6.0 * dx * (h0 - h1);                                     // dx^4 P''''
+  R P5 = -(10.0 / dx) * (fm + 9.0 * f0 - 9.0 * f1 - f2) - 60.0 * (h0 + h1);                    // dx^4 P^(5)
   Df = -(1.0 / 24.0) * P2 + (7.0 / 5760.0) * P4;
   Dh = -(1.0 / 24.0) * P3 + (7.0 / 5760.0) * P5;
 }
@@ -413,7 +449,8 @@ inline double reflect_sign(const Cfg& c, int dir, int field, int comp) {
   return dir == 0 ? X[field][comp] : Y[field][comp];
 }
 
-// index of the interior cell that supplies ghost/interior index i on an axis of n cells
+// index of the interior cell that supplies ghost/interior index i on an axis of n cells, for a
+// side of type bc (periodic, transmissive or reflective)
 inline int bc_source(int bc, int i, int n, bool* flipped) {
   *flipped = false;
   if (i >= 0 && i < n) return i;
@@ -423,23 +460,51 @@ inline int bc_source(int bc, int i, int n, bool* flipped) {
   return i < 0 ? -1 - i : 2 * n - 1 - i;
 }
 
+// Where the value of field f, component k at cell (j, i) (interior or ghost) comes from: either
+// sgn * S[idx], or the constant `value` (a fixed-state side).
+struct Source {
+  bool fixed;
+  double value, sgn;
+  size_t idx;
+};
+
+inline Source boundary_source(const Cfg& c, int f, int k, int j, int i) {
+  const int m = ncomp(c);
+  const int nx = c.nx, ny = c.dim == 2 ? c.ny : 1;
+  Source s{false, 0.0, 1.0, 0};
+  int si = i, sj = j;
+  const int sx = i < 0 ? 0 : (i >= nx ? 1 : -1);
+  const int sy = c.dim == 1 ? -1 : (j < 0 ? 2 : (j >= ny ? 3 : -1));
+  for (int side : {sx, sy}) {
+    if (side < 0) continue;
+    if (c.side[side] == BC_FIXED) {
+      s.fixed = true;
+      s.value = f == 0 ? c.fixed[side][k] : 0.0;  // the state, with zero derivatives
+      return s;
+    }
+  }
+  bool fx = false, fy = false;
+  if (sx >= 0) si = bc_source(c.side[sx], i, nx, &fx);
+  if (sy >= 0) sj = bc_source(c.side[sy], j, ny, &fy);
+  if (fx) s.sgn *= reflect_sign(c, 0, f, k);
+  if (fy) s.sgn *= reflect_sign(c, 1, f, k);
+  s.idx = ((size_t)f * m + k) * ((size_t)nx * ny) + (size_t)sj * nx + si;
+  return s;
+}
+
+template <class R>
+R boundary_value(const Cfg& c, const R* S, int f, int k, int j, int i) {
+  const Source s = boundary_source(c, f, k, j, i);
+  if (s.fixed) return R(s.value);
+  return s.sgn == 1.0 ? S[s.idx] : -S[s.idx];
+}
+
 template <class R>
 void fill_padded(const Cfg& c, const R* S, Padded<R>& P) {
-  const size_t plane = (size_t)P.nx * P.ny;
   for (int f = 0; f < P.nf; ++f)
     for (int k = 0; k < P.nc; ++k)
       for (int j = -P.gy; j < P.ny + P.gy; ++j)
-        for (int i = -P.gx; i < P.nx + P.gx; ++i) {
-          bool fx, fy;
-          int si = bc_source(c.bc, i, P.nx, &fx);
-          int sj = c.dim == 2 ? bc_source(c.bc, j, P.ny, &fy) : 0;
-          if (c.dim == 1) fy = false;
-          double sgn = 1.0;
-          if (fx) sgn *= reflect_sign(c, 0, f, k);
-          if (fy) sgn *= reflect_sign(c, 1, f, k);
-          R val = S[((size_t)f * P.nc + k) * plane + (size_t)sj * P.nx + si];
-          P.at(f, k, j, i) = sgn == 1.0 ? val : -val;
-        }
+        for (int i = -P.gx; i < P.nx + P.gx; ++i) P.at(f, k, j, i) = boundary_value(c, S, f, k, j, i);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -463,32 +528,53 @@ struct Operator {
   // cells k-1..k+2 around face k+1/2 -> U^-, D^-, U^+, D^+ at the face.
   void face_states(int dir, R Uc[4][4], R Dc[4][4], R* Um, R* Dm, R* Up, R* Dp) const {
     double h = dir == 0 ? c.dx : c.dy;
+    const bool vw = (c.flags & FLAG_V_WEIGHTED) != 0;
     if (c.system != EULER) {
       R vmod;
-      interp_minus(Uc[0][0], Uc[1][0], Uc[2][0], Dc[0][0], Dc[2][0], h, g, d, c.eps, Um[0], Dm[0], vmod);
-      interp_plus(Uc[1][0], Uc[2][0], Uc[3][0], Dc[1][0], Dc[3][0], h, g, d, c.eps, Up[0], Dp[0]);
+      interp_minus(Uc[0][0], Uc[1][0], Uc[2][0], Dc[0][0], Dc[2][0], h, g, d, c.eps, Um[0], Dm[0], vmod, vw);
+      interp_plus(Uc[1][0], Uc[2][0], Uc[3][0], Dc[1][0], Dc[3][0], h, g, d, c.eps, Up[0], Dp[0], vw);
       return;
     }
-    // local characteristic decomposition at the face
-    EigenState<R> s = roe_average(c, Uc[1], Uc[2]);
-    R Rm[16], Lm[16];
-    right_eigen(c, dir, s, Rm);
-    left_eigen(c, dir, s, Lm);
-    R W[4][4], Z[4][4];
+    // local characteristic decomposition: one basis at the face (Roe average), or with FLAG_R2
+    // the basis of each side's centre cell (U_k for the minus side, U_{k+1} for the plus side)
+    const bool r2 = (c.flags & FLAG_R2) != 0;
+    EigenState<R> sm = r2 ? cell_state(c, Uc[1]) : roe_average(c, Uc[1], Uc[2]);
+    EigenState<R> sp = r2 ? cell_state(c, Uc[2]) : sm;
+    R Rmm[16], Lmm[16], Rpp[16], Lpp[16];
+    right_eigen(c, dir, sm, Rmm);
+    left_eigen(c, dir, sm, Lmm);
+    if (r2) {
+      right_eigen(c, dir, sp, Rpp);
+      left_eigen(c, dir, sp, Lpp);
+    } else {
+      for (int e = 0; e < 16; ++e) {
+        Rpp[e] = Rmm[e];
+        Lpp[e] = Lmm[e];
+      }
+    }
+    R Wm[4][4], Zm[4][4], Wp[4][4], Zp[4][4];
     for (int q = 0; q < 4; ++q) {
-      matvec(m, Lm, Uc[q], W[q]);
-      matvec(m, Lm, Dc[q], Z[q]);
+      matvec(m, Lmm, Uc[q], Wm[q]);
+      matvec(m, Lmm, Dc[q], Zm[q]);
+      for (int k = 0; k < m; ++k) {
+        Wp[q][k] = Wm[q][k];
+        Zp[q][k] = Zm[q][k];
+      }
+      if (r2) {
+        matvec(m, Lpp, Uc[q], Wp[q]);
+        matvec(m, Lpp, Dc[q], Zp[q]);
+      }
     }
     R wm[4], zm[4], wp[4], zp[4];
     for (int s2 = 0; s2 < m; ++s2) {
       R vmod;
-      interp_minus(W[0][s2], W[1][s2], W[2][s2], Z[0][s2], Z[2][s2], h, g, d, c.eps, wm[s2], zm[s2], vmod);
-      interp_plus(W[1][s2], W[2][s2], W[3][s2], Z[1][s2], Z[3][s2], h, g, d, c.eps, wp[s2], zp[s2]);
+      interp_minus(Wm[0][s2], Wm[1][s2], Wm[2][s2], Zm[0][s2], Zm[2][s2], h, g, d, c.eps, wm[s2], zm[s2], vmod, vw);
+      interp_plus(Wp[1][s2], Wp[2][s2], Wp[3][s2], Zp[1][s2], Zp[3][s2], h, g, d, c.eps, wp[s2], zp[s2], vw);
     }
-    matvec(m, Rm, wm, Um);
-    matvec(m, Rm, zm, Dm);
-    matvec(m, Rm, wp, Up);
-    matvec(m, Rm, zp, Dp);
+    matvec(m, Rmm, wm, Um);
+    matvec(m, Rmm, zm, Dm);
+    matvec(m, Rpp, wp, Up);
+    matvec(m, Rpp, zp, Dp);
   }
 
   // modified derivative of one cell from U, D of cells i-1, i, i+1 (Eq. limiter)
@@ -538,7 +624,7 @@ struct Operator {
     // Step 1.1: interface values
     R Um[4], Dm[4], Up[4], Dp[4];
     face_states(dir, Uc, Dc, Um, Dm, Up, Dp);
-    // nodal fluxes for the D-terms (Eq. Pc: f at k-1..k+2, h at k-1 and k+2)
+    // nodal fluxes for the D-terms (Eq. Pc: f at k-1..k+2, h at k-1 and k+2; Eq. Pc2: h at k, k+1)
     R fn[4][4], hn[4][4], on[4][4];
     for (int q = 0; q < 4; ++q) {
       ph.flux(dir, Uc[q], fn[q]);
@@ -553,7 +639,10 @@ struct Operator {
     ph.jac_vec(dir, Up, Dp, HDp);
     for (int k = 0; k < m; ++k) {
       R Df, Dh;
-      dterms(fn[0][k], fn[1][k], fn[2][k], fn[3][k], hn[0][k], hn[3][k], h, Df, Dh);
+      if (c.flags & FLAG_CD2)
+        dterms2(fn[0][k], fn[1][k], fn[2][k], fn[3][k], hn[1][k], hn[2][k], h, Df, Dh);
+      else
+        dterms(fn[0][k], fn[1][k], fn[2][k], fn[3][k], hn[0][k], hn[3][k], h, Df, Dh);
       fhat[k] = 0.5 * (FUm[k] + FUp[k] - alpha * (Up[k] - Um[k])) + Df;
       hhat[k] = 0.5 * (HDm[k] + HDp[k] - alpha * (Dp[k] - Dm[k])) + Dh;
       if (c.dim == 2) {
@@ -633,8 +722,26 @@ struct Operator {
             if (c.dim == 2) val = val - (1.0 / c.dy) * (fy(f, k, j + 1, i) - fy(f, k, j, i));
             Lout[((size_t)f * m + k) * plane + (size_t)j * nx + i] = val;
           }
+    if (c.grav != 0.0)
+      for (int f = 0; f < nfl; ++f)
+        for (size_t p = 0; p < plane; ++p) {
+          R src[4];
+          source(f, [&](int k) { return S[((size_t)f * m + k) * plane + p]; }, src);
+          for (int k = 0; k < m; ++k) Lout[((size_t)f * m + k) * plane + p] = Lout[((size_t)f * m + k) * plane + p] + src[k];
+        }
     for (int k = 0; k < m; ++k)
       for (size_t p = 0; p < plane; ++p) Mout[(size_t)k * plane + p] = S[(size_t)k * plane + p];
+  }
+
+  // Eq. (euler2d-s): the gravity source of field f (U: g (0, 0, rho, rho nu); a derivative field:
+  // the same expression in that field's components), with val(k) the cell's component k of field f.
+  template <class Get>
+  void source(int f, Get val, R* src) const {
+    (void)f;
+    for (int k = 0; k < m; ++k) src[k] = R(0.0);
+    if (c.grav == 0.0) return;
+    src[2] = c.grav * val(0);
+    src[3] = c.grav * val(2);
   }
 
   // The same L and M at selected cells only, reading S through the boundary map (for checks at
@@ -642,16 +749,8 @@ struct Operator {
   void rhs_cells(const R* S, R alpha_x, R alpha_y, long long ncell, const long long* idx, R* Lout, R* Mout) const {
     const int nx = c.nx, ny = c.dim == 2 ? c.ny : 1;
     const size_t plane = (size_t)nx * ny;
-    auto value = [&](int f, int k, int j, int i) -> R {
-      bool fx, fy = false;
-      int si = bc_source(c.bc, i, nx, &fx);
-      int sj = c.dim == 2 ? bc_source(c.bc, j, ny, &fy) : 0;
-      double sgn = 1.0;
-      if (fx) sgn *= reflect_sign(c, 0, f, k);
-      if (fy) sgn *= reflect_sign(c, 1, f, k);
-      R v = S[((size_t)f * m + k) * plane + (size_t)sj * nx + si];
-      return sgn == 1.0 ? v : -v;
-    };
+    (void)plane;
+    auto value = [&](int f, int k, int j, int i) -> R { return boundary_value(c, S, f, k, j, i); };
     for (long long s = 0; s < ncell; ++s) {
       const int i = (int)(idx[s] % nx), j = (int)(idx[s] / nx);
       R Lc[3][4], Mc[3][4];
@@ -692,6 +791,12 @@ struct Operator {
         modified_derivative(dir, Uc, Dc, Dt);
         for (int k = 0; k < m; ++k) Mc[own][k] = Dt[k];
       }
+      if (c.grav != 0.0)
+        for (int f = 0; f < nf; ++f) {
+          R src[4];
+          source(f, [&](int k) { return value(f, k, j, i); }, src);
+          for (int k = 0; k < m; ++k) Lc[f][k] = Lc[f][k] + src[k];
+        }
       for (int f = 0; f < nf; ++f)
         for (int k = 0; k < m; ++k) {
           Lout[((size_t)s * nf + f) * m + k] = Lc[f][k];
@@ -858,16 +963,26 @@ inline void stage_vjp(const Cfg& c, const double* S, double ax, double ay, const
   for (int k = 0; k < m; ++k)
     for (size_t p = 0; p < plane; ++p) lam[k * plane + p] += muM[k * plane + p];  // M = (U, ...)
   // boundary map of a cell (f, k, j, i) to its source cell and sign
-  auto source = [&](int f, int k, int j, int i, size_t* idx) -> double {
-    bool fx, fy = false;
-    int si = bc_source(c.bc, i, nx, &fx);
-    int sj = c.dim == 2 ? bc_source(c.bc, j, ny, &fy) : 0;
-    double sgn = 1.0;
-    if (fx) sgn *= reflect_sign(c, 0, f, k);
-    if (fy) sgn *= reflect_sign(c, 1, f, k);
-    *idx = ((size_t)f * m + k) * plane + (size_t)sj * nx + si;
-    return sgn;
+  // (a fixed-state ghost value is a constant: sign 0, so it receives no adjoint)
+  auto source = [&](int f, int k, int j, int i, size_t* idx, double* val) -> double {
+    const Source s = boundary_source(c, f, k, j, i);
+    if (s.fixed) {
+      *idx = 0;
+      *val = s.value;
+      return 0.0;
+    }
+    *idx = s.idx;
+    *val = s.sgn * S[s.idx];
+    return s.sgn;
   };
+  double vu = 0.0, vd = 0.0, vo = 0.0;
+  // the gravity source is linear in S: L_f[2] += g S_f[0], L_f[3] += g S_f[2]
+  if (c.grav != 0.0)
+    for (int f = 0; f < nf; ++f)
+      for (size_t p = 0; p < plane; ++p) {
+        lam[((size_t)f * m + 0) * plane + p] += c.grav * muL[((size_t)f * m + 2) * plane + p];
+        lam[((size_t)f * m + 2) * plane + p] += c.grav * muL[((size_t)f * m + 3) * plane + p];
+      }
   std::vector<double> g;
   for (int dir = 0; dir < c.dim; ++dir) {
     const double h = dir == 0 ? c.dx : c.dy;
@@ -895,13 +1010,13 @@ inline void stage_vjp(const Cfg& c, const double* S, double ax, double ay, const
           int jj, ii;
           cell(a - 1 + q, &jj, &ii);
           for (int k = 0; k < m; ++k) {
-            su[q][k] = source(0, k, jj, ii, &iu[q][k]);
-            sd[q][k] = source(own, k, jj, ii, &id[q][k]);
-            Uc[q][k] = adj_var(su[q][k] * S[iu[q][k]]);
-            Dc[q][k] = adj_var(sd[q][k] * S[id[q][k]]);
+            su[q][k] = source(0, k, jj, ii, &iu[q][k], &vu);
+            sd[q][k] = source(own, k, jj, ii, &id[q][k], &vd);
+            Uc[q][k] = adj_var(vu);
+            Dc[q][k] = adj_var(vd);
             if (c.dim == 2) {
-              so[q][k] = source(other, k, jj, ii, &io[q][k]);
-              Oc[q][k] = adj_var(so[q][k] * S[io[q][k]]);
+              so[q][k] = source(other, k, jj, ii, &io[q][k], &vo);
+              Oc[q][k] = adj_var(vo);
             }
           }
         }
@@ -932,10 +1047,10 @@ inline void stage_vjp(const Cfg& c, const double* S, double ax, double ay, const
           int jj, ii;
           cell(a - 1 + q, &jj, &ii);
           for (int k = 0; k < m; ++k) {
-            su[q][k] = source(0, k, jj, ii, &iu[q][k]);
-            sd[q][k] = source(own, k, jj, ii, &id[q][k]);
-            Uc[q][k] = adj_var(su[q][k] * S[iu[q][k]]);
-            Dc[q][k] = adj_var(sd[q][k] * S[id[q][k]]);
+            su[q][k] = source(0, k, jj, ii, &iu[q][k], &vu);
+            sd[q][k] = source(own, k, jj, ii, &id[q][k], &vd);
+            Uc[q][k] = adj_var(vu);
+            Dc[q][k] = adj_var(vd);
           }
         }
         op.modified_derivative(dir, Uc, Dc, Dt);
@@ -1043,8 +1158,15 @@ static int check_cfg(const oracle_cfg* c) {
   if (c->nx < 5 || (c->dim == 2 && c->ny < 5)) return -1;
   if (!(c->dx > 0) || (c->dim == 2 && !(c->dy > 0))) return -1;
   if (c->system == hwo::EULER && !(c->gamma > 1.0)) return -1;
-  if (c->bc < 0 || c->bc > 2) return -1;
-  if (c->bc == hwo::BC_REFLECTIVE && c->system != hwo::EULER) return -1;
+  for (int sd = 0; sd < (c->dim == 2 ? 4 : 2); ++sd) {
+    if (c->side[sd] < 0 || c->side[sd] > hwo::BC_FIXED) return -1;
+    if (c->side[sd] == hwo::BC_REFLECTIVE && c->system != hwo::EULER) return -1;
+  }
+  // periodic pairs opposite sides
+  if ((c->side[0] == hwo::BC_PERIODIC) != (c->side[1] == hwo::BC_PERIODIC)) return -1;
+  if (c->dim == 2 && (c->side[2] == hwo::BC_PERIODIC) != (c->side[3] == hwo::BC_PERIODIC)) return -1;
+  if (c->grav != 0.0 && !(c->dim == 2 && c->system == hwo::EULER)) return -1;  // Eq. (euler2d-s) only
+  if (c->flags < 0 || c->flags > 7) return -1;
   if (!(c->gamma0 > 0 && c->gamma0 < 1) || !(c->d0 > 0 && c->d0 < 1) || !(c->eps > 0)) return -1;
   return 0;
 }
@@ -1244,11 +1366,13 @@ int oracle_adjoint_step(const oracle_cfg* c, const double* Sn, double dt, const 
 // out[0..2] p_l(x_{i+1/2}); out[3] p0'(x_{i+1/2}); out[4..6] p_l'(x_i); out[7..9] beta_l; out[10] tau;
 // out[11..13] omega^gamma; out[14..16] omega^d; out[17] u^-_{i+1/2}; out[18] v^-_{i+1/2};
 // out[19] v~_i; out[20] u^+_{i-1/2}; out[21] v^+_{i-1/2}.
-int oracle_stencil(const double* u3, const double* v2, double dx, double gamma0, double d0, double eps, double* out) {
+int oracle_stencil(const double* u3, const double* v2, double dx, double gamma0, double d0, double eps, int v_weighted,
+                   double* out) {
   double g[3] = {gamma0, 0.5 * (1.0 - gamma0), 0.5 * (1.0 - gamma0)};
   double d[3] = {d0, 0.5 * (1.0 - d0), 0.5 * (1.0 - d0)};
+  const bool vw = v_weighted != 0;
   hwo::StencilOut<double> o;
-  hwo::hweno_stencil(u3[0], u3[1], u3[2], v2[0], v2[1], dx, g, d, eps, o);
+  hwo::hweno_stencil(u3[0], u3[1], u3[2], v2[0], v2[1], dx, g, d, eps, o, vw);
   for (int l = 0; l < 3; ++l) out[l] = o.p[l];
   out[3] = o.dp0;
   for (int l = 0; l < 3; ++l) out[4 + l] = o.dpc[l];
@@ -1259,13 +1383,19 @@ int oracle_stencil(const double* u3, const double* v2, double dx, double gamma0,
   out[17] = o.u_half;
   out[18] = o.v_half;
   out[19] = o.v_mod;
-  hwo::interp_plus(u3[0], u3[1], u3[2], v2[0], v2[1], dx, g, d, eps, out[20], out[21]);
+  hwo::interp_plus(u3[0], u3[1], u3[2], v2[0], v2[1], dx, g, d, eps, out[20], out[21], vw);
   return 0;
 }
 
 // D-terms of Eqs. (Cd-1), (DfDh): f4 = f_{i-1..i+2}, h2 = (h_{i-1}, h_{i+2}); out = (Df, Dh)
 int oracle_dterms(const double* f4, const double* h2, double dx, double* out) {
   hwo::dterms(f4[0], f4[1], f4[2], f4[3], h2[0], h2[1], dx, out[0], out[1]);
+  return 0;
+}
+
+// Eq. (Cd-2): h2 = (h_i, h_{i+1})
+int oracle_dterms2(const double* f4, const double* h2, double dx, double* out) {
+  hwo::dterms2(f4[0], f4[1], f4[2], f4[3], h2[0], h2[1], dx, out[0], out[1]);
   return 0;
 }
 

@@ -454,3 +454,45 @@ def blast_wave_1d(n: int, gamma: float = 1.4, p_mid: float = 0.01):
     S = np.zeros((2, 3, 1, n))
     S[0, :, 0] = U
     return S, 1.0 / n
+
+
+def rayleigh_taylor(nx: int, ny: int = None, gamma: float = 5.0 / 3.0):
+    """Rayleigh-Taylor instability of Example 4.11 on [0, 0.25] x [0, 1] (gravity g = 1 along +y):
+    rho = 2, P = 2y + 1 below y = 1/2; rho = 1, P = y + 1.5 above; u = 0,
+    v = -0.025 c cos(8 pi x) with c = sqrt(gamma P / rho).  Derivatives are the exact derivatives of
+    each side's smooth expressions (the interface is a jump).  Reflective walls left and right;
+    the bottom and top hold the fixed states (2, 0, 0, 1) and (1, 0, 0, 2.5).
+    Returns (S, dx, dy, fixed) with fixed = {2: U_bottom, 3: U_top} in conserved variables."""
+    ny = 4 * nx if ny is None else ny
+    x = centres(nx, 0.0, 0.25)[None, :] * np.ones((ny, 1))
+    y = centres(ny, 0.0, 1.0)[:, None] * np.ones((1, nx))
+    low = y < 0.5
+    rho = np.where(low, 2.0, 1.0)
+    p = np.where(low, 2.0 * y + 1.0, y + 1.5)
+    p_y = np.where(low, 2.0, 1.0)
+    c = np.sqrt(gamma * p / rho)
+    c_y = 0.5 * gamma * p_y / (rho * c)
+    cosx, sinx = np.cos(8 * np.pi * x), np.sin(8 * np.pi * x)
+    v = -0.025 * c * cosx
+    v_x = 0.025 * c * 8 * np.pi * sinx
+    v_y = -0.025 * c_y * cosx
+    zero = np.zeros_like(x)
+    U, V = euler_from_primitive_2d(rho, zero, v, p, zero, zero, v_x, zero, gamma)
+    _, Wd = euler_from_primitive_2d(rho, zero, v, p, zero, zero, v_y, p_y, gamma)
+    S = np.stack([U, V, Wd])
+    fixed = {2: [2.0, 0.0, 0.0, 1.0 / (gamma - 1)], 3: [1.0, 0.0, 0.0, 2.5 / (gamma - 1)]}
+    return S, 0.25 / nx, 1.0 / ny, fixed
+
+
+def hydrostatic_column(nx: int, ny: int, rho0: float = 1.5, p0: float = 2.0, g: float = 1.0,
+                       gamma: float = 1.4):
+    """Fluid at rest with constant density and P = p0 + g rho0 y on [0, 1]^2 (exact derivatives):
+    the pressure gradient balances the gravity source of Eq. (euler2d-s)."""
+    x = centres(nx, 0.0, 1.0)[None, :] * np.ones((ny, 1))
+    y = centres(ny, 0.0, 1.0)[:, None] * np.ones((1, nx))
+    rho = rho0 * np.ones_like(x)
+    p = p0 + g * rho0 * y
+    zero = np.zeros_like(x)
+    U, V = euler_from_primitive_2d(rho, zero, zero, p, zero, zero, zero, zero, gamma)
+    _, Wd = euler_from_primitive_2d(rho, zero, zero, p, zero, zero, zero, g * rho0 * np.ones_like(x), gamma)
+    return np.stack([U, V, Wd]), 1.0 / nx, 1.0 / ny
