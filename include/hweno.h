@@ -47,7 +47,9 @@ extern "C" {
 typedef struct hweno_ctx hweno_t;
 
 enum { HWENO_ADVECTION = 0, HWENO_BURGERS = 1, HWENO_EULER = 2 };
-enum { HWENO_BC_PERIODIC = 0, HWENO_BC_TRANSMISSIVE = 1, HWENO_BC_REFLECTIVE = 2 };
+enum { HWENO_BC_PERIODIC = 0, HWENO_BC_TRANSMISSIVE = 1, HWENO_BC_REFLECTIVE = 2, HWENO_BC_FIXED = 3 };
+/* scheme variants of hweno_create_ex */
+enum { HWENO_FLAG_V_WEIGHTED = 1, HWENO_FLAG_CD2 = 2, HWENO_FLAG_R2 = 4 };
 enum {
   HWENO_OK = 0,
   HWENO_EINVAL = -1,   /* invalid argument */
@@ -70,6 +72,43 @@ enum {
  * Defaults (Sec. 4): gamma0 = 0.95 (1D) / 0.99 (2D), d0 = 0.9, eps = 1e-10, CFL = 0.6, a = (1, 1). */
 int hweno_create(int dim, int system, int64_t nx, int64_t ny, double dx, double dy, double gamma,
                  int bc, hweno_t **out);
+
+/* Extensions of the scheme for hweno_create_ex.
+ *   flags: any of
+ *     HWENO_FLAG_V_WEIGHTED  v^+/- formed with the nonlinear weights of u^+/- (the same combination
+ *                            of the candidates' derivatives, p1' and p2' being their slopes) instead
+ *                            of the linear value p0' of Eq. (interp);
+ *     HWENO_FLAG_CD2         the D-terms of Eq. (Cd-2) (Hermite data h_i, h_{i+1}, the alternative
+ *                            the paper describes after Eq. D6) instead of Eq. (Cd-1);
+ *     HWENO_FLAG_R2          characteristic decomposition with the eigenvectors of each stencil's
+ *                            centre cell (U_i for u^-_{i+1/2}, U_{i+1} for u^+_{i+1/2}) instead of
+ *                            the Roe average at the face (Euler; no effect on scalar laws).  Every
+ *                            cell then interpolates both of its faces in its own characteristic
+ *                            fields in one pass.
+ *   side[4]: boundary type of the sides x-low, x-high, y-low, y-high (side[2], side[3] unused in
+ *     1D): HWENO_BC_PERIODIC (both ends of an axis or neither), _TRANSMISSIVE, _REFLECTIVE (Euler),
+ *     or HWENO_BC_FIXED: the ghost cells hold the conserved state fixed[side] with zero derivatives
+ *     (the fixed top and bottom states of Example 4.11).
+ *   grav: g of the gravity source of Eq. (euler2d-s), (0, 0, g rho, g rho nu) on U and its
+ *     derivatives g (0, 0, rho_x, (rho nu)_x) and g (0, 0, rho_y, (rho nu)_y) on the derivative
+ *     equations, taken from the stage input (2D Euler only; 0 = none).
+ *   fixed[side]: conserved state (rho, rho mu[, rho nu], E) or (u) of a HWENO_BC_FIXED side. */
+typedef struct hweno_ext {
+  int32_t flags;
+  int32_t side[4];
+  int32_t pad_;
+  double grav;
+  double fixed[4][4];
+} hweno_ext;
+
+/* hweno_create with the extensions above (ext is read during the call only).  A configuration
+ * with no flag, no gravity and one non-fixed type on every side is exactly hweno_create with that
+ * type.  EINVAL: as hweno_create, and an unknown flag or side type, periodic on one end of an axis
+ * only, reflective with a scalar system, gravity outside 2D Euler, a non-finite or (Euler)
+ * non-physical fixed state.  The adjoint entry points return EINVAL for a handle with
+ * extensions. */
+int hweno_create_ex(int dim, int system, int64_t nx, int64_t ny, double dx, double dy, double gamma,
+                    const hweno_ext *ext, hweno_t **out);
 
 /* Linear weights gamma = (gamma0, (1-gamma0)/2, (1-gamma0)/2) and d = (d0, (1-d0)/2, (1-d0)/2)
  * (Sec. 4), epsilon of Eq. (nonlinear), the CFL number, and the advection speeds.

@@ -11,7 +11,8 @@ import threading
 from . import _make as _build
 
 HWENO_ADVECTION, HWENO_BURGERS, HWENO_EULER = 0, 1, 2
-HWENO_BC_PERIODIC, HWENO_BC_TRANSMISSIVE, HWENO_BC_REFLECTIVE = 0, 1, 2
+HWENO_BC_PERIODIC, HWENO_BC_TRANSMISSIVE, HWENO_BC_REFLECTIVE, HWENO_BC_FIXED = 0, 1, 2, 3
+HWENO_FLAG_V_WEIGHTED, HWENO_FLAG_CD2, HWENO_FLAG_R2 = 1, 2, 4
 HWENO_OK, HWENO_EINVAL, HWENO_ECUDA, HWENO_ENOMEM, HWENO_ENONPHYS, HWENO_ESTATE = 0, -1, -2, -3, -4, -5
 HWENO_ETOOBIG = -6
 
@@ -22,6 +23,7 @@ _I = ctypes.c_int
 _H = ctypes.c_void_p
 SIGNATURES = {
     "hweno_create": (_I, [_I, _I, ctypes.c_int64, ctypes.c_int64, _D, _D, _D, _I, ctypes.POINTER(_H)]),
+    "hweno_create_ex": (_I, [_I, _I, ctypes.c_int64, ctypes.c_int64, _D, _D, _D, _P, ctypes.POINTER(_H)]),
     "hweno_set_params": (_I, [_H, _D, _D, _D, _D, _D, _D]),
     "hweno_set_stream": (_I, [_H, _P]),
     "hweno_state_doubles": (ctypes.c_size_t, [_H]),
@@ -64,6 +66,12 @@ SIGNATURES = {
     "hweno_strerror": (ctypes.c_char_p, [_I]),
     "hweno_launch_count": (ctypes.c_longlong, [_H]),
 }
+
+class HwenoExt(ctypes.Structure):
+    """hweno_ext of include/hweno.h"""
+    _fields_ = [("flags", ctypes.c_int32), ("side", ctypes.c_int32 * 4), ("pad_", ctypes.c_int32),
+                ("grav", ctypes.c_double), ("fixed", (ctypes.c_double * 4) * 4)]
+
 
 class HwenoDesc(ctypes.Structure):
     """hweno_desc of include/hweno.h"""

@@ -573,7 +573,7 @@ extern "C" {
 int hweno_adjoint_step(hweno_t* h, const double* Sn, double dt, const double* alpha6, const double* lam_in,
                        double* lam_out, void* adj_ws) {
   if (!h || !Sn || !alpha6 || !lam_in || !lam_out || !adj_ws) return HWENO_EINVAL;
-  if (h->system != HWENO_EULER || h->bc == HWENO_BC_REFLECTIVE) return HWENO_EINVAL;
+  if (h->system != HWENO_EULER || h->bc == HWENO_BC_REFLECTIVE || h->var != 0) return HWENO_EINVAL;
   if (!(dt > 0.0) || ((uintptr_t)adj_ws & 255)) return HWENO_EINVAL;
   if (!h->ws) return HWENO_ESTATE;
   const AdjPtrs a = adj_ptrs(h, adj_ws);
@@ -591,7 +591,7 @@ int hweno_adjoint_step(hweno_t* h, const double* Sn, double dt, const double* al
 int hweno_adjoint_step_stages(hweno_t* h, const double* Sn, const double* S1, const double* S2, double dt,
                               const double* alpha6, const double* lam_in, double* lam_out, void* adj_ws) {
   if (!h || !Sn || !S1 || !S2 || !alpha6 || !lam_in || !lam_out || !adj_ws) return HWENO_EINVAL;
-  if (h->system != HWENO_EULER || h->bc == HWENO_BC_REFLECTIVE) return HWENO_EINVAL;
+  if (h->system != HWENO_EULER || h->bc == HWENO_BC_REFLECTIVE || h->var != 0) return HWENO_EINVAL;
   if (!(dt > 0.0) || ((uintptr_t)adj_ws & 255)) return HWENO_EINVAL;
   return adjoint_from_stages(h, adj_ptrs(h, adj_ws), Sn, S1, S2, dt, alpha6, lam_in, lam_out);
 }
@@ -633,7 +633,7 @@ int hweno_step_record(hweno_t* h, double* rec7) {
 int hweno_stage_vjp(hweno_t* h, const double* S, const double* alpha2, const double* muM, const double* muL,
                     double* lam, void* adj_ws) {
   if (!h || !S || !alpha2 || !muM || !muL || !lam || !adj_ws) return HWENO_EINVAL;
-  if (h->system != HWENO_EULER || h->bc == HWENO_BC_REFLECTIVE) return HWENO_EINVAL;
+  if (h->system != HWENO_EULER || h->bc == HWENO_BC_REFLECTIVE || h->var != 0) return HWENO_EINVAL;
   if ((uintptr_t)adj_ws & 255) return HWENO_EINVAL;
   const AdjPtrs a = adj_ptrs(h, adj_ws);
   const Grid g = grid_of(h);

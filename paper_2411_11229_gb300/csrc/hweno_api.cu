@@ -11,6 +11,19 @@ __global__ void k_rcp_check(const double* __restrict__ x, double* __restrict__ r
 }
 }  // namespace hw
 
+namespace {
+// the scheme of the paper with one boundary type on every side
+void set_plain_scheme(hweno_ctx* h, int bc) {
+  h->var = 0;
+  h->flags = 0;
+  h->grav = 0.0;
+  for (int sd = 0; sd < 4; ++sd) {
+    h->side[sd] = bc;
+    for (int k = 0; k < 4; ++k) h->fixed[sd][k] = 0.0;
+  }
+}
+}  // namespace
+
 extern "C" {
 
 int hweno_create(int dim, int system, int64_t nx, int64_t ny, double dx, double dy, double gamma, int bc,
@@ -34,6 +47,7 @@ int hweno_create(int dim, int system, int64_t nx, int64_t ny, double dx, double 
   h->dim = dim;
   h->system = system;
   h->bc = bc;
+  set_plain_scheme(h, bc);
   h->nx = nx;
   h->ny = ny;
   h->dx = dx;
@@ -55,6 +69,53 @@ int hweno_create(int dim, int system, int64_t nx, int64_t ny, double dx, double 
     h->kernel_n[k] = 0;
   }
   *out = h;
+  return HWENO_OK;
+}
+
+int hweno_create_ex(int dim, int system, int64_t nx, int64_t ny, double dx, double dy, double gamma,
+                    const hweno_ext* ext, hweno_t** out) {
+  if (!out) return HWENO_EINVAL;
+  *out = nullptr;
+  if (!ext) return HWENO_EINVAL;
+  const int nsides = dim == 2 ? 4 : 2;
+  for (int sd = 0; sd < nsides; ++sd) {
+    const int t = ext->side[sd];
+    if (t < HWENO_BC_PERIODIC || t > HWENO_BC_FIXED) return HWENO_EINVAL;
+    if (t == HWENO_BC_REFLECTIVE && system != HWENO_EULER) return HWENO_EINVAL;
+  }
+  // periodic pairs the two ends of an axis
+  if ((ext->side[0] == HWENO_BC_PERIODIC) != (ext->side[1] == HWENO_BC_PERIODIC)) return HWENO_EINVAL;
+  if (dim == 2 && (ext->side[2] == HWENO_BC_PERIODIC) != (ext->side[3] == HWENO_BC_PERIODIC)) return HWENO_EINVAL;
+  if (ext->flags < 0 || ext->flags > (HWENO_FLAG_V_WEIGHTED | HWENO_FLAG_CD2 | HWENO_FLAG_R2)) return HWENO_EINVAL;
+  if (!std::isfinite(ext->grav)) return HWENO_EINVAL;
+  if (ext->grav != 0.0 && !(dim == 2 && system == HWENO_EULER)) return HWENO_EINVAL;
+  const int nc = system == HWENO_EULER ? (dim == 1 ? 3 : 4) : 1;
+  bool uniform = true, any_fixed = false;
+  for (int sd = 0; sd < nsides; ++sd) {
+    uniform = uniform && ext->side[sd] == ext->side[0];
+    if (ext->side[sd] != HWENO_BC_FIXED) continue;
+    any_fixed = true;
+    const double* U = ext->fixed[sd];
+    for (int k = 0; k < nc; ++k)
+      if (!std::isfinite(U[k])) return HWENO_EINVAL;
+    if (system == HWENO_EULER) {
+      const double vv = dim == 2 ? U[1] * U[1] + U[2] * U[2] : U[1] * U[1];
+      if (!(U[0] > 0.0) || !((gamma - 1.0) * (U[nc - 1] - 0.5 * vv / U[0]) > 0.0)) return HWENO_EINVAL;
+    }
+  }
+  const int bc0 = any_fixed ? HWENO_BC_TRANSMISSIVE : ext->side[0];
+  int rc = hweno_create(dim, system, nx, ny, dx, dy, gamma, bc0, out);
+  if (rc) return rc;
+  hweno_ctx* h = *out;
+  h->flags = ext->flags;
+  h->grav = ext->grav;
+  for (int sd = 0; sd < 4; ++sd) {
+    h->side[sd] = sd < nsides ? ext->side[sd] : HWENO_BC_PERIODIC;
+    for (int k = 0; k < 4; ++k) h->fixed[sd][k] = k < nc ? ext->fixed[sd][k] : 0.0;
+  }
+  // the scheme of the paper with one boundary type runs the plain kernels
+  const bool plain = ext->flags == 0 && ext->grav == 0.0 && uniform && !any_fixed;
+  h->var = plain ? 0 : ((ext->flags & HWENO_FLAG_R2) && system == HWENO_EULER ? 2 : 1);
   return HWENO_OK;
 }
 
@@ -110,6 +171,11 @@ int hweno_bind(hweno_t* h, double* state_dev, void* ws) {
   h->w.status = reinterpret_cast<unsigned int*>(p);
   h->w.astride = 2;
   p += l.status;
+  h->w.FS = l.FS ? reinterpret_cast<double*>(p) : nullptr;
+  p += l.FS;
+  h->w.GFS = l.GFS ? reinterpret_cast<double*>(p) : nullptr;
+  p += l.GFS;
+  h->w.gstride = gstride_of(h);
   h->state = state_dev;
   h->ws = static_cast<unsigned char*>(ws);
   if (cudaMemsetAsync(scal_begin, 0, l.alpha + l.scal + l.status, h->stream) != cudaSuccess) return HWENO_ECUDA;
@@ -314,6 +380,7 @@ extern "C" int hweno_rhs_static(int dim, int system, int64_t nx, int64_t ny, dou
   if (!S || !Lo || !Mo || S == Lo || S == Mo || Lo == Mo) return HWENO_EINVAL;
   // the same validation as hweno_create, on a handle that lives on this stack frame
   hweno_ctx h;
+  set_plain_scheme(&h, bc);
   if (dim != 1 && dim != 2) return HWENO_EINVAL;
   if (system < HWENO_ADVECTION || system > HWENO_EULER) return HWENO_EINVAL;
   if (bc < HWENO_BC_PERIODIC || bc > HWENO_BC_REFLECTIVE) return HWENO_EINVAL;
@@ -381,6 +448,8 @@ extern "C" int hweno_rhs_static(int dim, int system, int64_t nx, int64_t ny, dou
   p += l.scal;
   h.w.status = reinterpret_cast<unsigned int*>(p);
   h.w.astride = 2;
+  h.w.FS = h.w.GFS = nullptr;
+  h.w.gstride = 0;
   // the array keeps the previous call's contents: clear the wavespeed slots and the status word
   if (cudaMemsetAsync(scal_begin, 0, l.alpha + l.scal + l.status, h.stream) != cudaSuccess) return HWENO_ECUDA;
   return stage(&h, S, const_cast<double*>(S), 1, 0, 0.0, 3, Lo, Mo);

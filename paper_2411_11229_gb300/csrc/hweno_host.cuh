@@ -25,34 +25,47 @@ struct Launchers {
   void (*update)(const Grid&, double*, const Work&, int, int, double, double, double, int, double*, double*,
                  cudaStream_t);
   void (*wavespeed)(const Grid&, const double*, const Work&, int, cudaStream_t);
+  void (*ghost)(const Grid&, const double*, const Work&, cudaStream_t);  // R2 only, else null
 };
 
 inline unsigned blocks_for(long long n) { return (unsigned)((n + hw::kThreads - 1) / hw::kThreads); }
 
-template <int DIM, int SYS>
+template <int DIM, int SYS, int VAR>
 struct L {
   static void cell(const Grid& g, const double* S, const Work& w, int slot, cudaStream_t st) {
-    hw::k_cell<DIM, SYS><<<blocks_for(g.plane), hw::kThreads, 0, st>>>(g, S, w, slot);
+    hw::k_cell<DIM, SYS, VAR><<<blocks_for(g.plane), hw::kThreads, 0, st>>>(g, S, w, slot);
   }
   static void face(const Grid& g, const double* S, const Work& w, int slot, cudaStream_t st) {
     const long long nfx = (long long)(g.nx + 1) * g.ny;
     const long long nfy = DIM == 2 ? (long long)(g.ny + 1) * g.nx : 0;
     dim3 grid(blocks_for(nfx > nfy ? nfx : nfy), DIM);
-    hw::k_face<DIM, SYS><<<grid, hw::kThreads, 0, st>>>(g, S, w, slot);
+    hw::k_face<DIM, SYS, VAR><<<grid, hw::kThreads, 0, st>>>(g, S, w, slot);
   }
   static void update(const Grid& g, double* S, const Work& w, int mode, int stage, double a, double b,
                      double dt, int slot, double* Lo, double* Mo, cudaStream_t st) {
-    hw::k_update<DIM, SYS><<<blocks_for(g.plane), hw::kThreads, 0, st>>>(g, S, w, mode, stage, a, b, dt, slot, Lo, Mo);
+    hw::k_update<DIM, SYS, VAR><<<blocks_for(g.plane), hw::kThreads, 0, st>>>(g, S, w, mode, stage, a, b, dt, slot,
+                                                                            Lo, Mo);
   }
   static void wavespeed(const Grid& g, const double* S, const Work& w, int slot, cudaStream_t st) {
     hw::k_wavespeed<DIM, SYS><<<blocks_for(g.plane), hw::kThreads, 0, st>>>(g, S, w, slot);
   }
-  static constexpr Launchers table() { return Launchers{&cell, &face, &update, &wavespeed}; }
+  static void ghost(const Grid& g, const double* S, const Work& w, cudaStream_t st) {
+    hw::k_r2_ghost<DIM><<<blocks_for(2LL * DIM * w.gstride), hw::kThreads, 0, st>>>(g, S, w);
+  }
+  static constexpr Launchers table() {
+    return Launchers{&cell, &face, &update, &wavespeed, VAR == 2 ? &ghost : nullptr};
+  }
 };
 
-static const Launchers kTable[2][3] = {
-    {L<1, hw::SYS_ADV>::table(), L<1, hw::SYS_BURGERS>::table(), L<1, hw::SYS_EULER>::table()},
-    {L<2, hw::SYS_ADV>::table(), L<2, hw::SYS_BURGERS>::table(), L<2, hw::SYS_EULER>::table()}};
+// [VAR][dim - 1][system]; R2 exists for the Euler equations only (for a scalar law the per-cell
+// and per-face bases coincide, and the host runs VAR 1)
+static const Launchers kTable[3][2][3] = {
+    {{L<1, hw::SYS_ADV, 0>::table(), L<1, hw::SYS_BURGERS, 0>::table(), L<1, hw::SYS_EULER, 0>::table()},
+     {L<2, hw::SYS_ADV, 0>::table(), L<2, hw::SYS_BURGERS, 0>::table(), L<2, hw::SYS_EULER, 0>::table()}},
+    {{L<1, hw::SYS_ADV, 1>::table(), L<1, hw::SYS_BURGERS, 1>::table(), L<1, hw::SYS_EULER, 1>::table()},
+     {L<2, hw::SYS_ADV, 1>::table(), L<2, hw::SYS_BURGERS, 1>::table(), L<2, hw::SYS_EULER, 1>::table()}},
+    {{L<1, hw::SYS_ADV, 1>::table(), L<1, hw::SYS_BURGERS, 1>::table(), L<1, hw::SYS_EULER, 2>::table()},
+     {L<2, hw::SYS_ADV, 1>::table(), L<2, hw::SYS_BURGERS, 1>::table(), L<2, hw::SYS_EULER, 2>::table()}}};
 
 inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -63,6 +76,12 @@ struct hweno_ctx {
   int64_t nx, ny;
   double dx, dy, gamma;
   double gamma0, d0, eps, cfl, ax, ay;
+  // extended scheme (hweno_create_ex); var = 0 for the scheme of the paper with one boundary
+  // type, 1 with any extension, 2 with the per-cell characteristic decomposition (Euler)
+  int var, flags;
+  int side[4];
+  double grav;
+  double fixed[4][4];
   cudaStream_t stream;
   double* state;
   unsigned char* ws;
@@ -84,8 +103,10 @@ inline int np_of(const hweno_ctx* h) { return h->system == HWENO_EULER ? (h->dim
 
 // workspace sub-buffers in bytes, in layout order
 struct Layout {
-  size_t B, MD, NOD, PRIM, FX, FY, alpha, scal, status, total;
+  size_t B, MD, NOD, PRIM, FX, FY, alpha, scal, status, FS, GFS, total;
 };
+
+inline long long gstride_of(const hweno_ctx* h) { return h->nx > h->ny ? h->nx : h->ny; }
 
 inline Layout layout_of(const hweno_ctx* h) {
   const size_t plane = (size_t)h->nx * h->ny;
@@ -100,7 +121,9 @@ inline Layout layout_of(const hweno_ctx* h) {
   l.alpha = align_up(8 * 8);
   l.scal = align_up(8 * 8);
   l.status = align_up(16);
-  l.total = l.B + l.MD + l.NOD + l.PRIM + l.FX + l.FY + l.alpha + l.scal + l.status;
+  l.FS = h->var == 2 ? align_up((size_t)h->dim * 4 * nc * plane * 8) : 0;
+  l.GFS = h->var == 2 ? align_up((size_t)h->dim * 4 * nc * (size_t)gstride_of(h) * 8) : 0;
+  l.total = l.B + l.MD + l.NOD + l.PRIM + l.FX + l.FY + l.alpha + l.scal + l.status + l.FS + l.GFS;
   return l;
 }
 
@@ -109,7 +132,7 @@ inline Grid grid_of(const hweno_ctx* h) {
   g.nx = (int)h->nx;
   g.ny = (int)h->ny;
   g.bc = h->bc;
-  g.pad_ = 0;
+  g.flags = h->flags;
   g.plane = (long long)h->nx * h->ny;
   g.dx = h->dx;
   g.dy = h->dy;
@@ -147,6 +170,46 @@ inline Grid grid_of(const hweno_ctx* h) {
     g.efih[d] = hw::DCoef::ef / hs[d];
     g.egih[d] = hw::DCoef::eg / hs[d];
     g.hih[d] = 0.5 / hs[d];
+    g.c2h[d] = hw::DCoef2::ch * hs[d];
+    g.e2fih[d] = hw::DCoef2::ef / hs[d];
+    g.e2gih[d] = hw::DCoef2::eg / hs[d];
+  }
+  g.ig1 = 1.0 / g1;
+  g.grav = h->grav;
+  for (int sd = 0; sd < 4; ++sd) {
+    g.side[sd] = h->side[sd];
+    for (int k = 0; k < 4; ++k) g.fixU[sd][k] = g.fixP[sd][k] = g.fixF[sd][k] = 0.0;
+    if (h->side[sd] != hw::BC_FIXED) continue;
+    const double* U = h->fixed[sd];
+    for (int k = 0; k < 4; ++k) g.fixU[sd][k] = U[k];
+    const int nc = nc_of(h);
+    if (h->system != HWENO_EULER) {
+      // scalar: the flux of the state along the side's normal
+      const double a = sd < 2 ? h->ax : h->ay;
+      g.fixF[sd][0] = h->system == HWENO_ADVECTION ? a * U[0] : 0.5 * U[0] * U[0];
+      continue;
+    }
+    // primitives in the original frame, flux in the side's normal frame
+    const double rho = U[0], u = U[1] / rho, v = h->dim == 2 ? U[2] / rho : 0.0, E = U[nc - 1];
+    const double p = (h->gamma - 1.0) * (E - 0.5 * rho * (u * u + v * v));
+    const double H = (E + p) / rho;
+    g.fixP[sd][0] = std::sqrt(rho);
+    g.fixP[sd][1] = u;
+    if (h->dim == 2) {
+      g.fixP[sd][2] = v;
+      g.fixP[sd][3] = H;
+    } else {
+      g.fixP[sd][2] = H;
+    }
+    const double un = sd < 2 ? u : v, mn = rho * un, mt = sd < 2 ? U[2] : U[1];
+    g.fixF[sd][0] = mn;
+    g.fixF[sd][1] = mn * un + p;
+    if (h->dim == 2) {
+      g.fixF[sd][2] = mt * un;
+      g.fixF[sd][3] = (E + p) * un;
+    } else {
+      g.fixF[sd][2] = (E + p) * un;
+    }
   }
   return g;
 }
@@ -161,7 +224,7 @@ inline int read_status(hweno_ctx* h) {
   return st ? HWENO_ENONPHYS : HWENO_OK;
 }
 
-inline const Launchers& launchers(const hweno_ctx* h) { return kTable[h->dim - 1][h->system]; }
+inline const Launchers& launchers(const hweno_ctx* h) { return kTable[h->var][h->dim - 1][h->system]; }
 
 // one spatial-operator evaluation: cell, face; then update in the requested mode
 // alpha_override (device, 2 doubles, may be null): LF coefficients to use instead of the
@@ -182,6 +245,10 @@ inline int stage(hweno_ctx* h, const double* S_in, double* S_out, int mode, int 
   static const double b_k[3] = {1.0, 0.25, 2.0 / 3.0};
   if (ev[0]) cudaEventRecord(ev[0], h->stream);
   f.cell(g, S_in, h->w, slot, h->stream);
+  if (f.ghost) {
+    f.ghost(g, S_in, h->w, h->stream);
+    h->launches += 1;
+  }
   if (alpha_override &&
       cudaMemcpyAsync(h->w.alpha + slot * h->w.astride, alpha_override, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
                       h->stream) != cudaSuccess)

@@ -15,6 +15,13 @@
 // The path is bound by the FP64 pipe (a few thousand FP64 operations per cell and stage against
 // roughly a kilobyte of traffic), so the split keeps every warp's lanes busy on one kind of work
 // and exchanges intermediates through L2/HBM, which has bandwidth to spare.
+//
+// VAR selects the scheme: 0 is the scheme of the paper with one boundary type on every side;
+// 1 adds the runtime options (per-side boundary types with fixed-state sides, v^+/- with the
+// nonlinear weights, the D-terms of Eq. Cd-2, the gravity source of Eq. euler2d-s); 2 is 1 with
+// the per-cell characteristic decomposition (R2): k_cell interpolates both faces of every cell in
+// the cell's own characteristic fields and k_face only forms the fluxes; k_r2_ghost supplies the
+// face states of the ghost cells at the ends of every line.
 #pragma once
 #include "hweno_math.cuh"
 
@@ -33,6 +40,13 @@ struct Work {
   double* scal;               // [0] dt of the current step, [1] t, [2] t_end
   unsigned int* status;       // bit 0: non-physical state met
   long long astride;          // distance between slots (2 for a single grid)
+  // R2 only: face states of every cell, normal frame, derivatives scaled by h:
+  // FS [DIM][4][NC][plane] = (u^- and h v^- at the right face, u^+ and h v^+ at the left face);
+  // GFS [DIM][2 ends][2][NC][gstride] = the low ghost's right-face and the high ghost's
+  // left-face states of every line.
+  double* FS;
+  double* GFS;
+  long long gstride;
 };
 
 constexpr int kThreads = 128;
@@ -109,9 +123,96 @@ __device__ __forceinline__ void modified_derivative(const double (&U3)[3][NC], c
   }
 }
 
+// The ghost cell of a fixed-state side: the side's state (normal frame), zero derivatives.
+template <int NC, int SYS>
+__device__ __forceinline__ void load_fixed(const Grid& g, int side, int dir, double* U, double* D) {
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    U[k] = g.fixU[side][k];
+    D[k] = 0.0;
+  }
+  if (SYS == SYS_EULER && dir == 1) swap_frame<NC>(U);
+}
+
+// The three cells i-1, i, i+1 of cell (i, j) along direction d, through the boundary map (normal
+// frame, mirrored or fixed where the map says so).  U3[1] is taken from Uc (already loaded).
+template <int DIM, int SYS, int VAR, int NC>
+__device__ __forceinline__ void load_stencil3(const Grid& g, const double* __restrict__ S, int d, int i, int j,
+                                              int a0, const double* Uc, double (&U3)[3][NC], double (&D3)[3][NC]) {
+  const long long plane = g.plane;
+  const int n = d == 0 ? g.nx : g.ny;
+  const int fld = d == 0 ? 1 : 2;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    bool refl, fixed = false;
+    const int ac = VAR ? bc_map_ext(a0 - 1 + q, n, g.side[2 * d], g.side[2 * d + 1], refl, fixed)
+                       : bc_map(a0 - 1 + q, n, g.bc, refl);
+    const long long pc = d == 0 ? (long long)j * g.nx + ac : (long long)ac * g.nx + i;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      U3[q][k] = (q == 1 && Uc) ? Uc[k] : S[k * plane + pc];
+      D3[q][k] = S[(fld * NC + k) * plane + pc];
+    }
+    if (SYS == SYS_EULER && d == 1) {
+      swap_frame<NC>(U3[q]);
+      swap_frame<NC>(D3[q]);
+    }
+    if (SYS == SYS_EULER) {
+      mirror_U<NC>(U3[q], refl);
+      mirror_D<NC>(D3[q], refl);
+    }
+    if (VAR && fixed) load_fixed<NC, SYS>(g, 2 * d + (a0 - 1 + q < 0 ? 0 : 1), d, U3[q], D3[q]);
+  }
+}
+
+// R2: the modified derivative and the face states of one cell in one direction from its own
+// stencil in its own characteristic fields (normal frame; derivatives out scaled by h, v~ not).
+template <int NC, int SYS>
+__device__ __forceinline__ void r2_cell(const double (&U3)[3][NC], const double (&D3)[3][NC], const Eig<NC>& e,
+                                        int dir, const Grid& g, double* md, double (&fs)[4][NC]) {
+  const double h = g.h[dir], ih = g.ih[dir];
+  const bool vw = (g.flags & FLAG_V_WEIGHTED) != 0;
+  double W[3][NC], Zm[NC], Zp[NC], hDm[NC], hDp[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    hDm[k] = h * D3[0][k];
+    hDp[k] = h * D3[2][k];
+  }
+  if (SYS == SYS_EULER) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) e.project(U3[q], W[q]);
+    e.project(hDm, Zm);
+    e.project(hDp, Zp);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) W[q][0] = U3[q][0];
+    Zm[0] = hDm[0];
+    Zp[0] = hDp[0];
+  }
+  double cm[NC], chm[NC], cp[NC], chp[NC], ht[NC];
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    cell_faces_field(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], g, vw, cm[s], chm[s], cp[s], chp[s], ht[s]);
+    ht[s] *= ih;
+  }
+  if (SYS == SYS_EULER) {
+    e.back(cm, fs[0]);
+    e.back(chm, fs[1]);
+    e.back(cp, fs[2]);
+    e.back(chp, fs[3]);
+    e.back(ht, md);
+  } else {
+    fs[0][0] = cm[0];
+    fs[1][0] = chm[0];
+    fs[2][0] = cp[0];
+    fs[3][0] = chp[0];
+    md[0] = ht[0];
+  }
+}
+
 // Cell work of one stage at cell p: primitives and wavespeeds (returned in wsx, wsy), nodal
-// values per direction, modified derivatives.
-template <int DIM, int SYS>
+// values per direction, modified derivatives (and, for R2, the face states of the cell).
+template <int DIM, int SYS, int VAR = 0>
 __device__ __forceinline__ void cell_body(const Grid& g, const double* __restrict__ S, const Work& w, long long p,
                                           double& wsx, double& wsy) {
   using T = Traits<DIM, SYS>;
@@ -201,33 +302,23 @@ __device__ __forceinline__ void cell_body(const Grid& g, const double* __restric
     // modified derivatives (Eq. limiter), one per direction
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-      const int n = d == 0 ? g.nx : g.ny;
       const int a0 = d == 0 ? i : j;
-      const int fld = d == 0 ? 1 : 2;
       double U3[3][NC], D3[3][NC];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        bool refl;
-        const int ac = bc_map(a0 - 1 + q, n, g.bc, refl);
-        const long long pc = d == 0 ? (long long)j * g.nx + ac : (long long)ac * g.nx + i;
-#pragma unroll
-        for (int k = 0; k < NC; ++k) {
-          U3[q][k] = q == 1 ? U[k] : S[k * plane + pc];
-          D3[q][k] = S[(fld * NC + k) * plane + pc];
-        }
-        if (SYS == SYS_EULER && d == 1) {
-          swap_frame<NC>(U3[q]);
-          swap_frame<NC>(D3[q]);
-        }
-        if (SYS == SYS_EULER) {
-          mirror_U<NC>(U3[q], refl);
-          mirror_D<NC>(D3[q], refl);
-        }
-      }
+      load_stencil3<DIM, SYS, VAR, NC>(g, S, d, i, j, a0, U, U3, D3);
       Eig<NC> e;
       if (SYS == SYS_EULER) e.setup(d == 0 ? u : v, d == 0 ? v : u, H, c, ic, g.gm1);
       double out[NC];
-      modified_derivative<NC, SYS>(U3, D3, e, d, g, out);
+      if (VAR == 2) {
+        double fs[4][NC];
+        r2_cell<NC, SYS>(U3, D3, e, d, g, out, fs);
+        double* FSd = w.FS + (long long)d * 4 * NC * plane;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int k = 0; k < NC; ++k) FSd[(q * NC + k) * plane + p] = fs[q][k];
+      } else {
+        modified_derivative<NC, SYS>(U3, D3, e, d, g, out);
+      }
       if (SYS == SYS_EULER && d == 1) swap_frame<NC>(out);
 #pragma unroll
       for (int k = 0; k < NC; ++k) w.MD[((long long)d * NC + k) * plane + p] = out[k];
@@ -235,18 +326,18 @@ __device__ __forceinline__ void cell_body(const Grid& g, const double* __restric
   }
 }
 
-template <int DIM, int SYS>
+template <int DIM, int SYS, int VAR>
 __global__ void __launch_bounds__(kThreads) k_cell(Grid g, const double* __restrict__ S, Work w, int slot) {
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   double wsx = 0.0, wsy = 0.0;
-  if (p < g.plane) cell_body<DIM, SYS>(g, S, w, p, wsx, wsy);
+  if (p < g.plane) cell_body<DIM, SYS, VAR>(g, S, w, p, wsx, wsy);
   block_max2(wsx, wsy, w.alpha + slot * w.astride);
 }
 
 // ---------------------------------------------------------------------------------------------
 // Face work of one stage: face f of direction dir (x faces: f = j (nx+1) + i; y faces:
 // f = j nx + i), alpha = the LF coefficient of that direction.
-template <int DIM, int SYS>
+template <int DIM, int SYS, int VAR = 0>
 __device__ __forceinline__ void face_body(const Grid& g, const double* __restrict__ S, const Work& w, int dir,
                                           long long f, double alpha) {
   using T = Traits<DIM, SYS>;
@@ -263,85 +354,120 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
   }
   // cells fa-2 .. fa+1 around face fa (between cells fa-1 and fa)
   long long pc[4];
-  bool refl[4];
+  bool refl[4], fixed[4];
+  int fside[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const int a = bc_map(fa - 2 + q, n, g.bc, refl[q]);
+    fixed[q] = false;
+    fside[q] = 2 * dir + (fa - 2 + q < 0 ? 0 : 1);
+    const int a = VAR ? bc_map_ext(fa - 2 + q, n, g.side[2 * dir], g.side[2 * dir + 1], refl[q], fixed[q])
+                      : bc_map(fa - 2 + q, n, g.bc, refl[q]);
     pc[q] = dir == 0 ? (long long)line * g.nx + a : (long long)a * g.nx + line;
   }
   const int fown = dir == 0 ? 1 : 2, foth = dir == 0 ? 2 : 1;
   const double h = g.h[dir];
-  double Uq[4][NC], Zq[4][NC];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  double Um[NC], Up[NC], Dm[NC], Dp[NC];
+  if (VAR == 2) {
+    // R2: the face states were formed per cell (the low and high ghosts by k_r2_ghost)
+    const double* FSd = w.FS + (long long)dir * 4 * NC * plane;
+    const long long gs = w.gstride;
+    const double* Glo = w.GFS + (long long)(dir * 2 + 0) * 2 * NC * gs;
+    const double* Ghi = w.GFS + (long long)(dir * 2 + 1) * 2 * NC * gs;
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-      Uq[q][k] = S[k * plane + pc[q]];
-      Zq[q][k] = h * S[(fown * NC + k) * plane + pc[q]];
+      Um[k] = fa >= 1 ? FSd[(0 * NC + k) * plane + pc[1]] : Glo[(0 * NC + k) * gs + line];
+      Dm[k] = fa >= 1 ? FSd[(1 * NC + k) * plane + pc[1]] : Glo[(1 * NC + k) * gs + line];
+      Up[k] = fa < n ? FSd[(2 * NC + k) * plane + pc[2]] : Ghi[(0 * NC + k) * gs + line];
+      Dp[k] = fa < n ? FSd[(3 * NC + k) * plane + pc[2]] : Ghi[(1 * NC + k) * gs + line];
     }
-    if (SYS == SYS_EULER && dir == 1) {
-      swap_frame<NC>(Uq[q]);
-      swap_frame<NC>(Zq[q]);
+  } else {
+    double Uq[4][NC], Zq[4][NC];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        Uq[q][k] = S[k * plane + pc[q]];
+        Zq[q][k] = h * S[(fown * NC + k) * plane + pc[q]];
+      }
+      if (SYS == SYS_EULER && dir == 1) {
+        swap_frame<NC>(Uq[q]);
+        swap_frame<NC>(Zq[q]);
+      }
+      if (SYS == SYS_EULER) {
+        mirror_U<NC>(Uq[q], refl[q]);
+        mirror_D<NC>(Zq[q], refl[q]);
+      }
+      if (VAR && fixed[q]) load_fixed<NC, SYS>(g, fside[q], dir, Uq[q], Zq[q]);
     }
+    // characteristic fields at the face: Roe average of the two adjacent cells
+    Eig<NC> e;
+    double Wq[4][NC], Yq[4][NC];
     if (SYS == SYS_EULER) {
-      mirror_U<NC>(Uq[q], refl[q]);
-      mirror_D<NC>(Zq[q], refl[q]);
-    }
-  }
-  // characteristic fields at the face: Roe average of the two adjacent cells
-  Eig<NC> e;
-  double Wq[4][NC], Yq[4][NC];
-  if (SYS == SYS_EULER) {
-    const double sl = w.PRIM[pc[1]], sr = w.PRIM[pc[2]];
-    const int ou = dir == 0 ? 1 : 2, ov = dir == 0 ? 2 : 1;
-    // a mirrored neighbour has the opposite normal velocity
-    const double ul = neg_if(w.PRIM[ou * plane + pc[1]], refl[1]);
-    const double ur = neg_if(w.PRIM[ou * plane + pc[2]], refl[2]);
-    double vl = 0, vr = 0;
-    if (DIM == 2) {
-      vl = w.PRIM[ov * plane + pc[1]];
-      vr = w.PRIM[ov * plane + pc[2]];
-    }
-    const int oh = DIM == 2 ? 3 : 2;
-    const double Hl = w.PRIM[oh * plane + pc[1]], Hr = w.PRIM[oh * plane + pc[2]];
-    const double iw = rcp(sl + sr);
-    const double ub = fma(sl, ul, sr * ur) * iw;
-    const double vb = DIM == 2 ? fma(sl, vl, sr * vr) * iw : 0.0;
-    const double Hb = fma(sl, Hl, sr * Hr) * iw;
-    const double c2 = g.gm1 * fma(-0.5, DIM == 2 ? fma(ub, ub, vb * vb) : ub * ub, Hb);
-    const double ic = rsqrt(c2);
-    e.setup(ub, vb, Hb, c2 * ic, ic, g.gm1);
+      const int ou = dir == 0 ? 1 : 2, ov = dir == 0 ? 2 : 1;
+      const int oh = DIM == 2 ? 3 : 2;
+      double sl = w.PRIM[pc[1]], sr = w.PRIM[pc[2]];
+      // a mirrored neighbour has the opposite normal velocity
+      double ul = neg_if(w.PRIM[ou * plane + pc[1]], refl[1]);
+      double ur = neg_if(w.PRIM[ou * plane + pc[2]], refl[2]);
+      double vl = 0, vr = 0;
+      if (DIM == 2) {
+        vl = w.PRIM[ov * plane + pc[1]];
+        vr = w.PRIM[ov * plane + pc[2]];
+      }
+      double Hl = w.PRIM[oh * plane + pc[1]], Hr = w.PRIM[oh * plane + pc[2]];
+      if (VAR && fixed[1]) {
+        const double* P = g.fixP[fside[1]];
+        sl = P[0];
+        ul = P[ou];
+        if (DIM == 2) vl = P[ov];
+        Hl = P[oh];
+      }
+      if (VAR && fixed[2]) {
+        const double* P = g.fixP[fside[2]];
+        sr = P[0];
+        ur = P[ou];
+        if (DIM == 2) vr = P[ov];
+        Hr = P[oh];
+      }
+      const double iw = rcp(sl + sr);
+      const double ub = fma(sl, ul, sr * ur) * iw;
+      const double vb = DIM == 2 ? fma(sl, vl, sr * vr) * iw : 0.0;
+      const double Hb = fma(sl, Hl, sr * Hr) * iw;
+      const double c2 = g.gm1 * fma(-0.5, DIM == 2 ? fma(ub, ub, vb * vb) : ub * ub, Hb);
+      const double ic = rsqrt(c2);
+      e.setup(ub, vb, Hb, c2 * ic, ic, g.gm1);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      e.project(Uq[q], Wq[q]);
-      e.project(Zq[q], Yq[q]);
-    }
-  } else {
+      for (int q = 0; q < 4; ++q) {
+        e.project(Uq[q], Wq[q]);
+        e.project(Zq[q], Yq[q]);
+      }
+    } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      Wq[q][0] = Uq[q][0];
-      Yq[q][0] = Zq[q][0];
+      for (int q = 0; q < 4; ++q) {
+        Wq[q][0] = Uq[q][0];
+        Yq[q][0] = Zq[q][0];
+      }
     }
-  }
-  // HWENO interpolation in each characteristic field: u^- from the stencil of cell fa-1,
-  // u^+ from the stencil of cell fa (mirror image)
-  double cm[NC], chm[NC], cp[NC], chp[NC];
+    // HWENO interpolation in each characteristic field: u^- from the stencil of cell fa-1,
+    // u^+ from the stencil of cell fa (mirror image)
+    const bool vw = VAR && (g.flags & FLAG_V_WEIGHTED) != 0;
+    double cm[NC], chm[NC], cp[NC], chp[NC];
 #pragma unroll
-  for (int s = 0; s < NC; ++s)
-    face_field(Wq[0][s], Wq[1][s], Wq[2][s], Wq[3][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, cm[s], chm[s],
-               cp[s], chp[s]);
-  // back to conserved variables; the derivatives stay scaled by h
-  double Um[NC], Up[NC], Dm[NC], Dp[NC];
-  if (SYS == SYS_EULER) {
-    e.back(cm, Um);
-    e.back(cp, Up);
-    e.back(chm, Dm);
-    e.back(chp, Dp);
-  } else {
-    Um[0] = cm[0];
-    Up[0] = cp[0];
-    Dm[0] = chm[0];
-    Dp[0] = chp[0];
+    for (int s = 0; s < NC; ++s)
+      face_field(Wq[0][s], Wq[1][s], Wq[2][s], Wq[3][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, cm[s], chm[s],
+                 cp[s], chp[s], vw);
+    // back to conserved variables; the derivatives stay scaled by h
+    if (SYS == SYS_EULER) {
+      e.back(cm, Um);
+      e.back(cp, Up);
+      e.back(chm, Dm);
+      e.back(chp, Dp);
+    } else {
+      Um[0] = cm[0];
+      Up[0] = cp[0];
+      Dm[0] = chm[0];
+      Dp[0] = chp[0];
+    }
   }
   // Lax-Friedrichs fluxes at the interpolated states (Eq. flux-LF)
   const double a_adv = dir == 0 ? g.ax : g.ay;
@@ -354,6 +480,7 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
   double* out = dir == 0 ? w.FX : w.FY;
   const long long oplane = dir == 0 ? (long long)g.ny * (g.nx + 1) : (long long)(g.ny + 1) * g.nx;
   const long long fo = dir == 0 ? (long long)line * (g.nx + 1) + fa : (long long)fa * g.nx + line;
+  const bool cd2 = VAR && (g.flags & FLAG_CD2) != 0;
   double fh[NC], hh[NC], mh[NC];
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
@@ -361,21 +488,44 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
     // for the normal momentum, the normal-derivative flux changes sign only for the normal momentum
     const bool nm = k == 1;
     const bool s0 = refl[0] && !nm, s1 = refl[1] && !nm, s2 = refl[2] && !nm, s3 = refl[3] && !nm;
-    const double f0 = neg_if(nod[k * plane + pc[0]], s0), f1 = neg_if(nod[k * plane + pc[1]], s1);
-    const double f2 = neg_if(nod[k * plane + pc[2]], s2), f3 = neg_if(nod[k * plane + pc[3]], s3);
-    const double h0 = neg_if(nod[(NC + k) * plane + pc[0]], refl[0] && nm);
-    const double h3 = neg_if(nod[(NC + k) * plane + pc[3]], refl[3] && nm);
-    // D-terms (Eqs. Cd-1, DfDh)
-    const double Df = fma(DCoef::cf, (f0 - f1) + (f3 - f2), g.chh[dir] * (h0 - h3));
-    const double Dh = fma(g.efih[dir], f0 - f3, fma(g.egih[dir], f2 - f1, DCoef::eh * (h0 + h3)));
+    double f0 = neg_if(nod[k * plane + pc[0]], s0), f1 = neg_if(nod[k * plane + pc[1]], s1);
+    double f2 = neg_if(nod[k * plane + pc[2]], s2), f3 = neg_if(nod[k * plane + pc[3]], s3);
+    // h at the outer nodes (Eq. Cd-1) or, for Cd-2, at the inner ones
+    double ha = neg_if(nod[(NC + k) * plane + pc[cd2 ? 1 : 0]], refl[cd2 ? 1 : 0] && nm);
+    double hb = neg_if(nod[(NC + k) * plane + pc[cd2 ? 2 : 3]], refl[cd2 ? 2 : 3] && nm);
+    if (VAR) {
+      // a fixed-state ghost: the side's flux, zero derivative fluxes
+      if (fixed[0]) f0 = g.fixF[fside[0]][k];
+      if (fixed[1]) f1 = g.fixF[fside[1]][k];
+      if (fixed[2]) f2 = g.fixF[fside[2]][k];
+      if (fixed[3]) f3 = g.fixF[fside[3]][k];
+      if (fixed[cd2 ? 1 : 0]) ha = 0.0;
+      if (fixed[cd2 ? 2 : 3]) hb = 0.0;
+    }
+    double Df, Dh;
+    if (cd2) {
+      // D-terms (Eqs. Cd-2, DfDh)
+      Df = fma(DCoef2::cf, (f0 - f1) + (f3 - f2), g.c2h[dir] * (ha - hb));
+      Dh = fma(g.e2fih[dir], f0 - f3, fma(g.e2gih[dir], f1 - f2, DCoef2::eh * (ha + hb)));
+    } else {
+      // D-terms (Eqs. Cd-1, DfDh)
+      Df = fma(DCoef::cf, (f0 - f1) + (f3 - f2), g.chh[dir] * (ha - hb));
+      Dh = fma(g.efih[dir], f0 - f3, fma(g.egih[dir], f2 - f1, DCoef::eh * (ha + hb)));
+    }
     fh[k] = fma(0.5, fma(-alpha, Up[k] - Um[k], FUm[k] + FUp[k]), Df);
     // Dm, Dp and the Jacobian products carry the factor h: 1/(2h) restores both
     hh[k] = fma(g.hih[dir], fma(-alpha, Dp[k] - Dm[k], HDm[k] + HDp[k]), Dh);
     if (DIM == 2) {
-      const double o0 = neg_if(nod[(2 * NC + k) * plane + pc[0]], s0);
-      const double o1 = neg_if(nod[(2 * NC + k) * plane + pc[1]], s1);
-      const double o2 = neg_if(nod[(2 * NC + k) * plane + pc[2]], s2);
-      const double o3 = neg_if(nod[(2 * NC + k) * plane + pc[3]], s3);
+      double o0 = neg_if(nod[(2 * NC + k) * plane + pc[0]], s0);
+      double o1 = neg_if(nod[(2 * NC + k) * plane + pc[1]], s1);
+      double o2 = neg_if(nod[(2 * NC + k) * plane + pc[2]], s2);
+      double o3 = neg_if(nod[(2 * NC + k) * plane + pc[3]], s3);
+      if (VAR) {
+        if (fixed[0]) o0 = 0.0;
+        if (fixed[1]) o1 = 0.0;
+        if (fixed[2]) o2 = 0.0;
+        if (fixed[3]) o3 = 0.0;
+      }
       // Eq. (mixed)
       mh[k] = fma(7.0 / 12.0, o1 + o2, (-1.0 / 12.0) * (o0 + o3));
     }
@@ -393,36 +543,45 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
   }
 }
 
-template <int DIM, int SYS>
+template <int DIM, int SYS, int VAR>
 __global__ void __launch_bounds__(kThreads) k_face(Grid g, const double* __restrict__ S, Work w, int slot) {
   const int dir = blockIdx.y;
   const int n = dir == 0 ? g.nx : g.ny;
   const int nlines = dir == 0 ? g.ny : g.nx;
   const long long f = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (f >= (long long)(n + 1) * nlines) return;
-  face_body<DIM, SYS>(g, S, w, dir, f, __longlong_as_double((long long)w.alpha[slot * w.astride + dir]));
+  face_body<DIM, SYS, VAR>(g, S, w, dir, f, __longlong_as_double((long long)w.alpha[slot * w.astride + dir]));
 }
 
 // ---------------------------------------------------------------------------------------------
 // Update of one cell p.  mode 0: Runge-Kutta stage in place, S = a B + b (M + dt L) (stage 0:
 // B := M, S = M + dt L).  mode 1: write L and M to Lout, Mout.
-template <int DIM, int SYS>
+template <int DIM, int SYS, int VAR = 0>
 __device__ __forceinline__ void update_body(const Grid& g, double* __restrict__ S, const Work& w, int mode, int stage,
                                             double a_k, double b_k, double dt, long long p,
                                             double* __restrict__ Lout, double* __restrict__ Mout) {
   using T = Traits<DIM, SYS>;
   constexpr int NC = T::NC, NF = T::NF;
+  constexpr bool SRC = VAR != 0 && DIM == 2 && SYS == SYS_EULER;  // gravity source possible
   const long long plane = g.plane;
   const int i = (int)(p % g.nx), j = (int)(p / g.nx);
   const long long px = (long long)j * (g.nx + 1) + i;
   const long long oplx = (long long)g.ny * (g.nx + 1), oply = (long long)(g.ny + 1) * g.nx;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
+    // Eq. (euler2d-s): field f gains g (0, 0, S_f[rho], S_f[rho nu]) (read before S is overwritten)
+    double src2 = 0.0, src3 = 0.0;
+    if (SRC && g.grav != 0.0) {
+      src2 = g.grav * S[(f * NC + 0) * plane + p];
+      src3 = g.grav * S[(f * NC + 2) * plane + p];
+    }
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
       const int fk = f * NC + k;
       double L = -(w.FX[fk * oplx + px + 1] - w.FX[fk * oplx + px]) * g.inv_dx;
       if (DIM == 2) L = fma(-(w.FY[fk * oply + p + g.nx] - w.FY[fk * oply + p]), g.inv_dy, L);
+      if (SRC && k == 2) L += src2;
+      if (SRC && k == 3) L += src3;
       const double M = f == 0 ? S[fk * plane + p] : w.MD[((long long)(f - 1) * NC + k) * plane + p];
       if (mode == 1) {
         Lout[fk * plane + p] = L;
@@ -453,7 +612,7 @@ __device__ __forceinline__ double stage_dt(const Grid& g, const Work& w, int sta
 
 // dt of stage 0 is stored in scal[0] by block 0 and reused by stages 1 and 2; the time advances
 // at stage 2.
-template <int DIM, int SYS>
+template <int DIM, int SYS, int VAR>
 __global__ void __launch_bounds__(kThreads) k_update(Grid g, double* __restrict__ S, Work w, int mode, int stage,
                                                       double a_k, double b_k, double dt_fixed, int slot,
                                                       double* __restrict__ Lout, double* __restrict__ Mout) {
@@ -469,8 +628,48 @@ __global__ void __launch_bounds__(kThreads) k_update(Grid g, double* __restrict_
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (p >= g.plane) return;
   const double dt = mode == 0 ? s_dt : 0.0;
-  update_body<DIM, SYS>(g, S, w, mode, stage, a_k, b_k, dt, p, Lout, Mout);
+  update_body<DIM, SYS, VAR>(g, S, w, mode, stage, a_k, b_k, dt, p, Lout, Mout);
   if (mode == 0 && stage == 2 && p == 0) w.scal[1] += dt;
+}
+
+// R2: face states of the ghost cells at both ends of every line (the low ghost's right-face
+// state, the high ghost's left-face state), from the ghost's own stencil and characteristic
+// fields through the boundary map.  Threads: [dir][end][line], gstride lines per (dir, end).
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_r2_ghost(Grid g, const double* __restrict__ S, Work w) {
+  constexpr int NC = Traits<DIM, SYS_EULER>::NC;
+  const long long gs = w.gstride;
+  const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
+  const int dir = (int)(t / (2 * gs));
+  const int end = (int)((t / gs) % 2);
+  const int line = (int)(t % gs);
+  if (dir >= DIM) return;
+  const int n = dir == 0 ? g.nx : g.ny, nlines = dir == 0 ? g.ny : g.nx;
+  if (line >= nlines) return;
+  const int a0 = end == 0 ? -1 : n;
+  const int i = dir == 0 ? 0 : line, j = dir == 0 ? line : 0;  // the line's coordinates
+  double U3[3][NC], D3[3][NC];
+  load_stencil3<DIM, SYS_EULER, 1, NC>(g, S, dir, i, j, a0, nullptr, U3, D3);
+  // eigenvectors of the ghost's own state (normal frame)
+  const double* U = U3[1];
+  const double ir = rcp(U[0]);
+  const double u = U[1] * ir, v = DIM == 2 ? U[2] * ir : 0.0;
+  const double ke = DIM == 2 ? fma(U[1], u, U[2] * v) : U[1] * u;
+  const double pr = g.gm1 * fma(-0.5, ke, U[NC - 1]);
+  const double H = (U[NC - 1] + pr) * ir;
+  const double c2 = g.gamma * pr * ir;
+  const double ic = rsqrt(c2);
+  Eig<NC> e;
+  e.setup(u, v, H, c2 * ic, ic, g.gm1);
+  double md[NC], fs[4][NC];
+  r2_cell<NC, SYS_EULER>(U3, D3, e, dir, g, md, fs);
+  double* G = w.GFS + (long long)(dir * 2 + end) * 2 * NC * gs;
+  const int q0 = end == 0 ? 0 : 2;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    G[(0 * NC + k) * gs + line] = fs[q0][k];
+    G[(1 * NC + k) * gs + line] = fs[q0 + 1][k];
+  }
 }
 
 // alpha of a state only (hweno_max_wavespeed)

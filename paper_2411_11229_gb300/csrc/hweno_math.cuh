@@ -14,7 +14,9 @@
 namespace hw {
 
 enum { SYS_ADV = 0, SYS_BURGERS = 1, SYS_EULER = 2 };
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2, BC_FIXED = 3 };
+// scheme variants of the extended kernels (VAR != 0)
+enum { FLAG_V_WEIGHTED = 1, FLAG_CD2 = 2, FLAG_R2 = 4 };
 
 template <int DIM, int SYS>
 struct Traits {
@@ -28,7 +30,7 @@ struct Traits {
 struct Grid {
   int nx, ny;   // ny = 1 in 1D
   int bc;
-  int pad_;
+  int flags;    // FLAG_* (read by the extended kernels only)
   long long plane;  // nx * ny
   double dx, dy, inv_dx, inv_dy;
   double gamma, gm1;
@@ -45,6 +47,16 @@ struct Grid {
   double cr[5], cl[5], G;
   double cdu, csv, Gd;
   double h[2], ih[2], chh[2], efih[2], egih[2], hih[2];
+  // Extended scheme (read only by the kernels instantiated with VAR != 0):
+  //   side: boundary type of x-low, x-high, y-low, y-high; grav: g of Eq. (euler2d-s);
+  //   ig1 = 1/gamma1 (weighted derivative); Cd-2 folded per direction: c2h = c2 h,
+  //   e2fih = e2f/h, e2gih = e2g/h;
+  //   fixU, fixP, fixF: the state of a BC_FIXED side (original frame), its primitives
+  //   (sqrt rho, u[, v], H) and its flux normal to the side (normal frame).
+  int side[4];
+  double grav, ig1;
+  double c2h[2], e2fih[2], e2gih[2];
+  double fixU[4][4], fixP[4][4], fixF[4][4];
 };
 
 // 1/x for normal, finite x: the hardware approximation (rcp.approx.ftz.f64) refined by two
@@ -106,7 +118,7 @@ __device__ __forceinline__ Wts weights(double b0, double b1, double b2, double e
 // image about x_{k+1}).  gamma1 = gamma2; both weight sets normalise with one reciprocal each.
 __device__ __forceinline__ void face_field(double w0, double w1, double w2, double w3, double y0, double y1,
                                            double y2, double y3, const Grid& g, double& um, double& hvm,
-                                           double& up, double& hvp) {
+                                           double& up, double& hvp, bool vw = false) {
   const double d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2;
   const double b01 = d01 * d01, b12 = d12 * d12, b23 = d23 * d23;
   const double e01 = b01 + g.eps, e12 = b12 + g.eps, e23 = b23 + g.eps;
@@ -120,8 +132,11 @@ __device__ __forceinline__ void face_field(double w0, double w1, double w2, doub
     const double p1 = fma(-0.5, w0, 1.5 * w1);
     const double num = fma(wt.W0, r, fma(wt.W1, p1, wt.W2 * pmid));
     const double den = fma(g.G, wt.W0, wt.W1 + wt.W2);
-    um = num * rcp(den);
+    const double rden = rcp(den);
+    um = num * rden;
     hvm = fma(0.1875, w0, fma(-1.5, w1, fma(1.3125, w2, fma(0.0625, y0, -0.1875 * y2))));
+    // weighted: the same combination of h p0', h p1' = d01, h p2' = d12
+    if (vw) hvm = fma(wt.W0, fma(hvm, g.ig1, -du), fma(wt.W1, d01, wt.W2 * d12)) * rden;
   }
   {
     // stencil of cell k+1: u_{i-1..i+1} = w1, w2, w3; its candidate on {i, i+1} carries beta2,
@@ -132,9 +147,41 @@ __device__ __forceinline__ void face_field(double w0, double w1, double w2, doub
     const double q1 = fma(-0.5, w3, 1.5 * w2);
     const double num = fma(wt.W0, r, fma(wt.W2, q1, wt.W1 * pmid));
     const double den = fma(g.G, wt.W0, wt.W1 + wt.W2);
-    up = num * rcp(den);
+    const double rden = rcp(den);
+    up = num * rden;
     hvp = fma(-1.3125, w1, fma(1.5, w2, fma(-0.1875, w3, fma(-0.1875, y1, 0.0625 * y3))));
+    if (vw) hvp = fma(wt.W0, fma(hvp, g.ig1, -du), fma(wt.W1, d12, wt.W2 * d23)) * rden;
   }
+}
+
+// R2 variant: one characteristic field of cell i from its own stencil w0..w2 = u_{i-1..i+1},
+// y0, y2 = h v_{i-1}, h v_{i+1}: u^- and h v^- at x_{i+1/2}, u^+ and h v^+ at x_{i-1/2} (the
+// mirror image) and h v~_i.  The three share beta, tau and the unnormalised weights; u^+/- share
+// one reciprocal (gamma1 = gamma2 makes the mirrored weights the same numbers).
+__device__ __forceinline__ void cell_faces_field(double w0, double w1, double w2, double y0, double y2, const Grid& g,
+                                                 bool vw, double& um, double& hvm, double& up, double& hvp,
+                                                 double& hvt) {
+  const double d01 = w1 - w0, d12 = w2 - w1;
+  const double b1 = d01 * d01, b2 = d12 * d12;
+  double du, sv;
+  const double b0 = beta0(d01, d12, y0, y2, du, sv);
+  const Wts wt = weights(b0, b1, b2, b1 + g.eps, b2 + g.eps, g.eps);
+  const double rden = rcp(fma(g.G, wt.W0, wt.W1 + wt.W2));
+  const double rm = fma(g.cr[0], w0, fma(g.cr[1], w1, fma(g.cr[2], w2, fma(g.cr[3], y0, g.cr[4] * y2))));
+  const double rp = fma(g.cl[0], w0, fma(g.cl[1], w1, fma(g.cl[2], w2, fma(g.cl[3], y0, g.cl[4] * y2))));
+  const double p1 = fma(-0.5, w0, 1.5 * w1), p2 = 0.5 * (w1 + w2);  // candidates at x_{i+1/2}
+  const double q2 = fma(-0.5, w2, 1.5 * w1), q1 = 0.5 * (w0 + w1);  // and at x_{i-1/2}
+  um = fma(wt.W0, rm, fma(wt.W1, p1, wt.W2 * p2)) * rden;
+  up = fma(wt.W0, rp, fma(wt.W2, q2, wt.W1 * q1)) * rden;
+  hvm = fma(0.1875, w0, fma(-1.5, w1, fma(1.3125, w2, fma(0.0625, y0, -0.1875 * y2))));
+  hvp = fma(-1.3125, w0, fma(1.5, w1, fma(-0.1875, w2, fma(-0.1875, y0, 0.0625 * y2))));
+  const double sl = fma(wt.W1, d01, wt.W2 * d12);
+  if (vw) {
+    hvm = fma(wt.W0, fma(hvm, g.ig1, -du), sl) * rden;
+    hvp = fma(wt.W0, fma(hvp, g.ig1, -du), sl) * rden;
+  }
+  const double t = fma(g.cdu, du, -g.csv * sv);
+  hvt = fma(wt.W0, t, sl) * rcp(fma(g.Gd, wt.W0, wt.W1 + wt.W2));
 }
 
 // h v~_i of one characteristic field (Eq. limiter with the derivatives of Eq. limiter-p) from
@@ -162,6 +209,17 @@ struct DCoef {
   static constexpr double ef = (1.0 / 24.0) * (101.0 / 36.0) + (7.0 / 5760.0) * (130.0 / 9.0);
   static constexpr double eg = (1.0 / 24.0) * (27.0 / 4.0) + (7.0 / 5760.0) * 30.0;
   static constexpr double eh = (1.0 / 24.0) * (5.0 / 6.0) + (7.0 / 5760.0) * (20.0 / 3.0);
+};
+
+// The alternative D-terms of Eq. (Cd-2) (h at the two inner nodes), combined the same way:
+// D(f) = c2f (f_{i-1} - f_i - f_{i+1} + f_{i+2}) + c2 h (h_i - h_{i+1})
+// D(h) = (1/h) (e2f (f_{i-1} - f_{i+2}) + e2g (f_i - f_{i+1})) + e2h (h_i + h_{i+1})
+struct DCoef2 {
+  static constexpr double cf = -(1.0 / 24.0) * (-1.0 / 8.0) + (7.0 / 5760.0) * 3.0;
+  static constexpr double ch = -(1.0 / 24.0) * (-5.0 / 4.0) + (7.0 / 5760.0) * 6.0;
+  static constexpr double ef = -(1.0 / 24.0) * (1.0 / 4.0) + (7.0 / 5760.0) * (-10.0);
+  static constexpr double eg = -(1.0 / 24.0) * (57.0 / 4.0) + (7.0 / 5760.0) * (-90.0);
+  static constexpr double eh = -(1.0 / 24.0) * (15.0 / 2.0) + (7.0 / 5760.0) * (-60.0);
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -309,6 +367,21 @@ __device__ __forceinline__ int bc_map(int k, int n, int bc, bool& refl) {
   if (bc == BC_TRANSMISSIVE) return k < 0 ? 0 : n - 1;
   refl = true;
   return k < 0 ? -1 - k : 2 * n - 1 - k;
+}
+
+// Per-side version for the extended kernels: lo and hi are the types of the two ends of the
+// axis.  A BC_FIXED ghost sets fixed and returns the nearest interior index (its loads are then
+// replaced by the side's state, so every load stays in bounds).
+__device__ __forceinline__ int bc_map_ext(int k, int n, int lo, int hi, bool& refl, bool& fixed) {
+  refl = false;
+  fixed = false;
+  if (k >= 0 && k < n) return k;
+  const int t = k < 0 ? lo : hi;
+  if (t == BC_FIXED) {
+    fixed = true;
+    return k < 0 ? 0 : n - 1;
+  }
+  return bc_map(k, n, t, refl);
 }
 
 __device__ __forceinline__ int bc_index(int k, int n, int bc) {

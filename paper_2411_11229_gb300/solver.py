@@ -11,7 +11,7 @@ from . import _capi as C
 
 _SYSTEMS = {"advection": C.HWENO_ADVECTION, "burgers": C.HWENO_BURGERS, "euler": C.HWENO_EULER}
 _BCS = {"periodic": C.HWENO_BC_PERIODIC, "transmissive": C.HWENO_BC_TRANSMISSIVE,
-        "reflective": C.HWENO_BC_REFLECTIVE}
+        "reflective": C.HWENO_BC_REFLECTIVE, "fixed": C.HWENO_BC_FIXED}
 
 
 def _ptr(t: torch.Tensor) -> int:
@@ -28,7 +28,10 @@ class Solver:
     def __init__(self, dim: int, system: str, nx: int, ny: int = 1, dx: float = 1.0, dy: float = None,
                  gamma: float = 1.4, bc: str = "periodic", gamma0: float = None, d0: float = 0.9,
                  eps: float = 1e-10, cfl: float = 0.6, ax: float = 1.0, ay: float = 1.0,
-                 device="cuda", stream: torch.cuda.Stream = None):
+                 device="cuda", stream: torch.cuda.Stream = None, flags: int = 0, grav: float = 0.0,
+                 sides=None, fixed=None):
+        """flags (HWENO_FLAG_*), grav, sides (four boundary types: x-low, x-high, y-low, y-high) and
+        fixed ({side: conserved state}) select the extensions of hweno_create_ex."""
         if not torch.cuda.is_available():
             raise RuntimeError("HWENO solver needs a CUDA device")
         self.lib = C.load()
@@ -36,9 +39,21 @@ class Solver:
         self.nx, self.ny = int(nx), (int(ny) if dim == 2 else 1)
         dy = dx if dy is None else dy
         h = ctypes.c_void_p()
-        C.check(self.lib.hweno_create(self.dim, self.system, self.nx, self.ny, float(dx), float(dy),
-                                      float(gamma), _BCS[bc] if isinstance(bc, str) else int(bc),
-                                      ctypes.byref(h)), "hweno_create")
+        bct = _BCS[bc] if isinstance(bc, str) else int(bc)
+        if flags or grav or sides is not None or fixed:
+            ext = C.HwenoExt()
+            ext.flags = int(flags)
+            ext.grav = float(grav)
+            for k, t in enumerate(sides if sides is not None else (bct,) * 4):
+                ext.side[k] = _BCS[t] if isinstance(t, str) else int(t)
+            for k, U in (fixed or {}).items():
+                for j, u in enumerate(U):
+                    ext.fixed[k][j] = float(u)
+            C.check(self.lib.hweno_create_ex(self.dim, self.system, self.nx, self.ny, float(dx), float(dy),
+                                             float(gamma), ctypes.byref(ext), ctypes.byref(h)), "hweno_create_ex")
+        else:
+            C.check(self.lib.hweno_create(self.dim, self.system, self.nx, self.ny, float(dx), float(dy),
+                                          float(gamma), bct, ctypes.byref(h)), "hweno_create")
         self.h = h
         if gamma0 is None:
             gamma0 = 0.95 if dim == 1 else 0.99

@@ -65,3 +65,61 @@ def test_sizes_and_params():
     finally:
         lib.hweno_destroy(h)
     assert lib.hweno_strerror(C.HWENO_ENONPHYS).startswith(b"non-physical")
+
+
+def _ext(flags=0, sides=(0, 0, 0, 0), grav=0.0, fixed=None):
+    e = C.HwenoExt()
+    e.flags = flags
+    for k, t in enumerate(sides):
+        e.side[k] = t
+    e.grav = grav
+    for k, U in (fixed or {}).items():
+        for j, u in enumerate(U):
+            e.fixed[k][j] = u
+    return e
+
+
+def _create_ex(dim, system, e, nx=40, ny=30):
+    h = ctypes.c_void_p()
+    rc = C.load().hweno_create_ex(dim, system, nx, ny, 0.05, 0.05, 1.4, ctypes.byref(e), ctypes.byref(h))
+    return rc, h
+
+
+P, T, R, F = C.HWENO_BC_PERIODIC, C.HWENO_BC_TRANSMISSIVE, C.HWENO_BC_REFLECTIVE, C.HWENO_BC_FIXED
+
+
+@pytest.mark.parametrize("dim,system,e", [
+    (2, C.HWENO_EULER, _ext(flags=8)),                                        # unknown flag
+    (2, C.HWENO_EULER, _ext(sides=(P, T, P, P))),                             # periodic on one end
+    (2, C.HWENO_EULER, _ext(sides=(P, P, T, P))),
+    (2, C.HWENO_EULER, _ext(sides=(P, P, 4, 4))),                             # unknown type
+    (2, C.HWENO_BURGERS, _ext(sides=(R, R, P, P))),                           # reflective scalar
+    (1, C.HWENO_EULER, _ext(grav=1.0)),                                       # gravity in 1D
+    (2, C.HWENO_BURGERS, _ext(grav=1.0)),                                     # gravity, scalar
+    (2, C.HWENO_EULER, _ext(sides=(F, T, P, P), fixed={0: [-1.0, 0, 0, 2.5]})),  # rho <= 0
+    (2, C.HWENO_EULER, _ext(sides=(F, T, P, P), fixed={0: [1.0, 3.0, 0, 1.0]})),  # P <= 0
+])
+def test_create_ex_rejects_invalid(dim, system, e):
+    rc, h = _create_ex(dim, system, e)
+    assert rc == C.HWENO_EINVAL and not h.value
+
+
+def test_create_ex_sizes_and_adjoint_refusal():
+    """R2 keeps four face states per cell and direction (and those of the line-end ghosts); the
+    plain configuration keeps the plain workspace; the adjoint refuses extended handles."""
+    lib = C.load()
+    rc0, h0 = _create(2, C.HWENO_EULER, 40, 30, 0.05, 0.05, 1.4, C.HWENO_BC_PERIODIC)
+    rc1, h1 = _create_ex(2, C.HWENO_EULER, _ext())                     # plain, through the ex entry
+    rc2, h2 = _create_ex(2, C.HWENO_EULER, _ext(flags=C.HWENO_FLAG_R2))
+    rc3, h3 = _create_ex(2, C.HWENO_EULER, _ext(flags=C.HWENO_FLAG_CD2, grav=1.0))
+    try:
+        assert rc0 == rc1 == rc2 == rc3 == 0
+        w0, w1, w2, w3 = (lib.hweno_workspace_bytes(h) for h in (h0, h1, h2, h3))
+        assert w0 == w1 == w3
+        assert w2 >= w0 + 8 * 2 * 4 * 4 * 40 * 30
+        for h in (h2, h3):
+            assert lib.hweno_adjoint_step(h, 8, 0.1, 16, 24, 32, 256) == C.HWENO_EINVAL
+            assert lib.hweno_stage_vjp(h, 8, 16, 24, 32, 40, 256) == C.HWENO_EINVAL
+    finally:
+        for h in (h0, h1, h2, h3):
+            lib.hweno_destroy(h)
