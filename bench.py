@@ -224,6 +224,77 @@ def run_adjoint(dev, n: int = 1024, nsteps: int = 200, every: int = 20):
     return res
 
 
+def run_variants(dev, n: int, plain_ms: float, steps: int = 5):
+    """The same workload with the per-cell characteristic decomposition (R2, one interpolation per
+    cell and direction) and with the other two variants on the extended kernels (v^+/- with the
+    nonlinear weights, Eq. Cd-2 D-terms): ms per step against the scheme of the paper."""
+    import torch
+
+    import workloads as W
+    from paper_2411_11229_gb300 import Solver
+    from paper_2411_11229_gb300 import _capi as C
+
+    S, dx, dy = W.euler2d_smooth(n)
+    out = {"workload": f"2D Euler {n}x{n}, the benchmark's state", "plain_ms_per_step": plain_ms}
+    for name, flags in (("r2", C.HWENO_FLAG_R2), ("vw_cd2", C.HWENO_FLAG_V_WEIGHTED | C.HWENO_FLAG_CD2)):
+        s = Solver(2, "euler", n, n, dx=dx, dy=dy, device=dev, flags=flags)
+        s.set_state(S)
+        s.set_time(0.0, 0.0)
+        s.step(0.0, 3)
+        s.sync()
+        s.set_profiling(True)
+        s.kernel_times()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.step(0.0, steps)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        kt = s.kernel_times()
+        s.set_profiling(False)
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_step": ms, "speedup_vs_plain": plain_ms / ms,
+                     "mcell_updates_per_s": n * n / (ms * 1e-3) / 1e6,
+                     "kernel_avg_ms": {k: v[0] / max(v[1], 1) for k, v in kt.items()}}
+        del s
+        torch.cuda.empty_cache()
+    return out
+
+
+# CPU seconds of the HWENO-I scheme for Example 4.11 to t = 1.95 printed in the paper (its CPU-time
+# table; serial MATLAB on one Apple M1 core): context for the wall time of the same runs here.
+RT_PAPER_SECONDS = {(60, 240): 229.58, (120, 480): 1843.07, (240, 960): 17574.21}
+
+
+def run_rayleigh_taylor(dev, meshes=((60, 240), (120, 480), (240, 960)), t_end: float = 1.95):
+    """Example 4.11 (Rayleigh-Taylor, gravity, reflective sides, fixed top and bottom, gamma 5/3)
+    to t = 1.95 on the paper's three meshes, through hweno_run: host wall time of the whole run."""
+    import torch
+
+    import workloads as W
+    from paper_2411_11229_gb300 import Solver
+
+    res = {"workload": "Example 4.11, Rayleigh-Taylor to t = 1.95, CFL 0.6", "runs": []}
+    for nx, ny in meshes:
+        S, dx, dy, fixed = W.rayleigh_taylor(nx, ny)
+        kw = dict(gamma=5.0 / 3.0, grav=1.0, sides=("reflective", "reflective", "fixed", "fixed"), fixed=fixed)
+        s = Solver(2, "euler", nx, ny, dx=dx, dy=dy, device=dev, **kw)
+        s.set_state(S)
+        s.run(0.01)  # first use: loads the kernels
+        s.set_state(S)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nsteps = s.run(t_end)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        rho = s.state[0, 0]
+        res["runs"].append({"mesh": f"{nx}x{ny}", "steps": nsteps, "seconds": sec,
+                            "mcell_updates_per_s": nx * ny * nsteps / sec / 1e6,
+                            "rho_min": float(rho.min()), "rho_max": float(rho.max()),
+                            "paper_hweno_i_seconds": RT_PAPER_SECONDS.get((nx, ny))})
+        del s
+    return res
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
@@ -377,6 +448,11 @@ def run_ours(args, ws, rank, local):
         "kernel_avg_ms": {k: v[0] / max(v[1], 1) for k, v in ktimes.items()},
         "flops_per_cell_step": counts["per_cell_step"],
     }
+    if ws == 1 and not args.no_variants:
+        torch.cuda.empty_cache()
+        line["variants"] = run_variants(dev, n, ms_max / args.steps)
+    if ws == 1 and not args.no_rt:
+        line["rayleigh_taylor"] = run_rayleigh_taylor(dev)
     if ws == 1 and not args.no_batched:
         del solver
         torch.cuda.empty_cache()
@@ -400,6 +476,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-rt", action="store_true")
     ap.add_argument("--adjoint-n", type=int, default=1024)
     ap.add_argument("--adjoint-steps", type=int, default=200)
     args = ap.parse_args()

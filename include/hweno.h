@@ -142,14 +142,26 @@ int hweno_rhs(hweno_t *h, const double *S_dev, double *L_dev, double *M_dev);
  *   S1 = M(S^n) + dt L(S^n);  S2 = 3/4 B + 1/4 (M(S1) + dt L(S1));  S^{n+1} = 1/3 B + 2/3 (M(S2) + dt L(S2))
  * with B = M(S^n).  dt > 0: fixed step.  dt <= 0: CFL step computed on the device from the
  * wavespeeds of S^n: dt = CFL dx / alpha (1D), CFL / (alpha_x/dx + alpha_y/dy) (2D), clamped to the
- * end time set by hweno_set_time() if one was set.  No host synchronisation. */
+ * end time set by hweno_set_time() if one was set; a CFL step issued once that end time is reached
+ * has dt = 0 and leaves the state unchanged.  No host synchronisation. */
 int hweno_step(hweno_t *h, double dt);
 
 /* nsteps calls of hweno_step(h, dt). */
 int hweno_steps(hweno_t *h, double dt, int nsteps);
 
-/* Device time and end time used by CFL steps (t_end <= 0: no clamp). */
+/* Device time and end time used by CFL steps (t_end <= 0: no clamp); resets the count of steps
+ * taken that hweno_run reports. */
 int hweno_set_time(hweno_t *h, double t, double t_end);
+
+/* CFL steps of the bound state from t = 0 to t_end (> 0), the last one clamped (the way every
+ * example of Sec. 4 runs), or until max_steps steps.  steps_done (may be NULL) receives the number
+ * of steps taken.  The steps are issued in chunks of 16 without host synchronisation, replayed from
+ * a CUDA graph recorded on a private stream that is ordered after and before the handle's stream;
+ * steps of a chunk beyond the end time change nothing.  Returns when the device time has reached
+ * t_end, with HWENO_ENONPHYS if a non-physical state was met (the state is then that of the step
+ * that met it, or later).  EINVAL: t_end not finite and positive, max_steps < 0; ESTATE: nothing
+ * bound. */
+int hweno_run(hweno_t *h, double t_end, int64_t max_steps, int64_t *steps_done);
 
 /* Synchronise the stream; read the dt of the last step (and the device time). */
 int hweno_last_dt(hweno_t *h, double *dt_host, double *t_host);

@@ -25,6 +25,7 @@ SIGNATURES = {
     "hweno_create": (_I, [_I, _I, ctypes.c_int64, ctypes.c_int64, _D, _D, _D, _I, ctypes.POINTER(_H)]),
     "hweno_create_ex": (_I, [_I, _I, ctypes.c_int64, ctypes.c_int64, _D, _D, _D, _P, ctypes.POINTER(_H)]),
     "hweno_set_params": (_I, [_H, _D, _D, _D, _D, _D, _D]),
+    "hweno_run": (_I, [_H, _D, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "hweno_set_stream": (_I, [_H, _P]),
     "hweno_state_doubles": (ctypes.c_size_t, [_H]),
     "hweno_workspace_bytes": (ctypes.c_size_t, [_H]),

@@ -213,11 +213,86 @@ int hweno_set_time(hweno_t* h, double t, double t_end) {
   if (!h) return HWENO_EINVAL;
   if (!h->ws) return HWENO_ESTATE;
   if (!std::isfinite(t) || !std::isfinite(t_end)) return HWENO_EINVAL;
-  double v[2] = {t, t_end};
+  double v[3] = {t, t_end, 0.0};  // time, end time, steps taken
   if (cudaMemcpyAsync(h->w.scal + 1, v, sizeof(v), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
     return HWENO_ECUDA;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return HWENO_ECUDA;
   return HWENO_OK;
+}
+
+int hweno_run(hweno_t* h, double t_end, int64_t max_steps, int64_t* steps_done) {
+  if (!h || !(t_end > 0.0) || !std::isfinite(t_end) || max_steps < 0) return HWENO_EINVAL;
+  if (!h->ws || !h->state) return HWENO_ESTATE;
+  if (steps_done) *steps_done = 0;
+  int rc = hweno_set_time(h, 0.0, t_end);
+  if (rc) return rc;
+  constexpr int kChunk = 16;  // CFL steps issued between two looks at the device clock
+  // Record one chunk as a CUDA graph on a private stream (the handle's stream may be the legacy
+  // default stream, which cannot be captured); steps past the end time leave the state unchanged,
+  // so a whole chunk can be issued without knowing where in it the end time falls.
+  cudaStream_t user = h->stream, priv = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  long long chunk_launches = 0;
+  if (!h->profiling && max_steps >= kChunk &&
+      cudaStreamCreateWithFlags(&priv, cudaStreamNonBlocking) == cudaSuccess &&
+      cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
+      cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess) {
+    h->stream = priv;
+    const long long l0 = h->launches;
+    cudaGraph_t gr = nullptr;
+    bool ok = cudaStreamBeginCapture(priv, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      for (int k = 0; k < kChunk && ok; ++k)
+        for (int st = 0; st < 3 && ok; ++st) ok = stage(h, h->state, h->state, 0, st, 0.0, st, nullptr, nullptr) == HWENO_OK;
+      const bool ended = cudaStreamEndCapture(priv, &gr) == cudaSuccess;
+      ok = ok && ended && gr;
+    }
+    chunk_launches = h->launches - l0;
+    h->launches = l0;
+    if (!ok || cudaGraphInstantiate(&exec, gr, 0) != cudaSuccess) exec = nullptr;
+    if (gr) cudaGraphDestroy(gr);
+    h->stream = user;
+    cudaGetLastError();  // a failed capture leaves the plain path
+  }
+  rc = HWENO_OK;
+  for (;;) {
+    double v[4] = {0, 0, 0, 0};
+    if (cudaMemcpyAsync(v, h->w.scal, sizeof(v), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) {
+      rc = HWENO_ECUDA;
+      break;
+    }
+    rc = read_status(h);  // synchronises
+    if (rc) break;
+    const int64_t done = (int64_t)v[3];
+    if (steps_done) *steps_done = done;
+    if (!std::isfinite(v[1])) {
+      rc = HWENO_ENONPHYS;
+      break;
+    }
+    if (v[1] >= t_end || done >= max_steps) break;
+    const int64_t left = max_steps - done;
+    if (exec && left >= kChunk) {
+      if (cudaEventRecord(fork, user) != cudaSuccess || cudaStreamWaitEvent(priv, fork, 0) != cudaSuccess ||
+          cudaGraphLaunch(exec, priv) != cudaSuccess || cudaEventRecord(join, priv) != cudaSuccess ||
+          cudaStreamWaitEvent(user, join, 0) != cudaSuccess) {
+        rc = HWENO_ECUDA;
+        break;
+      }
+      h->launches += chunk_launches;
+    } else {
+      for (int64_t k = 0; k < (left < kChunk ? left : kChunk) && !rc; ++k) rc = hweno_step(h, 0.0);
+      if (rc) break;
+    }
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (fork) cudaEventDestroy(fork);
+  if (join) cudaEventDestroy(join);
+  if (priv) {
+    cudaStreamSynchronize(priv);
+    cudaStreamDestroy(priv);
+  }
+  return rc;
 }
 
 int hweno_last_dt(hweno_t* h, double* dt_host, double* t_host) {

@@ -71,11 +71,15 @@ template <int DIM>
 __device__ __forceinline__ void batch_update(const BatchInst& I, long long p0, int tpi, const BatchArgs& a) {
   const double dt = stage_dt<DIM>(I.g, I.w, a.stage, 0.0, a.slot);
   if (a.stage == 0 && p0 == 0 && threadIdx.x == 0) I.w.scal[0] = dt;
+  if (dt == 0.0) return;  // the instance has reached its end time
   for (int t = 0; t < tpi; ++t) {
     const long long p = p0 + (long long)t * kThreads + threadIdx.x;
     if (p < I.g.plane) update_body<DIM, SYS_EULER>(I.g, I.S, I.w, 0, a.stage, a.a_k, a.b_k, dt, p, nullptr, nullptr);
   }
-  if (a.stage == 2 && p0 == 0 && threadIdx.x == 0) I.w.scal[1] += dt;
+  if (a.stage == 2 && p0 == 0 && threadIdx.x == 0) {
+    I.w.scal[1] += dt;
+    I.w.scal[3] += 1.0;
+  }
 }
 
 // One Runge-Kutta stage of every instance.  Launched cooperatively with every block resident.

@@ -37,7 +37,7 @@ struct Work {
   double* FY;    // y-face fluxes: [NF][NC][ny+1][nx]
   unsigned long long* alpha;  // wavespeed slots (bit patterns of non-negative doubles): slot s of
                               // direction d at alpha[s * astride + d]
-  double* scal;               // [0] dt of the current step, [1] t, [2] t_end
+  double* scal;               // [0] dt of the current step, [1] t, [2] t_end, [3] steps taken
   unsigned int* status;       // bit 0: non-physical state met
   long long astride;          // distance between slots (2 for a single grid)
   // R2 only: face states of every cell, normal frame, derivatives scaled by h:
@@ -628,8 +628,14 @@ __global__ void __launch_bounds__(kThreads) k_update(Grid g, double* __restrict_
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (p >= g.plane) return;
   const double dt = mode == 0 ? s_dt : 0.0;
+  // a CFL step at the end time has dt = 0: it leaves the state as it is, so that steps issued
+  // past the end time (without waiting for the host) change nothing
+  if (mode == 0 && dt_fixed <= 0.0 && dt == 0.0) return;
   update_body<DIM, SYS, VAR>(g, S, w, mode, stage, a_k, b_k, dt, p, Lout, Mout);
-  if (mode == 0 && stage == 2 && p == 0) w.scal[1] += dt;
+  if (mode == 0 && stage == 2 && p == 0) {
+    w.scal[1] += dt;
+    w.scal[3] += 1.0;  // steps taken
+  }
 }
 
 // R2: face states of the ghost cells at both ends of every line (the low ghost's right-face

@@ -230,3 +230,48 @@ def test_reciprocal_accuracy():
     exact = 1.0 / x
     ulps = np.abs(r - exact) / np.spacing(np.abs(exact))
     assert ulps.max() <= 1.0, ulps.max()
+
+
+@pytest.mark.parametrize("ext", [False, True])
+def test_run_matches_stepping_and_stops_at_the_end(ext):
+    """hweno_run (graph-replayed chunks of 16 CFL steps) against one hweno_step call per step:
+    bit for bit, with max_steps honoured exactly; steps issued after the end time leave the state
+    unchanged.  ext: the Rayleigh-Taylor set-up of Example 4.11 through the extended kernels."""
+    if ext:
+        S, dx, dy, fixed = W.rayleigh_taylor(12, 48)
+        kw = dict(gamma=5.0 / 3.0, grav=1.0, sides=("reflective", "reflective", "fixed", "fixed"), fixed=fixed)
+        nx, ny, t_end = 12, 48, 0.1
+    else:
+        S, dx, dy = W.euler2d_smooth(24, 20)
+        kw = {}
+        nx, ny, t_end = 24, 20, 0.5
+    a = Solver(2, "euler", nx, ny, dx=dx, dy=dy, **kw)
+    b = Solver(2, "euler", nx, ny, dx=dx, dy=dy, **kw)
+    a.set_state(S)
+    b.set_state(S)
+    n = a.run(t_end)
+    b.set_time(0.0, t_end)
+    m = 0
+    while True:
+        b.step(0.0)
+        m += 1
+        dt, t = b.last_dt()
+        if t >= t_end:
+            break
+    assert n == m and n > 16
+    assert torch.equal(a.state, b.state)
+    _, ta = a.last_dt()
+    assert ta == t_end
+    before = a.state.clone()
+    a.step(0.0, 3)
+    dt, ta2 = a.last_dt()
+    assert dt == 0.0 and ta2 == t_end and torch.equal(a.state, before)
+    # max_steps: 37 steps of a run that would take more
+    c = Solver(2, "euler", nx, ny, dx=dx, dy=dy, **kw)
+    c.set_state(S)
+    assert c.run(10.0, max_steps=37) == 37
+    d = Solver(2, "euler", nx, ny, dx=dx, dy=dy, **kw)
+    d.set_state(S)
+    d.set_time(0.0, 10.0)
+    d.step(0.0, 37)
+    assert torch.equal(c.state, d.state)
