@@ -45,6 +45,23 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    """The largest x of all ranks (the job's time is its slowest rank's)."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ws: int, cells: int, steps: int, ms_max: float) -> float:
+    """Whole-job Mcell-updates/s: every rank advances its own grid (weak scaling)."""
+    return ws * cells * steps / (ms_max * 1e-3) / 1e6
+
+
 def _measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -380,11 +397,8 @@ def run_ours(args, ws, rank, local):
     launches = solver.launch_count() - launches0
     ktimes = solver.kernel_times()
     solver.set_profiling(False)
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = ws * cells * args.steps / (ms_max * 1e-3) / 1e6
+    ms_max = max_over_ranks(ms, ws, dev)
+    value = job_throughput(ws, cells, args.steps, ms_max)
 
     # end to end through the C ABI with host buffers: upload, step, download every step
     host_in = torch.from_numpy(np.ascontiguousarray(solver.state.cpu().numpy())).pin_memory()
@@ -407,11 +421,8 @@ def run_ours(args, ws, rank, local):
     f1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms_e2e = f0.elapsed_time(f1)
-    te = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
-    if ws > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = ws * cells * ke2e / (float(te.item()) * 1e-3) / 1e6
+    ms_e2e = max_over_ranks(f0.elapsed_time(f1), ws, dev)
+    e2e_value = job_throughput(ws, cells, ke2e, ms_e2e)
 
     if rank != 0:
         return 0
