@@ -219,7 +219,9 @@ int hweno_step_replay(hweno_t *h, double dt, const double *alpha6_dev);
  * products in reverse order, the stage inputs recomputed from S^n).  Uses the bound workspace as
  * scratch (its stage base and wavespeed slots are overwritten; the bound state and time are not)
  * and adj_ws_dev (hweno_adjoint_workspace_bytes, 256-byte aligned).  S_n, lam_in and lam_out must
- * not alias each other.  EINVAL for scalar systems, reflective walls or dt <= 0. */
+ * not alias each other.  All three boundary types of hweno_create (a reflective wall reads its
+ * mirrored neighbours through the sign tables, and their adjoints go back through the same
+ * tables).  EINVAL for scalar systems, handles of hweno_create_ex with extensions, or dt <= 0. */
 int hweno_adjoint_step(hweno_t *h, const double *S_n_dev, double dt, const double *alpha6_dev,
                        const double *lam_in_dev, double *lam_out_dev, void *adj_ws_dev);
 

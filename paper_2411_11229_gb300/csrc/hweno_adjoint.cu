@@ -49,9 +49,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
   const double h = g.h[d], ih = g.ih[d];
   double U3[3][NC], hD3[3][NC];
   long long pc[3];
+  bool refl[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    const int ac = bc_index(a0 - 1 + q, n, g.bc);
+    const int ac = bc_map(a0 - 1 + q, n, g.bc, refl[q]);
     pc[q] = d == 0 ? (long long)j * g.nx + ac : (long long)ac * g.nx + i;
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
@@ -62,6 +63,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
       swap_frame<NC>(U3[q]);
       swap_frame<NC>(hD3[q]);
     }
+    mirror_U<NC>(U3[q], refl[q]);
+    mirror_D<NC>(hD3[q], refl[q]);
   }
   // forward: eigenvectors of the cell's own state
   const Prim<NC> pr = prim_of<NC>(U3[1], g.gm1);
@@ -120,6 +123,12 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
   double irb = c2b * g.gamma * pr.p + eb.H * (U3[1][NC - 1] + pr.p);
   Ub[1][NC - 1] += eb.H * pr.ir;
   prim_bwd<NC>(U3[1], pr, g.gm1, irb, eb.u, eb.v, pb, Ub[1]);
+  // a mirrored neighbour was read through the sign table: its contributions go back through it
+  // (the table is its own transpose)
+#pragma unroll
+  for (int q = 0; q < 3; ++q) mirror_U<NC>(Ub[q], refl[q]);
+  mirror_D<NC>(hDmb, refl[0]);
+  mirror_D<NC>(hDpb, refl[2]);
   // store (original frame): 3 U contributions, then h * (derivative adjoints) of cells i-1, i+1
   double* out = aw.CM + ((long long)d * plane + p) * 5 * NC;
 #pragma unroll
@@ -159,9 +168,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
     line = (int)(f % g.nx);
   }
   long long pc[4];
+  bool refl[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const int a = bc_index(fa - 2 + q, n, g.bc);
+    const int a = bc_map(fa - 2 + q, n, g.bc, refl[q]);
     pc[q] = dir == 0 ? (long long)line * g.nx + a : (long long)a * g.nx + line;
   }
   const int fown = dir == 0 ? 1 : 2;
@@ -179,6 +189,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
       swap_frame<NC>(Uq[q]);
       swap_frame<NC>(Zq[q]);
     }
+    mirror_U<NC>(Uq[q], refl[q]);
+    mirror_D<NC>(Zq[q], refl[q]);
   }
   // adjoints of the face fluxes of U and of the own derivative (normal frame)
   double nuf[NC], nuh[NC];
@@ -299,6 +311,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
   const long long base = ((dir == 0 ? 0 : (long long)(g.nx + 1) * g.ny) + fo) * 4 * NC;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
+    mirror_U<NC>(Uqb[q], refl[q]);
+    mirror_D<NC>(Zqb[q], refl[q]);
     if (dir == 1) {
       swap_frame<NC>(Uqb[q]);
       swap_frame<NC>(Zqb[q]);
@@ -319,6 +333,10 @@ __device__ __forceinline__ int aliases(int a, int n, int bc, int* x) {
   if (bc == BC_PERIODIC) {
     if (a + n <= n + 1) x[k++] = a + n;
     if (a - n >= -2) x[k++] = a - n;
+  } else if (bc == BC_REFLECTIVE) {
+    // ghost -1-a mirrors cell a (a = 0, 1), ghost 2n-1-a mirrors it (a = n-1, n-2)
+    if (-1 - a >= -2) x[k++] = -1 - a;
+    if (2 * n - 1 - a <= n + 1) x[k++] = 2 * n - 1 - a;
   } else {
     if (a == 0) {
       x[k++] = -1;
@@ -368,8 +386,12 @@ __global__ void __launch_bounds__(kThreads) k_adj_gather(Grid g, const double* _
     double nf[NC], nh[NC], no[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) nf[k] = nh[k] = no[k] = 0.0;
+    // the normal momentum (original frame) and the nodal sign tables of a mirrored alias: f and
+    // the mixed value change sign except for the normal momentum, h only for it
+    const int km = d == 0 ? 1 : 2;
     for (int t = 0; t < nx_; ++t) {
       const int x = xs[t];
+      const bool mir = g.bc == BC_REFLECTIVE && (x < 0 || x >= n);
       // faces fa = x + 2 - q hold this cell at position q
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -400,9 +422,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_gather(Grid g, const double* _
             return (r - l) * ih;
           };
           const double nfh = nu(0), nhh = nu(fown);
-          nf[k] = fma(s1, nfh, fma(sdh, nhh, nf[k]));
-          nh[k] = fma(th, nfh, fma(th2, nhh, nh[k]));
-          if (DIM == 2) no[k] = fma(mq, nu(foth), no[k]);
+          const bool flip_f = mir && k != km, flip_h = mir && k == km;
+          nf[k] += neg_if(fma(s1, nfh, sdh * nhh), flip_f);
+          nh[k] += neg_if(fma(th, nfh, th2 * nhh), flip_h);
+          if (DIM == 2) no[k] += neg_if(mq * nu(foth), flip_f);
         }
       }
       // modified derivatives of cells c = x + 1 - q hold this cell at stencil position q
@@ -573,7 +596,7 @@ extern "C" {
 int hweno_adjoint_step(hweno_t* h, const double* Sn, double dt, const double* alpha6, const double* lam_in,
                        double* lam_out, void* adj_ws) {
   if (!h || !Sn || !alpha6 || !lam_in || !lam_out || !adj_ws) return HWENO_EINVAL;
-  if (h->system != HWENO_EULER || h->bc == HWENO_BC_REFLECTIVE || h->var != 0) return HWENO_EINVAL;
+  if (h->system != HWENO_EULER || h->var != 0) return HWENO_EINVAL;
   if (!(dt > 0.0) || ((uintptr_t)adj_ws & 255)) return HWENO_EINVAL;
   if (!h->ws) return HWENO_ESTATE;
   const AdjPtrs a = adj_ptrs(h, adj_ws);
@@ -591,7 +614,7 @@ int hweno_adjoint_step(hweno_t* h, const double* Sn, double dt, const double* al
 int hweno_adjoint_step_stages(hweno_t* h, const double* Sn, const double* S1, const double* S2, double dt,
                               const double* alpha6, const double* lam_in, double* lam_out, void* adj_ws) {
   if (!h || !Sn || !S1 || !S2 || !alpha6 || !lam_in || !lam_out || !adj_ws) return HWENO_EINVAL;
-  if (h->system != HWENO_EULER || h->bc == HWENO_BC_REFLECTIVE || h->var != 0) return HWENO_EINVAL;
+  if (h->system != HWENO_EULER || h->var != 0) return HWENO_EINVAL;
   if (!(dt > 0.0) || ((uintptr_t)adj_ws & 255)) return HWENO_EINVAL;
   return adjoint_from_stages(h, adj_ptrs(h, adj_ws), Sn, S1, S2, dt, alpha6, lam_in, lam_out);
 }
@@ -633,7 +656,7 @@ int hweno_step_record(hweno_t* h, double* rec7) {
 int hweno_stage_vjp(hweno_t* h, const double* S, const double* alpha2, const double* muM, const double* muL,
                     double* lam, void* adj_ws) {
   if (!h || !S || !alpha2 || !muM || !muL || !lam || !adj_ws) return HWENO_EINVAL;
-  if (h->system != HWENO_EULER || h->bc == HWENO_BC_REFLECTIVE || h->var != 0) return HWENO_EINVAL;
+  if (h->system != HWENO_EULER || h->var != 0) return HWENO_EINVAL;
   if ((uintptr_t)adj_ws & 255) return HWENO_EINVAL;
   const AdjPtrs a = adj_ptrs(h, adj_ws);
   const Grid g = grid_of(h);

@@ -35,8 +35,8 @@ def _setup(dim, nx, ny, kind, bc, seed):
     else:
         S, dx = W.euler1d_random(nx, seed, kind)
         dy = dx
-    cfg = O.make_cfg(dim, O.EULER, nx, ny, dx=dx, dy=dy,
-                     bc=O.BC_TRANSMISSIVE if bc == "transmissive" else O.BC_PERIODIC)
+    obc = {"periodic": O.BC_PERIODIC, "transmissive": O.BC_TRANSMISSIVE, "reflective": O.BC_REFLECTIVE}[bc]
+    cfg = O.make_cfg(dim, O.EULER, nx, ny, dx=dx, dy=dy, bc=obc)
     s = Solver(dim, "euler", nx, ny, dx=dx, dy=dy, bc=bc)
     s.set_state(S)
     aws = torch.empty(int(C.load().hweno_adjoint_workspace_bytes(s.h)), dtype=torch.uint8, device="cuda")
@@ -44,7 +44,9 @@ def _setup(dim, nx, ny, kind, bc, seed):
 
 
 CASES = [(2, 12, 10, "smooth", "periodic"), (2, 12, 10, "jumps", "periodic"), (2, 11, 13, "smooth", "transmissive"),
-         (2, 9, 7, "jumps", "transmissive"), (1, 23, 1, "smooth", "periodic"), (1, 19, 1, "jumps", "transmissive")]
+         (2, 9, 7, "jumps", "transmissive"), (1, 23, 1, "smooth", "periodic"), (1, 19, 1, "jumps", "transmissive"),
+         (2, 12, 11, "smooth", "reflective"), (2, 10, 9, "jumps", "reflective"), (1, 21, 1, "smooth", "reflective"),
+         (1, 6, 1, "jumps", "reflective"), (2, 6, 5, "smooth", "reflective")]
 
 
 @pytest.mark.parametrize("dim,nx,ny,kind,bc", CASES)

@@ -26,11 +26,13 @@ def _cases():
     S2, dx2, dy2 = W.euler2d_random(11, 13, 22, "smooth")
     S3, dx3 = W.euler1d_random(17, 23, "jumps")
     S4, dx4, _ = W.scalar_random(2, 9, 8, 24, "smooth")
+    S5, dx5, dy5 = W.euler2d_random(11, 9, 25, "jumps")
     return [
         (O.make_cfg(2, O.EULER, 12, 10, dx=dx, dy=dy), S1),
         (O.make_cfg(2, O.EULER, 11, 13, dx=dx2, dy=dy2, bc=O.BC_TRANSMISSIVE), S2),
         (O.make_cfg(1, O.EULER, 17, dx=dx3, bc=O.BC_TRANSMISSIVE), S3),
         (O.make_cfg(2, O.BURGERS, 9, 8, dx=dx4, dy=dx4), S4),
+        (O.make_cfg(2, O.EULER, 11, 9, dx=dx5, dy=dy5, bc=O.BC_REFLECTIVE), S5),
     ]
 
 
@@ -53,7 +55,7 @@ def test_jvp_matches_central_differences(case):
     assert np.abs(jM - fdM).max() <= 1e-6 * np.abs(fdM).max()
 
 
-@pytest.mark.parametrize("case", range(4))
+@pytest.mark.parametrize("case", range(5))
 def test_vjp_dot_product_identity(case):
     cfg, S = _cases()[case]
     alpha = O.max_wavespeed(cfg, S)
