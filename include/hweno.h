@@ -49,7 +49,13 @@ typedef struct hweno_ctx hweno_t;
 enum { HWENO_ADVECTION = 0, HWENO_BURGERS = 1, HWENO_EULER = 2 };
 enum { HWENO_BC_PERIODIC = 0, HWENO_BC_TRANSMISSIVE = 1, HWENO_BC_REFLECTIVE = 2, HWENO_BC_FIXED = 3 };
 /* scheme variants of hweno_create_ex */
-enum { HWENO_FLAG_V_WEIGHTED = 1, HWENO_FLAG_CD2 = 2, HWENO_FLAG_R2 = 4 };
+enum {
+  HWENO_FLAG_V_WEIGHTED = 1,
+  HWENO_FLAG_CD2 = 2,
+  HWENO_FLAG_R2 = 4,
+  HWENO_FLAG_ALPHA_STEP = 8,
+  HWENO_FLAG_ALPHA_LOCAL = 16
+};
 enum {
   HWENO_OK = 0,
   HWENO_EINVAL = -1,   /* invalid argument */
@@ -85,6 +91,12 @@ int hweno_create(int dim, int system, int64_t nx, int64_t ny, double dx, double 
  *                            the Roe average at the face (Euler; no effect on scalar laws).  Every
  *                            cell then interpolates both of its faces in its own characteristic
  *                            fields in one pass.
+ *     HWENO_FLAG_ALPHA_STEP  the LF coefficients alpha of Eq. (flux-LF) taken from the input of the
+ *                            step's first stage and held for its three stages (the paper does not
+ *                            say when alpha is updated; the default recomputes it at every stage);
+ *     HWENO_FLAG_ALPHA_LOCAL local LF: alpha at each face is the larger spectral radius of its two
+ *                            cells (ghost cells through the boundary map) instead of one maximum
+ *                            over the grid (the paper's alpha = max |f'(u)| is read as global).
  *   side[4]: boundary type of the sides x-low, x-high, y-low, y-high (side[2], side[3] unused in
  *     1D): HWENO_BC_PERIODIC (both ends of an axis or neither), _TRANSMISSIVE, _REFLECTIVE (Euler),
  *     or HWENO_BC_FIXED: the ghost cells hold the conserved state fixed[side] with zero derivatives

@@ -26,8 +26,9 @@ _lib = None
 ADVECTION, BURGERS, EULER = 0, 1, 2
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_FIXED = 0, 1, 2, 3
 # scheme variants: v^+/- with the nonlinear weights, D-terms of Eq. (Cd-2), characteristic
-# decomposition with the eigenvectors of each side's centre cell
-FLAG_V_WEIGHTED, FLAG_CD2, FLAG_R2 = 1, 2, 4
+# decomposition with the eigenvectors of each side's centre cell, LF coefficients held for the
+# whole step, local LF coefficients (per face)
+FLAG_V_WEIGHTED, FLAG_CD2, FLAG_R2, FLAG_ALPHA_STEP, FLAG_ALPHA_LOCAL = 1, 2, 4, 8, 16
 
 
 def build(force: bool = False) -> str:

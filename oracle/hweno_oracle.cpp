@@ -45,6 +45,9 @@
 //   FLAG_R2          characteristic decomposition with the eigenvectors of the stencil's own
 //                    centre cell (U_i for u^-_{i+1/2}, U_{i+1} for u^+_{i+1/2}) instead of the
 //                    Roe average at the face.
+//   FLAG_ALPHA_STEP  the LF coefficients of the first stage's input held for all three stages.
+//   FLAG_ALPHA_LOCAL local LF (Rusanov): alpha at face i+1/2 is the larger spectral radius of the
+//                    two adjacent cells i, i+1 (ghost cells through the boundary map).
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -58,7 +61,7 @@ using std::sqrt;
 
 enum { ADVECTION = 0, BURGERS = 1, EULER = 2 };
 enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2, BC_FIXED = 3 };
-enum { FLAG_V_WEIGHTED = 1, FLAG_CD2 = 2, FLAG_R2 = 4 };
+enum { FLAG_V_WEIGHTED = 1, FLAG_CD2 = 2, FLAG_R2 = 4, FLAG_ALPHA_STEP = 8, FLAG_ALPHA_LOCAL = 16 };
 
 struct Cfg {
   int32_t dim, system, nx, ny, bc, flags;
@@ -621,6 +624,10 @@ struct Operator {
   // the mixed flux of O (eta^ or xi^).
   void face_flux(int dir, R Uc[4][4], R Dc[4][4], R Oc[4][4], R alpha, R* fhat, R* hhat, R* mixed) const {
     double h = dir == 0 ? c.dx : c.dy;
+    if (c.flags & FLAG_ALPHA_LOCAL) {
+      const R al = ph.wavespeed(dir, Uc[1]), ar = ph.wavespeed(dir, Uc[2]);
+      alpha = ar > al ? ar : al;
+    }
     // Step 1.1: interface values
     R Um[4], Dm[4], Up[4], Dp[4];
     face_states(dir, Uc, Dc, Um, Dm, Up, Dp);
@@ -816,9 +823,18 @@ void rk3_step(const Cfg& c, R* S, double dt) {
   std::vector<R> L(n), M(n), B(n), S1(n);
   static const double a_k[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0};
   static const double b_k[3] = {1.0, 1.0 / 4.0, 2.0 / 3.0};
+  R ax0 = R(0.0), ay0 = R(0.0);
   for (int st = 0; st < 3; ++st) {
     R ax = op.max_wavespeed(0, S);
     R ay = c.dim == 2 ? op.max_wavespeed(1, S) : R(0.0);
+    if (c.flags & FLAG_ALPHA_STEP) {
+      if (st == 0) {
+        ax0 = ax;
+        ay0 = ay;
+      }
+      ax = ax0;
+      ay = ay0;
+    }
     op.rhs(S, L.data(), M.data(), ax, ay);
     if (st == 0) {
       for (size_t p = 0; p < n; ++p) B[p] = M[p];  // (u^n, v~^n, w~^n)
@@ -1166,7 +1182,7 @@ static int check_cfg(const oracle_cfg* c) {
   if ((c->side[0] == hwo::BC_PERIODIC) != (c->side[1] == hwo::BC_PERIODIC)) return -1;
   if (c->dim == 2 && (c->side[2] == hwo::BC_PERIODIC) != (c->side[3] == hwo::BC_PERIODIC)) return -1;
   if (c->grav != 0.0 && !(c->dim == 2 && c->system == hwo::EULER)) return -1;  // Eq. (euler2d-s) only
-  if (c->flags < 0 || c->flags > 7) return -1;
+  if (c->flags < 0 || c->flags > 31) return -1;
   if (!(c->gamma0 > 0 && c->gamma0 < 1) || !(c->d0 > 0 && c->d0 < 1) || !(c->eps > 0)) return -1;
   return 0;
 }
@@ -1332,8 +1348,9 @@ int oracle_steps_record(const oracle_cfg* c, double* S, int nsteps, double cfl, 
     const double dt = hwo::cfl_dt(*c, S, cfl, 1.0);
     dts[s] = dt;
     for (int st = 0; st < 3; ++st) {
-      const double ax = op.max_wavespeed(0, S);
-      const double ay = c->dim == 2 ? op.max_wavespeed(1, S) : 0.0;
+      const bool held = (c->flags & hwo::FLAG_ALPHA_STEP) && st > 0;
+      const double ax = held ? alphas[6 * s] : op.max_wavespeed(0, S);
+      const double ay = held ? alphas[6 * s + 1] : (c->dim == 2 ? op.max_wavespeed(1, S) : 0.0);
       alphas[6 * s + 2 * st] = ax;
       alphas[6 * s + 2 * st + 1] = ay;
       op.rhs(S, L.data(), M.data(), ax, ay);

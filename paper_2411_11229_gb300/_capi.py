@@ -12,7 +12,7 @@ from . import _make as _build
 
 HWENO_ADVECTION, HWENO_BURGERS, HWENO_EULER = 0, 1, 2
 HWENO_BC_PERIODIC, HWENO_BC_TRANSMISSIVE, HWENO_BC_REFLECTIVE, HWENO_BC_FIXED = 0, 1, 2, 3
-HWENO_FLAG_V_WEIGHTED, HWENO_FLAG_CD2, HWENO_FLAG_R2 = 1, 2, 4
+HWENO_FLAG_V_WEIGHTED, HWENO_FLAG_CD2, HWENO_FLAG_R2, HWENO_FLAG_ALPHA_STEP, HWENO_FLAG_ALPHA_LOCAL = 1, 2, 4, 8, 16
 HWENO_OK, HWENO_EINVAL, HWENO_ECUDA, HWENO_ENOMEM, HWENO_ENONPHYS, HWENO_ESTATE = 0, -1, -2, -3, -4, -5
 HWENO_ETOOBIG = -6
 

@@ -86,7 +86,9 @@ int hweno_create_ex(int dim, int system, int64_t nx, int64_t ny, double dx, doub
   // periodic pairs the two ends of an axis
   if ((ext->side[0] == HWENO_BC_PERIODIC) != (ext->side[1] == HWENO_BC_PERIODIC)) return HWENO_EINVAL;
   if (dim == 2 && (ext->side[2] == HWENO_BC_PERIODIC) != (ext->side[3] == HWENO_BC_PERIODIC)) return HWENO_EINVAL;
-  if (ext->flags < 0 || ext->flags > (HWENO_FLAG_V_WEIGHTED | HWENO_FLAG_CD2 | HWENO_FLAG_R2)) return HWENO_EINVAL;
+  const int all_flags = HWENO_FLAG_V_WEIGHTED | HWENO_FLAG_CD2 | HWENO_FLAG_R2 | HWENO_FLAG_ALPHA_STEP |
+                        HWENO_FLAG_ALPHA_LOCAL;
+  if (ext->flags < 0 || (ext->flags & ~all_flags)) return HWENO_EINVAL;
   if (!std::isfinite(ext->grav)) return HWENO_EINVAL;
   if (ext->grav != 0.0 && !(dim == 2 && system == HWENO_EULER)) return HWENO_EINVAL;
   const int nc = system == HWENO_EULER ? (dim == 1 ? 3 : 4) : 1;
@@ -176,6 +178,8 @@ int hweno_bind(hweno_t* h, double* state_dev, void* ws) {
   h->w.GFS = l.GFS ? reinterpret_cast<double*>(p) : nullptr;
   p += l.GFS;
   h->w.gstride = gstride_of(h);
+  h->w.WS = l.WS ? reinterpret_cast<double*>(p) : nullptr;
+  p += l.WS;
   h->state = state_dev;
   h->ws = static_cast<unsigned char*>(ws);
   if (cudaMemsetAsync(scal_begin, 0, l.alpha + l.scal + l.status, h->stream) != cudaSuccess) return HWENO_ECUDA;
@@ -523,7 +527,7 @@ extern "C" int hweno_rhs_static(int dim, int system, int64_t nx, int64_t ny, dou
   p += l.scal;
   h.w.status = reinterpret_cast<unsigned int*>(p);
   h.w.astride = 2;
-  h.w.FS = h.w.GFS = nullptr;
+  h.w.FS = h.w.GFS = h.w.WS = nullptr;
   h.w.gstride = 0;
   // the array keeps the previous call's contents: clear the wavespeed slots and the status word
   if (cudaMemsetAsync(scal_begin, 0, l.alpha + l.scal + l.status, h.stream) != cudaSuccess) return HWENO_ECUDA;

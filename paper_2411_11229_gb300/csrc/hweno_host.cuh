@@ -103,7 +103,7 @@ inline int np_of(const hweno_ctx* h) { return h->system == HWENO_EULER ? (h->dim
 
 // workspace sub-buffers in bytes, in layout order
 struct Layout {
-  size_t B, MD, NOD, PRIM, FX, FY, alpha, scal, status, FS, GFS, total;
+  size_t B, MD, NOD, PRIM, FX, FY, alpha, scal, status, FS, GFS, WS, total;
 };
 
 inline long long gstride_of(const hweno_ctx* h) { return h->nx > h->ny ? h->nx : h->ny; }
@@ -123,7 +123,8 @@ inline Layout layout_of(const hweno_ctx* h) {
   l.status = align_up(16);
   l.FS = h->var == 2 ? align_up((size_t)h->dim * 4 * nc * plane * 8) : 0;
   l.GFS = h->var == 2 ? align_up((size_t)h->dim * 4 * nc * (size_t)gstride_of(h) * 8) : 0;
-  l.total = l.B + l.MD + l.NOD + l.PRIM + l.FX + l.FY + l.alpha + l.scal + l.status + l.FS + l.GFS;
+  l.WS = (h->var != 0 && (h->flags & HWENO_FLAG_ALPHA_LOCAL)) ? align_up((size_t)h->dim * plane * 8) : 0;
+  l.total = l.B + l.MD + l.NOD + l.PRIM + l.FX + l.FY + l.alpha + l.scal + l.status + l.FS + l.GFS + l.WS;
   return l;
 }
 
@@ -178,15 +179,17 @@ inline Grid grid_of(const hweno_ctx* h) {
   g.grav = h->grav;
   for (int sd = 0; sd < 4; ++sd) {
     g.side[sd] = h->side[sd];
+    g.fixA[sd] = 0.0;
     for (int k = 0; k < 4; ++k) g.fixU[sd][k] = g.fixP[sd][k] = g.fixF[sd][k] = 0.0;
     if (h->side[sd] != hw::BC_FIXED) continue;
     const double* U = h->fixed[sd];
     for (int k = 0; k < 4; ++k) g.fixU[sd][k] = U[k];
     const int nc = nc_of(h);
     if (h->system != HWENO_EULER) {
-      // scalar: the flux of the state along the side's normal
+      // scalar: the flux of the state along the side's normal, and |f'(u)|
       const double a = sd < 2 ? h->ax : h->ay;
       g.fixF[sd][0] = h->system == HWENO_ADVECTION ? a * U[0] : 0.5 * U[0] * U[0];
+      g.fixA[sd] = h->system == HWENO_ADVECTION ? std::fabs(a) : std::fabs(U[0]);
       continue;
     }
     // primitives in the original frame, flux in the side's normal frame
@@ -202,6 +205,7 @@ inline Grid grid_of(const hweno_ctx* h) {
       g.fixP[sd][2] = H;
     }
     const double un = sd < 2 ? u : v, mn = rho * un, mt = sd < 2 ? U[2] : U[1];
+    g.fixA[sd] = std::fabs(un) + std::sqrt(h->gamma * p / rho);
     g.fixF[sd][0] = mn;
     g.fixF[sd][1] = mn * un + p;
     if (h->dim == 2) {
@@ -254,7 +258,9 @@ inline int stage(hweno_ctx* h, const double* S_in, double* S_out, int mode, int 
                       h->stream) != cudaSuccess)
     return HWENO_ECUDA;
   if (ev[1]) cudaEventRecord(ev[1], h->stream);
-  f.face(g, S_in, h->w, slot, h->stream);
+  // LF coefficients held for the whole step: stages 2 and 3 read the first stage's slot
+  const bool held = h->var != 0 && (h->flags & HWENO_FLAG_ALPHA_STEP) && mode == 0 && st > 0;
+  f.face(g, S_in, h->w, held ? slot - st : slot, h->stream);
   if (ev[2]) cudaEventRecord(ev[2], h->stream);
   f.update(g, S_out, h->w, mode, st, a_k[st], b_k[st], dt, slot, Lo, Mo, h->stream);
   if (ev[3]) cudaEventRecord(ev[3], h->stream);

@@ -47,6 +47,8 @@ struct Work {
   double* FS;
   double* GFS;
   long long gstride;
+  // local LF coefficients only: the spectral radius of every cell per direction [DIM][plane]
+  double* WS;
 };
 
 constexpr int kThreads = 128;
@@ -258,6 +260,10 @@ __device__ __forceinline__ void cell_body(const Grid& g, const double* __restric
       wsx = fabs(g.ax);
       wsy = DIM == 2 ? fabs(g.ay) : 0.0;
     }
+    if (VAR && (g.flags & FLAG_ALPHA_LOCAL)) {
+      w.WS[p] = wsx;
+      if (DIM == 2) w.WS[plane + p] = wsy;
+    }
     // nodal values per direction (normal frame)
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
@@ -468,6 +474,12 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
       Dm[0] = chm[0];
       Dp[0] = chp[0];
     }
+  }
+  // local LF: the larger spectral radius of the two cells of the face
+  if (VAR && (g.flags & FLAG_ALPHA_LOCAL)) {
+    const double al = fixed[1] ? g.fixA[fside[1]] : w.WS[dir * plane + pc[1]];
+    const double ar = fixed[2] ? g.fixA[fside[2]] : w.WS[dir * plane + pc[2]];
+    alpha = fmax(al, ar);
   }
   // Lax-Friedrichs fluxes at the interpolated states (Eq. flux-LF)
   const double a_adv = dir == 0 ? g.ax : g.ay;

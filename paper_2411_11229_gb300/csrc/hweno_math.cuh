@@ -16,7 +16,7 @@ namespace hw {
 enum { SYS_ADV = 0, SYS_BURGERS = 1, SYS_EULER = 2 };
 enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2, BC_FIXED = 3 };
 // scheme variants of the extended kernels (VAR != 0)
-enum { FLAG_V_WEIGHTED = 1, FLAG_CD2 = 2, FLAG_R2 = 4 };
+enum { FLAG_V_WEIGHTED = 1, FLAG_CD2 = 2, FLAG_R2 = 4, FLAG_ALPHA_STEP = 8, FLAG_ALPHA_LOCAL = 16 };
 
 template <int DIM, int SYS>
 struct Traits {
@@ -52,11 +52,12 @@ struct Grid {
   //   ig1 = 1/gamma1 (weighted derivative); Cd-2 folded per direction: c2h = c2 h,
   //   e2fih = e2f/h, e2gih = e2g/h;
   //   fixU, fixP, fixF: the state of a BC_FIXED side (original frame), its primitives
-  //   (sqrt rho, u[, v], H) and its flux normal to the side (normal frame).
+  //   (sqrt rho, u[, v], H) and its flux normal to the side (normal frame); fixA: its spectral
+  //   radius normal to the side (local LF coefficient).
   int side[4];
   double grav, ig1;
   double c2h[2], e2fih[2], e2gih[2];
-  double fixU[4][4], fixP[4][4], fixF[4][4];
+  double fixU[4][4], fixP[4][4], fixF[4][4], fixA[4];
 };
 
 // 1/x for normal, finite x: the hardware approximation (rcp.approx.ftz.f64) refined by two

@@ -89,7 +89,7 @@ P, T, R, F = C.HWENO_BC_PERIODIC, C.HWENO_BC_TRANSMISSIVE, C.HWENO_BC_REFLECTIVE
 
 
 @pytest.mark.parametrize("dim,system,e", [
-    (2, C.HWENO_EULER, _ext(flags=8)),                                        # unknown flag
+    (2, C.HWENO_EULER, _ext(flags=32)),                                       # unknown flag
     (2, C.HWENO_EULER, _ext(sides=(P, T, P, P))),                             # periodic on one end
     (2, C.HWENO_EULER, _ext(sides=(P, P, T, P))),
     (2, C.HWENO_EULER, _ext(sides=(P, P, 4, 4))),                             # unknown type

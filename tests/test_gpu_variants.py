@@ -23,6 +23,7 @@ from paper_2411_11229_gb300 import Solver  # noqa: E402
 SYS = {"advection": O.ADVECTION, "burgers": O.BURGERS, "euler": O.EULER}
 P, T, R, F = O.BC_PERIODIC, O.BC_TRANSMISSIVE, O.BC_REFLECTIVE, O.BC_FIXED
 VW, CD2, R2 = O.FLAG_V_WEIGHTED, O.FLAG_CD2, O.FLAG_R2
+AST, ALOC = O.FLAG_ALPHA_STEP, O.FLAG_ALPHA_LOCAL
 ALL = VW | CD2 | R2
 
 
@@ -95,6 +96,11 @@ CASES = [
     (2, "euler", 30, 27, ALL, (F, T, R, F)),
     (2, "euler", 6, 9, ALL, (R, R, F, F)),
     (2, "euler", 35, 22, 0, (F, R, P, P)),
+    (1, "burgers", 47, 1, ALOC, (T, F, P, P)),
+    (1, "euler", 88, 1, ALOC, (F, R, P, P)),
+    (2, "euler", 33, 21, ALOC, (P, P, P, P)),
+    (2, "euler", 30, 27, ALOC | R2, (R, R, F, F)),
+    (2, "euler", 29, 24, AST | ALL, (T, F, R, R)),
 ]
 
 
@@ -187,7 +193,7 @@ def _gpu_steps(s, n):
     return s.state.cpu().numpy()
 
 
-@pytest.mark.parametrize("flags", [R2, ALL])
+@pytest.mark.parametrize("flags", [R2, ALL, AST, ALOC, AST | ALOC | R2])
 def test_hundred_smooth_steps(flags):
     S, dx, dy = W.euler2d_smooth(40, 32)
     cfg, s = pair(2, "euler", 40, 32, S, dx, dy, flags=flags)
@@ -197,7 +203,7 @@ def test_hundred_smooth_steps(flags):
     assert rel_planes(out, ref) <= 1e-10
 
 
-@pytest.mark.parametrize("flags", [0, R2])
+@pytest.mark.parametrize("flags", [0, R2, AST | ALOC])
 @pytest.mark.parametrize("nsteps", [20, 100])
 def test_rayleigh_taylor_run(flags, nsteps):
     """Example 4.11 at 16 x 64: the discontinuous interface amplifies rounding, so the bar is

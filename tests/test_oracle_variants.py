@@ -229,7 +229,7 @@ def test_invalid_extensions_rejected():
     with pytest.raises(ValueError):  # periodic on one side only
         O.state_size(O.make_cfg(2, O.EULER, 8, 8, sides=(O.BC_PERIODIC, O.BC_FIXED, 0, 0)))
     with pytest.raises(ValueError):
-        O.state_size(O.make_cfg(2, O.EULER, 8, 8, flags=8))
+        O.state_size(O.make_cfg(2, O.EULER, 8, 8, flags=32))
 
 
 # ------------------------------------------------------------------------------------------------
@@ -287,3 +287,83 @@ def test_operator_commutes_with_mirroring(flags, kind):
     Lm, Mm = O.rhs(cfg, _mirror(S))
     for a, b in ((Lm, _mirror(L)), (Mm, _mirror(M))):
         assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_characteristic_bases_agree_when_the_weights_are_linear(dim):
+    """With linear weights (eps far above every smoothness indicator) the interpolation is linear
+    in its data, so it commutes with any projection: the Roe basis at the face (default) and the
+    centre cells' bases (R2) give the same face states, and those are the componentwise ones.
+    This pins the pairing of every projection with its back projection."""
+    if dim == 1:
+        S, dx = W.euler1d_random(24, 51, "jumps")
+        dy = dx
+        nx, ny = 24, 1
+    else:
+        S, dx, dy = W.euler2d_random(14, 11, 52, "jumps")
+        nx, ny = 14, 11
+    kw = dict(dx=dx, dy=dy, eps=1e30, bc=O.BC_TRANSMISSIVE)
+    L1, M1 = O.rhs(O.make_cfg(dim, O.EULER, nx, ny, **kw), S)
+    L2, M2 = O.rhs(O.make_cfg(dim, O.EULER, nx, ny, flags=O.FLAG_R2, **kw), S)
+    for a, b in ((L1, L2), (M1, M2)):
+        assert np.abs(a - b).max() <= 1e-11 * np.abs(a).max()
+    # and with real weights on blocky data they differ
+    L3, _ = O.rhs(O.make_cfg(dim, O.EULER, nx, ny, dx=dx, dy=dy, bc=O.BC_TRANSMISSIVE), S)
+    L4, _ = O.rhs(O.make_cfg(dim, O.EULER, nx, ny, dx=dx, dy=dy, bc=O.BC_TRANSMISSIVE, flags=O.FLAG_R2), S)
+    assert np.abs(L3 - L4).max() > 1e-10 * np.abs(L3).max()
+
+
+# ------------------------------------------------------------------------------------------------
+# LF coefficient scope (global per stage by default; per step; local per face)
+
+def _three_region_1d(n, fast):
+    """1D Euler: left state | right state with a jump at the middle face, both with the same
+    |u| + c (same u; rho and P scaled together keep c), and (if fast) a region of large wavespeed
+    far from the jump."""
+    rho = np.where(np.arange(n) < n // 2, 1.0, 0.4)
+    u = np.full(n, 0.2)
+    p = np.where(np.arange(n) < n // 2, 1.0, 0.4)
+    if fast:
+        u[-6:] = 30.0
+    zero = np.zeros(n)
+    U, V = W.euler_from_primitive_1d(rho, u, p, zero, zero, zero)
+    S = np.zeros((2, 3, 1, n))
+    S[0, :, 0] = U
+    return S
+
+
+def test_local_alpha_is_the_adjacent_cells_maximum():
+    """Local LF: at a face the coefficient is max(|u| + c) of its two adjacent cells, whatever the
+    rest of the grid holds.  Near the jump every cell has the same |u| + c, so there the local
+    operator on data with a far, fast region equals the global operator on the same data without
+    that region (whose global maximum is that common value)."""
+    n = 40
+    S3, S2 = _three_region_1d(n, True), _three_region_1d(n, False)
+    cfg_loc = O.make_cfg(1, O.EULER, n, dx=0.05, bc=O.BC_TRANSMISSIVE, flags=O.FLAG_ALPHA_LOCAL)
+    cfg_glob = O.make_cfg(1, O.EULER, n, dx=0.05, bc=O.BC_TRANSMISSIVE)
+    L3, _ = O.rhs(cfg_loc, S3)
+    L2, _ = O.rhs(cfg_glob, S2)
+    near = slice(n // 2 - 3, n // 2 + 3)
+    assert np.abs(L3[..., near] - L2[..., near]).max() <= 1e-13 * np.abs(L2[..., near]).max()
+    # and the global coefficient (set by the fast region) dissipates more there
+    L3g, _ = O.rhs(cfg_glob, S3)
+    assert np.abs(L3g[..., near] - L2[..., near]).max() > 1e-3 * np.abs(L2[..., near]).max()
+
+
+def test_alpha_held_for_the_step_equals_a_replay_with_stage_one_alphas():
+    S, dx, dy = W.euler2d_random(12, 10, 53, "jumps")
+    cfg = O.make_cfg(2, O.EULER, 12, 10, dx=dx, dy=dy, flags=O.FLAG_ALPHA_STEP)
+    out, dts, alphas = O.steps_record(cfg, S, 3)
+    assert np.array_equal(alphas[:, 2:4], alphas[:, 0:2]) and np.array_equal(alphas[:, 4:6], alphas[:, 0:2])
+    base = O.make_cfg(2, O.EULER, 12, 10, dx=dx, dy=dy)
+    rep = O.steps_replay(base, S, dts, alphas)
+    assert np.array_equal(out, rep)
+    # the default scheme recomputes alpha at every stage, which differs on this data
+    _, _, a_def = O.steps_record(base, S, 3)
+    assert not np.array_equal(a_def[:, 2:4], a_def[:, 0:2])
+
+
+@pytest.mark.parametrize("flags", [O.FLAG_ALPHA_STEP, O.FLAG_ALPHA_LOCAL, O.FLAG_ALPHA_LOCAL | O.FLAG_R2])
+def test_alpha_modes_keep_fifth_order_euler1d(flags):
+    e40, e80 = _euler1d_error(40, flags), _euler1d_error(80, flags)
+    assert np.log2(e40 / e80) >= 4.6, (e40, e80)
