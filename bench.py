@@ -32,6 +32,12 @@ UNIT = "Mcell-updates/s"
 # FP64 peak for the ALU roofline, from the SM count (152), the maximum SM clock (2070 MHz) and the
 # FP64 rate of GB300 (2 DFMA per SM per clock = 4 flop/clk/SM): 152 * 2.07e9 * 4.
 FP64_PEAK_FLOPS = 152 * 2.07e9 * 4
+# FP64 rate of a DFMA-chain probe on this GPU (595 G DFMA/s at ~1.96 GHz)
+FP64_PROBE_FLOPS = 1.19e12
+# algorithmic HBM bytes of one SSP-RK3 step per 2D Euler cell: the state planes each stage must
+# touch once (stage 1: read 12, write 12, write the 8-plane base; stages 2, 3: read 12, read the
+# base 12, write 12) = 104 planes of 8 bytes
+STEP_BYTES_PER_CELL = 104 * 8
 HBM_PEAK_GBS_FALLBACK = 6800.0
 # DRAM bytes per face of the 2D Euler face kernel from an ncu capture at 2048^2 (profiles/); the
 # traffic grows in proportion to the faces, so a 4096^2 launch moves this times its faces.
@@ -455,6 +461,14 @@ def run_ours(args, ws, rank, local):
                      "faces_per_launch": faces, "avg_launch_ms": face_avg_ms,
                      "peak_note": "FP64 derived: 152 SMs x 2070 MHz x 4 flop/clk",
                      "hbm_peak_gbs": hbm_peak},
+        "hbm": {"bytes_per_cell_step_algorithmic": STEP_BYTES_PER_CELL,
+                "achieved_gbs": value * 1e6 * STEP_BYTES_PER_CELL / 1e9,
+                "frac": value * 1e6 * STEP_BYTES_PER_CELL / 1e9 / hbm_peak,
+                "face_kernel_dram_gbs": None if traffic is None else traffic / (face_avg_ms * 1e-3) / 1e9,
+                "face_kernel_frac": None if traffic is None else traffic / (face_avg_ms * 1e-3) / 1e9 / hbm_peak,
+                "peak_gbs": hbm_peak, "peak_note": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback",
+                "note": "the step is bound by the FP64 pipe; HBM is reported beside it"},
+        "fp64_frac_of_probe": achieved / FP64_PROBE_FLOPS,
         "kernel_share": {k: v[0] / total_ms for k, v in ktimes.items()} if total_ms > 0 else None,
         "kernel_avg_ms": {k: v[0] / max(v[1], 1) for k, v in ktimes.items()},
         "flops_per_cell_step": counts["per_cell_step"],
