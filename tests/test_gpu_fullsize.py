@@ -1,7 +1,8 @@
 """Parity at the full workload sizes, in the launch configuration the benchmark times.
 
-2D Euler 4096^2 (the benchmark workload): the one-stage operator checked cell by cell against the
-oracle at sampled cells (interior, edges, corners, across the discontinuities), plus properties
+2D Euler 4096^2 (the benchmark workload, with the scheme of the paper and with the R2 variant): the
+one-stage operator checked cell by cell against the oracle at sampled cells (interior, edges,
+corners, across the discontinuities), plus properties
 of 10 CFL steps that hold at any size (conservation to round-off, the exact translation of the
 smooth wave).  2D Euler 1024^2 and 1D Euler 16384: full-field comparisons.
 """
@@ -40,20 +41,22 @@ def _perturbed(S, seed):
     return S * (1.0 + sign * 2.0 ** -52)
 
 
+@pytest.mark.parametrize("flags", [0, O.FLAG_R2])
 @pytest.mark.parametrize("kind", ["smooth", "quadrants"])
-def test_rhs_4096_sampled(kind):
+def test_rhs_4096_sampled(kind, flags):
     """One stage at 4096^2: L, M and the state after the stage, S1 = M + dt L with the CFL dt,
     within 1e-12 or ten times the oracle's own rounding envelope at these cells (the oracle
     against itself with a one-ulp input perturbation), whichever is larger.  L of a derivative
     field is a difference quotient of fluxes that carry 1/h, so its rounding noise grows like
-    1/h^2, and that of S1 like 1/h."""
+    1/h^2, and that of S1 like 1/h.  flags: the scheme of the paper and the per-cell
+    characteristic decomposition (R2), the two configurations the benchmark times at this size."""
     n = 4096
     if kind == "smooth":
         S, dx, dy = W.euler2d_smooth(n)
     else:
         S, dx, dy = W.euler2d_quadrants(n, seed=2000)
-    cfg = O.make_cfg(2, O.EULER, n, n, dx=dx, dy=dy)
-    s = Solver(2, "euler", n, n, dx=dx, dy=dy)
+    cfg = O.make_cfg(2, O.EULER, n, n, dx=dx, dy=dy, flags=flags)
+    s = Solver(2, "euler", n, n, dx=dx, dy=dy, flags=flags)
     s.set_state(S)
     L, M = s.rhs()
     idx = _samples(n, n, np.random.default_rng(7))
