@@ -26,7 +26,8 @@ from paper_2411_11229_gb300 import Solver  # noqa: E402
 from paper_2411_11229_gb300 import _capi as C  # noqa: E402
 
 SYSTEMS = {"advection": C.HWENO_ADVECTION, "burgers": C.HWENO_BURGERS, "euler": C.HWENO_EULER}
-BCS = {"periodic": C.HWENO_BC_PERIODIC, "transmissive": C.HWENO_BC_TRANSMISSIVE}
+BCS = {"periodic": C.HWENO_BC_PERIODIC, "transmissive": C.HWENO_BC_TRANSMISSIVE,
+       "reflective": C.HWENO_BC_REFLECTIVE}
 
 
 def _static_rhs(dim, system, nx, ny, dx, dy, bc, S):
@@ -63,6 +64,8 @@ def test_static_rhs_matches_workspace_rhs_on_two_calls():
         (2, "euler", 37, 29, "periodic", W.euler2d_random(37, 29, 11, "jumps")[0]),
         (1, "euler", 300, 1, "transmissive", W.euler1d_random(300, 12, "smooth")[0]),
         (2, "euler", 180, 180, "periodic", W.euler2d_quadrants(180, seed=2000)[0]),
+        (2, "euler", 61, 47, "reflective", W.euler2d_quadrants(61, 47, seed=2001)[0]),
+        (1, "euler", 400, 1, "reflective", W.blast_wave_1d(400, p_mid=1.0)[0]),
     ]
     for dim, system, nx, ny, bc, S in cases:
         dx = 2.0 / nx
