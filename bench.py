@@ -429,6 +429,20 @@ def run_ours(args, ws, rank, local):
     barrier()
     ms_e2e = max_over_ranks(f0.elapsed_time(f1), ws, dev)
     e2e_value = job_throughput(ws, cells, ke2e, ms_e2e)
+    # one more end-to-end step outside the timed region, with an event between its phases: where
+    # the end-to-end time goes (the copies run at the host link's rate, which varies between boxes)
+    g = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    g[0].record(stream)
+    solver.upload(host_in)
+    g[1].record(stream)
+    solver.step(0.0)
+    g[2].record(stream)
+    solver.download(host_out)
+    g[3].record(stream)
+    torch.cuda.synchronize()
+    phases = {"upload_ms": g[0].elapsed_time(g[1]), "step_ms": g[1].elapsed_time(g[2]),
+              "download_ms": g[2].elapsed_time(g[3])}
+    phases["copy_gbs"] = 2 * nbytes / ((phases["upload_ms"] + phases["download_ms"]) * 1e-3) / 1e9
 
     if rank != 0:
         return 0
@@ -454,7 +468,8 @@ def run_ours(args, ws, rank, local):
         "clocks": clocks,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-                "steps": ke2e, "path": "hweno_upload + hweno_step + hweno_download, pinned host buffers"},
+                "steps": ke2e, "path": "hweno_upload + hweno_step + hweno_download, pinned host buffers",
+                "phases_one_step": phases},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic,
                      "kernel": "k_face<2,EULER>", "flops_per_face": counts["face"],
