@@ -40,6 +40,9 @@ def _create(*args):
     (1, 2, 64, 1, -0.1, 0.1, 1.4, 0),     # dx <= 0
     (1, 2, 64, 1, 0.1, 0.1, 1.0, 0),      # gamma <= 1
     (1, 2, 64, 1, 0.1, 0.1, 1.4, 9),      # bc
+    (1, 2, (1 << 28) + 1, 1, 0.1, 0.1, 1.4, 0),    # nx beyond the largest axis
+    (2, 2, 1 << 16, (1 << 15) + 1, 0.1, 0.1, 1.4, 0),  # nx * ny beyond 2^31 cells
+    (2, 2, 64, 64, float("inf"), 0.1, 1.4, 0),     # non-finite spacing
 ])
 def test_create_rejects_invalid(args):
     rc, h = _create(*args)

@@ -275,3 +275,31 @@ def test_run_matches_stepping_and_stops_at_the_end(ext):
     d.set_time(0.0, 10.0)
     d.step(0.0, 37)
     assert torch.equal(c.state, d.state)
+
+
+@pytest.mark.parametrize("dim,system,bc", [(1, "advection", "periodic"), (1, "burgers", "transmissive"),
+                                           (1, "euler", "reflective"), (2, "burgers", "periodic"),
+                                           (2, "euler", "transmissive"), (2, "euler", "reflective")])
+def test_uniform_state_is_steady(dim, system, bc):
+    """The degenerate case of every smoothness indicator: a uniform state at rest (flowing where the
+    boundary allows it) with zero derivatives.  All fluxes of a line are equal, so L is zero exactly
+    and M = (U, 0, 0), on both sides; a step leaves the state as it is up to the rounding of the
+    third stage's weights 1/3 and 2/3 (not binary fractions)."""
+    nx, ny = 23, (17 if dim == 2 else 1)
+    if system == "euler":
+        nc = 3 if dim == 1 else 4
+        U = np.array([1.3, 0.0, 2.7]) if dim == 1 else np.array([1.3, 0.0, 0.0, 2.7])
+        if bc != "reflective":
+            U[1] = 0.4
+    else:
+        nc, U = 1, np.array([0.7])
+    S = np.zeros((dim + 1, nc, ny, nx))
+    S[0] = U[:, None, None]
+    cfg, s = pair(dim, system, nx, ny, bc, S, 0.1, 0.1)
+    L, M = s.rhs()
+    assert torch.count_nonzero(L).item() == 0
+    assert np.array_equal(M.cpu().numpy(), S)
+    Lo, Mo = O.rhs(cfg, S)
+    assert not Lo.any() and np.array_equal(Mo, S)
+    s.step(0.0)
+    assert np.abs(s.state.cpu().numpy() - S).max() <= 1e-15 * np.abs(S).max()
