@@ -159,6 +159,14 @@ inline Grid grid_of(const hweno_ctx* h) {
     g.cr[k] = cr[k];
     g.cl[k] = cl[k];
   }
+  // the centre-value-free forms: right face on (d01, d12, hvm, hvp) of the stencil {i-1, i, i+1};
+  // left face (mirror) on (d_{i,i+1} of its own stencil's first pair, second pair, h v_{i-1}, h v_{i+1})
+  const double dm[4] = {-cr[0], cr[2], cr[3], cr[4]};
+  const double dp[4] = {-cl[0], cl[2], cl[3], cl[4]};
+  for (int k = 0; k < 4; ++k) {
+    g.dm[k] = dm[k];
+    g.dp[k] = dp[k];
+  }
   g.G = g.g0 / g1;
   g.cdu = (0.75 - g.d1) / g.d1;
   g.csv = 0.25 / g.d1;

@@ -45,6 +45,10 @@ struct Grid {
   //   G = gamma0 / gamma1;  limiter: cdu = (3/4 - d1)/d1, csv = (1/4)/d1, Gd = d0 / d1;
   //   per direction: h, 1/h, ch*h, ef/h, eg/h (D-terms), 1/(2h).
   double cr[5], cl[5], G;
+  //   dm, dp: the same combinations with the centre value taken out (their value coefficients
+  //           sum to G): (p0 - gamma1 (p1 + p2))/gamma1 - G u_i on (d01, d12, hvm, hvp) at the
+  //           right face and, mirrored, on (d_{i-1,i}, d_{i,i+1}, ...) at the left face;
+  double dm[4], dp[4];
   double cdu, csv, Gd;
   double h[2], ih[2], chh[2], efih[2], egih[2], hih[2];
   // Extended scheme (read only by the kernels instantiated with VAR != 0):
@@ -122,38 +126,39 @@ __device__ __forceinline__ Wts weights(double b0, double b1, double b2, double e
 __device__ __forceinline__ void face_field(double w0, double w1, double w2, double w3, double y0, double y1,
                                            double y2, double y3, const Grid& g, double& um, double& hvm,
                                            double& up, double& hvp, bool vw = false) {
+  // Every candidate reproduces constants and the candidates' value coefficients sum to G, so each
+  // value is written as the centre value plus a combination of cell differences:
+  //   num / den = u_c + (W0 (r - G u_c) + W1 (p1 - u_c) + W2 (p2 - u_c)) / den,
+  // with p1 - u_c and p2 - u_c half a cell difference each.
   const double d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2;
   const double b01 = d01 * d01, b12 = d12 * d12, b23 = d23 * d23;
   const double e01 = b01 + g.eps, e12 = b12 + g.eps, e23 = b23 + g.eps;
-  const double pmid = 0.5 * (w1 + w2);  // linear candidate on {k, k+1}, shared by both stencils
   double du, sv;
   {
-    // stencil of cell k: u_{i-1..i+1} = w0, w1, w2
+    // stencil of cell k: u_{i-1..i+1} = w0, w1, w2; candidates on {i-1, i} (W1), {i, i+1} (W2)
     const double b0 = beta0(d01, d12, y0, y2, du, sv);
     const Wts wt = weights(b0, b01, b12, e01, e12, g.eps);
-    const double r = fma(g.cr[0], w0, fma(g.cr[1], w1, fma(g.cr[2], w2, fma(g.cr[3], y0, g.cr[4] * y2))));
-    const double p1 = fma(-0.5, w0, 1.5 * w1);
-    const double num = fma(wt.W0, r, fma(wt.W1, p1, wt.W2 * pmid));
+    const double r = fma(g.dm[0], d01, fma(g.dm[1], d12, fma(g.dm[2], y0, g.dm[3] * y2)));
+    const double sl = fma(wt.W1, d01, wt.W2 * d12);
     const double den = fma(g.G, wt.W0, wt.W1 + wt.W2);
     const double rden = rcp(den);
-    um = num * rden;
-    hvm = fma(0.1875, w0, fma(-1.5, w1, fma(1.3125, w2, fma(0.0625, y0, -0.1875 * y2))));
+    um = fma(fma(wt.W0, r, 0.5 * sl), rden, w1);
+    hvm = fma(1.3125, d12, fma(-0.1875, d01, fma(0.0625, y0, -0.1875 * y2)));
     // weighted: the same combination of h p0', h p1' = d01, h p2' = d12
-    if (vw) hvm = fma(wt.W0, fma(hvm, g.ig1, -du), fma(wt.W1, d01, wt.W2 * d12)) * rden;
+    if (vw) hvm = fma(wt.W0, fma(hvm, g.ig1, -du), sl) * rden;
   }
   {
     // stencil of cell k+1: u_{i-1..i+1} = w1, w2, w3; its candidate on {i, i+1} carries beta2,
-    // the one on {i-1, i} (pmid) carries beta1 (mirror image)
+    // the one on {i-1, i} carries beta1 (mirror image)
     const double b0 = beta0(d12, d23, y1, y3, du, sv);
     const Wts wt = weights(b0, b12, b23, e12, e23, g.eps);
-    const double r = fma(g.cl[0], w1, fma(g.cl[1], w2, fma(g.cl[2], w3, fma(g.cl[3], y1, g.cl[4] * y3))));
-    const double q1 = fma(-0.5, w3, 1.5 * w2);
-    const double num = fma(wt.W0, r, fma(wt.W2, q1, wt.W1 * pmid));
+    const double r = fma(g.dp[0], d12, fma(g.dp[1], d23, fma(g.dp[2], y1, g.dp[3] * y3)));
+    const double sl = fma(wt.W1, d12, wt.W2 * d23);
     const double den = fma(g.G, wt.W0, wt.W1 + wt.W2);
     const double rden = rcp(den);
-    up = num * rden;
-    hvp = fma(-1.3125, w1, fma(1.5, w2, fma(-0.1875, w3, fma(-0.1875, y1, 0.0625 * y3))));
-    if (vw) hvp = fma(wt.W0, fma(hvp, g.ig1, -du), fma(wt.W1, d12, wt.W2 * d23)) * rden;
+    up = fma(fma(wt.W0, r, -0.5 * sl), rden, w2);
+    hvp = fma(1.3125, d12, fma(-0.1875, d23, fma(-0.1875, y1, 0.0625 * y3)));
+    if (vw) hvp = fma(wt.W0, fma(hvp, g.ig1, -du), sl) * rden;
   }
 }
 
@@ -170,15 +175,16 @@ __device__ __forceinline__ void cell_faces_field(double w0, double w1, double w2
   const double b0 = beta0(d01, d12, y0, y2, du, sv);
   const Wts wt = weights(b0, b1, b2, b1 + g.eps, b2 + g.eps, g.eps);
   const double rden = rcp(fma(g.G, wt.W0, wt.W1 + wt.W2));
-  const double rm = fma(g.cr[0], w0, fma(g.cr[1], w1, fma(g.cr[2], w2, fma(g.cr[3], y0, g.cr[4] * y2))));
-  const double rp = fma(g.cl[0], w0, fma(g.cl[1], w1, fma(g.cl[2], w2, fma(g.cl[3], y0, g.cl[4] * y2))));
-  const double p1 = fma(-0.5, w0, 1.5 * w1), p2 = 0.5 * (w1 + w2);  // candidates at x_{i+1/2}
-  const double q2 = fma(-0.5, w2, 1.5 * w1), q1 = 0.5 * (w0 + w1);  // and at x_{i-1/2}
-  um = fma(wt.W0, rm, fma(wt.W1, p1, wt.W2 * p2)) * rden;
-  up = fma(wt.W0, rp, fma(wt.W2, q2, wt.W1 * q1)) * rden;
-  hvm = fma(0.1875, w0, fma(-1.5, w1, fma(1.3125, w2, fma(0.0625, y0, -0.1875 * y2))));
-  hvp = fma(-1.3125, w0, fma(1.5, w1, fma(-0.1875, w2, fma(-0.1875, y0, 0.0625 * y2))));
+  // centre value plus differences (see face_field): the candidates at x_{i+1/2} differ from u_i by
+  // (d01, d12)/2, those at x_{i-1/2} by (-d01, -d12)/2, so both faces share W1 d01 + W2 d12
+  const double rm = fma(g.dm[0], d01, fma(g.dm[1], d12, fma(g.dm[2], y0, g.dm[3] * y2)));
+  const double rp = fma(g.dp[0], d01, fma(g.dp[1], d12, fma(g.dp[2], y0, g.dp[3] * y2)));
   const double sl = fma(wt.W1, d01, wt.W2 * d12);
+  const double hs = 0.5 * sl;
+  um = fma(fma(wt.W0, rm, hs), rden, w1);
+  up = fma(fma(wt.W0, rp, -hs), rden, w1);
+  hvm = fma(1.3125, d12, fma(-0.1875, d01, fma(0.0625, y0, -0.1875 * y2)));
+  hvp = fma(1.3125, d01, fma(-0.1875, d12, fma(-0.1875, y0, 0.0625 * y2)));
   if (vw) {
     hvm = fma(wt.W0, fma(hvm, g.ig1, -du), sl) * rden;
     hvp = fma(wt.W0, fma(hvp, g.ig1, -du), sl) * rden;
