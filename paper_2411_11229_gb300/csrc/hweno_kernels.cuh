@@ -264,6 +264,12 @@ __device__ __forceinline__ void cell_body(const Grid& g, const double* __restric
       w.WS[p] = wsx;
       if (DIM == 2) w.WS[plane + p] = wsy;
     }
+    // primitive derivatives along V and W (2D Euler: shared by the Jacobians of both directions)
+    double pdV[3] = {0.0, 0.0, 0.0}, pdW[3] = {0.0, 0.0, 0.0};
+    if (SYS == SYS_EULER && DIM == 2) {
+      Phys<2, SYS_EULER>::prim_deriv(U, u, v, ir, V, g.gm1, pdV[0], pdV[1], pdV[2]);
+      Phys<2, SYS_EULER>::prim_deriv(U, u, v, ir, Wd, g.gm1, pdW[0], pdW[1], pdW[2]);
+    }
     // nodal values per direction (normal frame)
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
@@ -281,14 +287,19 @@ __device__ __forceinline__ void cell_body(const Grid& g, const double* __restric
           swap_frame<NC>(Dn);
           swap_frame<NC>(On);
         }
-        const double un = d == 0 ? u : v, vt = d == 0 ? v : u;
+        const double un = d == 0 ? u : v;
         F[0] = Un[1];
         F[1] = fma(Un[1], un, pr);
         if (DIM == 2) F[2] = Un[2] * un;
         F[NC - 1] = (Un[NC - 1] + pr) * un;
         if (DIM == 2) {
-          Phys<2, SYS_EULER>::jvp_prim(Un, un, vt, pr, ir, Dn, Hn, g.gm1);
-          Phys<2, SYS_EULER>::jvp_prim(Un, un, vt, pr, ir, On, Mx, g.gm1);
+          // own-direction field (V in x, W in y) and the other one, each with its normal-velocity
+          // derivative (u' in x, v' in y)
+          const double* po = d == 0 ? pdV : pdW;
+          const double* pt = d == 0 ? pdW : pdV;
+          const double hp = U[NC - 1] + pr;
+          Phys<2, SYS_EULER>::jvp_apply(Un, Dn, un, po[d], po[2], hp, Hn);
+          Phys<2, SYS_EULER>::jvp_apply(Un, On, un, pt[d], pt[2], hp, Mx);
         } else {
           Phys<1, SYS_EULER>::jvp_prim(Un, un, pr, ir, Dn, Hn, g.gm1);
         }
@@ -484,10 +495,8 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
   // Lax-Friedrichs fluxes at the interpolated states (Eq. flux-LF)
   const double a_adv = dir == 0 ? g.ax : g.ay;
   double FUm[NC], FUp[NC], HDm[NC], HDp[NC];
-  Phys<DIM, SYS>::flux(Um, FUm, a_adv, g.gm1);
-  Phys<DIM, SYS>::flux(Up, FUp, a_adv, g.gm1);
-  Phys<DIM, SYS>::jvp(Um, Dm, HDm, a_adv, g.gm1);
-  Phys<DIM, SYS>::jvp(Up, Dp, HDp, a_adv, g.gm1);
+  Phys<DIM, SYS>::flux_jvp(Um, Dm, FUm, HDm, a_adv, g.gm1);
+  Phys<DIM, SYS>::flux_jvp(Up, Dp, FUp, HDp, a_adv, g.gm1);
   const double* nod = w.NOD + (long long)dir * NG * NC * plane;
   double* out = dir == 0 ? w.FX : w.FY;
   const long long oplane = dir == 0 ? (long long)g.ny * (g.nx + 1) : (long long)(g.ny + 1) * g.nx;

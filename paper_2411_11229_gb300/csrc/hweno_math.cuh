@@ -241,6 +241,10 @@ struct Phys<DIM, SYS_ADV> {
   static constexpr int NC = 1;
   __device__ static void flux(const double* U, double* F, double a, double) { F[0] = a * U[0]; }
   __device__ static void jvp(const double*, const double* D, double* out, double a, double) { out[0] = a * D[0]; }
+  __device__ static void flux_jvp(const double* U, const double* D, double* F, double* out, double a, double gm1) {
+    flux(U, F, a, gm1);
+    jvp(U, D, out, a, gm1);
+  }
 };
 
 template <int DIM>
@@ -248,6 +252,10 @@ struct Phys<DIM, SYS_BURGERS> {
   static constexpr int NC = 1;
   __device__ static void flux(const double* U, double* F, double, double) { F[0] = 0.5 * (U[0] * U[0]); }
   __device__ static void jvp(const double* U, const double* D, double* out, double, double) { out[0] = U[0] * D[0]; }
+  __device__ static void flux_jvp(const double* U, const double* D, double* F, double* out, double a, double gm1) {
+    flux(U, F, a, gm1);
+    jvp(U, D, out, a, gm1);
+  }
 };
 
 // 1D Euler, U = (rho, m, E), p = (gamma-1)(E - m u / 2)
@@ -275,6 +283,16 @@ struct Phys<1, SYS_EULER> {
     const double ir = rcp(U[0]);
     const double u = U[1] * ir;
     const double p = gm1 * fma(-0.5 * U[1], u, U[2]);
+    jvp_prim(U, u, p, ir, D, out, gm1);
+  }
+  // f(U) and A(U) D with one reciprocal and one pressure
+  __device__ static void flux_jvp(const double* U, const double* D, double* F, double* out, double, double gm1) {
+    const double ir = rcp(U[0]);
+    const double u = U[1] * ir;
+    const double p = gm1 * fma(-0.5 * U[1], u, U[2]);
+    F[0] = U[1];
+    F[1] = fma(U[1], u, p);
+    F[2] = (U[2] + p) * u;
     jvp_prim(U, u, p, ir, D, out, gm1);
   }
 };
@@ -308,6 +326,36 @@ struct Phys<2, SYS_EULER> {
     const double ir = rcp(U[0]);
     const double u = U[1] * ir, v = U[2] * ir;
     const double p = gm1 * fma(-0.5, fma(U[1], u, U[2] * v), U[3]);
+    jvp_prim(U, u, v, p, ir, D, out, gm1);
+  }
+  // The derivatives of the primitives along D (original frame): u' = (m' - u rho')/rho,
+  // v' = (n' - v rho')/rho, p' = (gamma-1)(E' - (m' u + m u' + n' v + n v')/2).  They do not depend
+  // on the direction, so a cell computes them once per derivative field for both Jacobians.
+  __device__ static void prim_deriv(const double* U, double u, double v, double ir, const double* D, double gm1,
+                                    double& du, double& dv, double& dp) {
+    du = fma(-u, D[0], D[1]) * ir;
+    dv = fma(-v, D[0], D[2]) * ir;
+    const double dk = fma(D[1], u, fma(U[1], du, fma(D[2], v, U[2] * dv)));
+    dp = gm1 * fma(-0.5, dk, D[3]);
+  }
+  // A(U) D in the normal frame from the primitive derivatives: Un, Dn normal-frame vectors, un
+  // the normal velocity, dun its derivative, hp = E + p
+  __device__ static void jvp_apply(const double* Un, const double* Dn, double un, double dun, double dp, double hp,
+                                   double* out) {
+    out[0] = Dn[1];
+    out[1] = fma(Dn[1], un, fma(Un[1], dun, dp));
+    out[2] = fma(Dn[2], un, Un[2] * dun);
+    out[3] = fma(Dn[3] + dp, un, hp * dun);
+  }
+  // f(U) and A(U) D with one reciprocal and one pressure
+  __device__ static void flux_jvp(const double* U, const double* D, double* F, double* out, double, double gm1) {
+    const double ir = rcp(U[0]);
+    const double u = U[1] * ir, v = U[2] * ir;
+    const double p = gm1 * fma(-0.5, fma(U[1], u, U[2] * v), U[3]);
+    F[0] = U[1];
+    F[1] = fma(U[1], u, p);
+    F[2] = U[2] * u;
+    F[3] = (U[3] + p) * u;
     jvp_prim(U, u, v, p, ir, D, out, gm1);
   }
 };
