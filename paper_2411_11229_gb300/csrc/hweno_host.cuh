@@ -180,6 +180,22 @@ inline Grid grid_of(const hweno_ctx* h) {
     g.egih[d] = hw::DCoef::eg / hs[d];
     g.hih[d] = 0.5 / hs[d];
     g.c2h[d] = hw::DCoef2::ch * hs[d];
+    // unscaled-derivative constants (see hw::Grid)
+    g.uA[d] = -0.1875 * hs[d];
+    g.uB[d] = (67.0 / 520.0) * hs[d];
+    g.uh[d] = hs[d];
+    g.uhh[d] = 0.5 * hs[d];
+    g.udm[d][0] = dm[0];
+    g.udm[d][1] = dm[1];
+    g.udm[d][2] = dm[2] * hs[d];
+    g.udm[d][3] = dm[3] * hs[d];
+    g.udp[d][0] = dp[0];
+    g.udp[d][1] = dp[1];
+    g.udp[d][2] = dp[2] * hs[d];
+    g.udp[d][3] = dp[3] * hs[d];
+    g.uvd[d][0] = 1.3125 / hs[d];
+    g.uvd[d][1] = 0.1875 / hs[d];
+    g.ucsv[d] = g.csv * hs[d];
     g.e2fih[d] = hw::DCoef2::ef / hs[d];
     g.e2gih[d] = hw::DCoef2::eg / hs[d];
   }

@@ -40,8 +40,8 @@ struct Work {
   double* scal;               // [0] dt of the current step, [1] t, [2] t_end, [3] steps taken
   unsigned int* status;       // bit 0: non-physical state met
   long long astride;          // distance between slots (2 for a single grid)
-  // R2 only: face states of every cell, normal frame, derivatives scaled by h:
-  // FS [DIM][4][NC][plane] = (u^- and h v^- at the right face, u^+ and h v^+ at the left face);
+  // R2 only: face states of every cell, normal frame:
+  // FS [DIM][4][NC][plane] = (u^- and v^- at the right face, u^+ and v^+ at the left face);
   // GFS [DIM][2 ends][2][NC][gstride] = the low ghost's right-face and the high ghost's
   // left-face states of every line.
   double* FS;
@@ -96,28 +96,22 @@ __device__ __forceinline__ void block_max2(double a, double b, unsigned long lon
 template <int NC, int SYS>
 __device__ __forceinline__ void modified_derivative(const double (&U3)[3][NC], const double (&D3)[3][NC],
                                                     const Eig<NC>& e, int dir, const Grid& g, double* out) {
-  const double h = g.h[dir], ih = g.ih[dir];
+  const double ih = g.ih[dir];
   double W[3][NC], Zm[NC], Zp[NC];
-  double hDm[NC], hDp[NC];
-#pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    hDm[k] = h * D3[0][k];
-    hDp[k] = h * D3[2][k];
-  }
   if (SYS == SYS_EULER) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) e.project(U3[q], W[q]);
-    e.project(hDm, Zm);
-    e.project(hDp, Zp);
+    e.project(D3[0], Zm);
+    e.project(D3[2], Zp);
   } else {
 #pragma unroll
     for (int q = 0; q < 3; ++q) W[q][0] = U3[q][0];
-    Zm[0] = hDm[0];
-    Zp[0] = hDp[0];
+    Zm[0] = D3[0][0];
+    Zp[0] = D3[2][0];
   }
   double ht[NC];
 #pragma unroll
-  for (int s = 0; s < NC; ++s) ht[s] = cell_field(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], g) * ih;
+  for (int s = 0; s < NC; ++s) ht[s] = cell_field_u(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], g, dir) * ih;
   if (SYS == SYS_EULER) {
     e.back(ht, out);
   } else {
@@ -168,33 +162,28 @@ __device__ __forceinline__ void load_stencil3(const Grid& g, const double* __res
 }
 
 // R2: the modified derivative and the face states of one cell in one direction from its own
-// stencil in its own characteristic fields (normal frame; derivatives out scaled by h, v~ not).
+// stencil in its own characteristic fields (normal frame, derivatives unscaled).
 template <int NC, int SYS>
 __device__ __forceinline__ void r2_cell(const double (&U3)[3][NC], const double (&D3)[3][NC], const Eig<NC>& e,
                                         int dir, const Grid& g, double* md, double (&fs)[4][NC]) {
-  const double h = g.h[dir], ih = g.ih[dir];
+  const double ih = g.ih[dir];
   const bool vw = (g.flags & FLAG_V_WEIGHTED) != 0;
-  double W[3][NC], Zm[NC], Zp[NC], hDm[NC], hDp[NC];
-#pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    hDm[k] = h * D3[0][k];
-    hDp[k] = h * D3[2][k];
-  }
+  double W[3][NC], Zm[NC], Zp[NC];
   if (SYS == SYS_EULER) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) e.project(U3[q], W[q]);
-    e.project(hDm, Zm);
-    e.project(hDp, Zp);
+    e.project(D3[0], Zm);
+    e.project(D3[2], Zp);
   } else {
 #pragma unroll
     for (int q = 0; q < 3; ++q) W[q][0] = U3[q][0];
-    Zm[0] = hDm[0];
-    Zp[0] = hDp[0];
+    Zm[0] = D3[0][0];
+    Zp[0] = D3[2][0];
   }
   double cm[NC], chm[NC], cp[NC], chp[NC], ht[NC];
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
-    cell_faces_field(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], g, vw, cm[s], chm[s], cp[s], chp[s], ht[s]);
+    cell_faces_field(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], g, dir, vw, cm[s], chm[s], cp[s], chp[s], ht[s]);
     ht[s] *= ih;
   }
   if (SYS == SYS_EULER) {
@@ -382,7 +371,6 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
     pc[q] = dir == 0 ? (long long)line * g.nx + a : (long long)a * g.nx + line;
   }
   const int fown = dir == 0 ? 1 : 2, foth = dir == 0 ? 2 : 1;
-  const double h = g.h[dir];
   double Um[NC], Up[NC], Dm[NC], Dp[NC];
   if (VAR == 2) {
     // R2: the face states were formed per cell (the low and high ghosts by k_r2_ghost)
@@ -404,7 +392,7 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
         Uq[q][k] = S[k * plane + pc[q]];
-        Zq[q][k] = h * S[(fown * NC + k) * plane + pc[q]];
+        Zq[q][k] = S[(fown * NC + k) * plane + pc[q]];
       }
       if (SYS == SYS_EULER && dir == 1) {
         swap_frame<NC>(Uq[q]);
@@ -471,9 +459,9 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
     double cm[NC], chm[NC], cp[NC], chp[NC];
 #pragma unroll
     for (int s = 0; s < NC; ++s)
-      face_field(Wq[0][s], Wq[1][s], Wq[2][s], Wq[3][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, cm[s], chm[s],
-                 cp[s], chp[s], vw);
-    // back to conserved variables; the derivatives stay scaled by h
+      face_field_u(Wq[0][s], Wq[1][s], Wq[2][s], Wq[3][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, dir, cm[s],
+                   chm[s], cp[s], chp[s], vw);
+    // back to conserved variables
     if (SYS == SYS_EULER) {
       e.back(cm, Um);
       e.back(cp, Up);
@@ -534,8 +522,7 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
       Dh = fma(g.efih[dir], f0 - f3, fma(g.egih[dir], f2 - f1, DCoef::eh * (ha + hb)));
     }
     fh[k] = fma(0.5, fma(-alpha, Up[k] - Um[k], FUm[k] + FUp[k]), Df);
-    // Dm, Dp and the Jacobian products carry the factor h: 1/(2h) restores both
-    hh[k] = fma(g.hih[dir], fma(-alpha, Dp[k] - Dm[k], HDm[k] + HDp[k]), Dh);
+    hh[k] = fma(0.5, fma(-alpha, Dp[k] - Dm[k], HDm[k] + HDp[k]), Dh);
     if (DIM == 2) {
       double o0 = neg_if(nod[(2 * NC + k) * plane + pc[0]], s0);
       double o1 = neg_if(nod[(2 * NC + k) * plane + pc[1]], s1);

@@ -50,6 +50,13 @@ struct Grid {
   //           right face and, mirrored, on (d_{i-1,i}, d_{i,i+1}, ...) at the left face;
   double dm[4], dp[4];
   double cdu, csv, Gd;
+  // The same arithmetic with the derivatives entering unscaled (v, not h v), per direction: the h
+  // of every derivative term folded into its coefficient.  uA, uB: the derivative coefficients of
+  // the smoothness indicator's first two linear forms; uh = h, uhh = h/2 for the other two;
+  // udm, udp: dm, dp with their derivative coefficients times h; uvd = (21/16, 3/16)/h: the cell
+  // differences in the derivative at the face; ucsv = csv h.
+  double uA[2], uB[2], uh[2], uhh[2];
+  double udm[2][4], udp[2][4], uvd[2][2], ucsv[2];
   double h[2], ih[2], chh[2], efih[2], egih[2], hih[2];
   // Extended scheme (read only by the kernels instantiated with VAR != 0):
   //   side: boundary type of x-low, x-high, y-low, y-high; grav: g of Eq. (euler2d-s);
@@ -97,6 +104,22 @@ __device__ __forceinline__ double beta0(double dm, double dp, double hvm, double
   du_out = du;
   sv_out = sv;
   return fma((1421461.0 / 2275.0 / 16.0) * D, D, fma((781.0 / 20.0 / 16.0) * C, C, fma((13.0 / 3.0) * B, B, A * A)));
+}
+
+// beta0 with unscaled derivatives vm = v_{i-1}, vp = v_{i+1} along direction dir (the h of the
+// derivative terms in the grid constants; D/2 replaces D with the factor 4 moved into its weight).
+// Returns beta0, du = dm + dp and the unscaled derivative sum sv = vm + vp.
+__device__ __forceinline__ double beta0_u(double dm, double dp, double vm, double vp, const Grid& g, int dir,
+                                          double& du_out, double& sv_out) {
+  const double du = dm + dp, d2 = dp - dm;
+  const double sv = vm + vp, dv = vm - vp;
+  const double A = fma(g.uA[dir], sv, 0.6875 * du);
+  const double B = fma(g.uB[dir], dv, (197.0 / 260.0) * d2);
+  const double C = fma(g.uh[dir], sv, -du);
+  const double Dh = fma(g.uhh[dir], dv, d2);
+  du_out = du;
+  sv_out = sv;
+  return fma((1421461.0 / 2275.0 / 4.0) * Dh, Dh, fma((781.0 / 20.0 / 16.0) * C, C, fma((13.0 / 3.0) * B, B, A * A)));
 }
 
 // Nonlinear weights of Eq. (nonlinear) up to a common factor: with e_l = beta_l + eps,
@@ -162,34 +185,81 @@ __device__ __forceinline__ void face_field(double w0, double w1, double w2, doub
   }
 }
 
+// face_field with unscaled derivatives (y = v, not h v) along direction dir; v^- and v^+ come out
+// unscaled.  The forward kernels use this form; the scaled one above serves the adjoint.
+__device__ __forceinline__ void face_field_u(double w0, double w1, double w2, double w3, double y0, double y1,
+                                             double y2, double y3, const Grid& g, int dir, double& um,
+                                             double& vm, double& up, double& vp, bool vw = false) {
+  const double d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2;
+  const double b01 = d01 * d01, b12 = d12 * d12, b23 = d23 * d23;
+  const double e01 = b01 + g.eps, e12 = b12 + g.eps, e23 = b23 + g.eps;
+  const double* cm = g.udm[dir];
+  const double* cp = g.udp[dir];
+  const double k21 = g.uvd[dir][0], k3 = g.uvd[dir][1];
+  double du, sv;
+  {
+    const double b0 = beta0_u(d01, d12, y0, y2, g, dir, du, sv);
+    const Wts wt = weights(b0, b01, b12, e01, e12, g.eps);
+    const double r = fma(cm[0], d01, fma(cm[1], d12, fma(cm[2], y0, cm[3] * y2)));
+    const double sl = fma(wt.W1, d01, wt.W2 * d12);
+    const double den = fma(g.G, wt.W0, wt.W1 + wt.W2);
+    const double rden = rcp(den);
+    um = fma(fma(wt.W0, r, 0.5 * sl), rden, w1);
+    vm = fma(k21, d12, fma(-k3, d01, fma(0.0625, y0, -0.1875 * y2)));
+    if (vw) {
+      const double ih = g.ih[dir];
+      vm = fma(wt.W0, fma(vm, g.ig1, -du * ih), sl * ih) * rden;
+    }
+  }
+  {
+    const double b0 = beta0_u(d12, d23, y1, y3, g, dir, du, sv);
+    const Wts wt = weights(b0, b12, b23, e12, e23, g.eps);
+    const double r = fma(cp[0], d12, fma(cp[1], d23, fma(cp[2], y1, cp[3] * y3)));
+    const double sl = fma(wt.W1, d12, wt.W2 * d23);
+    const double den = fma(g.G, wt.W0, wt.W1 + wt.W2);
+    const double rden = rcp(den);
+    up = fma(fma(wt.W0, r, -0.5 * sl), rden, w2);
+    vp = fma(k21, d12, fma(-k3, d23, fma(-0.1875, y1, 0.0625 * y3)));
+    if (vw) {
+      const double ih = g.ih[dir];
+      vp = fma(wt.W0, fma(vp, g.ig1, -du * ih), sl * ih) * rden;
+    }
+  }
+}
+
 // R2 variant: one characteristic field of cell i from its own stencil w0..w2 = u_{i-1..i+1},
 // y0, y2 = h v_{i-1}, h v_{i+1}: u^- and h v^- at x_{i+1/2}, u^+ and h v^+ at x_{i-1/2} (the
 // mirror image) and h v~_i.  The three share beta, tau and the unnormalised weights; u^+/- share
 // one reciprocal (gamma1 = gamma2 makes the mirrored weights the same numbers).
 __device__ __forceinline__ void cell_faces_field(double w0, double w1, double w2, double y0, double y2, const Grid& g,
-                                                 bool vw, double& um, double& hvm, double& up, double& hvp,
+                                                 int dir, bool vw, double& um, double& vm, double& up, double& vp,
                                                  double& hvt) {
+  // unscaled derivatives in (y0, y2) and out (vm, vp); hvt = h v~ as before
   const double d01 = w1 - w0, d12 = w2 - w1;
   const double b1 = d01 * d01, b2 = d12 * d12;
   double du, sv;
-  const double b0 = beta0(d01, d12, y0, y2, du, sv);
+  const double b0 = beta0_u(d01, d12, y0, y2, g, dir, du, sv);
   const Wts wt = weights(b0, b1, b2, b1 + g.eps, b2 + g.eps, g.eps);
   const double rden = rcp(fma(g.G, wt.W0, wt.W1 + wt.W2));
   // centre value plus differences (see face_field): the candidates at x_{i+1/2} differ from u_i by
   // (d01, d12)/2, those at x_{i-1/2} by (-d01, -d12)/2, so both faces share W1 d01 + W2 d12
-  const double rm = fma(g.dm[0], d01, fma(g.dm[1], d12, fma(g.dm[2], y0, g.dm[3] * y2)));
-  const double rp = fma(g.dp[0], d01, fma(g.dp[1], d12, fma(g.dp[2], y0, g.dp[3] * y2)));
+  const double* cm = g.udm[dir];
+  const double* cp = g.udp[dir];
+  const double rm = fma(cm[0], d01, fma(cm[1], d12, fma(cm[2], y0, cm[3] * y2)));
+  const double rp = fma(cp[0], d01, fma(cp[1], d12, fma(cp[2], y0, cp[3] * y2)));
   const double sl = fma(wt.W1, d01, wt.W2 * d12);
   const double hs = 0.5 * sl;
   um = fma(fma(wt.W0, rm, hs), rden, w1);
   up = fma(fma(wt.W0, rp, -hs), rden, w1);
-  hvm = fma(1.3125, d12, fma(-0.1875, d01, fma(0.0625, y0, -0.1875 * y2)));
-  hvp = fma(1.3125, d01, fma(-0.1875, d12, fma(-0.1875, y0, 0.0625 * y2)));
+  const double k21 = g.uvd[dir][0], k3 = g.uvd[dir][1];
+  vm = fma(k21, d12, fma(-k3, d01, fma(0.0625, y0, -0.1875 * y2)));
+  vp = fma(k21, d01, fma(-k3, d12, fma(-0.1875, y0, 0.0625 * y2)));
   if (vw) {
-    hvm = fma(wt.W0, fma(hvm, g.ig1, -du), sl) * rden;
-    hvp = fma(wt.W0, fma(hvp, g.ig1, -du), sl) * rden;
+    const double ih = g.ih[dir], ds = du * ih, ss = sl * ih;
+    vm = fma(wt.W0, fma(vm, g.ig1, -ds), ss) * rden;
+    vp = fma(wt.W0, fma(vp, g.ig1, -ds), ss) * rden;
   }
-  const double t = fma(g.cdu, du, -g.csv * sv);
+  const double t = fma(g.cdu, du, -g.ucsv[dir] * sv);
   hvt = fma(wt.W0, t, sl) * rcp(fma(g.Gd, wt.W0, wt.W1 + wt.W2));
 }
 
@@ -203,6 +273,21 @@ __device__ __forceinline__ double cell_field(double w0, double w1, double w2, do
   const Wts wt = weights(b0, b1, b2, b1 + g.eps, b2 + g.eps, g.eps);
   // (h p0'(x_i) - d1 (h p1' + h p2')) / d1 = cdu du - csv sv;  h p1' = d01, h p2' = d12
   const double t = fma(g.cdu, du, -g.csv * sv);
+  const double num = fma(wt.W0, t, fma(wt.W1, d01, wt.W2 * d12));
+  const double den = fma(g.Gd, wt.W0, wt.W1 + wt.W2);
+  return num * rcp(den);
+}
+
+// cell_field with unscaled derivatives y0 = v_{i-1}, y2 = v_{i+1} along direction dir; returns
+// h v~_i as cell_field does.
+__device__ __forceinline__ double cell_field_u(double w0, double w1, double w2, double y0, double y2, const Grid& g,
+                                               int dir) {
+  const double d01 = w1 - w0, d12 = w2 - w1;
+  const double b1 = d01 * d01, b2 = d12 * d12;
+  double du, sv;
+  const double b0 = beta0_u(d01, d12, y0, y2, g, dir, du, sv);
+  const Wts wt = weights(b0, b1, b2, b1 + g.eps, b2 + g.eps, g.eps);
+  const double t = fma(g.cdu, du, -g.ucsv[dir] * sv);
   const double num = fma(wt.W0, t, fma(wt.W1, d01, wt.W2 * d12));
   const double den = fma(g.Gd, wt.W0, wt.W1 + wt.W2);
   return num * rcp(den);
