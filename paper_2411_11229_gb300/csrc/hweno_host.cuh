@@ -182,7 +182,7 @@ inline Grid grid_of(const hweno_ctx* h) {
     g.c2h[d] = hw::DCoef2::ch * hs[d];
     // unscaled-derivative constants (see hw::Grid)
     g.uA[d] = -0.1875 * hs[d];
-    g.uB[d] = (67.0 / 520.0) * hs[d];
+    g.uB[d] = std::sqrt(13.0 / 3.0) * (67.0 / 520.0) * hs[d];
     g.uh[d] = hs[d];
     g.uhh[d] = 0.5 * hs[d];
     g.udm[d][0] = dm[0];
@@ -200,6 +200,7 @@ inline Grid grid_of(const hweno_ctx* h) {
     g.e2gih[d] = hw::DCoef2::eg / hs[d];
   }
   g.ig1 = 1.0 / g1;
+  g.kB = std::sqrt(13.0 / 3.0) * (197.0 / 260.0);
   g.grav = h->grav;
   for (int sd = 0; sd < 4; ++sd) {
     g.side[sd] = h->side[sd];

@@ -56,6 +56,7 @@ struct Grid {
   // udm, udp: dm, dp with their derivative coefficients times h; uvd = (21/16, 3/16)/h: the cell
   // differences in the derivative at the face; ucsv = csv h.
   double uA[2], uB[2], uh[2], uhh[2];
+  double kB;  // sqrt(13/3) 197/260: the second linear form carries the square root of its weight
   double udm[2][4], udp[2][4], uvd[2][2], ucsv[2];
   double h[2], ih[2], chh[2], efih[2], egih[2], hih[2];
   // Extended scheme (read only by the kernels instantiated with VAR != 0):
@@ -107,19 +108,20 @@ __device__ __forceinline__ double beta0(double dm, double dp, double hvm, double
 }
 
 // beta0 with unscaled derivatives vm = v_{i-1}, vp = v_{i+1} along direction dir (the h of the
-// derivative terms in the grid constants; D/2 replaces D with the factor 4 moved into its weight).
+// derivative terms in the grid constants; D/2 replaces D with the factor 4 moved into its weight;
+// the second form carries the square root of its weight 13/3, so its square needs no product).
 // Returns beta0, du = dm + dp and the unscaled derivative sum sv = vm + vp.
 __device__ __forceinline__ double beta0_u(double dm, double dp, double vm, double vp, const Grid& g, int dir,
                                           double& du_out, double& sv_out) {
   const double du = dm + dp, d2 = dp - dm;
   const double sv = vm + vp, dv = vm - vp;
   const double A = fma(g.uA[dir], sv, 0.6875 * du);
-  const double B = fma(g.uB[dir], dv, (197.0 / 260.0) * d2);
+  const double B = fma(g.uB[dir], dv, g.kB * d2);  // sqrt(13/3) times the second form
   const double C = fma(g.uh[dir], sv, -du);
   const double Dh = fma(g.uhh[dir], dv, d2);
   du_out = du;
   sv_out = sv;
-  return fma((1421461.0 / 2275.0 / 4.0) * Dh, Dh, fma((781.0 / 20.0 / 16.0) * C, C, fma((13.0 / 3.0) * B, B, A * A)));
+  return fma((1421461.0 / 2275.0 / 4.0) * Dh, Dh, fma((781.0 / 20.0 / 16.0) * C, C, fma(B, B, A * A)));
 }
 
 // Nonlinear weights of Eq. (nonlinear) up to a common factor: with e_l = beta_l + eps,
