@@ -79,8 +79,12 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
   for (int q = 0; q < 3; ++q) e.project(U3[q], W[q]);
   e.project(hD3[0], Zm);
   e.project(hD3[2], Zp);
+  // forward intermediates of the limiter, per field, kept in this thread's shared-memory slots
+  extern __shared__ double adj_cell_sm[];
+  double* const svb = adj_cell_sm + threadIdx.x;
 #pragma unroll
-  for (int s = 0; s < NC; ++s) ht[s] = cell_field(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], g) * ih;
+  for (int s = 0; s < NC; ++s)
+    ht[s] = cell_field_save(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], g, svb + s * kCellSaved * kThreads, kThreads) * ih;
   // backward from the adjoint of the modified derivative of this cell
   double ob[NC];
 #pragma unroll
@@ -101,7 +105,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
     double wb[3] = {0.0, 0.0, 0.0};
-    cell_field_bwd(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], g, htb[s] * ih, wb, Zmb[s], Zpb[s]);
+    cell_field_bwd_saved(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], g, htb[s] * ih, svb + s * kCellSaved * kThreads,
+                         kThreads, wb, Zmb[s], Zpb[s]);
     Wb[0][s] = wb[0];
     Wb[1][s] = wb[1];
     Wb[2][s] = wb[2];
@@ -230,10 +235,13 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
     e.project(Zq[q], Yq[q]);
   }
   double cm[NC], chm[NC], cp[NC], chp[NC];
+  // forward intermediates of the interpolation, per field, kept in this thread's shared-memory slots
+  extern __shared__ double adj_face_sm[];
+  double* const svb = adj_face_sm + threadIdx.x;
 #pragma unroll
   for (int s = 0; s < NC; ++s)
-    face_field(Wq[0][s], Wq[1][s], Wq[2][s], Wq[3][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, cm[s], chm[s],
-               cp[s], chp[s]);
+    face_field_save(Wq[0][s], Wq[1][s], Wq[2][s], Wq[3][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, cm[s],
+                    chm[s], cp[s], chp[s], svb + s * kFaceSaved * kThreads, kThreads);
   double Um[NC], Up[NC], Dm[NC], Dp[NC];
   e.back(cm, Um);
   e.back(cp, Up);
@@ -267,8 +275,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
     double wb[4] = {0.0, 0.0, 0.0, 0.0}, yb[4] = {0.0, 0.0, 0.0, 0.0};
-    face_field_bwd(Wq[0][s], Wq[1][s], Wq[2][s], Wq[3][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, cmb[s],
-                   chmb[s], cpb[s], chpb[s], wb, yb);
+    face_field_bwd_saved(Wq[0][s], Wq[1][s], Wq[2][s], Wq[3][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g,
+                         cmb[s], chmb[s], cpb[s], chpb[s], svb + s * kFaceSaved * kThreads, kThreads, wb, yb);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       Wb[q][s] = wb[q];
@@ -542,10 +550,18 @@ int stage_vjp(const hweno_ctx* h, const Grid& g, const double* S, const double* 
               const double* muL, const hw::AdjWork& aw, double* lam) {
   const cudaStream_t st = h->stream;
   const unsigned bc = blocks_for(g.plane);
-  hw::k_adj_cell<DIM><<<dim3(bc, DIM), hw::kThreads, 0, st>>>(g, S, muM, aw);
+  // shared memory for the saved forward intermediates: one slot per thread and value
+  constexpr int NC = DIM == 1 ? 3 : 4;
+  constexpr size_t cell_sm = (size_t)hw::kCellSaved * NC * hw::kThreads * sizeof(double);
+  constexpr size_t face_sm = (size_t)hw::kFaceSaved * NC * hw::kThreads * sizeof(double);
+  if (cudaFuncSetAttribute(hw::k_adj_face<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_sm) !=
+      cudaSuccess)
+    return HWENO_ECUDA;
+  hw::k_adj_cell<DIM><<<dim3(bc, DIM), hw::kThreads, cell_sm, st>>>(g, S, muM, aw);
   const long long nfx = (long long)(g.nx + 1) * g.ny;
   const long long nfy = DIM == 2 ? (long long)(g.ny + 1) * g.nx : 0;
-  hw::k_adj_face<DIM><<<dim3(blocks_for(nfx > nfy ? nfx : nfy), DIM), hw::kThreads, 0, st>>>(g, S, muL, aw, alpha2);
+  hw::k_adj_face<DIM><<<dim3(blocks_for(nfx > nfy ? nfx : nfy), DIM), hw::kThreads, face_sm, st>>>(g, S, muL, aw,
+                                                                                                  alpha2);
   hw::k_adj_gather<DIM><<<bc, hw::kThreads, 0, st>>>(g, S, muM, muL, aw, lam);
   return cudaGetLastError() == cudaSuccess ? HWENO_OK : HWENO_ECUDA;
 }

@@ -160,6 +160,170 @@ __device__ __forceinline__ void cell_field_bwd(double w0, double w1, double w2, 
 }
 
 // ---------------------------------------------------------------------------------------------
+// The same backward passes from saved forward values.  The adjoint kernels run the forward
+// interpolation once, keep each stencil's intermediates (beta0, the three weights, the candidate
+// combination, the weighted sum and 1/den) in shared memory, and the backward pass reads them
+// instead of recomputing them.  sv points at this thread's first slot; consecutive values are
+// `stride` doubles apart (one slot per thread of the block).
+constexpr int kFaceSaved = 14;  // per characteristic field of a face: 7 per stencil
+constexpr int kCellSaved = 7;   // per characteristic field of a cell
+
+// face_field (h-scaled derivatives, centre value plus weighted differences) saving its
+// intermediates: [b0, W0, W1, W2, r, X, 1/den] of the stencil of cell k, then of cell k+1
+__device__ __forceinline__ void face_field_save(double w0, double w1, double w2, double w3, double y0, double y1,
+                                                double y2, double y3, const Grid& g, double& um, double& hvm,
+                                                double& up, double& hvp, double* sv, int stride) {
+  const double d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2;
+  const double b01 = d01 * d01, b12 = d12 * d12, b23 = d23 * d23;
+  const double e01 = b01 + g.eps, e12 = b12 + g.eps, e23 = b23 + g.eps;
+  double du, svs;
+  {
+    const double b0 = beta0(d01, d12, y0, y2, du, svs);
+    const Wts wt = weights(b0, b01, b12, e01, e12, g.eps);
+    const double r = fma(g.dm[0], d01, fma(g.dm[1], d12, fma(g.dm[2], y0, g.dm[3] * y2)));
+    const double sl = fma(wt.W1, d01, wt.W2 * d12);
+    const double inv = rcp(fma(g.G, wt.W0, wt.W1 + wt.W2));
+    const double X = fma(wt.W0, r, 0.5 * sl);
+    um = fma(X, inv, w1);
+    hvm = fma(1.3125, d12, fma(-0.1875, d01, fma(0.0625, y0, -0.1875 * y2)));
+    sv[0] = b0;
+    sv[stride] = wt.W0;
+    sv[2 * stride] = wt.W1;
+    sv[3 * stride] = wt.W2;
+    sv[4 * stride] = r;
+    sv[5 * stride] = X;
+    sv[6 * stride] = inv;
+  }
+  {
+    const double b0 = beta0(d12, d23, y1, y3, du, svs);
+    const Wts wt = weights(b0, b12, b23, e12, e23, g.eps);
+    const double r = fma(g.dp[0], d12, fma(g.dp[1], d23, fma(g.dp[2], y1, g.dp[3] * y3)));
+    const double sl = fma(wt.W1, d12, wt.W2 * d23);
+    const double inv = rcp(fma(g.G, wt.W0, wt.W1 + wt.W2));
+    const double X = fma(wt.W0, r, -0.5 * sl);
+    up = fma(X, inv, w2);
+    hvp = fma(1.3125, d12, fma(-0.1875, d23, fma(-0.1875, y1, 0.0625 * y3)));
+    sv[7 * stride] = b0;
+    sv[8 * stride] = wt.W0;
+    sv[9 * stride] = wt.W1;
+    sv[10 * stride] = wt.W2;
+    sv[11 * stride] = r;
+    sv[12 * stride] = X;
+    sv[13 * stride] = inv;
+  }
+}
+
+// Backward of face_field_save: given the adjoints of um, hvm, up, hvp, adds those of w0..w3, y0..y3.
+// um = w1 + X / den with X = W0 r + (W1 d01 + W2 d12)/2, den = G W0 + W1 + W2 (up likewise with
+// w2, the differences d12, d23 and -1/2).
+__device__ __forceinline__ void face_field_bwd_saved(double w0, double w1, double w2, double w3, double y0,
+                                                     double y1, double y2, double y3, const Grid& g, double umb,
+                                                     double hvmb, double upb, double hvpb, const double* sv,
+                                                     int stride, double* wb, double* yb) {
+  const double d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2;
+  const double b01 = d01 * d01, b12 = d12 * d12, b23 = d23 * d23;
+  const double e01 = b01 + g.eps, e12 = b12 + g.eps, e23 = b23 + g.eps;
+  double d01b = 0.0, d12b = 0.0, d23b = 0.0, b01b = 0.0, b12b = 0.0, b23b = 0.0;
+  double e01b = 0.0, e12b = 0.0, e23b = 0.0;
+  {
+    const double b0 = sv[0], W0 = sv[stride], W1 = sv[2 * stride], W2 = sv[3 * stride];
+    const double r = sv[4 * stride], X = sv[5 * stride], inv = sv[6 * stride];
+    const double Xb = umb * inv;
+    const double denb = -Xb * X * inv;
+    const double hX = 0.5 * Xb;
+    const double W0b = fma(Xb, r, denb * g.G), W1b = fma(hX, d01, denb), W2b = fma(hX, d12, denb);
+    const double rb = Xb * W0;
+    d01b += fma(g.dm[0], rb, fma(hX, W1, -0.1875 * hvmb));
+    d12b += fma(g.dm[1], rb, fma(hX, W2, 1.3125 * hvmb));
+    yb[0] += fma(g.dm[2], rb, 0.0625 * hvmb);
+    yb[2] += fma(g.dm[3], rb, -0.1875 * hvmb);
+    wb[1] += umb;
+    double b0b = 0.0;
+    weights_bwd(b0, b01, b12, e01, e12, g.eps, W0b, W1b, W2b, b0b, b01b, b12b, e01b, e12b);
+    beta0_bwd(d01, d12, y0, y2, b0b, d01b, d12b, yb[0], yb[2]);
+  }
+  {
+    const double b0 = sv[7 * stride], W0 = sv[8 * stride], W1 = sv[9 * stride], W2 = sv[10 * stride];
+    const double r = sv[11 * stride], X = sv[12 * stride], inv = sv[13 * stride];
+    const double Xb = upb * inv;
+    const double denb = -Xb * X * inv;
+    const double hX = -0.5 * Xb;
+    const double W0b = fma(Xb, r, denb * g.G), W1b = fma(hX, d12, denb), W2b = fma(hX, d23, denb);
+    const double rb = Xb * W0;
+    d12b += fma(g.dp[0], rb, fma(hX, W1, 1.3125 * hvpb));
+    d23b += fma(g.dp[1], rb, fma(hX, W2, -0.1875 * hvpb));
+    yb[1] += fma(g.dp[2], rb, -0.1875 * hvpb);
+    yb[3] += fma(g.dp[3], rb, 0.0625 * hvpb);
+    wb[2] += upb;
+    double b0b = 0.0;
+    weights_bwd(b0, b12, b23, e12, e23, g.eps, W0b, W1b, W2b, b0b, b12b, b23b, e12b, e23b);
+    beta0_bwd(d12, d23, y1, y3, b0b, d12b, d23b, yb[1], yb[3]);
+  }
+  b01b += e01b;
+  b12b += e12b;
+  b23b += e23b;
+  d01b += 2.0 * d01 * b01b;
+  d12b += 2.0 * d12 * b12b;
+  d23b += 2.0 * d23 * b23b;
+  wb[0] -= d01b;
+  wb[1] += d01b - d12b;
+  wb[2] += d12b - d23b;
+  wb[3] += d23b;
+}
+
+// cell_field saving [b0, W0, W1, W2, t, num, 1/den]
+__device__ __forceinline__ double cell_field_save(double w0, double w1, double w2, double y0, double y2,
+                                                  const Grid& g, double* sv, int stride) {
+  const double d01 = w1 - w0, d12 = w2 - w1;
+  const double b1 = d01 * d01, b2 = d12 * d12;
+  double du, svs;
+  const double b0 = beta0(d01, d12, y0, y2, du, svs);
+  const Wts wt = weights(b0, b1, b2, b1 + g.eps, b2 + g.eps, g.eps);
+  const double t = fma(g.cdu, du, -g.csv * svs);
+  const double num = fma(wt.W0, t, fma(wt.W1, d01, wt.W2 * d12));
+  const double inv = rcp(fma(g.Gd, wt.W0, wt.W1 + wt.W2));
+  sv[0] = b0;
+  sv[stride] = wt.W0;
+  sv[2 * stride] = wt.W1;
+  sv[3 * stride] = wt.W2;
+  sv[4 * stride] = t;
+  sv[5 * stride] = num;
+  sv[6 * stride] = inv;
+  return num * inv;
+}
+
+// Backward of cell_field_save (the limiter) from its saved values.
+__device__ __forceinline__ void cell_field_bwd_saved(double w0, double w1, double w2, double y0, double y2,
+                                                     const Grid& g, double outb, const double* sv, int stride,
+                                                     double* wb, double& y0b, double& y2b) {
+  const double d01 = w1 - w0, d12 = w2 - w1;
+  const double b1 = d01 * d01, b2 = d12 * d12;
+  const double e1 = b1 + g.eps, e2 = b2 + g.eps;
+  const double b0 = sv[0], W0 = sv[stride], W1 = sv[2 * stride], W2 = sv[3 * stride];
+  const double t = sv[4 * stride], num = sv[5 * stride], inv = sv[6 * stride];
+  const double numb = outb * inv;
+  const double denb = -numb * num * inv;
+  const double W0b = fma(numb, t, denb * g.Gd), W1b = fma(numb, d01, denb), W2b = fma(numb, d12, denb);
+  const double tb = numb * W0;
+  double d01b = numb * W1, d12b = numb * W2;
+  // t = cdu (d01 + d12) - csv (y0 + y2)
+  d01b += g.cdu * tb;
+  d12b += g.cdu * tb;
+  y0b -= g.csv * tb;
+  y2b -= g.csv * tb;
+  double b0b = 0.0, b1b = 0.0, b2b = 0.0, e1b = 0.0, e2b = 0.0;
+  weights_bwd(b0, b1, b2, e1, e2, g.eps, W0b, W1b, W2b, b0b, b1b, b2b, e1b, e2b);
+  beta0_bwd(d01, d12, y0, y2, b0b, d01b, d12b, y0b, y2b);
+  b1b += e1b;
+  b2b += e2b;
+  d01b += 2.0 * d01 * b1b;
+  d12b += 2.0 * d12 * b2b;
+  wb[0] -= d01b;
+  wb[1] += d01b - d12b;
+  wb[2] += d12b;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Eigenvector products.  EigBar accumulates the adjoints of the eigen-state variables.
 struct EigBar {
   double u, v, H, c, ic;
