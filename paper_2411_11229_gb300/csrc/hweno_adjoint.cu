@@ -397,6 +397,9 @@ __global__ void __launch_bounds__(kThreads) k_adj_gather(Grid g, const double* _
     // the normal momentum (original frame) and the nodal sign tables of a mirrored alias: f and
     // the mixed value change sign except for the normal momentum, h only for it
     const int km = d == 0 ? 1 : 2;
+    const double cf_ih = DCoef::cf * ih, ef_ih = g.efih[d] * ih, eg_ih = g.egih[d] * ih;
+    const double ch_ih = g.chh[d] * ih, eh_ih = DCoef::eh * ih;
+    const double m7_ih = (7.0 / 12.0) * ih, m1_ih = (-1.0 / 12.0) * ih;
     for (int t = 0; t < nx_; ++t) {
       const int x = xs[t];
       const bool mir = g.bc == BC_REFLECTIVE && (x < 0 || x >= n);
@@ -417,23 +420,26 @@ __global__ void __launch_bounds__(kThreads) k_adj_gather(Grid g, const double* _
         const bool hasL = fa - 1 >= 0, hasR = fa <= n - 1;
         const long long cL = d == 0 ? (long long)line * g.nx + (fa - 1) : (long long)(fa - 1) * g.nx + line;
         const long long cR = d == 0 ? (long long)line * g.nx + fa : (long long)fa * g.nx + line;
-        const double s1 = (q == 0 || q == 3) ? DCoef::cf : -DCoef::cf;
-        const double sdh = q == 0 ? g.efih[d] : (q == 1 ? -g.egih[d] : (q == 2 ? g.egih[d] : -g.efih[d]));
-        const double th = q == 0 ? g.chh[d] : (q == 3 ? -g.chh[d] : 0.0);
-        const double th2 = (q == 0 || q == 3) ? DCoef::eh : 0.0;
-        const double mq = (q == 1 || q == 2) ? 7.0 / 12.0 : -1.0 / 12.0;
+        // the transposed D-term and mixed-flux coefficients of position q, with the 1/h of the flux
+        // adjoints folded in (only the outer positions carry h in Eq. Cd-1)
+        const double s1 = (q == 0 || q == 3) ? cf_ih : -cf_ih;
+        const double sdh = q == 0 ? ef_ih : (q == 1 ? -eg_ih : (q == 2 ? eg_ih : -ef_ih));
+        const double mq = (q == 1 || q == 2) ? m7_ih : m1_ih;
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
-          auto nu = [&](int fld) {
+          auto dmu = [&](int fld) {
             const double r = hasR ? muL[(fld * NC + k) * plane + cR] : 0.0;
             const double l = hasL ? muL[(fld * NC + k) * plane + cL] : 0.0;
-            return (r - l) * ih;
+            return r - l;
           };
-          const double nfh = nu(0), nhh = nu(fown);
+          // a mirrored alias takes the nodal sign tables: f and the mixed value flip except for the
+          // normal momentum, h only for it (sign flips in the integer pipe)
           const bool flip_f = mir && k != km, flip_h = mir && k == km;
-          nf[k] += neg_if(fma(s1, nfh, sdh * nhh), flip_f);
-          nh[k] += neg_if(fma(th, nfh, th2 * nhh), flip_h);
-          if (DIM == 2) no[k] += neg_if(mq * nu(foth), flip_f);
+          const double nfh = dmu(0), nhh = dmu(fown);
+          nf[k] = fma(s1, neg_if(nfh, flip_f), fma(sdh, neg_if(nhh, flip_f), nf[k]));
+          if (q == 0 || q == 3)
+            nh[k] = fma(q == 0 ? ch_ih : -ch_ih, neg_if(nfh, flip_h), fma(eh_ih, neg_if(nhh, flip_h), nh[k]));
+          if (DIM == 2) no[k] = fma(mq, neg_if(dmu(foth), flip_f), no[k]);
         }
       }
       // modified derivatives of cells c = x + 1 - q hold this cell at stencil position q
