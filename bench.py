@@ -42,6 +42,10 @@ HBM_PEAK_GBS_FALLBACK = 6800.0
 # DRAM bytes per face of the 2D Euler face kernel from an ncu capture at 2048^2 (profiles/); the
 # traffic grows in proportion to the faces, so a 4096^2 launch moves this times its faces.
 FACE_TRAFFIC_BYTES_PER_FACE = 285.1  # ncu dram bytes per face, 2048^2 capture of the current face kernel
+# from the same capture: FP64 pipe activity and FP64 instructions per face (the hardware's side of
+# the roofline fraction, which counts the scheme's operations as written)
+FACE_FP64_PIPE_ACTIVE = 0.874
+FACE_FP64_INSTR_PER_FACE = 706
 
 
 def _dist():
@@ -473,6 +477,11 @@ def run_ours(args, ws, rank, local):
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic,
                      "kernel": "k_face<2,EULER>", "flops_per_face": counts["face"],
+                     "fp64_pipe_active_ncu": None if traffic is None else FACE_FP64_PIPE_ACTIVE,
+                     "fp64_instructions_per_face_ncu": None if traffic is None else FACE_FP64_INSTR_PER_FACE,
+                     "frac_note": "algorithmic flops (every +, -, *, /, sqrt of the scheme as written) per second "
+                                  "over the FP64 peak; the kernel executes fewer FP64 instructions than that "
+                                  "count, so the fraction can exceed 1; the pipe activity is the hardware's figure",
                      "faces_per_launch": faces, "avg_launch_ms": face_avg_ms,
                      "peak_note": "FP64 derived: 152 SMs x 2070 MHz x 4 flop/clk",
                      "hbm_peak_gbs": hbm_peak},
