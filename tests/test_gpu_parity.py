@@ -232,14 +232,17 @@ def test_reciprocal_accuracy():
     assert ulps.max() <= 1.0, ulps.max()
 
 
-@pytest.mark.parametrize("ext", [False, True])
+@pytest.mark.parametrize("ext", [False, True, "r2"])
 def test_run_matches_stepping_and_stops_at_the_end(ext):
     """hweno_run (graph-replayed chunks of 16 CFL steps) against one hweno_step call per step:
     bit for bit, with max_steps honoured exactly; steps issued after the end time leave the state
-    unchanged.  ext: the Rayleigh-Taylor set-up of Example 4.11 through the extended kernels."""
+    unchanged.  ext: the Rayleigh-Taylor set-up of Example 4.11 through the extended kernels, also
+    with the per-cell characteristic decomposition (whose stages add the ghost-state launch)."""
     if ext:
         S, dx, dy, fixed = W.rayleigh_taylor(12, 48)
         kw = dict(gamma=5.0 / 3.0, grav=1.0, sides=("reflective", "reflective", "fixed", "fixed"), fixed=fixed)
+        if ext == "r2":
+            kw["flags"] = O.FLAG_R2
         nx, ny, t_end = 12, 48, 0.1
     else:
         S, dx, dy = W.euler2d_smooth(24, 20)
