@@ -181,26 +181,31 @@ def test_euler1d_riemann_2048_to_the_stop_time():
     fastest wave 80 % of the way to the boundary, from the exact Riemann solver) through hweno_run:
     the step count and the final time match the oracle's.  Over about a thousand steps through
     shocks, rounding differences move a shock by a fraction of a cell, which the max-norm reports
-    as one cell's jump; the state is therefore compared in the relative L1 norm per plane, within
-    1e-10 or ten times the oracle's own drift under one-ulp input perturbations (two seeds)."""
+    as one cell's jump; the state is therefore compared in the relative L1 norm of each plane,
+    within 1e-10 or ten times the largest drift of that plane among four oracle runs from inputs
+    moved by one ulp.  Where a shock crosses cells the drift is large and varies from run to run by
+    an order of magnitude, most of all in the derivative planes: in a shock cell the modified
+    derivative of Eq. (limiter) is of the size of the jump over h and depends on where the shock
+    sits inside the cell.  On the seeds whose waves stay smooth the same bar is near 1e-11."""
     import multiprocessing as mp
     from concurrent.futures import ProcessPoolExecutor
 
     import oracle_jobs
 
     seeds = list(range(1000, 1008))
-    jobs = [(2048, s, None) for s in seeds] + [(2048, s, p) for p in (7, 8) for s in seeds]
+    perturbations = (7, 8, 9, 10)
+    jobs = [(2048, s, None) for s in seeds] + [(2048, s, p) for p in perturbations for s in seeds]
     with ProcessPoolExecutor(max_workers=min(16, len(jobs)), mp_context=mp.get_context("spawn")) as ex:
         res = list(ex.map(oracle_jobs.riemann_run, jobs))
 
     def rel1(x, y):
         a, b = x.reshape(6, -1), y.reshape(6, -1)
-        return (np.abs(a - b).sum(axis=1) / np.abs(b).sum(axis=1)).max()
+        return np.abs(a - b).sum(axis=1) / np.abs(b).sum(axis=1)
 
     report = []
     for k, seed in enumerate(seeds):
         ref, n_ref, t_ref = res[k]
-        perts = [res[len(seeds) * (1 + j) + k][0] for j in range(2)]
+        perts = [res[len(seeds) * (1 + j) + k][0] for j in range(len(perturbations))]
         S, dx, t_stop = W.euler1d_riemann(2048, seed=seed)
         s = Solver(1, "euler", 2048, dx=dx, bc="transmissive")
         s.set_state(S)
@@ -208,8 +213,8 @@ def test_euler1d_riemann_2048_to_the_stop_time():
         _, t = s.last_dt()
         assert n == n_ref and t == t_ref, (seed, n, n_ref, t, t_ref)
         out = s.state.cpu().numpy()
-        env = max(rel1(p, ref) for p in perts)
+        env = np.max([rel1(p, ref) for p in perts], axis=0)
         report.append((seed, n, rel1(out, ref), env))
     print(report)
     for seed, n, err, env in report:
-        assert err <= max(1e-10, 10.0 * env), (seed, err, env)
+        assert np.all(err <= np.maximum(1e-10, 10.0 * env)), (seed, err, env)
