@@ -171,6 +171,28 @@ inline Grid grid_of(const hweno_ctx* h) {
   g.cdu = (0.75 - g.d1) / g.d1;
   g.csv = 0.25 / g.d1;
   g.Gd = g.d0 / g.d1;
+  // The smoothness indicator beta0 of Eq. (GHYZ) as two quadratic forms.  Its linear forms
+  // (coefficients on (h sv, du) and on (h dv, d2)) with their weights:
+  //   a1 + a3/4 = (-3/16, 11/16), weight 1;   a3 = (1/4, -1/4), weight 781/20;
+  //   a2 + 63/130 a4 = (67/520, 197/260), weight 13/3;   a4 = (-1/4, -1/2), weight 1421461/2275.
+  // Each pair makes s X^2 + 2 q X Y + r Y^2 = s (X + (q/s) Y)^2 + T Y^2 with T = det / s, det the
+  // weighted square of the pair's 2x2 determinant.
+  struct Pair {
+    double s, q, T;
+  };
+  auto pair = [](const double* f, double wf, const double* k, double wk) {
+    Pair o;
+    o.s = wf * f[0] * f[0] + wk * k[0] * k[0];
+    o.q = wf * f[0] * f[1] + wk * k[0] * k[1];
+    const double m = f[0] * k[1] - f[1] * k[0];
+    o.T = wf * wk * m * m / o.s;
+    return o;
+  };
+  const double fA[2] = {-3.0 / 16.0, 11.0 / 16.0}, fC[2] = {0.25, -0.25};
+  const double fB[2] = {67.0 / 520.0, 197.0 / 260.0}, fD[2] = {-0.25, -0.5};
+  const Pair p1 = pair(fA, 1.0, fC, 781.0 / 20.0), p2 = pair(fB, 13.0 / 3.0, fD, 1421461.0 / 2275.0);
+  g.bT1 = p1.T;
+  g.bT2 = p2.T;
   const double hs[2] = {h->dx, h->dy};
   for (int d = 0; d < 2; ++d) {
     g.h[d] = hs[d];
@@ -181,10 +203,10 @@ inline Grid grid_of(const hweno_ctx* h) {
     g.hih[d] = 0.5 / hs[d];
     g.c2h[d] = hw::DCoef2::ch * hs[d];
     // unscaled-derivative constants (see hw::Grid)
-    g.uA[d] = -0.1875 * hs[d];
-    g.uB[d] = std::sqrt(13.0 / 3.0) * (67.0 / 520.0) * hs[d];
-    g.uh[d] = hs[d];
-    g.uhh[d] = 0.5 * hs[d];
+    g.bS1[d] = p1.s * hs[d] * hs[d];
+    g.bN1[d] = p1.q / (p1.s * hs[d]);
+    g.bS2[d] = p2.s * hs[d] * hs[d];
+    g.bN2[d] = p2.q / (p2.s * hs[d]);
     g.udm[d][0] = dm[0];
     g.udm[d][1] = dm[1];
     g.udm[d][2] = dm[2] * hs[d];
@@ -200,7 +222,6 @@ inline Grid grid_of(const hweno_ctx* h) {
     g.e2gih[d] = hw::DCoef2::eg / hs[d];
   }
   g.ig1 = 1.0 / g1;
-  g.kB = std::sqrt(13.0 / 3.0) * (197.0 / 260.0);
   g.grav = h->grav;
   for (int sd = 0; sd < 4; ++sd) {
     g.side[sd] = h->side[sd];

@@ -92,26 +92,32 @@ __device__ __forceinline__ void block_max2(double a, double b, unsigned long lon
 
 // ---------------------------------------------------------------------------------------------
 // Modified derivative of one cell in one direction (normal frame).  U3/D3: cells i-1, i, i+1
-// (D = derivative along the sweep; only i-1 and i+1 enter).  e: eigenvectors of the cell.
+// (D = derivative along the sweep; only i-1 and i+1 enter).  e: eigenvectors of the cell.  The
+// limiter needs the characteristic fields only through the differences of neighbouring cells, so
+// the two conserved differences are projected (equal neighbours give exactly zero).
 template <int NC, int SYS>
 __device__ __forceinline__ void modified_derivative(const double (&U3)[3][NC], const double (&D3)[3][NC],
                                                     const Eig<NC>& e, int dir, const Grid& g, double* out) {
   const double ih = g.ih[dir];
-  double W[3][NC], Zm[NC], Zp[NC];
-  if (SYS == SYS_EULER) {
+  double dU[2][NC], Dq[2][NC], Zm[NC], Zp[NC];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) e.project(U3[q], W[q]);
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) dU[q][k] = U3[q + 1][k] - U3[q][k];
+  if (SYS == SYS_EULER) {
+    e.project(dU[0], Dq[0]);
+    e.project(dU[1], Dq[1]);
     e.project(D3[0], Zm);
     e.project(D3[2], Zp);
   } else {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) W[q][0] = U3[q][0];
+    Dq[0][0] = dU[0][0];
+    Dq[1][0] = dU[1][0];
     Zm[0] = D3[0][0];
     Zp[0] = D3[2][0];
   }
   double ht[NC];
 #pragma unroll
-  for (int s = 0; s < NC; ++s) ht[s] = cell_field_u(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], g, dir) * ih;
+  for (int s = 0; s < NC; ++s) ht[s] = cell_field_d(Dq[0][s], Dq[1][s], Zm[s], Zp[s], g, dir) * ih;
   if (SYS == SYS_EULER) {
     e.back(ht, out);
   } else {
@@ -162,43 +168,73 @@ __device__ __forceinline__ void load_stencil3(const Grid& g, const double* __res
 }
 
 // R2: the modified derivative and the face states of one cell in one direction from its own
-// stencil in its own characteristic fields (normal frame, derivatives unscaled).
-template <int NC, int SYS>
-__device__ __forceinline__ void r2_cell(const double (&U3)[3][NC], const double (&D3)[3][NC], const Eig<NC>& e,
-                                        int dir, const Grid& g, double* md, double (&fs)[4][NC]) {
+// stencil in its own characteristic fields (normal frame, derivatives unscaled).  The face values
+// are the cell's state plus back-projected corrections; without the weighted-derivative option the
+// face derivatives are linear in the stencil and are formed in conserved variables.
+template <int NC, int SYS, bool VW>
+__device__ __forceinline__ void r2_cell_vw(const double (&U3)[3][NC], const double (&D3)[3][NC], const Eig<NC>& e,
+                                           int dir, const Grid& g, double* md, double (&fs)[4][NC]) {
   const double ih = g.ih[dir];
-  const bool vw = (g.flags & FLAG_V_WEIGHTED) != 0;
-  double W[3][NC], Zm[NC], Zp[NC];
-  if (SYS == SYS_EULER) {
+  double dU[2][NC], Dq[2][NC], Zm[NC], Zp[NC];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) e.project(U3[q], W[q]);
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) dU[q][k] = U3[q + 1][k] - U3[q][k];
+  if (!VW) {
+    // the Hermite derivative of Eq. (P'xi) at the two faces (linear in the stencil)
+    const double k21 = g.uvd[dir][0], k3 = g.uvd[dir][1];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      fs[1][k] = fma(k21, dU[1][k], fma(-k3, dU[0][k], fma(0.0625, D3[0][k], -0.1875 * D3[2][k])));
+      fs[3][k] = fma(k21, dU[0][k], fma(-k3, dU[1][k], fma(-0.1875, D3[0][k], 0.0625 * D3[2][k])));
+    }
+  }
+  if (SYS == SYS_EULER) {
+    e.project(dU[0], Dq[0]);
+    e.project(dU[1], Dq[1]);
     e.project(D3[0], Zm);
     e.project(D3[2], Zp);
   } else {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) W[q][0] = U3[q][0];
+    Dq[0][0] = dU[0][0];
+    Dq[1][0] = dU[1][0];
     Zm[0] = D3[0][0];
     Zp[0] = D3[2][0];
   }
+  const double bc = SYS == SYS_EULER ? 0.0 : U3[1][0];
   double cm[NC], chm[NC], cp[NC], chp[NC], ht[NC];
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
-    cell_faces_field(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], g, dir, vw, cm[s], chm[s], cp[s], chp[s], ht[s]);
+    cell_faces_field<VW>(Dq[0][s], Dq[1][s], Zm[s], Zp[s], bc, g, dir, cm[s], chm[s], cp[s], chp[s], ht[s]);
     ht[s] *= ih;
   }
   if (SYS == SYS_EULER) {
-    e.back(cm, fs[0]);
-    e.back(chm, fs[1]);
-    e.back(cp, fs[2]);
-    e.back(chp, fs[3]);
+    e.back_add(cm, U3[1], fs[0]);
+    e.back_add(cp, U3[1], fs[2]);
     e.back(ht, md);
   } else {
     fs[0][0] = cm[0];
-    fs[1][0] = chm[0];
     fs[2][0] = cp[0];
-    fs[3][0] = chp[0];
     md[0] = ht[0];
   }
+  if (VW) {
+    if (SYS == SYS_EULER) {
+      e.back(chm, fs[1]);
+      e.back(chp, fs[3]);
+    } else {
+      fs[1][0] = chm[0];
+      fs[3][0] = chp[0];
+    }
+  }
+}
+
+// r2_cell_vw with the weighted-derivative option read from the grid's flags (one code path each)
+template <int NC, int SYS>
+__device__ __forceinline__ void r2_cell(const double (&U3)[3][NC], const double (&D3)[3][NC], const Eig<NC>& e,
+                                        int dir, const Grid& g, double* md, double (&fs)[4][NC]) {
+  if (g.flags & FLAG_V_WEIGHTED)
+    r2_cell_vw<NC, SYS, true>(U3, D3, e, dir, g, md, fs);
+  else
+    r2_cell_vw<NC, SYS, false>(U3, D3, e, dir, g, md, fs);
 }
 
 // Cell work of one stage at cell p: primitives and wavespeeds (returned in wsx, wsy), nodal
@@ -340,6 +376,70 @@ __global__ void __launch_bounds__(kThreads) k_cell(Grid g, const double* __restr
   block_max2(wsx, wsy, w.alpha + slot * w.astride);
 }
 
+// R1 face states: the interface values and derivatives from both sides of face k+1/2, from the
+// states Uq and derivatives Zq (normal frame) of the cells k-1..k+2, interpolated in the
+// characteristic fields of e (the Roe average at the face; unused for a scalar law).  The
+// interpolation needs the fields only through differences of neighbouring cells and the
+// derivatives: the three conserved differences are projected and the centre states added back in
+// conserved variables.  VW: the weighted-derivative option.
+template <int NC, int SYS, bool VW>
+__device__ __forceinline__ void r1_face_states(const double (&Uq)[4][NC], const double (&Zq)[4][NC],
+                                               const Eig<NC>& e, const Grid& g, int dir, double* Um, double* Up,
+                                               double* Dm, double* Dp) {
+  double dU[3][NC];
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) dU[q][k] = Uq[q + 1][k] - Uq[q][k];
+  if (!VW) {
+    // the Hermite derivative of Eq. (P'xi) at the face from both sides (linear in the stencil,
+    // formed first so that the differences and derivatives are not held through the fields)
+    const double k21 = g.uvd[dir][0], k3 = g.uvd[dir][1];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      Dm[k] = fma(k21, dU[1][k], fma(-k3, dU[0][k], fma(0.0625, Zq[0][k], -0.1875 * Zq[2][k])));
+      Dp[k] = fma(k21, dU[1][k], fma(-k3, dU[2][k], fma(-0.1875, Zq[1][k], 0.0625 * Zq[3][k])));
+    }
+  }
+  double Dq[3][NC], Yq[4][NC];
+  if (SYS == SYS_EULER) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) e.project(dU[q], Dq[q]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) e.project(Zq[q], Yq[q]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) Dq[q][0] = dU[q][0];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Yq[q][0] = Zq[q][0];
+  }
+  // HWENO interpolation in each characteristic field: u^- from the stencil of cell k, u^+ from the
+  // stencil of cell k+1 (mirror image)
+  const double bm = SYS == SYS_EULER ? 0.0 : Uq[1][0], bp = SYS == SYS_EULER ? 0.0 : Uq[2][0];
+  double cm[NC], chm[NC], cp[NC], chp[NC];
+#pragma unroll
+  for (int s = 0; s < NC; ++s)
+    face_field_d<VW>(Dq[0][s], Dq[1][s], Dq[2][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], bm, bp, g, dir, cm[s],
+                     chm[s], cp[s], chp[s]);
+  // back to conserved variables
+  if (SYS == SYS_EULER) {
+    e.back_add(cm, Uq[1], Um);
+    e.back_add(cp, Uq[2], Up);
+  } else {
+    Um[0] = cm[0];
+    Up[0] = cp[0];
+  }
+  if (VW) {
+    if (SYS == SYS_EULER) {
+      e.back(chm, Dm);
+      e.back(chp, Dp);
+    } else {
+      Dm[0] = chm[0];
+      Dp[0] = chp[0];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Face work of one stage: face f of direction dir (x faces: f = j (nx+1) + i; y faces:
 // f = j nx + i), alpha = the LF coefficient of that direction.
@@ -406,7 +506,6 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
     }
     // characteristic fields at the face: Roe average of the two adjacent cells
     Eig<NC> e;
-    double Wq[4][NC], Yq[4][NC];
     if (SYS == SYS_EULER) {
       const int ou = dir == 0 ? 1 : 2, ov = dir == 0 ? 2 : 1;
       const int oh = DIM == 2 ? 3 : 2;
@@ -441,38 +540,11 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
       const double c2 = g.gm1 * fma(-0.5, DIM == 2 ? fma(ub, ub, vb * vb) : ub * ub, Hb);
       const double ic = rsqrt(c2);
       e.setup(ub, vb, Hb, c2 * ic, ic, g.gm1);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        e.project(Uq[q], Wq[q]);
-        e.project(Zq[q], Yq[q]);
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        Wq[q][0] = Uq[q][0];
-        Yq[q][0] = Zq[q][0];
-      }
     }
-    // HWENO interpolation in each characteristic field: u^- from the stencil of cell fa-1,
-    // u^+ from the stencil of cell fa (mirror image)
-    const bool vw = VAR && (g.flags & FLAG_V_WEIGHTED) != 0;
-    double cm[NC], chm[NC], cp[NC], chp[NC];
-#pragma unroll
-    for (int s = 0; s < NC; ++s)
-      face_field_u(Wq[0][s], Wq[1][s], Wq[2][s], Wq[3][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, dir, cm[s],
-                   chm[s], cp[s], chp[s], vw);
-    // back to conserved variables
-    if (SYS == SYS_EULER) {
-      e.back(cm, Um);
-      e.back(cp, Up);
-      e.back(chm, Dm);
-      e.back(chp, Dp);
-    } else {
-      Um[0] = cm[0];
-      Up[0] = cp[0];
-      Dm[0] = chm[0];
-      Dp[0] = chp[0];
-    }
+    if (VAR && (g.flags & FLAG_V_WEIGHTED))
+      r1_face_states<NC, SYS, true>(Uq, Zq, e, g, dir, Um, Up, Dm, Dp);
+    else
+      r1_face_states<NC, SYS, false>(Uq, Zq, e, g, dir, Um, Up, Dm, Dp);
   }
   // local LF: the larger spectral radius of the two cells of the face
   if (VAR && (g.flags & FLAG_ALPHA_LOCAL)) {

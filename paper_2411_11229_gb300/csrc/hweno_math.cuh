@@ -51,12 +51,11 @@ struct Grid {
   double dm[4], dp[4];
   double cdu, csv, Gd;
   // The same arithmetic with the derivatives entering unscaled (v, not h v), per direction: the h
-  // of every derivative term folded into its coefficient.  uA, uB: the derivative coefficients of
-  // the smoothness indicator's first two linear forms; uh = h, uhh = h/2 for the other two;
-  // udm, udp: dm, dp with their derivative coefficients times h; uvd = (21/16, 3/16)/h: the cell
-  // differences in the derivative at the face; ucsv = csv h.
-  double uA[2], uB[2], uh[2], uhh[2];
-  double kB;  // sqrt(13/3) 197/260: the second linear form carries the square root of its weight
+  // of every derivative term folded into its coefficient.  bS1, bN1, bS2, bN2 (per direction) and
+  // bT1, bT2: the smoothness indicator as S1 (sv + N1 du)^2 + T1 du^2 + S2 (dv + N2 d2)^2 + T2 d2^2
+  // (see beta0_eps); udm, udp: dm, dp with their derivative coefficients times h;
+  // uvd = (21/16, 3/16)/h: the cell differences in the derivative at the face; ucsv = csv h.
+  double bS1[2], bN1[2], bS2[2], bN2[2], bT1, bT2;
   double udm[2][4], udp[2][4], uvd[2][2], ucsv[2];
   double h[2], ih[2], chh[2], efih[2], egih[2], hih[2];
   // Extended scheme (read only by the kernels instantiated with VAR != 0):
@@ -107,21 +106,19 @@ __device__ __forceinline__ double beta0(double dm, double dp, double hvm, double
   return fma((1421461.0 / 2275.0 / 16.0) * D, D, fma((781.0 / 20.0 / 16.0) * C, C, fma((13.0 / 3.0) * B, B, A * A)));
 }
 
-// beta0 with unscaled derivatives vm = v_{i-1}, vp = v_{i+1} along direction dir (the h of the
-// derivative terms in the grid constants; D/2 replaces D with the factor 4 moved into its weight;
-// the second form carries the square root of its weight 13/3, so its square needs no product).
-// Returns beta0, du = dm + dp and the unscaled derivative sum sv = vm + vp.
-__device__ __forceinline__ double beta0_u(double dm, double dp, double vm, double vp, const Grid& g, int dir,
-                                          double& du_out, double& sv_out) {
+// beta0 + eps with unscaled derivatives vm = v_{i-1}, vp = v_{i+1} along direction dir.  The four
+// squared forms of beta0 make one quadratic form in (h sv, du) and one in (h dv, d2); completing the
+// square in the derivative term writes them as S1 (sv + N1 du)^2 + T1 du^2 and
+// S2 (dv + N2 d2)^2 + T2 d2^2 (S, N per direction, T independent of h), a sum of four non-negative
+// terms, and eps enters as the first addend.  Returns beta0 + eps, du = dm + dp and sv = vm + vp.
+__device__ __forceinline__ double beta0_eps(double dm, double dp, double vm, double vp, const Grid& g, int dir,
+                                            double& du_out, double& sv_out) {
   const double du = dm + dp, d2 = dp - dm;
   const double sv = vm + vp, dv = vm - vp;
-  const double A = fma(g.uA[dir], sv, 0.6875 * du);
-  const double B = fma(g.uB[dir], dv, g.kB * d2);  // sqrt(13/3) times the second form
-  const double C = fma(g.uh[dir], sv, -du);
-  const double Dh = fma(g.uhh[dir], dv, d2);
+  const double y1 = fma(g.bN1[dir], du, sv), y2 = fma(g.bN2[dir], d2, dv);
   du_out = du;
   sv_out = sv;
-  return fma((1421461.0 / 2275.0 / 4.0) * Dh, Dh, fma((781.0 / 20.0 / 16.0) * C, C, fma(B, B, A * A)));
+  return fma(g.bS1[dir] * y1, y1, fma(g.bS2[dir] * y2, y2, fma(g.bT1 * du, du, fma(g.bT2 * d2, d2, g.eps))));
 }
 
 // Nonlinear weights of Eq. (nonlinear) up to a common factor: with e_l = beta_l + eps,
@@ -135,6 +132,19 @@ __device__ __forceinline__ Wts weights(double b0, double b1, double b2, double e
   const double ts = fabs(b0 - b1) + fabs(b0 - b2);
   const double tau = (0.25 * ts) * ts;
   const double e0 = b0 + eps;
+  const double Q0 = e1 * e2, Q1 = e0 * e2, Q2 = e0 * e1;
+  const double P = Q0 * e0;
+  Wts w;
+  w.W0 = fma(tau, Q0, P);
+  w.W1 = fma(tau, Q1, P);
+  w.W2 = fma(tau, Q2, P);
+  return w;
+}
+
+// Weights from e_l = beta_l + eps directly: e_l - e_k stands for beta_l - beta_k in tau.
+__device__ __forceinline__ Wts weights_e(double e0, double e1, double e2) {
+  const double ts = fabs(e0 - e1) + fabs(e0 - e2);
+  const double tau = (0.25 * ts) * ts;
   const double Q0 = e1 * e2, Q1 = e0 * e2, Q2 = e0 * e1;
   const double P = Q0 * e0;
   Wts w;
@@ -187,79 +197,84 @@ __device__ __forceinline__ void face_field(double w0, double w1, double w2, doub
   }
 }
 
-// face_field with unscaled derivatives (y = v, not h v) along direction dir; v^- and v^+ come out
-// unscaled.  The forward kernels use this form; the scaled one above serves the adjoint.
-__device__ __forceinline__ void face_field_u(double w0, double w1, double w2, double w3, double y0, double y1,
-                                             double y2, double y3, const Grid& g, int dir, double& um,
-                                             double& vm, double& up, double& vp, bool vw = false) {
-  const double d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2;
-  const double b01 = d01 * d01, b12 = d12 * d12, b23 = d23 * d23;
-  const double e01 = b01 + g.eps, e12 = b12 + g.eps, e23 = b23 + g.eps;
+// face_field on differences, with unscaled derivatives along direction dir (the forward kernels'
+// form; the scaled one above serves the adjoint).  In: d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2
+// of one characteristic field over the cells k-1..k+2 and their derivatives y0..y3.  Out: um, up =
+// the interface values less the centre values w1, w2, added to bm, bp (the centre values for a
+// scalar law, zero where the caller adds the centre states in conserved variables); with VW (the
+// weighted-derivative option), the weighted derivatives vm, vp (the unweighted ones are linear in
+// the stencil and formed by the caller).
+template <bool VW>
+__device__ __forceinline__ void face_field_d(double d01, double d12, double d23, double y0, double y1, double y2,
+                                             double y3, double bm, double bp, const Grid& g, int dir, double& um,
+                                             double& vm, double& up, double& vp) {
+  const double e01 = fma(d01, d01, g.eps), e12 = fma(d12, d12, g.eps), e23 = fma(d23, d23, g.eps);
   const double* cm = g.udm[dir];
   const double* cp = g.udp[dir];
   const double k21 = g.uvd[dir][0], k3 = g.uvd[dir][1];
+  vm = vp = 0.0;
   double du, sv;
   {
-    const double b0 = beta0_u(d01, d12, y0, y2, g, dir, du, sv);
-    const Wts wt = weights(b0, b01, b12, e01, e12, g.eps);
+    // stencil of cell k: candidates on {i-1, i} (W1), {i, i+1} (W2)
+    const double e0 = beta0_eps(d01, d12, y0, y2, g, dir, du, sv);
+    const Wts wt = weights_e(e0, e01, e12);
     const double r = fma(cm[0], d01, fma(cm[1], d12, fma(cm[2], y0, cm[3] * y2)));
     const double sl = fma(wt.W1, d01, wt.W2 * d12);
-    const double den = fma(g.G, wt.W0, wt.W1 + wt.W2);
-    const double rden = rcp(den);
-    um = fma(fma(wt.W0, r, 0.5 * sl), rden, w1);
-    vm = fma(k21, d12, fma(-k3, d01, fma(0.0625, y0, -0.1875 * y2)));
-    if (vw) {
+    const double rden = rcp(fma(g.G, wt.W0, wt.W1 + wt.W2));
+    um = fma(fma(wt.W0, r, 0.5 * sl), rden, bm);
+    if (VW) {
       const double ih = g.ih[dir];
-      vm = fma(wt.W0, fma(vm, g.ig1, -du * ih), sl * ih) * rden;
+      const double v0 = fma(k21, d12, fma(-k3, d01, fma(0.0625, y0, -0.1875 * y2)));
+      vm = fma(wt.W0, fma(v0, g.ig1, -du * ih), sl * ih) * rden;
     }
   }
   {
-    const double b0 = beta0_u(d12, d23, y1, y3, g, dir, du, sv);
-    const Wts wt = weights(b0, b12, b23, e12, e23, g.eps);
+    // stencil of cell k+1 (mirror image): its candidate on {i, i+1} carries beta2
+    const double e0 = beta0_eps(d12, d23, y1, y3, g, dir, du, sv);
+    const Wts wt = weights_e(e0, e12, e23);
     const double r = fma(cp[0], d12, fma(cp[1], d23, fma(cp[2], y1, cp[3] * y3)));
     const double sl = fma(wt.W1, d12, wt.W2 * d23);
-    const double den = fma(g.G, wt.W0, wt.W1 + wt.W2);
-    const double rden = rcp(den);
-    up = fma(fma(wt.W0, r, -0.5 * sl), rden, w2);
-    vp = fma(k21, d12, fma(-k3, d23, fma(-0.1875, y1, 0.0625 * y3)));
-    if (vw) {
+    const double rden = rcp(fma(g.G, wt.W0, wt.W1 + wt.W2));
+    up = fma(fma(wt.W0, r, -0.5 * sl), rden, bp);
+    if (VW) {
       const double ih = g.ih[dir];
-      vp = fma(wt.W0, fma(vp, g.ig1, -du * ih), sl * ih) * rden;
+      const double v0 = fma(k21, d12, fma(-k3, d23, fma(-0.1875, y1, 0.0625 * y3)));
+      vp = fma(wt.W0, fma(v0, g.ig1, -du * ih), sl * ih) * rden;
     }
   }
 }
 
-// R2 variant: one characteristic field of cell i from its own stencil w0..w2 = u_{i-1..i+1},
-// y0, y2 = h v_{i-1}, h v_{i+1}: u^- and h v^- at x_{i+1/2}, u^+ and h v^+ at x_{i-1/2} (the
-// mirror image) and h v~_i.  The three share beta, tau and the unnormalised weights; u^+/- share
-// one reciprocal (gamma1 = gamma2 makes the mirrored weights the same numbers).
-__device__ __forceinline__ void cell_faces_field(double w0, double w1, double w2, double y0, double y2, const Grid& g,
-                                                 int dir, bool vw, double& um, double& vm, double& up, double& vp,
-                                                 double& hvt) {
-  // unscaled derivatives in (y0, y2) and out (vm, vp); hvt = h v~ as before
-  const double d01 = w1 - w0, d12 = w2 - w1;
-  const double b1 = d01 * d01, b2 = d12 * d12;
+// R2 variant: one characteristic field of cell i from its own stencil, on differences
+// d01 = w1 - w0, d12 = w2 - w1 and unscaled derivatives y0 = v_{i-1}, y2 = v_{i+1}: u^- at
+// x_{i+1/2} and u^+ at x_{i-1/2} less the centre value, added to bc (as in face_field_d), with VW
+// the weighted derivatives v^- and v^+, and h v~_i.  The three share beta, tau and the unnormalised
+// weights; u^+/- share one reciprocal (gamma1 = gamma2 makes the mirrored weights the same numbers).
+template <bool VW>
+__device__ __forceinline__ void cell_faces_field(double d01, double d12, double y0, double y2, double bc,
+                                                 const Grid& g, int dir, double& um, double& vm, double& up,
+                                                 double& vp, double& hvt) {
   double du, sv;
-  const double b0 = beta0_u(d01, d12, y0, y2, g, dir, du, sv);
-  const Wts wt = weights(b0, b1, b2, b1 + g.eps, b2 + g.eps, g.eps);
+  const double e0 = beta0_eps(d01, d12, y0, y2, g, dir, du, sv);
+  const Wts wt = weights_e(e0, fma(d01, d01, g.eps), fma(d12, d12, g.eps));
   const double rden = rcp(fma(g.G, wt.W0, wt.W1 + wt.W2));
-  // centre value plus differences (see face_field): the candidates at x_{i+1/2} differ from u_i by
-  // (d01, d12)/2, those at x_{i-1/2} by (-d01, -d12)/2, so both faces share W1 d01 + W2 d12
+  // the candidates at x_{i+1/2} differ from u_i by (d01, d12)/2, those at x_{i-1/2} by
+  // (-d01, -d12)/2, so both faces share W1 d01 + W2 d12
   const double* cm = g.udm[dir];
   const double* cp = g.udp[dir];
   const double rm = fma(cm[0], d01, fma(cm[1], d12, fma(cm[2], y0, cm[3] * y2)));
   const double rp = fma(cp[0], d01, fma(cp[1], d12, fma(cp[2], y0, cp[3] * y2)));
   const double sl = fma(wt.W1, d01, wt.W2 * d12);
   const double hs = 0.5 * sl;
-  um = fma(fma(wt.W0, rm, hs), rden, w1);
-  up = fma(fma(wt.W0, rp, -hs), rden, w1);
-  const double k21 = g.uvd[dir][0], k3 = g.uvd[dir][1];
-  vm = fma(k21, d12, fma(-k3, d01, fma(0.0625, y0, -0.1875 * y2)));
-  vp = fma(k21, d01, fma(-k3, d12, fma(-0.1875, y0, 0.0625 * y2)));
-  if (vw) {
+  um = fma(fma(wt.W0, rm, hs), rden, bc);
+  up = fma(fma(wt.W0, rp, -hs), rden, bc);
+  vm = vp = 0.0;
+  if (VW) {
+    const double k21 = g.uvd[dir][0], k3 = g.uvd[dir][1];
     const double ih = g.ih[dir], ds = du * ih, ss = sl * ih;
-    vm = fma(wt.W0, fma(vm, g.ig1, -ds), ss) * rden;
-    vp = fma(wt.W0, fma(vp, g.ig1, -ds), ss) * rden;
+    const double v0m = fma(k21, d12, fma(-k3, d01, fma(0.0625, y0, -0.1875 * y2)));
+    const double v0p = fma(k21, d01, fma(-k3, d12, fma(-0.1875, y0, 0.0625 * y2)));
+    vm = fma(wt.W0, fma(v0m, g.ig1, -ds), ss) * rden;
+    vp = fma(wt.W0, fma(v0p, g.ig1, -ds), ss) * rden;
   }
   const double t = fma(g.cdu, du, -g.ucsv[dir] * sv);
   hvt = fma(wt.W0, t, sl) * rcp(fma(g.Gd, wt.W0, wt.W1 + wt.W2));
@@ -280,15 +295,12 @@ __device__ __forceinline__ double cell_field(double w0, double w1, double w2, do
   return num * rcp(den);
 }
 
-// cell_field with unscaled derivatives y0 = v_{i-1}, y2 = v_{i+1} along direction dir; returns
-// h v~_i as cell_field does.
-__device__ __forceinline__ double cell_field_u(double w0, double w1, double w2, double y0, double y2, const Grid& g,
-                                               int dir) {
-  const double d01 = w1 - w0, d12 = w2 - w1;
-  const double b1 = d01 * d01, b2 = d12 * d12;
+// cell_field on differences d01 = w1 - w0, d12 = w2 - w1 with unscaled derivatives y0 = v_{i-1},
+// y2 = v_{i+1} along direction dir; returns h v~_i as cell_field does.
+__device__ __forceinline__ double cell_field_d(double d01, double d12, double y0, double y2, const Grid& g, int dir) {
   double du, sv;
-  const double b0 = beta0_u(d01, d12, y0, y2, g, dir, du, sv);
-  const Wts wt = weights(b0, b1, b2, b1 + g.eps, b2 + g.eps, g.eps);
+  const double e0 = beta0_eps(d01, d12, y0, y2, g, dir, du, sv);
+  const Wts wt = weights_e(e0, fma(d01, d01, g.eps), fma(d12, d12, g.eps));
   const double t = fma(g.cdu, du, -g.ucsv[dir] * sv);
   const double num = fma(wt.W0, t, fma(wt.W1, d01, wt.W2 * d12));
   const double den = fma(g.Gd, wt.W0, wt.W1 + wt.W2);
@@ -484,6 +496,21 @@ struct Eig {
       w[3] = th - sh;
     } else {
       w[2] = th - sh;
+    }
+  }
+
+  // q = base + R w: the interface state as the centre state plus the back-projected correction
+  __device__ __forceinline__ void back_add(const double* w, const double* base, double* q) const {
+    const double wl = w[0], wr = NC == 4 ? w[3] : w[2];
+    const double sg = wl + wr, dl = wr - wl;
+    const double q0 = sg + w[1];
+    q[0] = base[0] + q0;
+    q[1] = fma(u, q0, fma(c, dl, base[1]));
+    if (NC == 4) {
+      q[2] = fma(v, q0, w[2] + base[2]);
+      q[3] = fma(H, sg, fma(hq2, w[1], fma(v, w[2], fma(uc, dl, base[3]))));
+    } else {
+      q[2] = fma(H, sg, fma(hq2, w[1], fma(uc, dl, base[2])));
     }
   }
 
