@@ -74,9 +74,14 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
   const double c = c2 * ic;
   Eig<NC> e;
   e.setup(pr.u, pr.v, H, c, ic, g.gm1);
-  double W[3][NC], Zm[NC], Zp[NC], ht[NC];
+  // the limiter sees the characteristic fields only through differences of neighbouring cells
+  double dU[2][NC], Dq[2][NC], Zm[NC], Zp[NC], ht[NC];
 #pragma unroll
-  for (int q = 0; q < 3; ++q) e.project(U3[q], W[q]);
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) dU[q][k] = U3[q + 1][k] - U3[q][k];
+  e.project(dU[0], Dq[0]);
+  e.project(dU[1], Dq[1]);
   e.project(hD3[0], Zm);
   e.project(hD3[2], Zp);
   // forward intermediates of the limiter, per field, kept in this thread's shared-memory slots
@@ -84,7 +89,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
   double* const svb = adj_cell_sm + threadIdx.x;
 #pragma unroll
   for (int s = 0; s < NC; ++s)
-    ht[s] = cell_field_save(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], g, svb + s * kCellSaved * kThreads, kThreads) * ih;
+    ht[s] = cell_field_save(Dq[0][s], Dq[1][s], Zm[s], Zp[s], g, svb + s * kCellSaved * kThreads, kThreads) * ih;
   // backward from the adjoint of the modified derivative of this cell
   double ob[NC];
 #pragma unroll
@@ -96,31 +101,32 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
 #pragma unroll
   for (int s = 0; s < NC; ++s) htb[s] = 0.0;
   back_bwd<NC>(e, ht, ob, htb, hq2b, ucb, eb);
-  double Wb[3][NC], Zmb[NC], Zpb[NC];
+  double Dqb[2][NC], Zmb[NC], Zpb[NC];
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
-    Wb[0][s] = Wb[1][s] = Wb[2][s] = 0.0;
+    double db[2] = {0.0, 0.0};
     Zmb[s] = Zpb[s] = 0.0;
+    cell_field_bwd_saved(Dq[0][s], Dq[1][s], Zm[s], Zp[s], g, htb[s] * ih, svb + s * kCellSaved * kThreads,
+                         kThreads, db, Zmb[s], Zpb[s]);
+    Dqb[0][s] = db[0];
+    Dqb[1][s] = db[1];
   }
-#pragma unroll
-  for (int s = 0; s < NC; ++s) {
-    double wb[3] = {0.0, 0.0, 0.0};
-    cell_field_bwd_saved(W[0][s], W[1][s], W[2][s], Zm[s], Zp[s], g, htb[s] * ih, svb + s * kCellSaved * kThreads,
-                         kThreads, wb, Zmb[s], Zpb[s]);
-    Wb[0][s] = wb[0];
-    Wb[1][s] = wb[1];
-    Wb[2][s] = wb[2];
-  }
-  double Ub[3][NC], hDmb[NC], hDpb[NC];
+  double dUb[2][NC], Ub[3][NC], hDmb[NC], hDpb[NC];
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
-    Ub[0][k] = Ub[1][k] = Ub[2][k] = 0.0;
+    dUb[0][k] = dUb[1][k] = 0.0;
     hDmb[k] = hDpb[k] = 0.0;
   }
 #pragma unroll
-  for (int q = 0; q < 3; ++q) project_bwd<NC>(e, U3[q], Wb[q], Ub[q], hb1b, hb2b, hicb, eb);
+  for (int q = 0; q < 2; ++q) project_bwd<NC>(e, dU[q], Dqb[q], dUb[q], hb1b, hb2b, hicb, eb);
   project_bwd<NC>(e, hD3[0], Zmb, hDmb, hb1b, hb2b, hicb, eb);
   project_bwd<NC>(e, hD3[2], Zpb, hDpb, hb1b, hb2b, hicb, eb);
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    Ub[0][k] = -dUb[0][k];
+    Ub[1][k] = dUb[0][k] - dUb[1][k];
+    Ub[2][k] = dUb[1][k];
+  }
   setup_bwd<NC>(e, g.gm1, ic, hb1b, hb2b, hicb, hq2b, ucb, eb);
   // c = sqrt(c2), ic = 1/sqrt(c2), c2 = gamma p ir, H = (E + p) ir
   const double c2b = 0.5 * ic * (eb.c - eb.ic * ic * ic);
@@ -228,25 +234,36 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
   const double ic = rsqrt(c2);
   Eig<NC> e;
   e.setup(ub, vb, Hb, c2 * ic, ic, g.gm1);
-  double Wq[4][NC], Yq[4][NC];
+  // the interpolation sees the characteristic fields only through differences of neighbouring
+  // cells; the interface derivatives (h-scaled, Eq. P'xi) are linear in the stencil and formed in
+  // conserved variables
+  double dU[3][NC], Dm[NC], Dp[NC];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    e.project(Uq[q], Wq[q]);
-    e.project(Zq[q], Yq[q]);
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) dU[q][k] = Uq[q + 1][k] - Uq[q][k];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    Dm[k] = fma(1.3125, dU[1][k], fma(-0.1875, dU[0][k], fma(0.0625, Zq[0][k], -0.1875 * Zq[2][k])));
+    Dp[k] = fma(1.3125, dU[1][k], fma(-0.1875, dU[2][k], fma(-0.1875, Zq[1][k], 0.0625 * Zq[3][k])));
   }
-  double cm[NC], chm[NC], cp[NC], chp[NC];
+  double Dq[3][NC], Yq[4][NC];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) e.project(dU[q], Dq[q]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) e.project(Zq[q], Yq[q]);
+  double cm[NC], cp[NC];
   // forward intermediates of the interpolation, per field, kept in this thread's shared-memory slots
   extern __shared__ double adj_face_sm[];
   double* const svb = adj_face_sm + threadIdx.x;
 #pragma unroll
   for (int s = 0; s < NC; ++s)
-    face_field_save(Wq[0][s], Wq[1][s], Wq[2][s], Wq[3][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, cm[s],
-                    chm[s], cp[s], chp[s], svb + s * kFaceSaved * kThreads, kThreads);
-  double Um[NC], Up[NC], Dm[NC], Dp[NC];
-  e.back(cm, Um);
-  e.back(cp, Up);
-  e.back(chm, Dm);
-  e.back(chp, Dp);
+    face_field_save(Dq[0][s], Dq[1][s], Dq[2][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, cm[s], cp[s],
+                    svb + s * kFaceSaved * kThreads, kThreads);
+  // interface states: centre states plus the back-projected corrections
+  double Um[NC], Up[NC];
+  e.back_add(cm, Uq[1], Um);
+  e.back_add(cp, Uq[2], Up);
   // ---- backward: fh = (FUm + FUp - alpha (Up - Um)) / 2 + Df, hh = hih (HDm + HDp - alpha (Dp - Dm)) + Dh
   double Umb[NC], Upb[NC], Dmb[NC], Dpb[NC], Fb[NC], Hb2[NC];
 #pragma unroll
@@ -264,33 +281,48 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
   jvp_bwd<NC>(Up, Dp, g.gm1, Hb2, Upb, Dpb);
   EigBar eb = {0.0, 0.0, 0.0, 0.0, 0.0};
   double hq2b = 0.0, ucb = 0.0, hb1b = 0.0, hb2b = 0.0, hicb = 0.0;
-  double cmb[NC], cpb[NC], chmb[NC], chpb[NC];
+  double cmb[NC], cpb[NC];
 #pragma unroll
-  for (int s = 0; s < NC; ++s) cmb[s] = cpb[s] = chmb[s] = chpb[s] = 0.0;
+  for (int s = 0; s < NC; ++s) cmb[s] = cpb[s] = 0.0;
   back_bwd<NC>(e, cm, Umb, cmb, hq2b, ucb, eb);
   back_bwd<NC>(e, cp, Upb, cpb, hq2b, ucb, eb);
-  back_bwd<NC>(e, chm, Dmb, chmb, hq2b, ucb, eb);
-  back_bwd<NC>(e, chp, Dpb, chpb, hq2b, ucb, eb);
-  double Wb[4][NC], Yb[4][NC];
+  double Uqb[4][NC], Zqb[4][NC], dUb[3][NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    // the centre states enter Um, Up directly; the derivatives linearly
+    Uqb[0][k] = Uqb[3][k] = 0.0;
+    Uqb[1][k] = Umb[k];
+    Uqb[2][k] = Upb[k];
+    dUb[0][k] = -0.1875 * Dmb[k];
+    dUb[1][k] = 1.3125 * (Dmb[k] + Dpb[k]);
+    dUb[2][k] = -0.1875 * Dpb[k];
+    Zqb[0][k] = 0.0625 * Dmb[k];
+    Zqb[1][k] = -0.1875 * Dpb[k];
+    Zqb[2][k] = -0.1875 * Dmb[k];
+    Zqb[3][k] = 0.0625 * Dpb[k];
+  }
+  double Dqb[3][NC], Yb[4][NC];
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
-    double wb[4] = {0.0, 0.0, 0.0, 0.0}, yb[4] = {0.0, 0.0, 0.0, 0.0};
-    face_field_bwd_saved(Wq[0][s], Wq[1][s], Wq[2][s], Wq[3][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g,
-                         cmb[s], chmb[s], cpb[s], chpb[s], svb + s * kFaceSaved * kThreads, kThreads, wb, yb);
+    double db[3] = {0.0, 0.0, 0.0}, yb[4] = {0.0, 0.0, 0.0, 0.0};
+    face_field_bwd_saved(Dq[0][s], Dq[1][s], Dq[2][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, cmb[s], cpb[s],
+                         svb + s * kFaceSaved * kThreads, kThreads, db, yb);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      Wb[q][s] = wb[q];
-      Yb[q][s] = yb[q];
+    for (int q = 0; q < 3; ++q) Dqb[q][s] = db[q];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Yb[q][s] = yb[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) project_bwd<NC>(e, dU[q], Dqb[q], dUb[q], hb1b, hb2b, hicb, eb);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) project_bwd<NC>(e, Zq[q], Yb[q], Zqb[q], hb1b, hb2b, hicb, eb);
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      Uqb[q + 1][k] += dUb[q][k];
+      Uqb[q][k] -= dUb[q][k];
     }
-  }
-  double Uqb[4][NC], Zqb[4][NC];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-#pragma unroll
-    for (int k = 0; k < NC; ++k) Uqb[q][k] = Zqb[q][k] = 0.0;
-    project_bwd<NC>(e, Uq[q], Wb[q], Uqb[q], hb1b, hb2b, hicb, eb);
-    project_bwd<NC>(e, Zq[q], Yb[q], Zqb[q], hb1b, hb2b, hicb, eb);
-  }
   setup_bwd<NC>(e, g.gm1, ic, hb1b, hb2b, hicb, hq2b, ucb, eb);
   // c = sqrt(c2), ic = 1/sqrt(c2); c2 = gm1 (Hb - (ub^2 + vb^2)/2)
   const double c2b = 0.5 * ic * (eb.c - eb.ic * ic * ic);

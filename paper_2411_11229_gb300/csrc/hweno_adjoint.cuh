@@ -54,126 +54,23 @@ __device__ __forceinline__ void weights_bwd(double b0, double b1, double b2, dou
   b2b -= tsb * s2;
 }
 
-// Backward of face_field: given the adjoints of um, hvm, up, hvp, adds those of w0..w3, y0..y3.
-__device__ __forceinline__ void face_field_bwd(double w0, double w1, double w2, double w3, double y0, double y1,
-                                               double y2, double y3, const Grid& g, double umb, double hvmb,
-                                               double upb, double hvpb, double* wb, double* yb) {
-  const double d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2;
-  const double b01 = d01 * d01, b12 = d12 * d12, b23 = d23 * d23;
-  const double e01 = b01 + g.eps, e12 = b12 + g.eps, e23 = b23 + g.eps;
-  const double pmid = 0.5 * (w1 + w2);
-  double d01b = 0.0, d12b = 0.0, d23b = 0.0, b01b = 0.0, b12b = 0.0, b23b = 0.0, pmidb = 0.0;
-  double e01b = 0.0, e12b = 0.0, e23b = 0.0;
-  double du, sv;
-  {
-    // stencil of cell k (w0, w1, w2)
-    const double b0 = beta0(d01, d12, y0, y2, du, sv);
-    const Wts wt = weights(b0, b01, b12, e01, e12, g.eps);
-    const double r = fma(g.cr[0], w0, fma(g.cr[1], w1, fma(g.cr[2], w2, fma(g.cr[3], y0, g.cr[4] * y2))));
-    const double p1 = fma(-0.5, w0, 1.5 * w1);
-    const double num = fma(wt.W0, r, fma(wt.W1, p1, wt.W2 * pmid));
-    const double den = fma(g.G, wt.W0, wt.W1 + wt.W2);
-    const double inv = rcp(den);
-    const double numb = umb * inv;
-    const double denb = -umb * num * inv * inv;
-    const double W0b = fma(numb, r, denb * g.G), W1b = fma(numb, p1, denb), W2b = fma(numb, pmid, denb);
-    const double rb = numb * wt.W0, p1b = numb * wt.W1;
-    pmidb += numb * wt.W2;
-    double b0b = 0.0;
-    weights_bwd(b0, b01, b12, e01, e12, g.eps, W0b, W1b, W2b, b0b, b01b, b12b, e01b, e12b);
-    beta0_bwd(d01, d12, y0, y2, b0b, d01b, d12b, yb[0], yb[2]);
-    wb[0] += fma(g.cr[0], rb, -0.5 * p1b) + 0.1875 * hvmb;
-    wb[1] += fma(g.cr[1], rb, 1.5 * p1b) - 1.5 * hvmb;
-    wb[2] += g.cr[2] * rb + 1.3125 * hvmb;
-    yb[0] += g.cr[3] * rb + 0.0625 * hvmb;
-    yb[2] += g.cr[4] * rb - 0.1875 * hvmb;
-  }
-  {
-    // stencil of cell k+1 (w1, w2, w3), evaluated at its left face
-    const double b0 = beta0(d12, d23, y1, y3, du, sv);
-    const Wts wt = weights(b0, b12, b23, e12, e23, g.eps);
-    const double r = fma(g.cl[0], w1, fma(g.cl[1], w2, fma(g.cl[2], w3, fma(g.cl[3], y1, g.cl[4] * y3))));
-    const double q1 = fma(-0.5, w3, 1.5 * w2);
-    const double num = fma(wt.W0, r, fma(wt.W2, q1, wt.W1 * pmid));
-    const double den = fma(g.G, wt.W0, wt.W1 + wt.W2);
-    const double inv = rcp(den);
-    const double numb = upb * inv;
-    const double denb = -upb * num * inv * inv;
-    const double W0b = fma(numb, r, denb * g.G), W1b = fma(numb, pmid, denb), W2b = fma(numb, q1, denb);
-    const double rb = numb * wt.W0, q1b = numb * wt.W2;
-    pmidb += numb * wt.W1;
-    double b0b = 0.0;
-    weights_bwd(b0, b12, b23, e12, e23, g.eps, W0b, W1b, W2b, b0b, b12b, b23b, e12b, e23b);
-    beta0_bwd(d12, d23, y1, y3, b0b, d12b, d23b, yb[1], yb[3]);
-    wb[1] += g.cl[0] * rb - 1.3125 * hvpb;
-    wb[2] += fma(g.cl[1], rb, 1.5 * q1b) + 1.5 * hvpb;
-    wb[3] += fma(g.cl[2], rb, -0.5 * q1b) - 0.1875 * hvpb;
-    yb[1] += g.cl[3] * rb - 0.1875 * hvpb;
-    yb[3] += g.cl[4] * rb + 0.0625 * hvpb;
-  }
-  b01b += e01b;
-  b12b += e12b;
-  b23b += e23b;
-  d01b += 2.0 * d01 * b01b;
-  d12b += 2.0 * d12 * b12b;
-  d23b += 2.0 * d23 * b23b;
-  wb[0] -= d01b;
-  wb[1] += d01b - d12b + 0.5 * pmidb;
-  wb[2] += d12b - d23b + 0.5 * pmidb;
-  wb[3] += d23b;
-}
-
-// Backward of cell_field (the limiter): given the adjoint of its output, adds those of
-// w0..w2, y0, y2.
-__device__ __forceinline__ void cell_field_bwd(double w0, double w1, double w2, double y0, double y2, const Grid& g,
-                                               double outb, double* wb, double& y0b, double& y2b) {
-  const double d01 = w1 - w0, d12 = w2 - w1;
-  const double b1 = d01 * d01, b2 = d12 * d12;
-  double du, sv;
-  const double b0 = beta0(d01, d12, y0, y2, du, sv);
-  const double e1 = b1 + g.eps, e2 = b2 + g.eps;
-  const Wts wt = weights(b0, b1, b2, e1, e2, g.eps);
-  const double t = fma(g.cdu, du, -g.csv * sv);
-  const double num = fma(wt.W0, t, fma(wt.W1, d01, wt.W2 * d12));
-  const double den = fma(g.Gd, wt.W0, wt.W1 + wt.W2);
-  const double inv = rcp(den);
-  const double numb = outb * inv;
-  const double denb = -outb * num * inv * inv;
-  const double W0b = fma(numb, t, denb * g.Gd), W1b = fma(numb, d01, denb), W2b = fma(numb, d12, denb);
-  const double tb = numb * wt.W0;
-  double d01b = numb * wt.W1, d12b = numb * wt.W2;
-  // t = cdu (d01 + d12) - csv (y0 + y2)
-  d01b += g.cdu * tb;
-  d12b += g.cdu * tb;
-  y0b -= g.csv * tb;
-  y2b -= g.csv * tb;
-  double b0b = 0.0, b1b = 0.0, b2b = 0.0, e1b = 0.0, e2b = 0.0;
-  weights_bwd(b0, b1, b2, e1, e2, g.eps, W0b, W1b, W2b, b0b, b1b, b2b, e1b, e2b);
-  beta0_bwd(d01, d12, y0, y2, b0b, d01b, d12b, y0b, y2b);
-  b1b += e1b;
-  b2b += e2b;
-  d01b += 2.0 * d01 * b1b;
-  d12b += 2.0 * d12 * b2b;
-  wb[0] -= d01b;
-  wb[1] += d01b - d12b;
-  wb[2] += d12b;
-}
-
 // ---------------------------------------------------------------------------------------------
-// The same backward passes from saved forward values.  The adjoint kernels run the forward
-// interpolation once, keep each stencil's intermediates (beta0, the three weights, the candidate
-// combination, the weighted sum and 1/den) in shared memory, and the backward pass reads them
-// instead of recomputing them.  sv points at this thread's first slot; consecutive values are
+// Backward passes from saved forward values.  The adjoint kernels run the forward interpolation
+// once, keep each stencil's intermediates (beta0, the three weights, the candidate combination,
+// the weighted sum and 1/den) in shared memory, and the backward pass reads them instead of
+// recomputing them.  The forward map is taken in difference form, as the forward kernels take it:
+// the characteristic fields enter only through differences of neighbouring cells.  sv points at this thread's first slot; consecutive values are
 // `stride` doubles apart (one slot per thread of the block).
 constexpr int kFaceSaved = 14;  // per characteristic field of a face: 7 per stencil
 constexpr int kCellSaved = 7;   // per characteristic field of a cell
 
-// face_field (h-scaled derivatives, centre value plus weighted differences) saving its
-// intermediates: [b0, W0, W1, W2, r, X, 1/den] of the stencil of cell k, then of cell k+1
-__device__ __forceinline__ void face_field_save(double w0, double w1, double w2, double w3, double y0, double y1,
-                                                double y2, double y3, const Grid& g, double& um, double& hvm,
-                                                double& up, double& hvp, double* sv, int stride) {
-  const double d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2;
+// One characteristic field at one face k+1/2 (h-scaled derivatives) from the differences
+// d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2 of the cells k-1..k+2 and their scaled derivatives
+// y0..y3: um - w1 and up - w2 (the interface values less the centre values; Eqs. Pxi, interp),
+// saving the intermediates [b0, W0, W1, W2, r, X, 1/den] of the stencil of cell k, then of cell k+1.
+__device__ __forceinline__ void face_field_save(double d01, double d12, double d23, double y0, double y1,
+                                                double y2, double y3, const Grid& g, double& dum, double& dup,
+                                                double* sv, int stride) {
   const double b01 = d01 * d01, b12 = d12 * d12, b23 = d23 * d23;
   const double e01 = b01 + g.eps, e12 = b12 + g.eps, e23 = b23 + g.eps;
   double du, svs;
@@ -184,8 +81,7 @@ __device__ __forceinline__ void face_field_save(double w0, double w1, double w2,
     const double sl = fma(wt.W1, d01, wt.W2 * d12);
     const double inv = rcp(fma(g.G, wt.W0, wt.W1 + wt.W2));
     const double X = fma(wt.W0, r, 0.5 * sl);
-    um = fma(X, inv, w1);
-    hvm = fma(1.3125, d12, fma(-0.1875, d01, fma(0.0625, y0, -0.1875 * y2)));
+    dum = X * inv;
     sv[0] = b0;
     sv[stride] = wt.W0;
     sv[2 * stride] = wt.W1;
@@ -201,8 +97,7 @@ __device__ __forceinline__ void face_field_save(double w0, double w1, double w2,
     const double sl = fma(wt.W1, d12, wt.W2 * d23);
     const double inv = rcp(fma(g.G, wt.W0, wt.W1 + wt.W2));
     const double X = fma(wt.W0, r, -0.5 * sl);
-    up = fma(X, inv, w2);
-    hvp = fma(1.3125, d12, fma(-0.1875, d23, fma(-0.1875, y1, 0.0625 * y3)));
+    dup = X * inv;
     sv[7 * stride] = b0;
     sv[8 * stride] = wt.W0;
     sv[9 * stride] = wt.W1;
@@ -213,14 +108,12 @@ __device__ __forceinline__ void face_field_save(double w0, double w1, double w2,
   }
 }
 
-// Backward of face_field_save: given the adjoints of um, hvm, up, hvp, adds those of w0..w3, y0..y3.
-// um = w1 + X / den with X = W0 r + (W1 d01 + W2 d12)/2, den = G W0 + W1 + W2 (up likewise with
-// w2, the differences d12, d23 and -1/2).
-__device__ __forceinline__ void face_field_bwd_saved(double w0, double w1, double w2, double w3, double y0,
-                                                     double y1, double y2, double y3, const Grid& g, double umb,
-                                                     double hvmb, double upb, double hvpb, const double* sv,
-                                                     int stride, double* wb, double* yb) {
-  const double d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2;
+// Backward of face_field_save: given the adjoints of um - w1 and up - w2, adds those of d01, d12,
+// d23 (db) and y0..y3 (yb).  um - w1 = X / den with X = W0 r + (W1 d01 + W2 d12)/2,
+// den = G W0 + W1 + W2 (up - w2 likewise with d12, d23 and -1/2).
+__device__ __forceinline__ void face_field_bwd_saved(double d01, double d12, double d23, double y0, double y1,
+                                                     double y2, double y3, const Grid& g, double umb, double upb,
+                                                     const double* sv, int stride, double* db, double* yb) {
   const double b01 = d01 * d01, b12 = d12 * d12, b23 = d23 * d23;
   const double e01 = b01 + g.eps, e12 = b12 + g.eps, e23 = b23 + g.eps;
   double d01b = 0.0, d12b = 0.0, d23b = 0.0, b01b = 0.0, b12b = 0.0, b23b = 0.0;
@@ -233,11 +126,10 @@ __device__ __forceinline__ void face_field_bwd_saved(double w0, double w1, doubl
     const double hX = 0.5 * Xb;
     const double W0b = fma(Xb, r, denb * g.G), W1b = fma(hX, d01, denb), W2b = fma(hX, d12, denb);
     const double rb = Xb * W0;
-    d01b += fma(g.dm[0], rb, fma(hX, W1, -0.1875 * hvmb));
-    d12b += fma(g.dm[1], rb, fma(hX, W2, 1.3125 * hvmb));
-    yb[0] += fma(g.dm[2], rb, 0.0625 * hvmb);
-    yb[2] += fma(g.dm[3], rb, -0.1875 * hvmb);
-    wb[1] += umb;
+    d01b += fma(g.dm[0], rb, hX * W1);
+    d12b += fma(g.dm[1], rb, hX * W2);
+    yb[0] += g.dm[2] * rb;
+    yb[2] += g.dm[3] * rb;
     double b0b = 0.0;
     weights_bwd(b0, b01, b12, e01, e12, g.eps, W0b, W1b, W2b, b0b, b01b, b12b, e01b, e12b);
     beta0_bwd(d01, d12, y0, y2, b0b, d01b, d12b, yb[0], yb[2]);
@@ -250,11 +142,10 @@ __device__ __forceinline__ void face_field_bwd_saved(double w0, double w1, doubl
     const double hX = -0.5 * Xb;
     const double W0b = fma(Xb, r, denb * g.G), W1b = fma(hX, d12, denb), W2b = fma(hX, d23, denb);
     const double rb = Xb * W0;
-    d12b += fma(g.dp[0], rb, fma(hX, W1, 1.3125 * hvpb));
-    d23b += fma(g.dp[1], rb, fma(hX, W2, -0.1875 * hvpb));
-    yb[1] += fma(g.dp[2], rb, -0.1875 * hvpb);
-    yb[3] += fma(g.dp[3], rb, 0.0625 * hvpb);
-    wb[2] += upb;
+    d12b += fma(g.dp[0], rb, hX * W1);
+    d23b += fma(g.dp[1], rb, hX * W2);
+    yb[1] += g.dp[2] * rb;
+    yb[3] += g.dp[3] * rb;
     double b0b = 0.0;
     weights_bwd(b0, b12, b23, e12, e23, g.eps, W0b, W1b, W2b, b0b, b12b, b23b, e12b, e23b);
     beta0_bwd(d12, d23, y1, y3, b0b, d12b, d23b, yb[1], yb[3]);
@@ -262,19 +153,15 @@ __device__ __forceinline__ void face_field_bwd_saved(double w0, double w1, doubl
   b01b += e01b;
   b12b += e12b;
   b23b += e23b;
-  d01b += 2.0 * d01 * b01b;
-  d12b += 2.0 * d12 * b12b;
-  d23b += 2.0 * d23 * b23b;
-  wb[0] -= d01b;
-  wb[1] += d01b - d12b;
-  wb[2] += d12b - d23b;
-  wb[3] += d23b;
+  db[0] += fma(2.0 * d01, b01b, d01b);
+  db[1] += fma(2.0 * d12, b12b, d12b);
+  db[2] += fma(2.0 * d23, b23b, d23b);
 }
 
-// cell_field saving [b0, W0, W1, W2, t, num, 1/den]
-__device__ __forceinline__ double cell_field_save(double w0, double w1, double w2, double y0, double y2,
-                                                  const Grid& g, double* sv, int stride) {
-  const double d01 = w1 - w0, d12 = w2 - w1;
+// The limiter (Eq. limiter) of one characteristic field from the differences d01 = w1 - w0,
+// d12 = w2 - w1 and the scaled derivatives y0, y2: h v~_i, saving [b0, W0, W1, W2, t, num, 1/den].
+__device__ __forceinline__ double cell_field_save(double d01, double d12, double y0, double y2, const Grid& g,
+                                                  double* sv, int stride) {
   const double b1 = d01 * d01, b2 = d12 * d12;
   double du, svs;
   const double b0 = beta0(d01, d12, y0, y2, du, svs);
@@ -292,11 +179,11 @@ __device__ __forceinline__ double cell_field_save(double w0, double w1, double w
   return num * inv;
 }
 
-// Backward of cell_field_save (the limiter) from its saved values.
-__device__ __forceinline__ void cell_field_bwd_saved(double w0, double w1, double w2, double y0, double y2,
-                                                     const Grid& g, double outb, const double* sv, int stride,
-                                                     double* wb, double& y0b, double& y2b) {
-  const double d01 = w1 - w0, d12 = w2 - w1;
+// Backward of cell_field_save from its saved values: given the adjoint of its output, adds those
+// of d01, d12 (db) and y0, y2.
+__device__ __forceinline__ void cell_field_bwd_saved(double d01, double d12, double y0, double y2, const Grid& g,
+                                                     double outb, const double* sv, int stride, double* db,
+                                                     double& y0b, double& y2b) {
   const double b1 = d01 * d01, b2 = d12 * d12;
   const double e1 = b1 + g.eps, e2 = b2 + g.eps;
   const double b0 = sv[0], W0 = sv[stride], W1 = sv[2 * stride], W2 = sv[3 * stride];
@@ -316,11 +203,8 @@ __device__ __forceinline__ void cell_field_bwd_saved(double w0, double w1, doubl
   beta0_bwd(d01, d12, y0, y2, b0b, d01b, d12b, y0b, y2b);
   b1b += e1b;
   b2b += e2b;
-  d01b += 2.0 * d01 * b1b;
-  d12b += 2.0 * d12 * b2b;
-  wb[0] -= d01b;
-  wb[1] += d01b - d12b;
-  wb[2] += d12b;
+  db[0] += fma(2.0 * d01, b1b, d01b);
+  db[1] += fma(2.0 * d12, b2b, d12b);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -154,56 +154,18 @@ __device__ __forceinline__ Wts weights_e(double e0, double e1, double e2) {
   return w;
 }
 
-// One characteristic field at one face k+1/2 from the four cells k-1..k+2 (values w0..w3,
-// scaled derivatives y0..y3):  u^- and h v^- from the stencil of cell k (Eqs. Pxi, P'xi,
-// interp), u^+ and h v^+ from the stencil of cell k+1 evaluated at its left face (the mirror
-// image about x_{k+1}).  gamma1 = gamma2; both weight sets normalise with one reciprocal each.
-__device__ __forceinline__ void face_field(double w0, double w1, double w2, double w3, double y0, double y1,
-                                           double y2, double y3, const Grid& g, double& um, double& hvm,
-                                           double& up, double& hvp, bool vw = false) {
-  // Every candidate reproduces constants and the candidates' value coefficients sum to G, so each
-  // value is written as the centre value plus a combination of cell differences:
-  //   num / den = u_c + (W0 (r - G u_c) + W1 (p1 - u_c) + W2 (p2 - u_c)) / den,
-  // with p1 - u_c and p2 - u_c half a cell difference each.
-  const double d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2;
-  const double b01 = d01 * d01, b12 = d12 * d12, b23 = d23 * d23;
-  const double e01 = b01 + g.eps, e12 = b12 + g.eps, e23 = b23 + g.eps;
-  double du, sv;
-  {
-    // stencil of cell k: u_{i-1..i+1} = w0, w1, w2; candidates on {i-1, i} (W1), {i, i+1} (W2)
-    const double b0 = beta0(d01, d12, y0, y2, du, sv);
-    const Wts wt = weights(b0, b01, b12, e01, e12, g.eps);
-    const double r = fma(g.dm[0], d01, fma(g.dm[1], d12, fma(g.dm[2], y0, g.dm[3] * y2)));
-    const double sl = fma(wt.W1, d01, wt.W2 * d12);
-    const double den = fma(g.G, wt.W0, wt.W1 + wt.W2);
-    const double rden = rcp(den);
-    um = fma(fma(wt.W0, r, 0.5 * sl), rden, w1);
-    hvm = fma(1.3125, d12, fma(-0.1875, d01, fma(0.0625, y0, -0.1875 * y2)));
-    // weighted: the same combination of h p0', h p1' = d01, h p2' = d12
-    if (vw) hvm = fma(wt.W0, fma(hvm, g.ig1, -du), sl) * rden;
-  }
-  {
-    // stencil of cell k+1: u_{i-1..i+1} = w1, w2, w3; its candidate on {i, i+1} carries beta2,
-    // the one on {i-1, i} carries beta1 (mirror image)
-    const double b0 = beta0(d12, d23, y1, y3, du, sv);
-    const Wts wt = weights(b0, b12, b23, e12, e23, g.eps);
-    const double r = fma(g.dp[0], d12, fma(g.dp[1], d23, fma(g.dp[2], y1, g.dp[3] * y3)));
-    const double sl = fma(wt.W1, d12, wt.W2 * d23);
-    const double den = fma(g.G, wt.W0, wt.W1 + wt.W2);
-    const double rden = rcp(den);
-    up = fma(fma(wt.W0, r, -0.5 * sl), rden, w2);
-    hvp = fma(1.3125, d12, fma(-0.1875, d23, fma(-0.1875, y1, 0.0625 * y3)));
-    if (vw) hvp = fma(wt.W0, fma(hvp, g.ig1, -du), sl) * rden;
-  }
-}
-
-// face_field on differences, with unscaled derivatives along direction dir (the forward kernels'
-// form; the scaled one above serves the adjoint).  In: d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2
-// of one characteristic field over the cells k-1..k+2 and their derivatives y0..y3.  Out: um, up =
-// the interface values less the centre values w1, w2, added to bm, bp (the centre values for a
-// scalar law, zero where the caller adds the centre states in conserved variables); with VW (the
-// weighted-derivative option), the weighted derivatives vm, vp (the unweighted ones are linear in
-// the stencil and formed by the caller).
+// One characteristic field at one face k+1/2: u^- from the stencil of cell k (Eqs. Pxi, P'xi,
+// interp) and u^+ from the stencil of cell k+1 evaluated at its left face (the mirror image about
+// x_{k+1}); gamma1 = gamma2, and each weight set normalises with one reciprocal.  Every candidate
+// reproduces constants and the candidates' value coefficients sum to G, so each value is the centre
+// value plus a combination of cell differences:
+//   num / den = u_c + (W0 (r - G u_c) + W1 (p1 - u_c) + W2 (p2 - u_c)) / den,
+// with p1 - u_c and p2 - u_c half a cell difference each.  In: d01 = w1 - w0, d12 = w2 - w1,
+// d23 = w3 - w2 over the cells k-1..k+2 and their derivatives y0..y3 along direction dir
+// (unscaled).  Out: um, up = the interface values less the centre values w1, w2, added to bm, bp
+// (the centre values for a scalar law, zero where the caller adds the centre states in conserved
+// variables); with VW (the weighted-derivative option), the weighted derivatives vm, vp (the
+// unweighted ones are linear in the stencil and formed by the caller).
 template <bool VW>
 __device__ __forceinline__ void face_field_d(double d01, double d12, double d23, double y0, double y1, double y2,
                                              double y3, double bm, double bp, const Grid& g, int dir, double& um,
@@ -280,23 +242,10 @@ __device__ __forceinline__ void cell_faces_field(double d01, double d12, double 
   hvt = fma(wt.W0, t, sl) * rcp(fma(g.Gd, wt.W0, wt.W1 + wt.W2));
 }
 
-// h v~_i of one characteristic field (Eq. limiter with the derivatives of Eq. limiter-p) from
-// w0..w2 = u_{i-1..i+1} and y0, y2 = h v_{i-1}, h v_{i+1}.
-__device__ __forceinline__ double cell_field(double w0, double w1, double w2, double y0, double y2, const Grid& g) {
-  const double d01 = w1 - w0, d12 = w2 - w1;
-  const double b1 = d01 * d01, b2 = d12 * d12;
-  double du, sv;
-  const double b0 = beta0(d01, d12, y0, y2, du, sv);
-  const Wts wt = weights(b0, b1, b2, b1 + g.eps, b2 + g.eps, g.eps);
-  // (h p0'(x_i) - d1 (h p1' + h p2')) / d1 = cdu du - csv sv;  h p1' = d01, h p2' = d12
-  const double t = fma(g.cdu, du, -g.csv * sv);
-  const double num = fma(wt.W0, t, fma(wt.W1, d01, wt.W2 * d12));
-  const double den = fma(g.Gd, wt.W0, wt.W1 + wt.W2);
-  return num * rcp(den);
-}
-
-// cell_field on differences d01 = w1 - w0, d12 = w2 - w1 with unscaled derivatives y0 = v_{i-1},
-// y2 = v_{i+1} along direction dir; returns h v~_i as cell_field does.
+// h v~_i of one characteristic field (Eq. limiter with the derivatives of Eq. limiter-p) from the
+// differences d01 = w1 - w0, d12 = w2 - w1 of u_{i-1..i+1} and the unscaled derivatives
+// y0 = v_{i-1}, y2 = v_{i+1} along direction dir:
+//   (h p0'(x_i) - d1 (h p1' + h p2')) / d1 = cdu du - csv h sv,  h p1' = d01, h p2' = d12.
 __device__ __forceinline__ double cell_field_d(double d01, double d12, double y0, double y2, const Grid& g, int dir) {
   double du, sv;
   const double e0 = beta0_eps(d01, d12, y0, y2, g, dir, du, sv);
