@@ -37,7 +37,8 @@ struct Work {
   double* FY;    // y-face fluxes: [NF][NC][ny+1][nx]
   unsigned long long* alpha;  // wavespeed slots (bit patterns of non-negative doubles): slot s of
                               // direction d at alpha[s * astride + d]
-  double* scal;               // [0] dt of the current step, [1] t, [2] t_end, [3] steps taken
+  double* scal;               // [0] dt of the current step, [1] t, [2] t_end, [3] steps taken,
+                              // [4..7] zero (read by fu_of; never written after creation)
   unsigned int* status;       // bit 0: non-physical state met
   long long astride;          // distance between slots (2 for a single grid)
   // R2 only: face states of every cell, normal frame:
@@ -52,6 +53,13 @@ struct Work {
 };
 
 constexpr int kThreads = 128;
+
+// The units of FU in thread registers: a zero read at a per-thread address of the zeroed slots
+// scal[4..7], so that the compiler can neither fold it nor keep it in a uniform register.
+__device__ __forceinline__ FU fu_of(const double* scal) {
+  const double z = scal[4 + (threadIdx.x & 3)];
+  return FU{1.0 + z, -z};
+}
 
 template <int NC>
 __device__ __forceinline__ void swap_frame(double* q) {
@@ -97,18 +105,19 @@ __device__ __forceinline__ void block_max2(double a, double b, unsigned long lon
 // the two conserved differences are projected (equal neighbours give exactly zero).
 template <int NC, int SYS>
 __device__ __forceinline__ void modified_derivative(const double (&U3)[3][NC], const double (&D3)[3][NC],
-                                                    const Eig<NC>& e, int dir, const Grid& g, double* out) {
+                                                    const Eig<NC>& e, int dir, const Grid& g, double* out,
+                                                    const FU& f) {
   const double ih = g.ih[dir];
   double dU[2][NC], Dq[2][NC], Zm[NC], Zp[NC];
 #pragma unroll
   for (int q = 0; q < 2; ++q)
 #pragma unroll
-    for (int k = 0; k < NC; ++k) dU[q][k] = U3[q + 1][k] - U3[q][k];
+    for (int k = 0; k < NC; ++k) dU[q][k] = f.sub(U3[q + 1][k], U3[q][k]);
   if (SYS == SYS_EULER) {
-    e.project(dU[0], Dq[0]);
-    e.project(dU[1], Dq[1]);
-    e.project(D3[0], Zm);
-    e.project(D3[2], Zp);
+    e.project(dU[0], Dq[0], f);
+    e.project(dU[1], Dq[1], f);
+    e.project(D3[0], Zm, f);
+    e.project(D3[2], Zp, f);
   } else {
     Dq[0][0] = dU[0][0];
     Dq[1][0] = dU[1][0];
@@ -117,9 +126,9 @@ __device__ __forceinline__ void modified_derivative(const double (&U3)[3][NC], c
   }
   double ht[NC];
 #pragma unroll
-  for (int s = 0; s < NC; ++s) ht[s] = cell_field_d(Dq[0][s], Dq[1][s], Zm[s], Zp[s], g, dir) * ih;
+  for (int s = 0; s < NC; ++s) ht[s] = cell_field_d(Dq[0][s], Dq[1][s], Zm[s], Zp[s], g, dir, f) * ih;
   if (SYS == SYS_EULER) {
-    e.back(ht, out);
+    e.back(ht, out, f);
   } else {
     out[0] = ht[0];
   }
@@ -173,13 +182,13 @@ __device__ __forceinline__ void load_stencil3(const Grid& g, const double* __res
 // face derivatives are linear in the stencil and are formed in conserved variables.
 template <int NC, int SYS, bool VW>
 __device__ __forceinline__ void r2_cell_vw(const double (&U3)[3][NC], const double (&D3)[3][NC], const Eig<NC>& e,
-                                           int dir, const Grid& g, double* md, double (&fs)[4][NC]) {
+                                           int dir, const Grid& g, double* md, double (&fs)[4][NC], const FU& f) {
   const double ih = g.ih[dir];
   double dU[2][NC], Dq[2][NC], Zm[NC], Zp[NC];
 #pragma unroll
   for (int q = 0; q < 2; ++q)
 #pragma unroll
-    for (int k = 0; k < NC; ++k) dU[q][k] = U3[q + 1][k] - U3[q][k];
+    for (int k = 0; k < NC; ++k) dU[q][k] = f.sub(U3[q + 1][k], U3[q][k]);
   if (!VW) {
     // the Hermite derivative of Eq. (P'xi) at the two faces (linear in the stencil)
     const double k21 = g.uvd[dir][0], k3 = g.uvd[dir][1];
@@ -190,10 +199,10 @@ __device__ __forceinline__ void r2_cell_vw(const double (&U3)[3][NC], const doub
     }
   }
   if (SYS == SYS_EULER) {
-    e.project(dU[0], Dq[0]);
-    e.project(dU[1], Dq[1]);
-    e.project(D3[0], Zm);
-    e.project(D3[2], Zp);
+    e.project(dU[0], Dq[0], f);
+    e.project(dU[1], Dq[1], f);
+    e.project(D3[0], Zm, f);
+    e.project(D3[2], Zp, f);
   } else {
     Dq[0][0] = dU[0][0];
     Dq[1][0] = dU[1][0];
@@ -204,13 +213,13 @@ __device__ __forceinline__ void r2_cell_vw(const double (&U3)[3][NC], const doub
   double cm[NC], chm[NC], cp[NC], chp[NC], ht[NC];
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
-    cell_faces_field<VW>(Dq[0][s], Dq[1][s], Zm[s], Zp[s], bc, g, dir, cm[s], chm[s], cp[s], chp[s], ht[s]);
+    cell_faces_field<VW>(Dq[0][s], Dq[1][s], Zm[s], Zp[s], bc, g, dir, cm[s], chm[s], cp[s], chp[s], ht[s], f);
     ht[s] *= ih;
   }
   if (SYS == SYS_EULER) {
-    e.back_add(cm, U3[1], fs[0]);
-    e.back_add(cp, U3[1], fs[2]);
-    e.back(ht, md);
+    e.back_add(cm, U3[1], fs[0], f);
+    e.back_add(cp, U3[1], fs[2], f);
+    e.back(ht, md, f);
   } else {
     fs[0][0] = cm[0];
     fs[2][0] = cp[0];
@@ -218,8 +227,8 @@ __device__ __forceinline__ void r2_cell_vw(const double (&U3)[3][NC], const doub
   }
   if (VW) {
     if (SYS == SYS_EULER) {
-      e.back(chm, fs[1]);
-      e.back(chp, fs[3]);
+      e.back(chm, fs[1], f);
+      e.back(chp, fs[3], f);
     } else {
       fs[1][0] = chm[0];
       fs[3][0] = chp[0];
@@ -230,11 +239,11 @@ __device__ __forceinline__ void r2_cell_vw(const double (&U3)[3][NC], const doub
 // r2_cell_vw with the weighted-derivative option read from the grid's flags (one code path each)
 template <int NC, int SYS>
 __device__ __forceinline__ void r2_cell(const double (&U3)[3][NC], const double (&D3)[3][NC], const Eig<NC>& e,
-                                        int dir, const Grid& g, double* md, double (&fs)[4][NC]) {
+                                        int dir, const Grid& g, double* md, double (&fs)[4][NC], const FU& f) {
   if (g.flags & FLAG_V_WEIGHTED)
-    r2_cell_vw<NC, SYS, true>(U3, D3, e, dir, g, md, fs);
+    r2_cell_vw<NC, SYS, true>(U3, D3, e, dir, g, md, fs, f);
   else
-    r2_cell_vw<NC, SYS, false>(U3, D3, e, dir, g, md, fs);
+    r2_cell_vw<NC, SYS, false>(U3, D3, e, dir, g, md, fs, f);
 }
 
 // Cell work of one stage at cell p: primitives and wavespeeds (returned in wsx, wsy), nodal
@@ -245,6 +254,7 @@ __device__ __forceinline__ void cell_body(const Grid& g, const double* __restric
   using T = Traits<DIM, SYS>;
   constexpr int NC = T::NC, NG = T::NG;
   const long long plane = g.plane;
+  const FU f = fu_of(w.scal);
   {
     const int i = (int)(p % g.nx), j = (int)(p / g.nx);
     double U[NC], V[NC], Wd[NC];
@@ -257,15 +267,15 @@ __device__ __forceinline__ void cell_body(const Grid& g, const double* __restric
     // primitives and wavespeeds
     double u = 0, v = 0, pr = 0, ir = 0, H = 0, c = 0, ic = 0;
     if (SYS == SYS_EULER) {
-      ir = rcp(U[0]);
-      u = U[1] * ir;
-      if (DIM == 2) v = U[2] * ir;
-      const double ke = DIM == 2 ? fma(U[1], u, U[2] * v) : U[1] * u;
+      ir = rcp(U[0], f);
+      u = f.mul(U[1], ir);
+      if (DIM == 2) v = f.mul(U[2], ir);
+      const double ke = DIM == 2 ? fma(U[1], u, f.mul(U[2], v)) : f.mul(U[1], u);
       pr = g.gm1 * fma(-0.5, ke, U[NC - 1]);
-      H = (U[NC - 1] + pr) * ir;
-      const double c2 = g.gamma * pr * ir;
+      H = f.mul(f.add(U[NC - 1], pr), ir);
+      const double c2 = f.mul(g.gamma * pr, ir);
       ic = rsqrt(c2);
-      c = c2 * ic;
+      c = f.mul(c2, ic);
       wsx = fabs(u) + c;
       wsy = DIM == 2 ? fabs(v) + c : 0.0;
       if (!(U[0] > 0.0) || !(pr > 0.0) || !isfinite(wsx) || !isfinite(wsy)) atomicOr(w.status, 1u);
@@ -292,8 +302,8 @@ __device__ __forceinline__ void cell_body(const Grid& g, const double* __restric
     // primitive derivatives along V and W (2D Euler: shared by the Jacobians of both directions)
     double pdV[3] = {0.0, 0.0, 0.0}, pdW[3] = {0.0, 0.0, 0.0};
     if (SYS == SYS_EULER && DIM == 2) {
-      Phys<2, SYS_EULER>::prim_deriv(U, u, v, ir, V, g.gm1, pdV[0], pdV[1], pdV[2]);
-      Phys<2, SYS_EULER>::prim_deriv(U, u, v, ir, Wd, g.gm1, pdW[0], pdW[1], pdW[2]);
+      Phys<2, SYS_EULER>::prim_deriv(U, u, v, ir, V, g.gm1, pdV[0], pdV[1], pdV[2], f);
+      Phys<2, SYS_EULER>::prim_deriv(U, u, v, ir, Wd, g.gm1, pdW[0], pdW[1], pdW[2], f);
     }
     // nodal values per direction (normal frame)
 #pragma unroll
@@ -315,18 +325,18 @@ __device__ __forceinline__ void cell_body(const Grid& g, const double* __restric
         const double un = d == 0 ? u : v;
         F[0] = Un[1];
         F[1] = fma(Un[1], un, pr);
-        if (DIM == 2) F[2] = Un[2] * un;
-        F[NC - 1] = (Un[NC - 1] + pr) * un;
+        if (DIM == 2) F[2] = f.mul(Un[2], un);
+        F[NC - 1] = f.mul(f.add(Un[NC - 1], pr), un);
         if (DIM == 2) {
           // own-direction field (V in x, W in y) and the other one, each with its normal-velocity
           // derivative (u' in x, v' in y)
           const double* po = d == 0 ? pdV : pdW;
           const double* pt = d == 0 ? pdW : pdV;
-          const double hp = U[NC - 1] + pr;
-          Phys<2, SYS_EULER>::jvp_apply(Un, Dn, un, po[d], po[2], hp, Hn);
-          Phys<2, SYS_EULER>::jvp_apply(Un, On, un, pt[d], pt[2], hp, Mx);
+          const double hp = f.add(U[NC - 1], pr);
+          Phys<2, SYS_EULER>::jvp_apply(Un, Dn, un, po[d], po[2], hp, Hn, f);
+          Phys<2, SYS_EULER>::jvp_apply(Un, On, un, pt[d], pt[2], hp, Mx, f);
         } else {
-          Phys<1, SYS_EULER>::jvp_prim(Un, un, pr, ir, Dn, Hn, g.gm1);
+          Phys<1, SYS_EULER>::jvp_prim(Un, un, pr, ir, Dn, Hn, g.gm1, f);
         }
       } else {
         Phys<DIM, SYS>::flux(Un, F, a, g.gm1);
@@ -352,14 +362,14 @@ __device__ __forceinline__ void cell_body(const Grid& g, const double* __restric
       double out[NC];
       if (VAR == 2) {
         double fs[4][NC];
-        r2_cell<NC, SYS>(U3, D3, e, d, g, out, fs);
+        r2_cell<NC, SYS>(U3, D3, e, d, g, out, fs, f);
         double* FSd = w.FS + (long long)d * 4 * NC * plane;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
           for (int k = 0; k < NC; ++k) FSd[(q * NC + k) * plane + p] = fs[q][k];
       } else {
-        modified_derivative<NC, SYS>(U3, D3, e, d, g, out);
+        modified_derivative<NC, SYS>(U3, D3, e, d, g, out, f);
       }
       if (SYS == SYS_EULER && d == 1) swap_frame<NC>(out);
 #pragma unroll
@@ -385,12 +395,12 @@ __global__ void __launch_bounds__(kThreads) k_cell(Grid g, const double* __restr
 template <int NC, int SYS, bool VW>
 __device__ __forceinline__ void r1_face_states(const double (&Uq)[4][NC], const double (&Zq)[4][NC],
                                                const Eig<NC>& e, const Grid& g, int dir, double* Um, double* Up,
-                                               double* Dm, double* Dp) {
+                                               double* Dm, double* Dp, const FU& f) {
   double dU[3][NC];
 #pragma unroll
   for (int q = 0; q < 3; ++q)
 #pragma unroll
-    for (int k = 0; k < NC; ++k) dU[q][k] = Uq[q + 1][k] - Uq[q][k];
+    for (int k = 0; k < NC; ++k) dU[q][k] = f.sub(Uq[q + 1][k], Uq[q][k]);
   if (!VW) {
     // the Hermite derivative of Eq. (P'xi) at the face from both sides (linear in the stencil,
     // formed first so that the differences and derivatives are not held through the fields)
@@ -404,9 +414,9 @@ __device__ __forceinline__ void r1_face_states(const double (&Uq)[4][NC], const 
   double Dq[3][NC], Yq[4][NC];
   if (SYS == SYS_EULER) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) e.project(dU[q], Dq[q]);
+    for (int q = 0; q < 3; ++q) e.project(dU[q], Dq[q], f);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) e.project(Zq[q], Yq[q]);
+    for (int q = 0; q < 4; ++q) e.project(Zq[q], Yq[q], f);
   } else {
 #pragma unroll
     for (int q = 0; q < 3; ++q) Dq[q][0] = dU[q][0];
@@ -420,19 +430,19 @@ __device__ __forceinline__ void r1_face_states(const double (&Uq)[4][NC], const 
 #pragma unroll
   for (int s = 0; s < NC; ++s)
     face_field_d<VW>(Dq[0][s], Dq[1][s], Dq[2][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], bm, bp, g, dir, cm[s],
-                     chm[s], cp[s], chp[s]);
+                     chm[s], cp[s], chp[s], f);
   // back to conserved variables
   if (SYS == SYS_EULER) {
-    e.back_add(cm, Uq[1], Um);
-    e.back_add(cp, Uq[2], Up);
+    e.back_add(cm, Uq[1], Um, f);
+    e.back_add(cp, Uq[2], Up, f);
   } else {
     Um[0] = cm[0];
     Up[0] = cp[0];
   }
   if (VW) {
     if (SYS == SYS_EULER) {
-      e.back(chm, Dm);
-      e.back(chp, Dp);
+      e.back(chm, Dm, f);
+      e.back(chp, Dp, f);
     } else {
       Dm[0] = chm[0];
       Dp[0] = chp[0];
@@ -449,6 +459,7 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
   using T = Traits<DIM, SYS>;
   constexpr int NC = T::NC, NG = T::NG;
   const long long plane = g.plane;
+  const FU fu = fu_of(w.scal);
   const int n = dir == 0 ? g.nx : g.ny;
   int fa, line;
   if (dir == 0) {
@@ -533,18 +544,18 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
         if (DIM == 2) vr = P[ov];
         Hr = P[oh];
       }
-      const double iw = rcp(sl + sr);
-      const double ub = fma(sl, ul, sr * ur) * iw;
-      const double vb = DIM == 2 ? fma(sl, vl, sr * vr) * iw : 0.0;
-      const double Hb = fma(sl, Hl, sr * Hr) * iw;
-      const double c2 = g.gm1 * fma(-0.5, DIM == 2 ? fma(ub, ub, vb * vb) : ub * ub, Hb);
+      const double iw = rcp(fu.add(sl, sr), fu);
+      const double ub = fu.mul(fma(sl, ul, fu.mul(sr, ur)), iw);
+      const double vb = DIM == 2 ? fu.mul(fma(sl, vl, fu.mul(sr, vr)), iw) : 0.0;
+      const double Hb = fu.mul(fma(sl, Hl, fu.mul(sr, Hr)), iw);
+      const double c2 = g.gm1 * fma(-0.5, DIM == 2 ? fma(ub, ub, fu.mul(vb, vb)) : fu.mul(ub, ub), Hb);
       const double ic = rsqrt(c2);
-      e.setup(ub, vb, Hb, c2 * ic, ic, g.gm1);
+      e.setup(ub, vb, Hb, fu.mul(c2, ic), ic, g.gm1);
     }
     if (VAR && (g.flags & FLAG_V_WEIGHTED))
-      r1_face_states<NC, SYS, true>(Uq, Zq, e, g, dir, Um, Up, Dm, Dp);
+      r1_face_states<NC, SYS, true>(Uq, Zq, e, g, dir, Um, Up, Dm, Dp, fu);
     else
-      r1_face_states<NC, SYS, false>(Uq, Zq, e, g, dir, Um, Up, Dm, Dp);
+      r1_face_states<NC, SYS, false>(Uq, Zq, e, g, dir, Um, Up, Dm, Dp, fu);
   }
   // local LF: the larger spectral radius of the two cells of the face
   if (VAR && (g.flags & FLAG_ALPHA_LOCAL)) {
@@ -555,8 +566,8 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
   // Lax-Friedrichs fluxes at the interpolated states (Eq. flux-LF)
   const double a_adv = dir == 0 ? g.ax : g.ay;
   double FUm[NC], FUp[NC], HDm[NC], HDp[NC];
-  Phys<DIM, SYS>::flux_jvp(Um, Dm, FUm, HDm, a_adv, g.gm1);
-  Phys<DIM, SYS>::flux_jvp(Up, Dp, FUp, HDp, a_adv, g.gm1);
+  Phys<DIM, SYS>::flux_jvp(Um, Dm, FUm, HDm, a_adv, g.gm1, fu);
+  Phys<DIM, SYS>::flux_jvp(Up, Dp, FUp, HDp, a_adv, g.gm1, fu);
   const double* nod = w.NOD + (long long)dir * NG * NC * plane;
   double* out = dir == 0 ? w.FX : w.FY;
   const long long oplane = dir == 0 ? (long long)g.ny * (g.nx + 1) : (long long)(g.ny + 1) * g.nx;
@@ -586,15 +597,15 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
     double Df, Dh;
     if (cd2) {
       // D-terms (Eqs. Cd-2, DfDh)
-      Df = fma(DCoef2::cf, (f0 - f1) + (f3 - f2), g.c2h[dir] * (ha - hb));
-      Dh = fma(g.e2fih[dir], f0 - f3, fma(g.e2gih[dir], f1 - f2, DCoef2::eh * (ha + hb)));
+      Df = fma(DCoef2::cf, fu.add(fu.sub(f0, f1), fu.sub(f3, f2)), g.c2h[dir] * fu.sub(ha, hb));
+      Dh = fma(g.e2fih[dir], fu.sub(f0, f3), fma(g.e2gih[dir], fu.sub(f1, f2), DCoef2::eh * fu.add(ha, hb)));
     } else {
       // D-terms (Eqs. Cd-1, DfDh)
-      Df = fma(DCoef::cf, (f0 - f1) + (f3 - f2), g.chh[dir] * (ha - hb));
-      Dh = fma(g.efih[dir], f0 - f3, fma(g.egih[dir], f2 - f1, DCoef::eh * (ha + hb)));
+      Df = fma(DCoef::cf, fu.add(fu.sub(f0, f1), fu.sub(f3, f2)), g.chh[dir] * fu.sub(ha, hb));
+      Dh = fma(g.efih[dir], fu.sub(f0, f3), fma(g.egih[dir], fu.sub(f2, f1), DCoef::eh * fu.add(ha, hb)));
     }
-    fh[k] = fma(0.5, fma(-alpha, Up[k] - Um[k], FUm[k] + FUp[k]), Df);
-    hh[k] = fma(0.5, fma(-alpha, Dp[k] - Dm[k], HDm[k] + HDp[k]), Dh);
+    fh[k] = fma(0.5, fma(-alpha, fu.sub(Up[k], Um[k]), fu.add(FUm[k], FUp[k])), Df);
+    hh[k] = fma(0.5, fma(-alpha, fu.sub(Dp[k], Dm[k]), fu.add(HDm[k], HDp[k])), Dh);
     if (DIM == 2) {
       double o0 = neg_if(nod[(2 * NC + k) * plane + pc[0]], s0);
       double o1 = neg_if(nod[(2 * NC + k) * plane + pc[1]], s1);
@@ -607,7 +618,7 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
         if (fixed[3]) o3 = 0.0;
       }
       // Eq. (mixed)
-      mh[k] = fma(7.0 / 12.0, o1 + o2, (-1.0 / 12.0) * (o0 + o3));
+      mh[k] = fma(7.0 / 12.0, fu.add(o1, o2), (-1.0 / 12.0) * fu.add(o0, o3));
     }
   }
   if (SYS == SYS_EULER && dir == 1) {
@@ -624,7 +635,7 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
 }
 
 template <int DIM, int SYS, int VAR>
-__global__ void __launch_bounds__(kThreads) k_face(Grid g, const double* __restrict__ S, Work w, int slot) {
+__global__ void __launch_bounds__(kThreads, 4) k_face(Grid g, const double* __restrict__ S, Work w, int slot) {
   const int dir = blockIdx.y;
   const int n = dir == 0 ? g.nx : g.ny;
   const int nlines = dir == 0 ? g.ny : g.nx;
@@ -748,7 +759,7 @@ __global__ void __launch_bounds__(kThreads) k_r2_ghost(Grid g, const double* __r
   Eig<NC> e;
   e.setup(u, v, H, c2 * ic, ic, g.gm1);
   double md[NC], fs[4][NC];
-  r2_cell<NC, SYS_EULER>(U3, D3, e, dir, g, md, fs);
+  r2_cell<NC, SYS_EULER>(U3, D3, e, dir, g, md, fs, fu_of(w.scal));
   double* G = w.GFS + (long long)(dir * 2 + end) * 2 * NC * gs;
   const int q0 = end == 0 ? 0 : 2;
 #pragma unroll

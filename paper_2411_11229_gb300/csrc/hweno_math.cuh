@@ -71,16 +71,31 @@ struct Grid {
   double fixU[4][4], fixP[4][4], fixF[4][4], fixA[4];
 };
 
+// FP64 issue on this GPU (measured with independent chains per thread): a DFMA whose three operands
+// are thread registers issues at 1.9 per SM-clock; DADD, DMUL, and a DFMA with an immediate,
+// constant-bank or block-uniform operand, at 1.6.  The forward kernels therefore issue their sums,
+// differences and products of register values as DFMAs against 1 and -0 held in thread registers:
+// fma(a, 1, b) = a + b and fma(a, b, -0) = a b exactly (the same rounding, signed zeros included).
+// FU carries the two units; the kernels load them through memory the compiler cannot see into
+// (fu_of), and the default FU{1, -0} folds back to plain sums and products.
+struct FU {
+  double one, mz;
+  __device__ __forceinline__ double add(double a, double b) const { return fma(a, one, b); }
+  __device__ __forceinline__ double sub(double a, double b) const { return fma(a, one, -b); }
+  __device__ __forceinline__ double mul(double a, double b) const { return fma(a, b, mz); }
+};
+#define HW_PLAIN_FU FU{1.0, -0.0}
+
 // 1/x for normal, finite x: the hardware approximation (rcp.approx.ftz.f64, relative error up to
 // about 2^-20 on this GPU) refined by one third-order step.  With e = 1 - x r the exact reciprocal
 // is r / (1 - e) = r (1 + e + e^2 + ...); keeping the series to e^2 leaves a relative error of
 // order e^3 (about 2^-60), so the result is within one unit in the last place (measured: 1 ulp at
 // most, on 0.03 % of inputs).  Three FMAs, against four for two Newton-Raphson steps
 // r <- r + r (1 - x r).
-__device__ __forceinline__ double rcp(double x) {
+__device__ __forceinline__ double rcp(double x, const FU& f = HW_PLAIN_FU) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  const double e = fma(-x, r, 1.0);
+  const double e = fma(-x, r, f.one);
   return fma(r, fma(e, e, e), r);
 }
 __device__ __forceinline__ double sqr(double x) { return x * x; }
@@ -112,9 +127,9 @@ __device__ __forceinline__ double beta0(double dm, double dp, double hvm, double
 // S2 (dv + N2 d2)^2 + T2 d2^2 (S, N per direction, T independent of h), a sum of four non-negative
 // terms, and eps enters as the first addend.  Returns beta0 + eps, du = dm + dp and sv = vm + vp.
 __device__ __forceinline__ double beta0_eps(double dm, double dp, double vm, double vp, const Grid& g, int dir,
-                                            double& du_out, double& sv_out) {
-  const double du = dm + dp, d2 = dp - dm;
-  const double sv = vm + vp, dv = vm - vp;
+                                            double& du_out, double& sv_out, const FU& f = HW_PLAIN_FU) {
+  const double du = f.add(dm, dp), d2 = f.sub(dp, dm);
+  const double sv = f.add(vm, vp), dv = f.sub(vm, vp);
   const double y1 = fma(g.bN1[dir], du, sv), y2 = fma(g.bN2[dir], d2, dv);
   du_out = du;
   sv_out = sv;
@@ -142,11 +157,11 @@ __device__ __forceinline__ Wts weights(double b0, double b1, double b2, double e
 }
 
 // Weights from e_l = beta_l + eps directly: e_l - e_k stands for beta_l - beta_k in tau.
-__device__ __forceinline__ Wts weights_e(double e0, double e1, double e2) {
-  const double ts = fabs(e0 - e1) + fabs(e0 - e2);
-  const double tau = (0.25 * ts) * ts;
-  const double Q0 = e1 * e2, Q1 = e0 * e2, Q2 = e0 * e1;
-  const double P = Q0 * e0;
+__device__ __forceinline__ Wts weights_e(double e0, double e1, double e2, const FU& f = HW_PLAIN_FU) {
+  const double ts = f.add(fabs(f.sub(e0, e1)), fabs(f.sub(e0, e2)));
+  const double tau = f.mul(0.25 * ts, ts);
+  const double Q0 = f.mul(e1, e2), Q1 = f.mul(e0, e2), Q2 = f.mul(e0, e1);
+  const double P = f.mul(Q0, e0);
   Wts w;
   w.W0 = fma(tau, Q0, P);
   w.W1 = fma(tau, Q1, P);
@@ -169,7 +184,7 @@ __device__ __forceinline__ Wts weights_e(double e0, double e1, double e2) {
 template <bool VW>
 __device__ __forceinline__ void face_field_d(double d01, double d12, double d23, double y0, double y1, double y2,
                                              double y3, double bm, double bp, const Grid& g, int dir, double& um,
-                                             double& vm, double& up, double& vp) {
+                                             double& vm, double& up, double& vp, const FU& f = HW_PLAIN_FU) {
   const double e01 = fma(d01, d01, g.eps), e12 = fma(d12, d12, g.eps), e23 = fma(d23, d23, g.eps);
   const double* cm = g.udm[dir];
   const double* cp = g.udp[dir];
@@ -178,30 +193,30 @@ __device__ __forceinline__ void face_field_d(double d01, double d12, double d23,
   double du, sv;
   {
     // stencil of cell k: candidates on {i-1, i} (W1), {i, i+1} (W2)
-    const double e0 = beta0_eps(d01, d12, y0, y2, g, dir, du, sv);
-    const Wts wt = weights_e(e0, e01, e12);
+    const double e0 = beta0_eps(d01, d12, y0, y2, g, dir, du, sv, f);
+    const Wts wt = weights_e(e0, e01, e12, f);
     const double r = fma(cm[0], d01, fma(cm[1], d12, fma(cm[2], y0, cm[3] * y2)));
-    const double sl = fma(wt.W1, d01, wt.W2 * d12);
-    const double rden = rcp(fma(g.G, wt.W0, wt.W1 + wt.W2));
+    const double sl = fma(wt.W1, d01, f.mul(wt.W2, d12));
+    const double rden = rcp(fma(g.G, wt.W0, f.add(wt.W1, wt.W2)), f);
     um = fma(fma(wt.W0, r, 0.5 * sl), rden, bm);
     if (VW) {
       const double ih = g.ih[dir];
       const double v0 = fma(k21, d12, fma(-k3, d01, fma(0.0625, y0, -0.1875 * y2)));
-      vm = fma(wt.W0, fma(v0, g.ig1, -du * ih), sl * ih) * rden;
+      vm = f.mul(fma(wt.W0, fma(v0, g.ig1, -du * ih), sl * ih), rden);
     }
   }
   {
     // stencil of cell k+1 (mirror image): its candidate on {i, i+1} carries beta2
-    const double e0 = beta0_eps(d12, d23, y1, y3, g, dir, du, sv);
-    const Wts wt = weights_e(e0, e12, e23);
+    const double e0 = beta0_eps(d12, d23, y1, y3, g, dir, du, sv, f);
+    const Wts wt = weights_e(e0, e12, e23, f);
     const double r = fma(cp[0], d12, fma(cp[1], d23, fma(cp[2], y1, cp[3] * y3)));
-    const double sl = fma(wt.W1, d12, wt.W2 * d23);
-    const double rden = rcp(fma(g.G, wt.W0, wt.W1 + wt.W2));
+    const double sl = fma(wt.W1, d12, f.mul(wt.W2, d23));
+    const double rden = rcp(fma(g.G, wt.W0, f.add(wt.W1, wt.W2)), f);
     up = fma(fma(wt.W0, r, -0.5 * sl), rden, bp);
     if (VW) {
       const double ih = g.ih[dir];
       const double v0 = fma(k21, d12, fma(-k3, d23, fma(-0.1875, y1, 0.0625 * y3)));
-      vp = fma(wt.W0, fma(v0, g.ig1, -du * ih), sl * ih) * rden;
+      vp = f.mul(fma(wt.W0, fma(v0, g.ig1, -du * ih), sl * ih), rden);
     }
   }
 }
@@ -214,18 +229,18 @@ __device__ __forceinline__ void face_field_d(double d01, double d12, double d23,
 template <bool VW>
 __device__ __forceinline__ void cell_faces_field(double d01, double d12, double y0, double y2, double bc,
                                                  const Grid& g, int dir, double& um, double& vm, double& up,
-                                                 double& vp, double& hvt) {
+                                                 double& vp, double& hvt, const FU& f = HW_PLAIN_FU) {
   double du, sv;
-  const double e0 = beta0_eps(d01, d12, y0, y2, g, dir, du, sv);
-  const Wts wt = weights_e(e0, fma(d01, d01, g.eps), fma(d12, d12, g.eps));
-  const double rden = rcp(fma(g.G, wt.W0, wt.W1 + wt.W2));
+  const double e0 = beta0_eps(d01, d12, y0, y2, g, dir, du, sv, f);
+  const Wts wt = weights_e(e0, fma(d01, d01, g.eps), fma(d12, d12, g.eps), f);
+  const double rden = rcp(fma(g.G, wt.W0, f.add(wt.W1, wt.W2)), f);
   // the candidates at x_{i+1/2} differ from u_i by (d01, d12)/2, those at x_{i-1/2} by
   // (-d01, -d12)/2, so both faces share W1 d01 + W2 d12
   const double* cm = g.udm[dir];
   const double* cp = g.udp[dir];
   const double rm = fma(cm[0], d01, fma(cm[1], d12, fma(cm[2], y0, cm[3] * y2)));
   const double rp = fma(cp[0], d01, fma(cp[1], d12, fma(cp[2], y0, cp[3] * y2)));
-  const double sl = fma(wt.W1, d01, wt.W2 * d12);
+  const double sl = fma(wt.W1, d01, f.mul(wt.W2, d12));
   const double hs = 0.5 * sl;
   um = fma(fma(wt.W0, rm, hs), rden, bc);
   up = fma(fma(wt.W0, rp, -hs), rden, bc);
@@ -235,25 +250,26 @@ __device__ __forceinline__ void cell_faces_field(double d01, double d12, double 
     const double ih = g.ih[dir], ds = du * ih, ss = sl * ih;
     const double v0m = fma(k21, d12, fma(-k3, d01, fma(0.0625, y0, -0.1875 * y2)));
     const double v0p = fma(k21, d01, fma(-k3, d12, fma(-0.1875, y0, 0.0625 * y2)));
-    vm = fma(wt.W0, fma(v0m, g.ig1, -ds), ss) * rden;
-    vp = fma(wt.W0, fma(v0p, g.ig1, -ds), ss) * rden;
+    vm = f.mul(fma(wt.W0, fma(v0m, g.ig1, -ds), ss), rden);
+    vp = f.mul(fma(wt.W0, fma(v0p, g.ig1, -ds), ss), rden);
   }
   const double t = fma(g.cdu, du, -g.ucsv[dir] * sv);
-  hvt = fma(wt.W0, t, sl) * rcp(fma(g.Gd, wt.W0, wt.W1 + wt.W2));
+  hvt = f.mul(fma(wt.W0, t, sl), rcp(fma(g.Gd, wt.W0, f.add(wt.W1, wt.W2)), f));
 }
 
 // h v~_i of one characteristic field (Eq. limiter with the derivatives of Eq. limiter-p) from the
 // differences d01 = w1 - w0, d12 = w2 - w1 of u_{i-1..i+1} and the unscaled derivatives
 // y0 = v_{i-1}, y2 = v_{i+1} along direction dir:
 //   (h p0'(x_i) - d1 (h p1' + h p2')) / d1 = cdu du - csv h sv,  h p1' = d01, h p2' = d12.
-__device__ __forceinline__ double cell_field_d(double d01, double d12, double y0, double y2, const Grid& g, int dir) {
+__device__ __forceinline__ double cell_field_d(double d01, double d12, double y0, double y2, const Grid& g, int dir,
+                                               const FU& f = HW_PLAIN_FU) {
   double du, sv;
-  const double e0 = beta0_eps(d01, d12, y0, y2, g, dir, du, sv);
-  const Wts wt = weights_e(e0, fma(d01, d01, g.eps), fma(d12, d12, g.eps));
+  const double e0 = beta0_eps(d01, d12, y0, y2, g, dir, du, sv, f);
+  const Wts wt = weights_e(e0, fma(d01, d01, g.eps), fma(d12, d12, g.eps), f);
   const double t = fma(g.cdu, du, -g.ucsv[dir] * sv);
-  const double num = fma(wt.W0, t, fma(wt.W1, d01, wt.W2 * d12));
-  const double den = fma(g.Gd, wt.W0, wt.W1 + wt.W2);
-  return num * rcp(den);
+  const double num = fma(wt.W0, t, fma(wt.W1, d01, f.mul(wt.W2, d12)));
+  const double den = fma(g.Gd, wt.W0, f.add(wt.W1, wt.W2));
+  return f.mul(num, rcp(den, f));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -289,7 +305,8 @@ struct Phys<DIM, SYS_ADV> {
   static constexpr int NC = 1;
   __device__ static void flux(const double* U, double* F, double a, double) { F[0] = a * U[0]; }
   __device__ static void jvp(const double*, const double* D, double* out, double a, double) { out[0] = a * D[0]; }
-  __device__ static void flux_jvp(const double* U, const double* D, double* F, double* out, double a, double gm1) {
+  __device__ static void flux_jvp(const double* U, const double* D, double* F, double* out, double a, double gm1,
+                                  const FU& = HW_PLAIN_FU) {
     flux(U, F, a, gm1);
     jvp(U, D, out, a, gm1);
   }
@@ -300,7 +317,8 @@ struct Phys<DIM, SYS_BURGERS> {
   static constexpr int NC = 1;
   __device__ static void flux(const double* U, double* F, double, double) { F[0] = 0.5 * (U[0] * U[0]); }
   __device__ static void jvp(const double* U, const double* D, double* out, double, double) { out[0] = U[0] * D[0]; }
-  __device__ static void flux_jvp(const double* U, const double* D, double* F, double* out, double a, double gm1) {
+  __device__ static void flux_jvp(const double* U, const double* D, double* F, double* out, double a, double gm1,
+                                  const FU& = HW_PLAIN_FU) {
     flux(U, F, a, gm1);
     jvp(U, D, out, a, gm1);
   }
@@ -320,12 +338,12 @@ struct Phys<1, SYS_EULER> {
   }
   // A(U) D via the chain rule: u' = (m' - u rho')/rho, p' = (gamma-1)(E' - (m' u + m u')/2)
   __device__ static void jvp_prim(const double* U, double u, double p, double ir, const double* D, double* out,
-                                  double gm1) {
-    const double du = fma(-u, D[0], D[1]) * ir;
-    const double dp = gm1 * fma(-0.5, fma(D[1], u, U[1] * du), D[2]);
+                                  double gm1, const FU& f = HW_PLAIN_FU) {
+    const double du = f.mul(fma(-u, D[0], D[1]), ir);
+    const double dp = gm1 * fma(-0.5, fma(D[1], u, f.mul(U[1], du)), D[2]);
     out[0] = D[1];
     out[1] = fma(D[1], u, fma(U[1], du, dp));
-    out[2] = fma(D[2] + dp, u, (U[2] + p) * du);
+    out[2] = fma(f.add(D[2], dp), u, f.mul(f.add(U[2], p), du));
   }
   __device__ static void jvp(const double* U, const double* D, double* out, double, double gm1) {
     const double ir = rcp(U[0]);
@@ -334,14 +352,15 @@ struct Phys<1, SYS_EULER> {
     jvp_prim(U, u, p, ir, D, out, gm1);
   }
   // f(U) and A(U) D with one reciprocal and one pressure
-  __device__ static void flux_jvp(const double* U, const double* D, double* F, double* out, double, double gm1) {
-    const double ir = rcp(U[0]);
-    const double u = U[1] * ir;
+  __device__ static void flux_jvp(const double* U, const double* D, double* F, double* out, double, double gm1,
+                                  const FU& f = HW_PLAIN_FU) {
+    const double ir = rcp(U[0], f);
+    const double u = f.mul(U[1], ir);
     const double p = gm1 * fma(-0.5 * U[1], u, U[2]);
     F[0] = U[1];
     F[1] = fma(U[1], u, p);
-    F[2] = (U[2] + p) * u;
-    jvp_prim(U, u, p, ir, D, out, gm1);
+    F[2] = f.mul(f.add(U[2], p), u);
+    jvp_prim(U, u, p, ir, D, out, gm1, f);
   }
 };
 
@@ -359,16 +378,16 @@ struct Phys<2, SYS_EULER> {
     F[3] = (U[3] + p) * u;
   }
   __device__ static void jvp_prim(const double* U, double u, double v, double p, double ir, const double* D,
-                                  double* out, double gm1) {
-    const double du = fma(-u, D[0], D[1]) * ir;
-    const double dv = fma(-v, D[0], D[2]) * ir;
+                                  double* out, double gm1, const FU& f = HW_PLAIN_FU) {
+    const double du = f.mul(fma(-u, D[0], D[1]), ir);
+    const double dv = f.mul(fma(-v, D[0], D[2]), ir);
     // d/dx of (m u + n v)/2 = (m' u + m u' + n' v + n v')/2
-    const double dk = fma(D[1], u, fma(U[1], du, fma(D[2], v, U[2] * dv)));
+    const double dk = fma(D[1], u, fma(U[1], du, fma(D[2], v, f.mul(U[2], dv))));
     const double dp = gm1 * fma(-0.5, dk, D[3]);
     out[0] = D[1];
     out[1] = fma(D[1], u, fma(U[1], du, dp));
-    out[2] = fma(D[2], u, U[2] * du);
-    out[3] = fma(D[3] + dp, u, (U[3] + p) * du);
+    out[2] = fma(D[2], u, f.mul(U[2], du));
+    out[3] = fma(f.add(D[3], dp), u, f.mul(f.add(U[3], p), du));
   }
   __device__ static void jvp(const double* U, const double* D, double* out, double, double gm1) {
     const double ir = rcp(U[0]);
@@ -380,31 +399,32 @@ struct Phys<2, SYS_EULER> {
   // v' = (n' - v rho')/rho, p' = (gamma-1)(E' - (m' u + m u' + n' v + n v')/2).  They do not depend
   // on the direction, so a cell computes them once per derivative field for both Jacobians.
   __device__ static void prim_deriv(const double* U, double u, double v, double ir, const double* D, double gm1,
-                                    double& du, double& dv, double& dp) {
-    du = fma(-u, D[0], D[1]) * ir;
-    dv = fma(-v, D[0], D[2]) * ir;
-    const double dk = fma(D[1], u, fma(U[1], du, fma(D[2], v, U[2] * dv)));
+                                    double& du, double& dv, double& dp, const FU& f = HW_PLAIN_FU) {
+    du = f.mul(fma(-u, D[0], D[1]), ir);
+    dv = f.mul(fma(-v, D[0], D[2]), ir);
+    const double dk = fma(D[1], u, fma(U[1], du, fma(D[2], v, f.mul(U[2], dv))));
     dp = gm1 * fma(-0.5, dk, D[3]);
   }
   // A(U) D in the normal frame from the primitive derivatives: Un, Dn normal-frame vectors, un
   // the normal velocity, dun its derivative, hp = E + p
   __device__ static void jvp_apply(const double* Un, const double* Dn, double un, double dun, double dp, double hp,
-                                   double* out) {
+                                   double* out, const FU& f = HW_PLAIN_FU) {
     out[0] = Dn[1];
     out[1] = fma(Dn[1], un, fma(Un[1], dun, dp));
-    out[2] = fma(Dn[2], un, Un[2] * dun);
-    out[3] = fma(Dn[3] + dp, un, hp * dun);
+    out[2] = fma(Dn[2], un, f.mul(Un[2], dun));
+    out[3] = fma(f.add(Dn[3], dp), un, f.mul(hp, dun));
   }
   // f(U) and A(U) D with one reciprocal and one pressure
-  __device__ static void flux_jvp(const double* U, const double* D, double* F, double* out, double, double gm1) {
-    const double ir = rcp(U[0]);
-    const double u = U[1] * ir, v = U[2] * ir;
-    const double p = gm1 * fma(-0.5, fma(U[1], u, U[2] * v), U[3]);
+  __device__ static void flux_jvp(const double* U, const double* D, double* F, double* out, double, double gm1,
+                                  const FU& f = HW_PLAIN_FU) {
+    const double ir = rcp(U[0], f);
+    const double u = f.mul(U[1], ir), v = f.mul(U[2], ir);
+    const double p = gm1 * fma(-0.5, fma(U[1], u, f.mul(U[2], v)), U[3]);
     F[0] = U[1];
     F[1] = fma(U[1], u, p);
-    F[2] = U[2] * u;
-    F[3] = (U[3] + p) * u;
-    jvp_prim(U, u, v, p, ir, D, out, gm1);
+    F[2] = f.mul(U[2], u);
+    F[3] = f.mul(f.add(U[3], p), u);
+    jvp_prim(U, u, v, p, ir, D, out, gm1, f);
   }
 };
 
@@ -434,45 +454,46 @@ struct Eig {
     uc = u * c;
   }
 
-  __device__ __forceinline__ void project(const double* q, double* w) const {
-    double k = NC == 4 ? fma(v, q[2], u * q[1]) - q[3] : fma(u, q[1], -q[NC - 1]);
-    const double th = fma(-hb1, k, hb2 * q[0]);  // t/2
-    const double sh = fma(u, q[0], -q[1]) * hic;  // s/2
-    w[0] = th + sh;
+  __device__ __forceinline__ void project(const double* q, double* w, const FU& f = HW_PLAIN_FU) const {
+    double k = NC == 4 ? f.sub(fma(v, q[2], f.mul(u, q[1])), q[3]) : fma(u, q[1], -q[NC - 1]);
+    const double th = fma(-hb1, k, f.mul(hb2, q[0]));  // t/2
+    const double sh = f.mul(fma(u, q[0], -q[1]), hic);  // s/2
+    w[0] = f.add(th, sh);
     w[1] = fma(-2.0, th, q[0]);
     if (NC == 4) {
       w[2] = fma(-v, q[0], q[2]);
-      w[3] = th - sh;
+      w[3] = f.sub(th, sh);
     } else {
-      w[2] = th - sh;
+      w[2] = f.sub(th, sh);
     }
   }
 
   // q = base + R w: the interface state as the centre state plus the back-projected correction
-  __device__ __forceinline__ void back_add(const double* w, const double* base, double* q) const {
+  __device__ __forceinline__ void back_add(const double* w, const double* base, double* q,
+                                           const FU& f = HW_PLAIN_FU) const {
     const double wl = w[0], wr = NC == 4 ? w[3] : w[2];
-    const double sg = wl + wr, dl = wr - wl;
-    const double q0 = sg + w[1];
-    q[0] = base[0] + q0;
+    const double sg = f.add(wl, wr), dl = f.sub(wr, wl);
+    const double q0 = f.add(sg, w[1]);
+    q[0] = f.add(base[0], q0);
     q[1] = fma(u, q0, fma(c, dl, base[1]));
     if (NC == 4) {
-      q[2] = fma(v, q0, w[2] + base[2]);
+      q[2] = fma(v, q0, f.add(w[2], base[2]));
       q[3] = fma(H, sg, fma(hq2, w[1], fma(v, w[2], fma(uc, dl, base[3]))));
     } else {
       q[2] = fma(H, sg, fma(hq2, w[1], fma(uc, dl, base[2])));
     }
   }
 
-  __device__ __forceinline__ void back(const double* w, double* q) const {
+  __device__ __forceinline__ void back(const double* w, double* q, const FU& f = HW_PLAIN_FU) const {
     const double wl = w[0], wr = NC == 4 ? w[3] : w[2];
-    const double sg = wl + wr, dl = wr - wl;
-    q[0] = sg + w[1];
-    q[1] = fma(u, q[0], c * dl);
+    const double sg = f.add(wl, wr), dl = f.sub(wr, wl);
+    q[0] = f.add(sg, w[1]);
+    q[1] = fma(u, q[0], f.mul(c, dl));
     if (NC == 4) {
       q[2] = fma(v, q[0], w[2]);
-      q[3] = fma(H, sg, fma(hq2, w[1], fma(v, w[2], uc * dl)));
+      q[3] = fma(H, sg, fma(hq2, w[1], fma(v, w[2], f.mul(uc, dl))));
     } else {
-      q[2] = fma(H, sg, fma(hq2, w[1], uc * dl));
+      q[2] = fma(H, sg, fma(hq2, w[1], f.mul(uc, dl)));
     }
   }
 };
