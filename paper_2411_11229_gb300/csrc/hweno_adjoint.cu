@@ -26,6 +26,7 @@ struct AdjWork {
   double* CU;  // face contributions to U: [dir][face][4 cells][NC] (original frame)
   double* CD;  // face contributions to the own-direction derivative, same layout
   double* CM;  // modified-derivative contributions: [dir][cell][3 U + 2 D][NC] (original frame)
+  const double* scal;  // the handle's scalars; [4..7] are zero (read by fu_of)
 };
 
 template <int DIM>
@@ -47,6 +48,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
   const int a0 = d == 0 ? i : j;
   const int fld = d == 0 ? 1 : 2;
   const double h = g.h[d], ih = g.ih[d];
+  const FU fu = fu_of(aw.scal);
   double U3[3][NC], hD3[3][NC];
   long long pc[3];
   bool refl[3];
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
     mirror_D<NC>(hD3[q], refl[q]);
   }
   // forward: eigenvectors of the cell's own state
-  const Prim<NC> pr = prim_of<NC>(U3[1], g.gm1);
+  const Prim<NC> pr = prim_of<NC>(U3[1], g.gm1, fu);
   const double H = (U3[1][NC - 1] + pr.p) * pr.ir;
   const double c2 = g.gamma * pr.p * pr.ir;
   const double ic = rsqrt(c2);
@@ -79,17 +81,17 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
 #pragma unroll
   for (int q = 0; q < 2; ++q)
 #pragma unroll
-    for (int k = 0; k < NC; ++k) dU[q][k] = U3[q + 1][k] - U3[q][k];
-  e.project(dU[0], Dq[0]);
-  e.project(dU[1], Dq[1]);
-  e.project(hD3[0], Zm);
-  e.project(hD3[2], Zp);
+    for (int k = 0; k < NC; ++k) dU[q][k] = fu.sub(U3[q + 1][k], U3[q][k]);
+  e.project(dU[0], Dq[0], fu);
+  e.project(dU[1], Dq[1], fu);
+  e.project(hD3[0], Zm, fu);
+  e.project(hD3[2], Zp, fu);
   // forward intermediates of the limiter, per field, kept in this thread's shared-memory slots
   extern __shared__ double adj_cell_sm[];
   double* const svb = adj_cell_sm + threadIdx.x;
 #pragma unroll
   for (int s = 0; s < NC; ++s)
-    ht[s] = cell_field_save(Dq[0][s], Dq[1][s], Zm[s], Zp[s], g, svb + s * kCellSaved * kThreads, kThreads) * ih;
+    ht[s] = cell_field_save(Dq[0][s], Dq[1][s], Zm[s], Zp[s], g, svb + s * kCellSaved * kThreads, kThreads, fu) * ih;
   // backward from the adjoint of the modified derivative of this cell
   double ob[NC];
 #pragma unroll
@@ -100,14 +102,14 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
   double htb[NC];
 #pragma unroll
   for (int s = 0; s < NC; ++s) htb[s] = 0.0;
-  back_bwd<NC>(e, ht, ob, htb, hq2b, ucb, eb);
+  back_bwd<NC>(e, ht, ob, htb, hq2b, ucb, eb, fu);
   double Dqb[2][NC], Zmb[NC], Zpb[NC];
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
     double db[2] = {0.0, 0.0};
     Zmb[s] = Zpb[s] = 0.0;
     cell_field_bwd_saved(Dq[0][s], Dq[1][s], Zm[s], Zp[s], g, htb[s] * ih, svb + s * kCellSaved * kThreads,
-                         kThreads, db, Zmb[s], Zpb[s]);
+                         kThreads, db, Zmb[s], Zpb[s], fu);
     Dqb[0][s] = db[0];
     Dqb[1][s] = db[1];
   }
@@ -118,13 +120,13 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
     hDmb[k] = hDpb[k] = 0.0;
   }
 #pragma unroll
-  for (int q = 0; q < 2; ++q) project_bwd<NC>(e, dU[q], Dqb[q], dUb[q], hb1b, hb2b, hicb, eb);
-  project_bwd<NC>(e, hD3[0], Zmb, hDmb, hb1b, hb2b, hicb, eb);
-  project_bwd<NC>(e, hD3[2], Zpb, hDpb, hb1b, hb2b, hicb, eb);
+  for (int q = 0; q < 2; ++q) project_bwd<NC>(e, dU[q], Dqb[q], dUb[q], hb1b, hb2b, hicb, eb, fu);
+  project_bwd<NC>(e, hD3[0], Zmb, hDmb, hb1b, hb2b, hicb, eb, fu);
+  project_bwd<NC>(e, hD3[2], Zpb, hDpb, hb1b, hb2b, hicb, eb, fu);
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
     Ub[0][k] = -dUb[0][k];
-    Ub[1][k] = dUb[0][k] - dUb[1][k];
+    Ub[1][k] = fu.sub(dUb[0][k], dUb[1][k]);
     Ub[2][k] = dUb[1][k];
   }
   setup_bwd<NC>(e, g.gm1, ic, hb1b, hb2b, hicb, hq2b, ucb, eb);
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
   double pb = c2b * g.gamma * pr.ir + eb.H * pr.ir;
   double irb = c2b * g.gamma * pr.p + eb.H * (U3[1][NC - 1] + pr.p);
   Ub[1][NC - 1] += eb.H * pr.ir;
-  prim_bwd<NC>(U3[1], pr, g.gm1, irb, eb.u, eb.v, pb, Ub[1]);
+  prim_bwd<NC>(U3[1], pr, g.gm1, irb, eb.u, eb.v, pb, Ub[1], fu);
   // a mirrored neighbour was read through the sign table: its contributions go back through it
   // (the table is its own transpose)
 #pragma unroll
@@ -188,6 +190,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
   const int fown = dir == 0 ? 1 : 2;
   const double h = g.h[dir], ih = g.ih[dir];
   const double alpha = alpha2[dir];
+  const FU fu = fu_of(aw.scal);
   double Uq[4][NC], Zq[4][NC];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -214,8 +217,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
       const double rf = hasR ? muL[k * plane + cR] : 0.0, lf = hasL ? muL[k * plane + cL] : 0.0;
       const double rh = hasR ? muL[(fown * NC + k) * plane + cR] : 0.0;
       const double lh = hasL ? muL[(fown * NC + k) * plane + cL] : 0.0;
-      nuf[k] = (rf - lf) * ih;
-      nuh[k] = (rh - lh) * ih;
+      nuf[k] = fu.sub(rf, lf) * ih;
+      nuh[k] = fu.sub(rh, lh) * ih;
     }
     if (dir == 1) {
       swap_frame<NC>(nuf);
@@ -223,13 +226,13 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
     }
   }
   // ---- forward recomputation
-  const Prim<NC> pl = prim_of<NC>(Uq[1], g.gm1), prr = prim_of<NC>(Uq[2], g.gm1);
+  const Prim<NC> pl = prim_of<NC>(Uq[1], g.gm1, fu), prr = prim_of<NC>(Uq[2], g.gm1, fu);
   const double sl = sqrt(Uq[1][0]), sr = sqrt(Uq[2][0]);
   const double Hl = (Uq[1][NC - 1] + pl.p) * pl.ir, Hr = (Uq[2][NC - 1] + prr.p) * prr.ir;
-  const double iw = rcp(sl + sr);
-  const double ub = fma(sl, pl.u, sr * prr.u) * iw;
-  const double vb = NC == 4 ? fma(sl, pl.v, sr * prr.v) * iw : 0.0;
-  const double Hb = fma(sl, Hl, sr * Hr) * iw;
+  const double iw = rcp(fu.add(sl, sr), fu);
+  const double ub = fu.mul(fma(sl, pl.u, fu.mul(sr, prr.u)), iw);
+  const double vb = NC == 4 ? fu.mul(fma(sl, pl.v, fu.mul(sr, prr.v)), iw) : 0.0;
+  const double Hb = fu.mul(fma(sl, Hl, fu.mul(sr, Hr)), iw);
   const double c2 = g.gm1 * fma(-0.5, NC == 4 ? fma(ub, ub, vb * vb) : ub * ub, Hb);
   const double ic = rsqrt(c2);
   Eig<NC> e;
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
 #pragma unroll
   for (int q = 0; q < 3; ++q)
 #pragma unroll
-    for (int k = 0; k < NC; ++k) dU[q][k] = Uq[q + 1][k] - Uq[q][k];
+    for (int k = 0; k < NC; ++k) dU[q][k] = fu.sub(Uq[q + 1][k], Uq[q][k]);
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
     Dm[k] = fma(1.3125, dU[1][k], fma(-0.1875, dU[0][k], fma(0.0625, Zq[0][k], -0.1875 * Zq[2][k])));
@@ -249,9 +252,9 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
   }
   double Dq[3][NC], Yq[4][NC];
 #pragma unroll
-  for (int q = 0; q < 3; ++q) e.project(dU[q], Dq[q]);
+  for (int q = 0; q < 3; ++q) e.project(dU[q], Dq[q], fu);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) e.project(Zq[q], Yq[q]);
+  for (int q = 0; q < 4; ++q) e.project(Zq[q], Yq[q], fu);
   double cm[NC], cp[NC];
   // forward intermediates of the interpolation, per field, kept in this thread's shared-memory slots
   extern __shared__ double adj_face_sm[];
@@ -259,11 +262,11 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
 #pragma unroll
   for (int s = 0; s < NC; ++s)
     face_field_save(Dq[0][s], Dq[1][s], Dq[2][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, cm[s], cp[s],
-                    svb + s * kFaceSaved * kThreads, kThreads);
+                    svb + s * kFaceSaved * kThreads, kThreads, fu);
   // interface states: centre states plus the back-projected corrections
   double Um[NC], Up[NC];
-  e.back_add(cm, Uq[1], Um);
-  e.back_add(cp, Uq[2], Up);
+  e.back_add(cm, Uq[1], Um, fu);
+  e.back_add(cp, Uq[2], Up, fu);
   // ---- backward: fh = (FUm + FUp - alpha (Up - Um)) / 2 + Df, hh = hih (HDm + HDp - alpha (Dp - Dm)) + Dh
   double Umb[NC], Upb[NC], Dmb[NC], Dpb[NC], Fb[NC], Hb2[NC];
 #pragma unroll
@@ -275,17 +278,17 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
     Fb[k] = 0.5 * nuf[k];
     Hb2[k] = g.hih[dir] * nuh[k];
   }
-  flux_bwd<NC>(Um, g.gm1, Fb, Umb);
-  flux_bwd<NC>(Up, g.gm1, Fb, Upb);
-  jvp_bwd<NC>(Um, Dm, g.gm1, Hb2, Umb, Dmb);
-  jvp_bwd<NC>(Up, Dp, g.gm1, Hb2, Upb, Dpb);
+  flux_bwd<NC>(Um, g.gm1, Fb, Umb, fu);
+  flux_bwd<NC>(Up, g.gm1, Fb, Upb, fu);
+  jvp_bwd<NC>(Um, Dm, g.gm1, Hb2, Umb, Dmb, fu);
+  jvp_bwd<NC>(Up, Dp, g.gm1, Hb2, Upb, Dpb, fu);
   EigBar eb = {0.0, 0.0, 0.0, 0.0, 0.0};
   double hq2b = 0.0, ucb = 0.0, hb1b = 0.0, hb2b = 0.0, hicb = 0.0;
   double cmb[NC], cpb[NC];
 #pragma unroll
   for (int s = 0; s < NC; ++s) cmb[s] = cpb[s] = 0.0;
-  back_bwd<NC>(e, cm, Umb, cmb, hq2b, ucb, eb);
-  back_bwd<NC>(e, cp, Upb, cpb, hq2b, ucb, eb);
+  back_bwd<NC>(e, cm, Umb, cmb, hq2b, ucb, eb, fu);
+  back_bwd<NC>(e, cp, Upb, cpb, hq2b, ucb, eb, fu);
   double Uqb[4][NC], Zqb[4][NC], dUb[3][NC];
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
@@ -294,7 +297,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
     Uqb[1][k] = Umb[k];
     Uqb[2][k] = Upb[k];
     dUb[0][k] = -0.1875 * Dmb[k];
-    dUb[1][k] = 1.3125 * (Dmb[k] + Dpb[k]);
+    dUb[1][k] = 1.3125 * fu.add(Dmb[k], Dpb[k]);
     dUb[2][k] = -0.1875 * Dpb[k];
     Zqb[0][k] = 0.0625 * Dmb[k];
     Zqb[1][k] = -0.1875 * Dpb[k];
@@ -306,22 +309,22 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
   for (int s = 0; s < NC; ++s) {
     double db[3] = {0.0, 0.0, 0.0}, yb[4] = {0.0, 0.0, 0.0, 0.0};
     face_field_bwd_saved(Dq[0][s], Dq[1][s], Dq[2][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, cmb[s], cpb[s],
-                         svb + s * kFaceSaved * kThreads, kThreads, db, yb);
+                         svb + s * kFaceSaved * kThreads, kThreads, db, yb, fu);
 #pragma unroll
     for (int q = 0; q < 3; ++q) Dqb[q][s] = db[q];
 #pragma unroll
     for (int q = 0; q < 4; ++q) Yb[q][s] = yb[q];
   }
 #pragma unroll
-  for (int q = 0; q < 3; ++q) project_bwd<NC>(e, dU[q], Dqb[q], dUb[q], hb1b, hb2b, hicb, eb);
+  for (int q = 0; q < 3; ++q) project_bwd<NC>(e, dU[q], Dqb[q], dUb[q], hb1b, hb2b, hicb, eb, fu);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) project_bwd<NC>(e, Zq[q], Yb[q], Zqb[q], hb1b, hb2b, hicb, eb);
+  for (int q = 0; q < 4; ++q) project_bwd<NC>(e, Zq[q], Yb[q], Zqb[q], hb1b, hb2b, hicb, eb, fu);
 #pragma unroll
   for (int q = 0; q < 3; ++q)
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-      Uqb[q + 1][k] += dUb[q][k];
-      Uqb[q][k] -= dUb[q][k];
+      Uqb[q + 1][k] = fu.add(Uqb[q + 1][k], dUb[q][k]);
+      Uqb[q][k] = fu.sub(Uqb[q][k], dUb[q][k]);
     }
   setup_bwd<NC>(e, g.gm1, ic, hb1b, hb2b, hicb, hq2b, ucb, eb);
   // c = sqrt(c2), ic = 1/sqrt(c2); c2 = gm1 (Hb - (ub^2 + vb^2)/2)
@@ -391,7 +394,7 @@ __device__ __forceinline__ int aliases(int a, int n, int bc, int* x) {
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) k_adj_gather(Grid g, const double* __restrict__ S,
+__global__ void __launch_bounds__(kThreads, 4) k_adj_gather(Grid g, const double* __restrict__ S,
                                                          const double* __restrict__ muM, const double* __restrict__ muL,
                                                          AdjWork aw, double* __restrict__ lam) {
   constexpr int NC = DIM == 1 ? 3 : 4;
@@ -399,6 +402,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_gather(Grid g, const double* _
   const long long plane = g.plane;
   const long long p = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (p >= plane) return;
+  const FU fu = fu_of(aw.scal);
   const int i = (int)(p % g.nx), j = (int)(p / g.nx);
   double lb[NF][NC];
 #pragma unroll
@@ -445,8 +449,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_gather(Grid g, const double* _
         const long long base = ((d == 0 ? 0 : oplx) + fo) * 4 * NC + q * NC;
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
-          lb[0][k] += aw.CU[base + k];
-          lb[fown][k] += aw.CD[base + k];
+          lb[0][k] = fu.add(lb[0][k], aw.CU[base + k]);
+          lb[fown][k] = fu.add(lb[fown][k], aw.CD[base + k]);
         }
         // flux adjoints of this face, for the nodal values (D-terms, mixed flux)
         const bool hasL = fa - 1 >= 0, hasR = fa <= n - 1;
@@ -462,7 +466,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_gather(Grid g, const double* _
           auto dmu = [&](int fld) {
             const double r = hasR ? muL[(fld * NC + k) * plane + cR] : 0.0;
             const double l = hasL ? muL[(fld * NC + k) * plane + cL] : 0.0;
-            return r - l;
+            return fu.sub(r, l);
           };
           // a mirrored alias takes the nodal sign tables: f and the mixed value flip except for the
           // normal momentum, h only for it (sign flips in the integer pipe)
@@ -482,13 +486,13 @@ __global__ void __launch_bounds__(kThreads) k_adj_gather(Grid g, const double* _
         const long long pcl = d == 0 ? (long long)j * g.nx + c : (long long)c * g.nx + i;
         const double* cm = aw.CM + ((long long)d * plane + pcl) * 5 * NC;
 #pragma unroll
-        for (int k = 0; k < NC; ++k) lb[0][k] += cm[q * NC + k];
+        for (int k = 0; k < NC; ++k) lb[0][k] = fu.add(lb[0][k], cm[q * NC + k]);
         if (q == 0) {
 #pragma unroll
-          for (int k = 0; k < NC; ++k) lb[fown][k] += cm[3 * NC + k];
+          for (int k = 0; k < NC; ++k) lb[fown][k] = fu.add(lb[fown][k], cm[3 * NC + k]);
         } else if (q == 2) {
 #pragma unroll
-          for (int k = 0; k < NC; ++k) lb[fown][k] += cm[4 * NC + k];
+          for (int k = 0; k < NC; ++k) lb[fown][k] = fu.add(lb[fown][k], cm[4 * NC + k]);
         }
       }
     }
@@ -509,9 +513,9 @@ __global__ void __launch_bounds__(kThreads) k_adj_gather(Grid g, const double* _
       swap_frame<NC>(nh);
       swap_frame<NC>(no);
     }
-    flux_bwd<NC>(Un, g.gm1, nf, Ub);
-    jvp_bwd<NC>(Un, Dn, g.gm1, nh, Ub, Db);
-    if (DIM == 2) jvp_bwd<NC>(Un, On, g.gm1, no, Ub, Ob);
+    flux_bwd<NC>(Un, g.gm1, nf, Ub, fu);
+    jvp_bwd<NC>(Un, Dn, g.gm1, nh, Ub, Db, fu);
+    if (DIM == 2) jvp_bwd<NC>(Un, On, g.gm1, no, Ub, Ob, fu);
     if (d == 1) {
       swap_frame<NC>(Ub);
       swap_frame<NC>(Db);
@@ -519,9 +523,9 @@ __global__ void __launch_bounds__(kThreads) k_adj_gather(Grid g, const double* _
     }
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-      lb[0][k] += Ub[k];
-      lb[fown][k] += Db[k];
-      if (DIM == 2) lb[foth][k] += Ob[k];
+      lb[0][k] = fu.add(lb[0][k], Ub[k]);
+      lb[fown][k] = fu.add(lb[fown][k], Db[k]);
+      if (DIM == 2) lb[foth][k] = fu.add(lb[foth][k], Ob[k]);
     }
   }
 #pragma unroll
@@ -580,6 +584,7 @@ AdjPtrs adj_ptrs(const hweno_ctx* h, void* ws) {
   a.aw.CD = reinterpret_cast<double*>(p);
   p += l.CD;
   a.aw.CM = reinterpret_cast<double*>(p);
+  a.aw.scal = h->w.scal;
   return a;
 }
 

@@ -12,44 +12,44 @@ __device__ __forceinline__ double sgn0(double x) { return x > 0.0 ? 1.0 : (x < 0
 
 // beta0 and its inputs: adds to dmb, dpb, ymb, ypb given b0b (adjoint of beta0)
 __device__ __forceinline__ void beta0_bwd(double dm, double dp, double ym, double yp, double b0b, double& dmb,
-                                          double& dpb, double& ymb, double& ypb) {
-  const double du = dm + dp, d2 = dp - dm;
-  const double sv = ym + yp, dv = ym - yp;
+                                          double& dpb, double& ymb, double& ypb, const FU& f = HW_PLAIN_FU) {
+  const double du = f.add(dm, dp), d2 = f.sub(dp, dm);
+  const double sv = f.add(ym, yp), dv = f.sub(ym, yp);
   const double A = fma(-0.1875, sv, 0.6875 * du);
   const double B = fma(67.0 / 520.0, dv, (197.0 / 260.0) * d2);
-  const double C = sv - du;
+  const double C = f.sub(sv, du);
   const double D = fma(2.0, d2, dv);
-  const double Ab = 2.0 * A * b0b;
-  const double Bb = 2.0 * (13.0 / 3.0) * B * b0b;
-  const double Cb = 2.0 * (781.0 / 20.0 / 16.0) * C * b0b;
-  const double Db = 2.0 * (1421461.0 / 2275.0 / 16.0) * D * b0b;
+  const double Ab = f.mul(2.0 * A, b0b);
+  const double Bb = f.mul(2.0 * (13.0 / 3.0) * B, b0b);
+  const double Cb = f.mul(2.0 * (781.0 / 20.0 / 16.0) * C, b0b);
+  const double Db = f.mul(2.0 * (1421461.0 / 2275.0 / 16.0) * D, b0b);
   const double svb = -0.1875 * Ab + Cb;
   const double dub = 0.6875 * Ab - Cb;
   const double dvb = (67.0 / 520.0) * Bb + Db;
   const double d2b = (197.0 / 260.0) * Bb + 2.0 * Db;
-  dmb += dub - d2b;
-  dpb += dub + d2b;
-  ymb += svb + dvb;
-  ypb += svb - dvb;
+  dmb = f.add(dmb, f.sub(dub, d2b));
+  dpb = f.add(dpb, f.add(dub, d2b));
+  ymb = f.add(ymb, f.add(svb, dvb));
+  ypb = f.add(ypb, f.sub(svb, dvb));
 }
 
 // weights: W_l = P + tau Q_l.  Given Wb, adds b0b, b1b, b2b (through tau and e0) and e1b, e2b.
 __device__ __forceinline__ void weights_bwd(double b0, double b1, double b2, double e1, double e2, double eps,
                                             double W0b, double W1b, double W2b, double& b0b, double& b1b,
-                                            double& b2b, double& e1b, double& e2b) {
-  const double ts = fabs(b0 - b1) + fabs(b0 - b2);
-  const double tau = (0.25 * ts) * ts;
+                                            double& b2b, double& e1b, double& e2b, const FU& f = HW_PLAIN_FU) {
+  const double ts = f.add(fabs(f.sub(b0, b1)), fabs(f.sub(b0, b2)));
+  const double tau = f.mul(0.25 * ts, ts);
   const double e0 = b0 + eps;
-  const double Q0 = e1 * e2, Q1 = e0 * e2, Q2 = e0 * e1;
-  const double Pb = W0b + W1b + W2b;
-  const double taub = fma(W0b, Q0, fma(W1b, Q1, W2b * Q2));
-  const double Q0b = fma(W0b, tau, Pb * e0), Q1b = W1b * tau, Q2b = W2b * tau;
-  const double e0b = fma(Pb, Q0, fma(Q1b, e2, Q2b * e1));
-  e1b += fma(Q0b, e2, Q2b * e0);
-  e2b += fma(Q0b, e1, Q1b * e0);
-  const double tsb = 0.5 * ts * taub;
+  const double Q0 = f.mul(e1, e2), Q1 = f.mul(e0, e2), Q2 = f.mul(e0, e1);
+  const double Pb = f.add(f.add(W0b, W1b), W2b);
+  const double taub = fma(W0b, Q0, fma(W1b, Q1, f.mul(W2b, Q2)));
+  const double Q0b = fma(W0b, tau, f.mul(Pb, e0)), Q1b = f.mul(W1b, tau), Q2b = f.mul(W2b, tau);
+  const double e0b = fma(Pb, Q0, fma(Q1b, e2, f.mul(Q2b, e1)));
+  e1b = f.add(e1b, fma(Q0b, e2, f.mul(Q2b, e0)));
+  e2b = f.add(e2b, fma(Q0b, e1, f.mul(Q1b, e0)));
+  const double tsb = f.mul(0.5 * ts, taub);
   const double s1 = sgn0(b0 - b1), s2 = sgn0(b0 - b2);
-  b0b += e0b + tsb * (s1 + s2);
+  b0b = f.add(b0b, fma(tsb, f.add(s1, s2), e0b));
   b1b -= tsb * s1;
   b2b -= tsb * s2;
 }
@@ -70,18 +70,18 @@ constexpr int kCellSaved = 7;   // per characteristic field of a cell
 // saving the intermediates [b0, W0, W1, W2, r, X, 1/den] of the stencil of cell k, then of cell k+1.
 __device__ __forceinline__ void face_field_save(double d01, double d12, double d23, double y0, double y1,
                                                 double y2, double y3, const Grid& g, double& dum, double& dup,
-                                                double* sv, int stride) {
-  const double b01 = d01 * d01, b12 = d12 * d12, b23 = d23 * d23;
+                                                double* sv, int stride, const FU& f = HW_PLAIN_FU) {
+  const double b01 = f.mul(d01, d01), b12 = f.mul(d12, d12), b23 = f.mul(d23, d23);
   const double e01 = b01 + g.eps, e12 = b12 + g.eps, e23 = b23 + g.eps;
   double du, svs;
   {
-    const double b0 = beta0(d01, d12, y0, y2, du, svs);
-    const Wts wt = weights(b0, b01, b12, e01, e12, g.eps);
+    const double b0 = beta0(d01, d12, y0, y2, du, svs, f);
+    const Wts wt = weights(b0, b01, b12, e01, e12, g.eps, f);
     const double r = fma(g.dm[0], d01, fma(g.dm[1], d12, fma(g.dm[2], y0, g.dm[3] * y2)));
-    const double sl = fma(wt.W1, d01, wt.W2 * d12);
-    const double inv = rcp(fma(g.G, wt.W0, wt.W1 + wt.W2));
+    const double sl = fma(wt.W1, d01, f.mul(wt.W2, d12));
+    const double inv = rcp(fma(g.G, wt.W0, f.add(wt.W1, wt.W2)), f);
     const double X = fma(wt.W0, r, 0.5 * sl);
-    dum = X * inv;
+    dum = f.mul(X, inv);
     sv[0] = b0;
     sv[stride] = wt.W0;
     sv[2 * stride] = wt.W1;
@@ -91,13 +91,13 @@ __device__ __forceinline__ void face_field_save(double d01, double d12, double d
     sv[6 * stride] = inv;
   }
   {
-    const double b0 = beta0(d12, d23, y1, y3, du, svs);
-    const Wts wt = weights(b0, b12, b23, e12, e23, g.eps);
+    const double b0 = beta0(d12, d23, y1, y3, du, svs, f);
+    const Wts wt = weights(b0, b12, b23, e12, e23, g.eps, f);
     const double r = fma(g.dp[0], d12, fma(g.dp[1], d23, fma(g.dp[2], y1, g.dp[3] * y3)));
-    const double sl = fma(wt.W1, d12, wt.W2 * d23);
-    const double inv = rcp(fma(g.G, wt.W0, wt.W1 + wt.W2));
+    const double sl = fma(wt.W1, d12, f.mul(wt.W2, d23));
+    const double inv = rcp(fma(g.G, wt.W0, f.add(wt.W1, wt.W2)), f);
     const double X = fma(wt.W0, r, -0.5 * sl);
-    dup = X * inv;
+    dup = f.mul(X, inv);
     sv[7 * stride] = b0;
     sv[8 * stride] = wt.W0;
     sv[9 * stride] = wt.W1;
@@ -113,62 +113,63 @@ __device__ __forceinline__ void face_field_save(double d01, double d12, double d
 // den = G W0 + W1 + W2 (up - w2 likewise with d12, d23 and -1/2).
 __device__ __forceinline__ void face_field_bwd_saved(double d01, double d12, double d23, double y0, double y1,
                                                      double y2, double y3, const Grid& g, double umb, double upb,
-                                                     const double* sv, int stride, double* db, double* yb) {
-  const double b01 = d01 * d01, b12 = d12 * d12, b23 = d23 * d23;
+                                                     const double* sv, int stride, double* db, double* yb,
+                                                     const FU& f = HW_PLAIN_FU) {
+  const double b01 = f.mul(d01, d01), b12 = f.mul(d12, d12), b23 = f.mul(d23, d23);
   const double e01 = b01 + g.eps, e12 = b12 + g.eps, e23 = b23 + g.eps;
   double d01b = 0.0, d12b = 0.0, d23b = 0.0, b01b = 0.0, b12b = 0.0, b23b = 0.0;
   double e01b = 0.0, e12b = 0.0, e23b = 0.0;
   {
     const double b0 = sv[0], W0 = sv[stride], W1 = sv[2 * stride], W2 = sv[3 * stride];
     const double r = sv[4 * stride], X = sv[5 * stride], inv = sv[6 * stride];
-    const double Xb = umb * inv;
-    const double denb = -Xb * X * inv;
+    const double Xb = f.mul(umb, inv);
+    const double denb = f.mul(f.mul(-Xb, X), inv);
     const double hX = 0.5 * Xb;
     const double W0b = fma(Xb, r, denb * g.G), W1b = fma(hX, d01, denb), W2b = fma(hX, d12, denb);
-    const double rb = Xb * W0;
-    d01b += fma(g.dm[0], rb, hX * W1);
-    d12b += fma(g.dm[1], rb, hX * W2);
+    const double rb = f.mul(Xb, W0);
+    d01b = f.add(d01b, fma(g.dm[0], rb, f.mul(hX, W1)));
+    d12b = f.add(d12b, fma(g.dm[1], rb, f.mul(hX, W2)));
     yb[0] += g.dm[2] * rb;
     yb[2] += g.dm[3] * rb;
     double b0b = 0.0;
-    weights_bwd(b0, b01, b12, e01, e12, g.eps, W0b, W1b, W2b, b0b, b01b, b12b, e01b, e12b);
-    beta0_bwd(d01, d12, y0, y2, b0b, d01b, d12b, yb[0], yb[2]);
+    weights_bwd(b0, b01, b12, e01, e12, g.eps, W0b, W1b, W2b, b0b, b01b, b12b, e01b, e12b, f);
+    beta0_bwd(d01, d12, y0, y2, b0b, d01b, d12b, yb[0], yb[2], f);
   }
   {
     const double b0 = sv[7 * stride], W0 = sv[8 * stride], W1 = sv[9 * stride], W2 = sv[10 * stride];
     const double r = sv[11 * stride], X = sv[12 * stride], inv = sv[13 * stride];
-    const double Xb = upb * inv;
-    const double denb = -Xb * X * inv;
+    const double Xb = f.mul(upb, inv);
+    const double denb = f.mul(f.mul(-Xb, X), inv);
     const double hX = -0.5 * Xb;
     const double W0b = fma(Xb, r, denb * g.G), W1b = fma(hX, d12, denb), W2b = fma(hX, d23, denb);
-    const double rb = Xb * W0;
-    d12b += fma(g.dp[0], rb, hX * W1);
-    d23b += fma(g.dp[1], rb, hX * W2);
+    const double rb = f.mul(Xb, W0);
+    d12b = f.add(d12b, fma(g.dp[0], rb, f.mul(hX, W1)));
+    d23b = f.add(d23b, fma(g.dp[1], rb, f.mul(hX, W2)));
     yb[1] += g.dp[2] * rb;
     yb[3] += g.dp[3] * rb;
     double b0b = 0.0;
-    weights_bwd(b0, b12, b23, e12, e23, g.eps, W0b, W1b, W2b, b0b, b12b, b23b, e12b, e23b);
-    beta0_bwd(d12, d23, y1, y3, b0b, d12b, d23b, yb[1], yb[3]);
+    weights_bwd(b0, b12, b23, e12, e23, g.eps, W0b, W1b, W2b, b0b, b12b, b23b, e12b, e23b, f);
+    beta0_bwd(d12, d23, y1, y3, b0b, d12b, d23b, yb[1], yb[3], f);
   }
-  b01b += e01b;
-  b12b += e12b;
-  b23b += e23b;
-  db[0] += fma(2.0 * d01, b01b, d01b);
-  db[1] += fma(2.0 * d12, b12b, d12b);
-  db[2] += fma(2.0 * d23, b23b, d23b);
+  b01b = f.add(b01b, e01b);
+  b12b = f.add(b12b, e12b);
+  b23b = f.add(b23b, e23b);
+  db[0] = f.add(db[0], fma(2.0 * d01, b01b, d01b));
+  db[1] = f.add(db[1], fma(2.0 * d12, b12b, d12b));
+  db[2] = f.add(db[2], fma(2.0 * d23, b23b, d23b));
 }
 
 // The limiter (Eq. limiter) of one characteristic field from the differences d01 = w1 - w0,
 // d12 = w2 - w1 and the scaled derivatives y0, y2: h v~_i, saving [b0, W0, W1, W2, t, num, 1/den].
 __device__ __forceinline__ double cell_field_save(double d01, double d12, double y0, double y2, const Grid& g,
-                                                  double* sv, int stride) {
-  const double b1 = d01 * d01, b2 = d12 * d12;
+                                                  double* sv, int stride, const FU& f = HW_PLAIN_FU) {
+  const double b1 = f.mul(d01, d01), b2 = f.mul(d12, d12);
   double du, svs;
-  const double b0 = beta0(d01, d12, y0, y2, du, svs);
-  const Wts wt = weights(b0, b1, b2, b1 + g.eps, b2 + g.eps, g.eps);
+  const double b0 = beta0(d01, d12, y0, y2, du, svs, f);
+  const Wts wt = weights(b0, b1, b2, b1 + g.eps, b2 + g.eps, g.eps, f);
   const double t = fma(g.cdu, du, -g.csv * svs);
-  const double num = fma(wt.W0, t, fma(wt.W1, d01, wt.W2 * d12));
-  const double inv = rcp(fma(g.Gd, wt.W0, wt.W1 + wt.W2));
+  const double num = fma(wt.W0, t, fma(wt.W1, d01, f.mul(wt.W2, d12)));
+  const double inv = rcp(fma(g.Gd, wt.W0, f.add(wt.W1, wt.W2)), f);
   sv[0] = b0;
   sv[stride] = wt.W0;
   sv[2 * stride] = wt.W1;
@@ -176,35 +177,35 @@ __device__ __forceinline__ double cell_field_save(double d01, double d12, double
   sv[4 * stride] = t;
   sv[5 * stride] = num;
   sv[6 * stride] = inv;
-  return num * inv;
+  return f.mul(num, inv);
 }
 
 // Backward of cell_field_save from its saved values: given the adjoint of its output, adds those
 // of d01, d12 (db) and y0, y2.
 __device__ __forceinline__ void cell_field_bwd_saved(double d01, double d12, double y0, double y2, const Grid& g,
                                                      double outb, const double* sv, int stride, double* db,
-                                                     double& y0b, double& y2b) {
-  const double b1 = d01 * d01, b2 = d12 * d12;
+                                                     double& y0b, double& y2b, const FU& f = HW_PLAIN_FU) {
+  const double b1 = f.mul(d01, d01), b2 = f.mul(d12, d12);
   const double e1 = b1 + g.eps, e2 = b2 + g.eps;
   const double b0 = sv[0], W0 = sv[stride], W1 = sv[2 * stride], W2 = sv[3 * stride];
   const double t = sv[4 * stride], num = sv[5 * stride], inv = sv[6 * stride];
-  const double numb = outb * inv;
-  const double denb = -numb * num * inv;
+  const double numb = f.mul(outb, inv);
+  const double denb = f.mul(f.mul(-numb, num), inv);
   const double W0b = fma(numb, t, denb * g.Gd), W1b = fma(numb, d01, denb), W2b = fma(numb, d12, denb);
-  const double tb = numb * W0;
-  double d01b = numb * W1, d12b = numb * W2;
+  const double tb = f.mul(numb, W0);
+  double d01b = f.mul(numb, W1), d12b = f.mul(numb, W2);
   // t = cdu (d01 + d12) - csv (y0 + y2)
   d01b += g.cdu * tb;
   d12b += g.cdu * tb;
   y0b -= g.csv * tb;
   y2b -= g.csv * tb;
   double b0b = 0.0, b1b = 0.0, b2b = 0.0, e1b = 0.0, e2b = 0.0;
-  weights_bwd(b0, b1, b2, e1, e2, g.eps, W0b, W1b, W2b, b0b, b1b, b2b, e1b, e2b);
-  beta0_bwd(d01, d12, y0, y2, b0b, d01b, d12b, y0b, y2b);
-  b1b += e1b;
-  b2b += e2b;
-  db[0] += fma(2.0 * d01, b1b, d01b);
-  db[1] += fma(2.0 * d12, b2b, d12b);
+  weights_bwd(b0, b1, b2, e1, e2, g.eps, W0b, W1b, W2b, b0b, b1b, b2b, e1b, e2b, f);
+  beta0_bwd(d01, d12, y0, y2, b0b, d01b, d12b, y0b, y2b, f);
+  b1b = f.add(b1b, e1b);
+  b2b = f.add(b2b, e2b);
+  db[0] = f.add(db[0], fma(2.0 * d01, b1b, d01b));
+  db[1] = f.add(db[1], fma(2.0 * d12, b2b, d12b));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -215,48 +216,49 @@ struct EigBar {
 
 template <int NC>
 __device__ __forceinline__ void project_bwd(const Eig<NC>& e, const double* q, const double* wbar, double* qbar,
-                                            double& hb1b, double& hb2b, double& hicb, EigBar& eb) {
+                                            double& hb1b, double& hb2b, double& hicb, EigBar& eb,
+                                            const FU& f = HW_PLAIN_FU) {
   // forward: k, th = hb2 q0 - hb1 k, sh = (u q0 - q1) hic
-  const double k = NC == 4 ? fma(e.v, q[2], e.u * q[1]) - q[3] : fma(e.u, q[1], -q[NC - 1]);
+  const double k = NC == 4 ? f.sub(fma(e.v, q[2], f.mul(e.u, q[1])), q[3]) : fma(e.u, q[1], -q[NC - 1]);
   const double m = fma(e.u, q[0], -q[1]);
   const double wr = NC == 4 ? wbar[3] : wbar[2];
-  const double thb = wbar[0] - 2.0 * wbar[1] + wr;
-  const double shb = wbar[0] - wr;
-  qbar[0] += wbar[1];
+  const double thb = f.add(fma(-2.0, wbar[1], wbar[0]), wr);
+  const double shb = f.sub(wbar[0], wr);
+  qbar[0] = f.add(qbar[0], wbar[1]);
   if (NC == 4) {
     qbar[0] -= e.v * wbar[2];
-    qbar[2] += wbar[2];
+    qbar[2] = f.add(qbar[2], wbar[2]);
     eb.v -= wbar[2] * q[0];
   }
   // th
   hb2b += thb * q[0];
   qbar[0] += thb * e.hb2;
   hb1b -= thb * k;
-  const double kb = -thb * e.hb1;
+  const double kb = f.mul(-thb, e.hb1);
   // sh
-  const double mb = shb * e.hic;
+  const double mb = f.mul(shb, e.hic);
   hicb += shb * m;
   eb.u += mb * q[0];
   qbar[0] += mb * e.u;
-  qbar[1] -= mb;
+  qbar[1] = f.sub(qbar[1], mb);
   // k
   eb.u += kb * q[1];
   qbar[1] += kb * e.u;
   if (NC == 4) {
     eb.v += kb * q[2];
     qbar[2] += kb * e.v;
-    qbar[3] -= kb;
+    qbar[3] = f.sub(qbar[3], kb);
   } else {
-    qbar[NC - 1] -= kb;
+    qbar[NC - 1] = f.sub(qbar[NC - 1], kb);
   }
 }
 
 template <int NC>
 __device__ __forceinline__ void back_bwd(const Eig<NC>& e, const double* w, const double* qbar, double* wbar,
-                                         double& hq2b, double& ucb, EigBar& eb) {
+                                         double& hq2b, double& ucb, EigBar& eb, const FU& f = HW_PLAIN_FU) {
   const double wl = w[0], wr = NC == 4 ? w[3] : w[2];
-  const double sg = wl + wr, dl = wr - wl;
-  const double q0 = sg + w[1];
+  const double sg = f.add(wl, wr), dl = f.sub(wr, wl);
+  const double q0 = f.add(sg, w[1]);
   double sgb = 0.0, dlb = 0.0, q0b = qbar[0];
   if (NC == 4) {
     // q3 = H sg + hq2 w1 + v w2 + uc dl
@@ -271,7 +273,7 @@ __device__ __forceinline__ void back_bwd(const Eig<NC>& e, const double* w, cons
     // q2 = v q0 + w2
     eb.v += qbar[2] * q0;
     q0b += qbar[2] * e.v;
-    wbar[2] += qbar[2];
+    wbar[2] = f.add(wbar[2], qbar[2]);
   } else {
     // q2 = H sg + hq2 w1 + uc dl
     eb.H += qbar[2] * sg;
@@ -287,13 +289,13 @@ __device__ __forceinline__ void back_bwd(const Eig<NC>& e, const double* w, cons
   eb.c += qbar[1] * dl;
   dlb += qbar[1] * e.c;
   // q0 = sg + w1
-  sgb += q0b;
-  wbar[1] += q0b;
-  wbar[0] += sgb - dlb;
+  sgb = f.add(sgb, q0b);
+  wbar[1] = f.add(wbar[1], q0b);
+  wbar[0] = f.add(wbar[0], f.sub(sgb, dlb));
   if (NC == 4)
-    wbar[3] += sgb + dlb;
+    wbar[3] = f.add(wbar[3], f.add(sgb, dlb));
   else
-    wbar[2] += sgb + dlb;
+    wbar[2] = f.add(wbar[2], f.add(sgb, dlb));
 }
 
 // adjoints of the derived eigen quantities (hb1, hb2, hic, hq2, uc) into (u, v, c, ic)
@@ -323,12 +325,12 @@ struct Prim {
 };
 
 template <int NC>
-__device__ __forceinline__ Prim<NC> prim_of(const double* U, double gm1) {
+__device__ __forceinline__ Prim<NC> prim_of(const double* U, double gm1, const FU& f = HW_PLAIN_FU) {
   Prim<NC> q;
-  q.ir = rcp(U[0]);
-  q.u = U[1] * q.ir;
-  q.v = NC == 4 ? U[2] * q.ir : 0.0;
-  const double ke = NC == 4 ? fma(U[1], q.u, U[2] * q.v) : U[1] * q.u;
+  q.ir = rcp(U[0], f);
+  q.u = f.mul(U[1], q.ir);
+  q.v = NC == 4 ? f.mul(U[2], q.ir) : 0.0;
+  const double ke = NC == 4 ? fma(U[1], q.u, f.mul(U[2], q.v)) : f.mul(U[1], q.u);
   q.p = gm1 * fma(-0.5, ke, U[NC - 1]);
   return q;
 }
@@ -336,7 +338,7 @@ __device__ __forceinline__ Prim<NC> prim_of(const double* U, double gm1) {
 // Given the adjoints of (ir, u, v, p) of a cell, adds those of U.
 template <int NC>
 __device__ __forceinline__ void prim_bwd(const double* U, const Prim<NC>& q, double gm1, double irb, double ub,
-                                         double vb, double pb, double* Ub) {
+                                         double vb, double pb, double* Ub, const FU& f = HW_PLAIN_FU) {
   // p = gm1 (E - (m u + n v)/2)
   Ub[NC - 1] += gm1 * pb;
   const double keb = -0.5 * gm1 * pb;
@@ -354,16 +356,17 @@ __device__ __forceinline__ void prim_bwd(const double* U, const Prim<NC>& q, dou
     irb += vb * U[2];
   }
   // ir = 1/rho
-  Ub[0] -= irb * q.ir * q.ir;
+  Ub[0] = fma(-f.mul(irb, q.ir), q.ir, Ub[0]);
 }
 
 // Flux F(U) in the normal frame: given Fb, adds Ub.
 template <int NC>
-__device__ __forceinline__ void flux_bwd(const double* U, double gm1, const double* Fb, double* Ub) {
-  const Prim<NC> q = prim_of<NC>(U, gm1);
+__device__ __forceinline__ void flux_bwd(const double* U, double gm1, const double* Fb, double* Ub,
+                                         const FU& f = HW_PLAIN_FU) {
+  const Prim<NC> q = prim_of<NC>(U, gm1, f);
   double ub = 0.0, vb = 0.0, pb = 0.0;
   // F = (m, m u + p, [n u,] (E + p) u)
-  Ub[1] += Fb[0] + Fb[1] * q.u;
+  Ub[1] = f.add(Ub[1], fma(Fb[1], q.u, Fb[0]));
   ub += Fb[1] * U[1];
   pb += Fb[1];
   if (NC == 4) {
@@ -372,28 +375,29 @@ __device__ __forceinline__ void flux_bwd(const double* U, double gm1, const doub
   }
   Ub[NC - 1] += Fb[NC - 1] * q.u;
   pb += Fb[NC - 1] * q.u;
-  ub += Fb[NC - 1] * (U[NC - 1] + q.p);
-  prim_bwd<NC>(U, q, gm1, 0.0, ub, vb, pb, Ub);
+  ub += Fb[NC - 1] * f.add(U[NC - 1], q.p);
+  prim_bwd<NC>(U, q, gm1, 0.0, ub, vb, pb, Ub, f);
 }
 
 // Jacobian product A(U) D in the normal frame: given ob, adds Ub and Db.
 template <int NC>
 __device__ __forceinline__ void jvp_bwd(const double* U, const double* D, double gm1, const double* ob, double* Ub,
-                                        double* Db) {
-  const Prim<NC> q = prim_of<NC>(U, gm1);
-  const double du = fma(-q.u, D[0], D[1]) * q.ir;
-  const double dv = NC == 4 ? fma(-q.v, D[0], D[2]) * q.ir : 0.0;
-  const double dk = NC == 4 ? fma(D[1], q.u, fma(U[1], du, fma(D[2], q.v, U[2] * dv))) : fma(D[1], q.u, U[1] * du);
+                                        double* Db, const FU& f = HW_PLAIN_FU) {
+  const Prim<NC> q = prim_of<NC>(U, gm1, f);
+  const double du = f.mul(fma(-q.u, D[0], D[1]), q.ir);
+  const double dv = NC == 4 ? f.mul(fma(-q.v, D[0], D[2]), q.ir) : 0.0;
+  const double dk = NC == 4 ? fma(D[1], q.u, fma(U[1], du, fma(D[2], q.v, f.mul(U[2], dv))))
+                            : fma(D[1], q.u, f.mul(U[1], du));
   const double dp = gm1 * fma(-0.5, dk, D[NC - 1]);
   double ub = 0.0, vb = 0.0, pb = 0.0, irb = 0.0, dub = 0.0, dvb = 0.0, dpb = 0.0;
   // out0 = D1
-  Db[1] += ob[0];
+  Db[1] = f.add(Db[1], ob[0]);
   // out1 = D1 u + m du + dp
   Db[1] += ob[1] * q.u;
   ub += ob[1] * D[1];
   Ub[1] += ob[1] * du;
   dub += ob[1] * U[1];
-  dpb += ob[1];
+  dpb = f.add(dpb, ob[1]);
   if (NC == 4) {
     // out2 = D2 u + n du
     Db[2] += ob[2] * q.u;
@@ -404,10 +408,10 @@ __device__ __forceinline__ void jvp_bwd(const double* U, const double* D, double
   // out_last = (D_E + dp) u + (E + p) du
   Db[NC - 1] += ob[NC - 1] * q.u;
   dpb += ob[NC - 1] * q.u;
-  ub += ob[NC - 1] * (D[NC - 1] + dp);
+  ub += ob[NC - 1] * f.add(D[NC - 1], dp);
   Ub[NC - 1] += ob[NC - 1] * du;
   pb += ob[NC - 1] * du;
-  dub += ob[NC - 1] * (U[NC - 1] + q.p);
+  dub += ob[NC - 1] * f.add(U[NC - 1], q.p);
   // dp = gm1 (D_E - dk/2)
   Db[NC - 1] += gm1 * dpb;
   const double dkb = -0.5 * gm1 * dpb;
@@ -424,16 +428,16 @@ __device__ __forceinline__ void jvp_bwd(const double* U, const double* D, double
   }
   // du = (D1 - u D0) ir, dv = (D2 - v D0) ir
   Db[1] += dub * q.ir;
-  ub -= dub * D[0] * q.ir;
-  Db[0] -= dub * q.u * q.ir;
+  ub = fma(-f.mul(dub, D[0]), q.ir, ub);
+  Db[0] = fma(-f.mul(dub, q.u), q.ir, Db[0]);
   irb += dub * fma(-q.u, D[0], D[1]);
   if (NC == 4) {
     Db[2] += dvb * q.ir;
-    vb -= dvb * D[0] * q.ir;
-    Db[0] -= dvb * q.v * q.ir;
+    vb = fma(-f.mul(dvb, D[0]), q.ir, vb);
+    Db[0] = fma(-f.mul(dvb, q.v), q.ir, Db[0]);
     irb += dvb * fma(-q.v, D[0], D[2]);
   }
-  prim_bwd<NC>(U, q, gm1, irb, ub, vb, pb, Ub);
+  prim_bwd<NC>(U, q, gm1, irb, ub, vb, pb, Ub, f);
 }
 
 }  // namespace hw

@@ -109,16 +109,16 @@ __device__ __forceinline__ double sqr(double x) { return x * x; }
 // beta0 = (a1 + a3/4)^2 + 13/3 (a2 + 63/130 a4)^2 + 781/20 a3^2 + 1421461/2275 a4^2,
 // beta1 = dm^2, beta2 = dp^2 (passed in: neighbouring stencils share them).
 __device__ __forceinline__ double beta0(double dm, double dp, double hvm, double hvp, double& du_out,
-                                        double& sv_out) {
-  const double du = dm + dp, d2 = dp - dm;
-  const double sv = hvm + hvp, dv = hvm - hvp;
+                                        double& sv_out, const FU& f = HW_PLAIN_FU) {
+  const double du = f.add(dm, dp), d2 = f.sub(dp, dm);
+  const double sv = f.add(hvm, hvp), dv = f.sub(hvm, hvp);
   const double A = fma(-0.1875, sv, 0.6875 * du);
   const double B = fma(67.0 / 520.0, dv, (197.0 / 260.0) * d2);
-  const double C = sv - du;
+  const double C = f.sub(sv, du);
   const double D = fma(2.0, d2, dv);
   du_out = du;
   sv_out = sv;
-  return fma((1421461.0 / 2275.0 / 16.0) * D, D, fma((781.0 / 20.0 / 16.0) * C, C, fma((13.0 / 3.0) * B, B, A * A)));
+  return fma((1421461.0 / 2275.0 / 16.0) * D, D, fma((781.0 / 20.0 / 16.0) * C, C, fma((13.0 / 3.0) * B, B, f.mul(A, A))));
 }
 
 // beta0 + eps with unscaled derivatives vm = v_{i-1}, vp = v_{i+1} along direction dir.  The four
@@ -143,12 +143,13 @@ struct Wts {
   double W0, W1, W2;
 };
 
-__device__ __forceinline__ Wts weights(double b0, double b1, double b2, double e1, double e2, double eps) {
-  const double ts = fabs(b0 - b1) + fabs(b0 - b2);
-  const double tau = (0.25 * ts) * ts;
+__device__ __forceinline__ Wts weights(double b0, double b1, double b2, double e1, double e2, double eps,
+                                       const FU& f = HW_PLAIN_FU) {
+  const double ts = f.add(fabs(f.sub(b0, b1)), fabs(f.sub(b0, b2)));
+  const double tau = f.mul(0.25 * ts, ts);
   const double e0 = b0 + eps;
-  const double Q0 = e1 * e2, Q1 = e0 * e2, Q2 = e0 * e1;
-  const double P = Q0 * e0;
+  const double Q0 = f.mul(e1, e2), Q1 = f.mul(e0, e2), Q2 = f.mul(e0, e1);
+  const double P = f.mul(Q0, e0);
   Wts w;
   w.W0 = fma(tau, Q0, P);
   w.W1 = fma(tau, Q1, P);
