@@ -41,11 +41,11 @@ STEP_BYTES_PER_CELL = 104 * 8
 HBM_PEAK_GBS_FALLBACK = 6800.0
 # DRAM bytes per face of the 2D Euler face kernel from an ncu capture at 2048^2 (profiles/); the
 # traffic grows in proportion to the faces, so a 4096^2 launch moves this times its faces.
-FACE_TRAFFIC_BYTES_PER_FACE = None  # None: the face kernel changed after its last ncu capture
+FACE_TRAFFIC_BYTES_PER_FACE = 285.2  # ncu dram bytes per face, 2048^2 capture of the current face kernel
 # from the same capture: FP64 pipe activity and FP64 instructions per face (the hardware's side of
 # the roofline fraction, which counts the scheme's operations as written)
-FACE_FP64_PIPE_ACTIVE = 0.870
-FACE_FP64_INSTR_PER_FACE = 658
+FACE_FP64_PIPE_ACTIVE = 0.915
+FACE_FP64_INSTR_PER_FACE = 670
 
 
 def _dist():
