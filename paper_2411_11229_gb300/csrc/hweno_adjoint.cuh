@@ -10,79 +10,84 @@ namespace hw {
 
 __device__ __forceinline__ double sgn0(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
 
-// beta0 and its inputs: adds to dmb, dpb, ymb, ypb given b0b (adjoint of beta0)
-__device__ __forceinline__ void beta0_bwd(double dm, double dp, double ym, double yp, double b0b, double& dmb,
-                                          double& dpb, double& ymb, double& ypb, const FU& f = HW_PLAIN_FU) {
+// e0 = beta0 + eps of the stencil {i-1, i, i+1} from the differences dm, dp and the h-scaled
+// derivatives ym = h v_{i-1}, yp = h v_{i+1} (Eq. GHYZ): the two quadratic forms of beta0 with the
+// square completed in the derivative term, S1 (sv + N1 du)^2 + T1 du^2 + S2 (dv + N2 d2)^2 + T2 d2^2
+// (du = dm + dp, d2 = dp - dm, sv = ym + yp, dv = ym - yp), eps as the first addend.  Returns e0,
+// du and sv.
+__device__ __forceinline__ double beta0_eps_s(double dm, double dp, double ym, double yp, const Grid& g, const FU& f,
+                                              double& du_out, double& sv_out) {
   const double du = f.add(dm, dp), d2 = f.sub(dp, dm);
   const double sv = f.add(ym, yp), dv = f.sub(ym, yp);
-  const double A = fma(-0.1875, sv, 0.6875 * du);
-  const double B = fma(67.0 / 520.0, dv, (197.0 / 260.0) * d2);
-  const double C = f.sub(sv, du);
-  const double D = fma(2.0, d2, dv);
-  const double Ab = f.mul(2.0 * A, b0b);
-  const double Bb = f.mul(2.0 * (13.0 / 3.0) * B, b0b);
-  const double Cb = f.mul(2.0 * (781.0 / 20.0 / 16.0) * C, b0b);
-  const double Db = f.mul(2.0 * (1421461.0 / 2275.0 / 16.0) * D, b0b);
-  const double svb = -0.1875 * Ab + Cb;
-  const double dub = 0.6875 * Ab - Cb;
-  const double dvb = (67.0 / 520.0) * Bb + Db;
-  const double d2b = (197.0 / 260.0) * Bb + 2.0 * Db;
-  dmb = f.add(dmb, f.sub(dub, d2b));
-  dpb = f.add(dpb, f.add(dub, d2b));
-  ymb = f.add(ymb, f.add(svb, dvb));
-  ypb = f.add(ypb, f.sub(svb, dvb));
+  const double y1 = fma(g.aN1, du, sv), y2 = fma(g.aN2, d2, dv);
+  du_out = du;
+  sv_out = sv;
+  return fma(g.aS1 * y1, y1, fma(g.aS2 * y2, y2, fma(g.bT1 * du, du, fma(g.bT2 * d2, d2, g.eps))));
 }
 
-// weights: W_l = P + tau Q_l.  Given Wb, adds b0b, b1b, b2b (through tau and e0) and e1b, e2b.
-__device__ __forceinline__ void weights_bwd(double b0, double b1, double b2, double e1, double e2, double eps,
-                                            double W0b, double W1b, double W2b, double& b0b, double& b1b,
-                                            double& b2b, double& e1b, double& e2b, const FU& f = HW_PLAIN_FU) {
-  const double ts = f.add(fabs(f.sub(b0, b1)), fabs(f.sub(b0, b2)));
+// Backward of beta0_eps_s: given e0b (the adjoint of beta0 + eps), adds those of dm, dp, ym, yp.
+//   d/dsv = 2 S1 y1, d/ddu = N1 2 S1 y1 + 2 T1 du, d/ddv = 2 S2 y2, d/dd2 = N2 2 S2 y2 + 2 T2 d2.
+__device__ __forceinline__ void beta0_eps_s_bwd(double dm, double dp, double ym, double yp, const Grid& g,
+                                                double e0b, double& dmb, double& dpb, double& ymb, double& ypb,
+                                                const FU& f) {
+  const double du = f.add(dm, dp), d2 = f.sub(dp, dm);
+  const double sv = f.add(ym, yp), dv = f.sub(ym, yp);
+  const double y1 = fma(g.aN1, du, sv), y2 = fma(g.aN2, d2, dv);
+  const double t1 = f.mul((2.0 * g.aS1) * y1, e0b), t2 = f.mul((2.0 * g.aS2) * y2, e0b);
+  const double dub = fma(g.aN1, t1, f.mul((2.0 * g.bT1) * du, e0b));
+  const double d2b = fma(g.aN2, t2, f.mul((2.0 * g.bT2) * d2, e0b));
+  dmb = f.add(dmb, f.sub(dub, d2b));
+  dpb = f.add(dpb, f.add(dub, d2b));
+  ymb = f.add(ymb, f.add(t1, t2));
+  ypb = f.add(ypb, f.sub(t1, t2));
+}
+
+// Backward of weights_e (W_l = P + tau Q_l from e_l = beta_l + eps, tau from e_0 - e_l): given
+// W0b..W2b, adds the adjoints of e0, e1, e2.
+__device__ __forceinline__ void weights_e_bwd(double e0, double e1, double e2, double W0b, double W1b, double W2b,
+                                              double& e0b, double& e1b, double& e2b, const FU& f) {
+  const double ts = f.add(fabs(f.sub(e0, e1)), fabs(f.sub(e0, e2)));
   const double tau = f.mul(0.25 * ts, ts);
-  const double e0 = b0 + eps;
   const double Q0 = f.mul(e1, e2), Q1 = f.mul(e0, e2), Q2 = f.mul(e0, e1);
   const double Pb = f.add(f.add(W0b, W1b), W2b);
   const double taub = fma(W0b, Q0, fma(W1b, Q1, f.mul(W2b, Q2)));
   const double Q0b = fma(W0b, tau, f.mul(Pb, e0)), Q1b = f.mul(W1b, tau), Q2b = f.mul(W2b, tau);
-  const double e0b = fma(Pb, Q0, fma(Q1b, e2, f.mul(Q2b, e1)));
-  e1b = f.add(e1b, fma(Q0b, e2, f.mul(Q2b, e0)));
-  e2b = f.add(e2b, fma(Q0b, e1, f.mul(Q1b, e0)));
   const double tsb = f.mul(0.5 * ts, taub);
-  const double s1 = sgn0(b0 - b1), s2 = sgn0(b0 - b2);
-  b0b = f.add(b0b, fma(tsb, f.add(s1, s2), e0b));
-  b1b -= tsb * s1;
-  b2b -= tsb * s2;
+  const double s1 = sgn0(e0 - e1), s2 = sgn0(e0 - e2);
+  e0b = f.add(e0b, fma(tsb, f.add(s1, s2), fma(Pb, Q0, fma(Q1b, e2, f.mul(Q2b, e1)))));
+  e1b = f.add(e1b, fma(-tsb, s1, fma(Q0b, e2, f.mul(Q2b, e0))));
+  e2b = f.add(e2b, fma(-tsb, s2, fma(Q0b, e1, f.mul(Q1b, e0))));
 }
 
 // ---------------------------------------------------------------------------------------------
 // Backward passes from saved forward values.  The adjoint kernels run the forward interpolation
-// once, keep each stencil's intermediates (beta0, the three weights, the candidate combination,
-// the weighted sum and 1/den) in shared memory, and the backward pass reads them instead of
-// recomputing them.  The forward map is taken in difference form, as the forward kernels take it:
-// the characteristic fields enter only through differences of neighbouring cells.  sv points at this thread's first slot; consecutive values are
-// `stride` doubles apart (one slot per thread of the block).
+// once, keep each stencil's intermediates (beta0 + eps, the three weights, the candidate
+// combination, the weighted sum and 1/den) in shared memory, and the backward pass reads them
+// instead of recomputing them.  The forward map is taken in difference form, as the forward kernels
+// take it: the characteristic fields enter only through differences of neighbouring cells.  sv
+// points at this thread's first slot; consecutive values are `stride` doubles apart (one slot per
+// thread of the block).
 constexpr int kFaceSaved = 14;  // per characteristic field of a face: 7 per stencil
 constexpr int kCellSaved = 7;   // per characteristic field of a cell
 
 // One characteristic field at one face k+1/2 (h-scaled derivatives) from the differences
 // d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2 of the cells k-1..k+2 and their scaled derivatives
 // y0..y3: um - w1 and up - w2 (the interface values less the centre values; Eqs. Pxi, interp),
-// saving the intermediates [b0, W0, W1, W2, r, X, 1/den] of the stencil of cell k, then of cell k+1.
+// saving the intermediates [e0, W0, W1, W2, r, X, 1/den] of the stencil of cell k, then of cell k+1.
 __device__ __forceinline__ void face_field_save(double d01, double d12, double d23, double y0, double y1,
                                                 double y2, double y3, const Grid& g, double& dum, double& dup,
-                                                double* sv, int stride, const FU& f = HW_PLAIN_FU) {
-  const double b01 = f.mul(d01, d01), b12 = f.mul(d12, d12), b23 = f.mul(d23, d23);
-  const double e01 = b01 + g.eps, e12 = b12 + g.eps, e23 = b23 + g.eps;
+                                                double* sv, int stride, const FU& f) {
+  const double e01 = fma(d01, d01, g.eps), e12 = fma(d12, d12, g.eps), e23 = fma(d23, d23, g.eps);
   double du, svs;
   {
-    const double b0 = beta0(d01, d12, y0, y2, du, svs, f);
-    const Wts wt = weights(b0, b01, b12, e01, e12, g.eps, f);
+    const double e0 = beta0_eps_s(d01, d12, y0, y2, g, f, du, svs);
+    const Wts wt = weights_e(e0, e01, e12, f);
     const double r = fma(g.dm[0], d01, fma(g.dm[1], d12, fma(g.dm[2], y0, g.dm[3] * y2)));
     const double sl = fma(wt.W1, d01, f.mul(wt.W2, d12));
     const double inv = rcp(fma(g.G, wt.W0, f.add(wt.W1, wt.W2)), f);
     const double X = fma(wt.W0, r, 0.5 * sl);
     dum = f.mul(X, inv);
-    sv[0] = b0;
+    sv[0] = e0;
     sv[stride] = wt.W0;
     sv[2 * stride] = wt.W1;
     sv[3 * stride] = wt.W2;
@@ -91,14 +96,14 @@ __device__ __forceinline__ void face_field_save(double d01, double d12, double d
     sv[6 * stride] = inv;
   }
   {
-    const double b0 = beta0(d12, d23, y1, y3, du, svs, f);
-    const Wts wt = weights(b0, b12, b23, e12, e23, g.eps, f);
+    const double e0 = beta0_eps_s(d12, d23, y1, y3, g, f, du, svs);
+    const Wts wt = weights_e(e0, e12, e23, f);
     const double r = fma(g.dp[0], d12, fma(g.dp[1], d23, fma(g.dp[2], y1, g.dp[3] * y3)));
     const double sl = fma(wt.W1, d12, f.mul(wt.W2, d23));
     const double inv = rcp(fma(g.G, wt.W0, f.add(wt.W1, wt.W2)), f);
     const double X = fma(wt.W0, r, -0.5 * sl);
     dup = f.mul(X, inv);
-    sv[7 * stride] = b0;
+    sv[7 * stride] = e0;
     sv[8 * stride] = wt.W0;
     sv[9 * stride] = wt.W1;
     sv[10 * stride] = wt.W2;
@@ -114,13 +119,11 @@ __device__ __forceinline__ void face_field_save(double d01, double d12, double d
 __device__ __forceinline__ void face_field_bwd_saved(double d01, double d12, double d23, double y0, double y1,
                                                      double y2, double y3, const Grid& g, double umb, double upb,
                                                      const double* sv, int stride, double* db, double* yb,
-                                                     const FU& f = HW_PLAIN_FU) {
-  const double b01 = f.mul(d01, d01), b12 = f.mul(d12, d12), b23 = f.mul(d23, d23);
-  const double e01 = b01 + g.eps, e12 = b12 + g.eps, e23 = b23 + g.eps;
-  double d01b = 0.0, d12b = 0.0, d23b = 0.0, b01b = 0.0, b12b = 0.0, b23b = 0.0;
-  double e01b = 0.0, e12b = 0.0, e23b = 0.0;
+                                                     const FU& f) {
+  const double e01 = fma(d01, d01, g.eps), e12 = fma(d12, d12, g.eps), e23 = fma(d23, d23, g.eps);
+  double d01b = 0.0, d12b = 0.0, d23b = 0.0, e01b = 0.0, e12b = 0.0, e23b = 0.0;
   {
-    const double b0 = sv[0], W0 = sv[stride], W1 = sv[2 * stride], W2 = sv[3 * stride];
+    const double e0 = sv[0], W0 = sv[stride], W1 = sv[2 * stride], W2 = sv[3 * stride];
     const double r = sv[4 * stride], X = sv[5 * stride], inv = sv[6 * stride];
     const double Xb = f.mul(umb, inv);
     const double denb = f.mul(f.mul(-Xb, X), inv);
@@ -131,12 +134,12 @@ __device__ __forceinline__ void face_field_bwd_saved(double d01, double d12, dou
     d12b = f.add(d12b, fma(g.dm[1], rb, f.mul(hX, W2)));
     yb[0] += g.dm[2] * rb;
     yb[2] += g.dm[3] * rb;
-    double b0b = 0.0;
-    weights_bwd(b0, b01, b12, e01, e12, g.eps, W0b, W1b, W2b, b0b, b01b, b12b, e01b, e12b, f);
-    beta0_bwd(d01, d12, y0, y2, b0b, d01b, d12b, yb[0], yb[2], f);
+    double e0b = 0.0;
+    weights_e_bwd(e0, e01, e12, W0b, W1b, W2b, e0b, e01b, e12b, f);
+    beta0_eps_s_bwd(d01, d12, y0, y2, g, e0b, d01b, d12b, yb[0], yb[2], f);
   }
   {
-    const double b0 = sv[7 * stride], W0 = sv[8 * stride], W1 = sv[9 * stride], W2 = sv[10 * stride];
+    const double e0 = sv[7 * stride], W0 = sv[8 * stride], W1 = sv[9 * stride], W2 = sv[10 * stride];
     const double r = sv[11 * stride], X = sv[12 * stride], inv = sv[13 * stride];
     const double Xb = f.mul(upb, inv);
     const double denb = f.mul(f.mul(-Xb, X), inv);
@@ -147,30 +150,27 @@ __device__ __forceinline__ void face_field_bwd_saved(double d01, double d12, dou
     d23b = f.add(d23b, fma(g.dp[1], rb, f.mul(hX, W2)));
     yb[1] += g.dp[2] * rb;
     yb[3] += g.dp[3] * rb;
-    double b0b = 0.0;
-    weights_bwd(b0, b12, b23, e12, e23, g.eps, W0b, W1b, W2b, b0b, b12b, b23b, e12b, e23b, f);
-    beta0_bwd(d12, d23, y1, y3, b0b, d12b, d23b, yb[1], yb[3], f);
+    double e0b = 0.0;
+    weights_e_bwd(e0, e12, e23, W0b, W1b, W2b, e0b, e12b, e23b, f);
+    beta0_eps_s_bwd(d12, d23, y1, y3, g, e0b, d12b, d23b, yb[1], yb[3], f);
   }
-  b01b = f.add(b01b, e01b);
-  b12b = f.add(b12b, e12b);
-  b23b = f.add(b23b, e23b);
-  db[0] = f.add(db[0], fma(2.0 * d01, b01b, d01b));
-  db[1] = f.add(db[1], fma(2.0 * d12, b12b, d12b));
-  db[2] = f.add(db[2], fma(2.0 * d23, b23b, d23b));
+  // e_kl = d_kl^2 + eps
+  db[0] = f.add(db[0], fma(2.0 * d01, e01b, d01b));
+  db[1] = f.add(db[1], fma(2.0 * d12, e12b, d12b));
+  db[2] = f.add(db[2], fma(2.0 * d23, e23b, d23b));
 }
 
 // The limiter (Eq. limiter) of one characteristic field from the differences d01 = w1 - w0,
-// d12 = w2 - w1 and the scaled derivatives y0, y2: h v~_i, saving [b0, W0, W1, W2, t, num, 1/den].
+// d12 = w2 - w1 and the scaled derivatives y0, y2: h v~_i, saving [e0, W0, W1, W2, t, num, 1/den].
 __device__ __forceinline__ double cell_field_save(double d01, double d12, double y0, double y2, const Grid& g,
-                                                  double* sv, int stride, const FU& f = HW_PLAIN_FU) {
-  const double b1 = f.mul(d01, d01), b2 = f.mul(d12, d12);
+                                                  double* sv, int stride, const FU& f) {
   double du, svs;
-  const double b0 = beta0(d01, d12, y0, y2, du, svs, f);
-  const Wts wt = weights(b0, b1, b2, b1 + g.eps, b2 + g.eps, g.eps, f);
+  const double e0 = beta0_eps_s(d01, d12, y0, y2, g, f, du, svs);
+  const Wts wt = weights_e(e0, fma(d01, d01, g.eps), fma(d12, d12, g.eps), f);
   const double t = fma(g.cdu, du, -g.csv * svs);
   const double num = fma(wt.W0, t, fma(wt.W1, d01, f.mul(wt.W2, d12)));
   const double inv = rcp(fma(g.Gd, wt.W0, f.add(wt.W1, wt.W2)), f);
-  sv[0] = b0;
+  sv[0] = e0;
   sv[stride] = wt.W0;
   sv[2 * stride] = wt.W1;
   sv[3 * stride] = wt.W2;
@@ -184,10 +184,9 @@ __device__ __forceinline__ double cell_field_save(double d01, double d12, double
 // of d01, d12 (db) and y0, y2.
 __device__ __forceinline__ void cell_field_bwd_saved(double d01, double d12, double y0, double y2, const Grid& g,
                                                      double outb, const double* sv, int stride, double* db,
-                                                     double& y0b, double& y2b, const FU& f = HW_PLAIN_FU) {
-  const double b1 = f.mul(d01, d01), b2 = f.mul(d12, d12);
-  const double e1 = b1 + g.eps, e2 = b2 + g.eps;
-  const double b0 = sv[0], W0 = sv[stride], W1 = sv[2 * stride], W2 = sv[3 * stride];
+                                                     double& y0b, double& y2b, const FU& f) {
+  const double e1 = fma(d01, d01, g.eps), e2 = fma(d12, d12, g.eps);
+  const double e0 = sv[0], W0 = sv[stride], W1 = sv[2 * stride], W2 = sv[3 * stride];
   const double t = sv[4 * stride], num = sv[5 * stride], inv = sv[6 * stride];
   const double numb = f.mul(outb, inv);
   const double denb = f.mul(f.mul(-numb, num), inv);
@@ -199,13 +198,11 @@ __device__ __forceinline__ void cell_field_bwd_saved(double d01, double d12, dou
   d12b += g.cdu * tb;
   y0b -= g.csv * tb;
   y2b -= g.csv * tb;
-  double b0b = 0.0, b1b = 0.0, b2b = 0.0, e1b = 0.0, e2b = 0.0;
-  weights_bwd(b0, b1, b2, e1, e2, g.eps, W0b, W1b, W2b, b0b, b1b, b2b, e1b, e2b, f);
-  beta0_bwd(d01, d12, y0, y2, b0b, d01b, d12b, y0b, y2b, f);
-  b1b = f.add(b1b, e1b);
-  b2b = f.add(b2b, e2b);
-  db[0] = f.add(db[0], fma(2.0 * d01, b1b, d01b));
-  db[1] = f.add(db[1], fma(2.0 * d12, b2b, d12b));
+  double e0b = 0.0, e1b = 0.0, e2b = 0.0;
+  weights_e_bwd(e0, e1, e2, W0b, W1b, W2b, e0b, e1b, e2b, f);
+  beta0_eps_s_bwd(d01, d12, y0, y2, g, e0b, d01b, d12b, y0b, y2b, f);
+  db[0] = f.add(db[0], fma(2.0 * d01, e1b, d01b));
+  db[1] = f.add(db[1], fma(2.0 * d12, e2b, d12b));
 }
 
 // ---------------------------------------------------------------------------------------------

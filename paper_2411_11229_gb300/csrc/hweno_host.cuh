@@ -193,6 +193,10 @@ inline Grid grid_of(const hweno_ctx* h) {
   const Pair p1 = pair(fA, 1.0, fC, 781.0 / 20.0), p2 = pair(fB, 13.0 / 3.0, fD, 1421461.0 / 2275.0);
   g.bT1 = p1.T;
   g.bT2 = p2.T;
+  g.aS1 = p1.s;
+  g.aN1 = p1.q / p1.s;
+  g.aS2 = p2.s;
+  g.aN2 = p2.q / p2.s;
   const double hs[2] = {h->dx, h->dy};
   for (int d = 0; d < 2; ++d) {
     g.h[d] = hs[d];

@@ -56,6 +56,8 @@ struct Grid {
   // (see beta0_eps); udm, udp: dm, dp with their derivative coefficients times h;
   // uvd = (21/16, 3/16)/h: the cell differences in the derivative at the face; ucsv = csv h.
   double bS1[2], bN1[2], bS2[2], bN2[2], bT1, bT2;
+  // the same split for h-scaled derivatives (h = 1 in S and N; the adjoint's form)
+  double aS1, aN1, aS2, aN2;
   double udm[2][4], udp[2][4], uvd[2][2], ucsv[2];
   double h[2], ih[2], chh[2], efih[2], egih[2], hih[2];
   // Extended scheme (read only by the kernels instantiated with VAR != 0):
@@ -107,19 +109,8 @@ __device__ __forceinline__ double sqr(double x) { return x * x; }
 //   a1 + a3/4 = -3/16 sv + 11/16 du,  a2 + 63/130 a4 = 67/520 dv + 197/260 d2,
 //   a3 = (sv - du)/4,  a4 = -(dv + 2 d2)/4,
 // beta0 = (a1 + a3/4)^2 + 13/3 (a2 + 63/130 a4)^2 + 781/20 a3^2 + 1421461/2275 a4^2,
-// beta1 = dm^2, beta2 = dp^2 (passed in: neighbouring stencils share them).
-__device__ __forceinline__ double beta0(double dm, double dp, double hvm, double hvp, double& du_out,
-                                        double& sv_out, const FU& f = HW_PLAIN_FU) {
-  const double du = f.add(dm, dp), d2 = f.sub(dp, dm);
-  const double sv = f.add(hvm, hvp), dv = f.sub(hvm, hvp);
-  const double A = fma(-0.1875, sv, 0.6875 * du);
-  const double B = fma(67.0 / 520.0, dv, (197.0 / 260.0) * d2);
-  const double C = f.sub(sv, du);
-  const double D = fma(2.0, d2, dv);
-  du_out = du;
-  sv_out = sv;
-  return fma((1421461.0 / 2275.0 / 16.0) * D, D, fma((781.0 / 20.0 / 16.0) * C, C, fma((13.0 / 3.0) * B, B, f.mul(A, A))));
-}
+// beta1 = dm^2, beta2 = dp^2 (passed in: neighbouring stencils share them).  The kernels evaluate
+// beta0 through the completed squares below (beta0_eps; the adjoint's beta0_eps_s).
 
 // beta0 + eps with unscaled derivatives vm = v_{i-1}, vp = v_{i+1} along direction dir.  The four
 // squared forms of beta0 make one quadratic form in (h sv, du) and one in (h dv, d2); completing the
@@ -142,20 +133,6 @@ __device__ __forceinline__ double beta0_eps(double dm, double dp, double vm, dou
 struct Wts {
   double W0, W1, W2;
 };
-
-__device__ __forceinline__ Wts weights(double b0, double b1, double b2, double e1, double e2, double eps,
-                                       const FU& f = HW_PLAIN_FU) {
-  const double ts = f.add(fabs(f.sub(b0, b1)), fabs(f.sub(b0, b2)));
-  const double tau = f.mul(0.25 * ts, ts);
-  const double e0 = b0 + eps;
-  const double Q0 = f.mul(e1, e2), Q1 = f.mul(e0, e2), Q2 = f.mul(e0, e1);
-  const double P = f.mul(Q0, e0);
-  Wts w;
-  w.W0 = fma(tau, Q0, P);
-  w.W1 = fma(tau, Q1, P);
-  w.W2 = fma(tau, Q2, P);
-  return w;
-}
 
 // Weights from e_l = beta_l + eps directly: e_l - e_k stands for beta_l - beta_k in tau.
 __device__ __forceinline__ Wts weights_e(double e0, double e1, double e2, const FU& f = HW_PLAIN_FU) {
