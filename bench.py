@@ -418,7 +418,7 @@ def run_ours(args, ws, rank, local):
     host_in = torch.from_numpy(np.ascontiguousarray(solver.state.cpu().numpy())).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     nbytes = host_in.numel() * 8
-    ke2e = max(2, min(args.steps, 6))
+    ke2e = max(2, args.steps)
     solver.upload(host_in)
     solver.step(0.0)
     solver.download(host_out)

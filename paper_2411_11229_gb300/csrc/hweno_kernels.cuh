@@ -658,6 +658,11 @@ __device__ __forceinline__ void update_body(const Grid& g, double* __restrict__ 
   const int i = (int)(p % g.nx), j = (int)(p / g.nx);
   const long long px = (long long)j * (g.nx + 1) + i;
   const long long oplx = (long long)g.ny * (g.nx + 1), oply = (long long)(g.ny + 1) * g.nx;
+  // the stage's constants copied into thread registers (exactly: c 1 + (-0) = c), so that every
+  // FP64 instruction below has register operands (see FU)
+  const FU fu = fu_of(w.scal);
+  const double mix = fu.mul(-g.inv_dx, fu.one), miy = fu.mul(-g.inv_dy, fu.one);
+  const double dtr = fu.mul(dt, fu.one), akr = fu.mul(a_k, fu.one), bkr = fu.mul(b_k, fu.one);
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     // Eq. (euler2d-s): field f gains g (0, 0, S_f[rho], S_f[rho nu]) (read before S is overwritten)
@@ -669,19 +674,20 @@ __device__ __forceinline__ void update_body(const Grid& g, double* __restrict__ 
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
       const int fk = f * NC + k;
-      double L = -(w.FX[fk * oplx + px + 1] - w.FX[fk * oplx + px]) * g.inv_dx;
-      if (DIM == 2) L = fma(-(w.FY[fk * oply + p + g.nx] - w.FY[fk * oply + p]), g.inv_dy, L);
-      if (SRC && k == 2) L += src2;
-      if (SRC && k == 3) L += src3;
+      // L = -(F_{i+1/2} - F_{i-1/2}) / dx [- (G_{j+1/2} - G_{j-1/2}) / dy] [+ source]
+      double L = fu.mul(fu.sub(w.FX[fk * oplx + px + 1], w.FX[fk * oplx + px]), mix);
+      if (DIM == 2) L = fma(fu.sub(w.FY[fk * oply + p + g.nx], w.FY[fk * oply + p]), miy, L);
+      if (SRC && k == 2) L = fu.add(L, src2);
+      if (SRC && k == 3) L = fu.add(L, src3);
       const double M = f == 0 ? S[fk * plane + p] : w.MD[((long long)(f - 1) * NC + k) * plane + p];
       if (mode == 1) {
         Lout[fk * plane + p] = L;
         Mout[fk * plane + p] = M;
       } else if (stage == 0) {
         w.B[fk * plane + p] = M;
-        S[fk * plane + p] = fma(dt, L, M);
+        S[fk * plane + p] = fma(dtr, L, M);
       } else {
-        S[fk * plane + p] = fma(a_k, w.B[fk * plane + p], b_k * fma(dt, L, M));
+        S[fk * plane + p] = fma(akr, w.B[fk * plane + p], fu.mul(bkr, fma(dtr, L, M)));
       }
     }
   }
