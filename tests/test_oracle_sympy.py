@@ -108,3 +108,28 @@ def test_dterms_match_degree5_hermite():
         assert abs(got[1] - ref[1]) <= 1e-12 * sc / hh
 
 
+
+
+def test_beta0_as_two_completed_squares():
+    """The kernels evaluate beta0 (Eq. GHYZ) as S1 (sv + N1 du)^2 + T1 du^2 + S2 (dv + N2 d2)^2
+    + T2 d2^2 with du = u_{i+1} - u_{i-1}, d2 = u_{i+1} - 2 u_i + u_{i-1}, sv = h (v_{i-1} +
+    v_{i+1}), dv = h (v_{i-1} - v_{i+1}): each pair of the explicit linear forms (a1 + a3/4 with a3;
+    a2 + 63/130 a4 with a4), with its weights, is one quadratic form s X^2 + 2 q X Y + r Y^2 =
+    s (X + (q/s) Y)^2 + (det/s) Y^2.  Exact in rationals against the integral definition."""
+    x, h, (um, u0, up, vm, vp), (p0, _, _) = _hermite_candidates()
+    beta0 = sp.expand(_beta(p0, x, h, 4))
+    R = sp.Rational
+
+    def pair(f, wf, k, wk):
+        s = wf * f[0] ** 2 + wk * k[0] ** 2
+        q = wf * f[0] * f[1] + wk * k[0] * k[1]
+        m = f[0] * k[1] - f[1] * k[0]
+        return s, q / s, wf * wk * m * m / s
+
+    S1, N1, T1 = pair((R(-3, 16), R(11, 16)), 1, (R(1, 4), R(-1, 4)), R(781, 20))
+    S2, N2, T2 = pair((R(67, 520), R(197, 260)), R(13, 3), (R(-1, 4), R(-1, 2)), R(1421461, 2275))
+    du, d2 = up - um, up - 2 * u0 + um
+    sv, dv = h * (vm + vp), h * (vm - vp)
+    squares = S1 * (sv + N1 * du) ** 2 + T1 * du ** 2 + S2 * (dv + N2 * d2) ** 2 + T2 * d2 ** 2
+    assert sp.simplify(sp.expand(squares) - beta0) == 0
+    assert T1 == R(781, 3169) and T1 > 0 and T2 > 0 and S1 > 0 and S2 > 0
