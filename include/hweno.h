@@ -139,8 +139,10 @@ size_t hweno_state_doubles(const hweno_t *h);
 size_t hweno_workspace_bytes(const hweno_t *h);
 
 /* Borrow the caller's device state (updated in place by hweno_step) and workspace (at least
- * hweno_workspace_bytes() bytes).  Clears the device scalars (wavespeed slots, time, status) with
- * an asynchronous memset on the handle's stream.  EINVAL: NULL pointers or unaligned pointers. */
+ * hweno_workspace_bytes() bytes).  Clears the device scalars (wavespeed slots, time, status, and
+ * four slots the kernels read as zero to hold the units of their arithmetic in registers) with an
+ * asynchronous memset on the handle's stream; the workspace belongs to the library until the
+ * handle is destroyed or rebound.  EINVAL: NULL pointers or unaligned pointers. */
 int hweno_bind(hweno_t *h, double *state_dev, void *workspace_dev);
 
 /* One evaluation of the spatial operator at S: L(S) (Eq. odeH / ode2H, every field) and
