@@ -75,8 +75,9 @@ struct Grid {
 
 // FP64 issue on this GPU (measured with independent chains per thread): a DFMA whose three operands
 // are thread registers issues at 1.9 per SM-clock; DADD, DMUL, and a DFMA with an immediate,
-// constant-bank or block-uniform operand, at 1.6.  The forward kernels therefore issue their sums,
-// differences and products of register values as DFMAs against 1 and -0 held in thread registers:
+// constant-bank or block-uniform operand, at 1.6.  The stage and adjoint kernels therefore issue
+// their sums, differences and products of register values as DFMAs against 1 and -0 held in thread
+// registers:
 // fma(a, 1, b) = a + b and fma(a, b, -0) = a b exactly (the same rounding, signed zeros included).
 // FU carries the two units; the kernels load them through memory the compiler cannot see into
 // (fu_of), and the default FU{1, -0} folds back to plain sums and products.
