@@ -154,6 +154,30 @@ def test_gravity_source_on_uniform_flow():
     assert np.abs(L - ref).max() <= 1e-12
 
 
+def test_ssp_rk3_integrates_the_gravity_source_exactly():
+    """Uniform flow with gravity stays uniform, so at every stage L is the source alone: rho nu grows
+    linearly and E quadratically in time.  That system is nilpotent, so a third-order Runge-Kutta
+    step (Eqs. fully-hweno, 2Dfully-hweno) integrates it exactly: one step and ten steps equal the
+    closed form rho nu(t) = rho nu_0 + g rho t, E(t) = E_0 + g (rho nu_0 t + g rho t^2 / 2) to
+    round-off, and the derivative fields stay zero.  A wrong stage coefficient breaks the t^2 term."""
+    n, g = 8, 0.7
+    rho, u, v, p, gam = 1.3, 0.4, -0.6, 2.1, 1.4
+    one = np.ones((n, n))
+    zero = 0 * one
+    U, _ = W.euler_from_primitive_2d(rho * one, u * one, v * one, p * one, zero, zero, zero, zero, gam)
+    S0 = np.stack([U, 0 * U, 0 * U])
+    cfg = O.make_cfg(2, O.EULER, n, n, dx=0.1, dy=0.1, gamma=gam, grav=g)
+    E0 = p / (gam - 1.0) + 0.5 * rho * (u * u + v * v)
+    dt = 0.013
+    for nsteps in (1, 10):
+        S = O.steps(cfg, S0, dt, nsteps)
+        t = dt * nsteps
+        exact = (rho, rho * u, rho * v + g * rho * t, E0 + g * (rho * v * t + 0.5 * g * rho * t * t))
+        for k, val in enumerate(exact):
+            assert np.abs(S[0, k] - val).max() <= 1e-13 * max(1.0, abs(val)), (nsteps, k)
+        assert np.abs(S[1:]).max() == 0.0
+
+
 def test_gravity_balances_a_hydrostatic_column():
     """Constant density, P = p0 + g rho0 y: the scheme differentiates the linear pressure exactly,
     so away from the fixed top and bottom (whose ghost values are constant) L vanishes to
