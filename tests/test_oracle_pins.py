@@ -403,3 +403,21 @@ def test_blast_wave_first_stage_momentum_is_the_central_d_term():
     m = S[0, 1, 0, 41] + dt * L[0, 1, 0, 41]
     E = S[0, 2, 0, 41] + dt * L[0, 2, 0, 41]
     assert 0.4 * (E - 0.5 * m * m / S[0, 0, 0, 41]) < 0.0
+
+
+def test_operation_counts_are_per_unit_and_compose():
+    """The oracle's operation counter (its own arithmetic run on a counting type; the algorithmic
+    flops of the roofline): per-unit counts that do not depend on the grid, the linear-advection
+    nodal values f = a u, f'(u) v = a v (and the mixed value a w in 2D) at one product each, and the
+    per-cell step as three stages of dim directions of (face, nodal, modified derivative,
+    wavespeed) plus the update.  (A scalar law's wavespeed |a| or |u| takes no counted operation.)"""
+    for dim, system in ((1, O.ADVECTION), (2, O.ADVECTION), (1, O.BURGERS), (1, O.EULER), (2, O.EULER)):
+        small = O.count_flops(O.make_cfg(dim, system, 16, 16, dx=0.1, dy=0.1))
+        large = O.count_flops(O.make_cfg(dim, system, 512, 256, dx=0.01, dy=0.02))
+        assert small == large
+        assert all(small[k] > 0 for k in ("face", "nodal_per_dir", "modified_derivative_per_dir", "update"))
+        per = small["face"] + small["nodal_per_dir"] + small["modified_derivative_per_dir"] + \
+            small["wavespeed_per_dir"]
+        assert small["per_cell_step"] == 3 * (dim * per + small["update"])
+    assert O.count_flops(O.make_cfg(1, O.ADVECTION, 16))["nodal_per_dir"] == 2
+    assert O.count_flops(O.make_cfg(2, O.ADVECTION, 16, 16))["nodal_per_dir"] == 3
