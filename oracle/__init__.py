@@ -36,7 +36,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-pthread",
            "-o", tmp, _SRC]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
@@ -81,6 +81,8 @@ def lib():
             build()
             L = ctypes.CDLL(_LIB)
             CP = ctypes.POINTER(Cfg)
+            L.oracle_set_threads.argtypes = [ctypes.c_int]
+            L.oracle_set_threads.restype = ctypes.c_int
             L.oracle_state_size.argtypes = [CP]
             L.oracle_state_size.restype = ctypes.c_longlong
             L.oracle_max_wavespeed.argtypes = [CP, _P, _P, _P]
@@ -109,6 +111,13 @@ def lib():
             L.oracle_euler_eigen.argtypes = [CP, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]
             _lib = L
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads the operator runs on (0: all hardware threads, the default; 1: one).  Lines of a
+    sweep and values of an update are split over the threads; the results are the same bit for bit
+    for every thread count.  Returns the count the next calls use."""
+    return int(lib().oracle_set_threads(int(n)))
 
 
 def _ptr(a: np.ndarray):

@@ -51,10 +51,40 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <thread>
 #include <vector>
 #include <algorithm>
 
 namespace hwo {
+
+// ---------------------------------------------------------------------------------------------
+// Threads.  The operator is evaluated line by line (a row for the x sweep, a column for the y
+// sweep) and cell by cell; every face flux, modified derivative and updated value is written by
+// exactly one line or cell, and no value's arithmetic depends on which thread computes it or on
+// the order in which lines are taken.  Splitting the lines (and the cell-wise loops) into
+// contiguous chunks over threads therefore gives results that are bit for bit those of one thread.
+inline int& thread_count() {
+  static int n = 0;  // 0: all hardware threads
+  return n;
+}
+inline int threads_used() {
+  int n = thread_count();
+  if (n <= 0) n = (int)std::thread::hardware_concurrency();
+  return n < 1 ? 1 : n;
+}
+// body(lo, hi) on contiguous chunks of [0, n), one chunk per thread
+template <class F>
+void parallel_for(long long n, F body) {
+  const long long T = std::min<long long>(threads_used(), n);
+  if (T <= 1) {
+    if (n > 0) body(0LL, n);
+    return;
+  }
+  const long long chunk = (n + T - 1) / T;
+  std::vector<std::thread> th;
+  for (long long lo = 0; lo < n; lo += chunk) th.emplace_back(body, lo, std::min(n, lo + chunk));
+  for (auto& t : th) t.join();
+}
 
 using std::fabs;
 using std::sqrt;
@@ -504,10 +534,13 @@ R boundary_value(const Cfg& c, const R* S, int f, int k, int j, int i) {
 
 template <class R>
 void fill_padded(const Cfg& c, const R* S, Padded<R>& P) {
-  for (int f = 0; f < P.nf; ++f)
-    for (int k = 0; k < P.nc; ++k)
-      for (int j = -P.gy; j < P.ny + P.gy; ++j)
-        for (int i = -P.gx; i < P.nx + P.gx; ++i) P.at(f, k, j, i) = boundary_value(c, S, f, k, j, i);
+  const long long rows = (long long)P.nf * P.nc * P.py;  // padded rows (f, k, j)
+  parallel_for(rows, [&](long long lo, long long hi) {
+    for (long long r = lo; r < hi; ++r) {
+      const int j = (int)(r % P.py) - P.gy, k = (int)((r / P.py) % P.nc), f = (int)(r / ((long long)P.py * P.nc));
+      for (int i = -P.gx; i < P.nx + P.gx; ++i) P.at(f, k, j, i) = boundary_value(c, S, f, k, j, i);
+    }
+  });
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -679,7 +712,9 @@ struct Operator {
       const int other = dir == 0 ? 2 : 1;  // derivative field with the mixed flux (2D)
       const int nlines = dir == 0 ? ny : nx;
       const int nalong = dir == 0 ? nx : ny;
-      for (int line = 0; line < nlines; ++line) {
+      // lines are independent: each writes only its own faces and cells
+      parallel_for(nlines, [&](long long line_lo, long long line_hi) {
+      for (int line = (int)line_lo; line < (int)line_hi; ++line) {
         auto cellF = [&](int f, int a, R* D) {
           for (int k = 0; k < m; ++k) D[k] = dir == 0 ? P.at(f, k, line, a) : P.at(f, k, a, line);
         };
@@ -719,16 +754,19 @@ struct Operator {
           }
         }
       }
+      });
     }
-    // Step 4: the conservative differences
-    for (int f = 0; f < nfl; ++f)
-      for (int k = 0; k < m; ++k)
-        for (int j = 0; j < ny; ++j)
-          for (int i = 0; i < nx; ++i) {
-            R val = -(1.0 / c.dx) * (fx(f, k, j, i + 1) - fx(f, k, j, i));
-            if (c.dim == 2) val = val - (1.0 / c.dy) * (fy(f, k, j + 1, i) - fy(f, k, j, i));
-            Lout[((size_t)f * m + k) * plane + (size_t)j * nx + i] = val;
-          }
+    // Step 4: the conservative differences (row by row)
+    parallel_for((long long)nfl * m * ny, [&](long long lo, long long hi) {
+      for (long long r = lo; r < hi; ++r) {
+        const int j = (int)(r % ny), k = (int)((r / ny) % m), f = (int)(r / ((long long)ny * m));
+        for (int i = 0; i < nx; ++i) {
+          R val = -(1.0 / c.dx) * (fx(f, k, j, i + 1) - fx(f, k, j, i));
+          if (c.dim == 2) val = val - (1.0 / c.dy) * (fy(f, k, j + 1, i) - fy(f, k, j, i));
+          Lout[((size_t)f * m + k) * plane + (size_t)j * nx + i] = val;
+        }
+      }
+    });
     if (c.grav != 0.0)
       for (int f = 0; f < nfl; ++f)
         for (size_t p = 0; p < plane; ++p) {
@@ -813,6 +851,25 @@ struct Operator {
   }
 };
 
+// Stage st of Eq. (fully-hweno) / (2Dfully-hweno) from L and M of the stage input: at the first
+// stage B = M(S^n) (u^n and the modified derivatives) and S = M + dt L; then
+// S = a_k B + b_k (M + dt L) with (a_k, b_k) = (3/4, 1/4), (1/3, 2/3).  Value by value.
+template <class R>
+void rk3_combine(int st, size_t n, double dt, const R* L, const R* M, R* B, R* S) {
+  static const double a_k[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0};
+  static const double b_k[3] = {1.0, 1.0 / 4.0, 2.0 / 3.0};
+  parallel_for((long long)n, [&](long long lo, long long hi) {
+    for (long long p = lo; p < hi; ++p) {
+      if (st == 0) {
+        B[p] = M[p];
+        S[p] = M[p] + dt * L[p];
+      } else {
+        S[p] = a_k[st] * B[p] + b_k[st] * (M[p] + dt * L[p]);
+      }
+    }
+  });
+}
+
 // One SSP-RK3 step with the modified derivative in the base (Eq. fully-hweno / 2Dfully-hweno).
 // S is updated in place.  alpha per stage from the stage input.
 template <class R>
@@ -820,9 +877,7 @@ void rk3_step(const Cfg& c, R* S, double dt) {
   Operator<R> op(c);
   const int ny = c.dim == 2 ? c.ny : 1;
   const size_t n = (size_t)nfield(c) * ncomp(c) * c.nx * ny;
-  std::vector<R> L(n), M(n), B(n), S1(n);
-  static const double a_k[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0};
-  static const double b_k[3] = {1.0, 1.0 / 4.0, 2.0 / 3.0};
+  std::vector<R> L(n), M(n), B(n);
   R ax0 = R(0.0), ay0 = R(0.0);
   for (int st = 0; st < 3; ++st) {
     R ax = op.max_wavespeed(0, S);
@@ -836,12 +891,7 @@ void rk3_step(const Cfg& c, R* S, double dt) {
       ay = ay0;
     }
     op.rhs(S, L.data(), M.data(), ax, ay);
-    if (st == 0) {
-      for (size_t p = 0; p < n; ++p) B[p] = M[p];  // (u^n, v~^n, w~^n)
-      for (size_t p = 0; p < n; ++p) S[p] = M[p] + dt * L[p];
-    } else {
-      for (size_t p = 0; p < n; ++p) S[p] = a_k[st] * B[p] + b_k[st] * (M[p] + dt * L[p]);
-    }
+    rk3_combine(st, n, dt, L.data(), M.data(), B.data(), S);
   }
 }
 
@@ -1108,16 +1158,9 @@ void rk3_step_alpha(const Cfg& c, R* S, double dt, const double* alpha6) {
   const int ny = c.dim == 2 ? c.ny : 1;
   const size_t n = (size_t)nfield(c) * ncomp(c) * c.nx * ny;
   std::vector<R> L(n), M(n), B(n);
-  static const double a_k[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0};
-  static const double b_k[3] = {1.0, 1.0 / 4.0, 2.0 / 3.0};
   for (int st = 0; st < 3; ++st) {
     op.rhs(S, L.data(), M.data(), R(alpha6[2 * st]), R(alpha6[2 * st + 1]));
-    if (st == 0) {
-      for (size_t p = 0; p < n; ++p) B[p] = M[p];
-      for (size_t p = 0; p < n; ++p) S[p] = M[p] + dt * L[p];
-    } else {
-      for (size_t p = 0; p < n; ++p) S[p] = a_k[st] * B[p] + b_k[st] * (M[p] + dt * L[p]);
-    }
+    rk3_combine(st, n, dt, L.data(), M.data(), B.data(), S);
   }
 }
 
@@ -1185,6 +1228,13 @@ static int check_cfg(const oracle_cfg* c) {
   if (c->flags < 0 || c->flags > 31) return -1;
   if (!(c->gamma0 > 0 && c->gamma0 < 1) || !(c->d0 > 0 && c->d0 < 1) || !(c->eps > 0)) return -1;
   return 0;
+}
+
+// Threads of the operator (0: all hardware threads, the default; 1: serial).  The results do not
+// depend on it (bit for bit).  Returns the number of threads the next calls use.
+int oracle_set_threads(int n) {
+  hwo::thread_count() = n < 0 ? 0 : n;
+  return hwo::threads_used();
 }
 
 // number of doubles in one state
@@ -1342,8 +1392,6 @@ int oracle_steps_record(const oracle_cfg* c, double* S, int nsteps, double cfl, 
   const int ny = c->dim == 2 ? c->ny : 1;
   const size_t n = (size_t)hwo::nfield(*c) * hwo::ncomp(*c) * c->nx * ny;
   std::vector<double> L(n), M(n), B(n);
-  static const double a_k[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0};
-  static const double b_k[3] = {1.0, 1.0 / 4.0, 2.0 / 3.0};
   for (int s = 0; s < nsteps; ++s) {
     const double dt = hwo::cfl_dt(*c, S, cfl, 1.0);
     dts[s] = dt;
@@ -1354,12 +1402,7 @@ int oracle_steps_record(const oracle_cfg* c, double* S, int nsteps, double cfl, 
       alphas[6 * s + 2 * st] = ax;
       alphas[6 * s + 2 * st + 1] = ay;
       op.rhs(S, L.data(), M.data(), ax, ay);
-      if (st == 0) {
-        for (size_t p = 0; p < n; ++p) B[p] = M[p];
-        for (size_t p = 0; p < n; ++p) S[p] = M[p] + dt * L[p];
-      } else {
-        for (size_t p = 0; p < n; ++p) S[p] = a_k[st] * B[p] + b_k[st] * (M[p] + dt * L[p]);
-      }
+      hwo::rk3_combine(st, n, dt, L.data(), M.data(), B.data(), S);
     }
   }
   return 0;
