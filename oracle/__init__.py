@@ -97,6 +97,7 @@ def lib():
                                      ctypes.c_longlong, _P]
             L.oracle_run.restype = ctypes.c_longlong
             L.oracle_count_flops.argtypes = [CP, ctypes.POINTER(ctypes.c_longlong)]
+            L.oracle_count_stencil.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
             L.oracle_stage_vjp.argtypes = [CP, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P]
             L.oracle_stage_jvp.argtypes = [CP, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P]
             L.oracle_steps_record.argtypes = [CP, _P, ctypes.c_int, ctypes.c_double, _P, _P]
@@ -195,12 +196,21 @@ def run(cfg: Cfg, S: np.ndarray, t_end: float, cfl: float = 0.6, dx_pow: float =
 
 
 def count_flops(cfg: Cfg) -> dict:
-    """Floating-point operation counts of the scheme as the oracle writes it (see the C source)."""
+    """Floating-point operation counts of the scheme as the oracle writes it, with nontrivial
+    operands (see the C source): per face, per cell and direction, and per cell-step."""
     out = (ctypes.c_longlong * 6)()
     _check(lib().oracle_count_flops(ctypes.byref(cfg), out))
     keys = ("face", "nodal_per_dir", "modified_derivative_per_dir", "wavespeed_per_dir",
             "update", "per_cell_step")
     return dict(zip(keys, [int(v) for v in out]))
+
+
+def count_stencil() -> dict:
+    """Operation counts of one scalar HWENO stencil: the face part (u^-, v^-), the face part with the
+    weighted derivative, and the cell part (v~)."""
+    out = (ctypes.c_longlong * 3)()
+    _check(lib().oracle_count_stencil(out))
+    return {"face": int(out[0]), "face_v_weighted": int(out[1]), "cell": int(out[2])}
 
 
 def stage_vjp(cfg: Cfg, S, alpha, muM, muL):

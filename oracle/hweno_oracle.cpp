@@ -108,9 +108,65 @@ template <class R> inline R sq(const R& a) { return a * a; }
 
 // ---------------------------------------------------------------------------------------------
 // Sec. 2.1: one HWENO stencil T0 = {i-1,i,i+1} with T1 = {i-1,i}, T2 = {i,i+1}.
-// Inputs: u_{i-1}, u_i, u_{i+1}, v_{i-1}, v_{i+1}.  Outputs the value and derivative at x_{i+1/2}
-// (u^-_{i+1/2}, v^-_{i+1/2}, Eq. interp), the modified derivative at x_i (Eq. limiter), and
-// the intermediate quantities for the unit tests.
+// Inputs: u_{i-1}, u_i, u_{i+1}, v_{i-1}, v_{i+1}.  A face needs the value and derivative at
+// x_{i+1/2} (u^-_{i+1/2}, v^-_{i+1/2}, Eq. interp, weights from gamma); a cell needs the modified
+// derivative at x_i (Eq. limiter, weights from d).  Both share the smoothness indicators; the
+// pieces below are combined per use, and hweno_stencil gives every intermediate for the unit tests.
+
+// Eqs. (Pxi), (P'xi): p_l(x_{i+1/2}) and p0'(x_{i+1/2})
+template <class R>
+void face_candidates(const R& um, const R& u0, const R& up, const R& vm, const R& vp, double dx, R p[3], R& dp0) {
+  p[0] = -(1.0 / 8.0) * um + (9.0 / 16.0) * u0 + (9.0 / 16.0) * up - dx * ((3.0 / 64.0) * vm + (9.0 / 64.0) * vp);
+  p[1] = -(1.0 / 2.0) * um + (3.0 / 2.0) * u0;
+  p[2] = (1.0 / 2.0) * u0 + (1.0 / 2.0) * up;
+  dp0 = (1.0 / dx) * ((3.0 / 16.0) * um - (3.0 / 2.0) * u0 + (21.0 / 16.0) * up) + (1.0 / 16.0) * vm - (3.0 / 16.0) * vp;
+}
+
+// the slopes p1', p2' of the two linear candidates (Eq. limiter-p)
+template <class R>
+void candidate_slopes(const R& um, const R& u0, const R& up, double dx, R& dp1, R& dp2) {
+  dp1 = (1.0 / dx) * (u0 - um);
+  dp2 = (1.0 / dx) * (up - u0);
+}
+
+// Eq. (limiter-p): p_l'(x_i)
+template <class R>
+void centre_derivatives(const R& um, const R& u0, const R& up, const R& vm, const R& vp, double dx, R dpc[3]) {
+  dpc[0] = (3.0 / (4.0 * dx)) * (up - um) - (1.0 / 4.0) * (vm + vp);
+  candidate_slopes(um, u0, up, dx, dpc[1], dpc[2]);
+}
+
+// smoothness indicators (explicit form of Eq. GHYZ) and tau of Eq. (nonlinear)
+template <class R>
+void indicators(const R& um, const R& u0, const R& up, const R& vm, const R& vp, double dx, R beta[3], R& tau) {
+  R a1 = -(dx / 4.0) * (vm + vp) + (3.0 / 4.0) * (up - um);
+  R a2 = (dx / 4.0) * (vm - vp) + (um - 2.0 * u0 + up);
+  R a3 = (dx / 4.0) * (vm + vp) + (1.0 / 4.0) * (um - up);
+  R a4 = (dx / 4.0) * (vp - vm) - (1.0 / 2.0) * (um - 2.0 * u0 + up);
+  beta[0] = sq(a1 + (1.0 / 4.0) * a3) + (13.0 / 3.0) * sq(a2 + (63.0 / 130.0) * a4) + (781.0 / 20.0) * sq(a3) +
+            (1421461.0 / 2275.0) * sq(a4);
+  beta[1] = sq(u0 - um);
+  beta[2] = sq(u0 - up);
+  tau = (1.0 / 4.0) * sq(fabs(beta[0] - beta[1]) + fabs(beta[0] - beta[2]));
+}
+
+// Eq. (nonlinear): the weights omega_l from the linear weights lin (gamma or d)
+template <class R>
+void nonlinear_weights(const R beta[3], const R& tau, const double lin[3], double eps, R w[3]) {
+  R wb[3];
+  for (int l = 0; l < 3; ++l) wb[l] = lin[l] * (1.0 + tau / (beta[l] + eps));
+  R s = wb[0] + wb[1] + wb[2];
+  for (int l = 0; l < 3; ++l) w[l] = wb[l] / s;
+}
+
+// Eqs. (interp), (limiter): w0 (c0 / lin0 - (lin1 / lin0) c1 - (lin2 / lin0) c2) + w1 c1 + w2 c2
+template <class R>
+R combine(const R w[3], const double lin[3], const R c[3]) {
+  return w[0] * ((1.0 / lin[0]) * c[0] - (lin[1] / lin[0]) * c[1] - (lin[2] / lin[0]) * c[2]) + w[1] * c[1] +
+         w[2] * c[2];
+}
+
+// every intermediate of one stencil (unit tests)
 template <class R>
 struct StencilOut {
   R p[3];      // p_l(x_{i+1/2}), Eq. (Pxi)
@@ -128,74 +184,58 @@ struct StencilOut {
 template <class R>
 void hweno_stencil(const R& um, const R& u0, const R& up, const R& vm, const R& vp, double dx,
                    const double g[3], const double d[3], double eps, StencilOut<R>& o, bool v_weighted = false) {
-  // Eq. (Pxi)
-  o.p[0] = -(1.0 / 8.0) * um + (9.0 / 16.0) * u0 + (9.0 / 16.0) * up - dx * ((3.0 / 64.0) * vm + (9.0 / 64.0) * vp);
-  o.p[1] = -(1.0 / 2.0) * um + (3.0 / 2.0) * u0;
-  o.p[2] = (1.0 / 2.0) * u0 + (1.0 / 2.0) * up;
-  // Eq. (P'xi)
-  o.dp0 = (1.0 / dx) * ((3.0 / 16.0) * um - (3.0 / 2.0) * u0 + (21.0 / 16.0) * up) + (1.0 / 16.0) * vm - (3.0 / 16.0) * vp;
-  // Eq. (limiter-p)
-  o.dpc[0] = (3.0 / (4.0 * dx)) * (up - um) - (1.0 / 4.0) * (vm + vp);
-  o.dpc[1] = (1.0 / dx) * (u0 - um);
-  o.dpc[2] = (1.0 / dx) * (up - u0);
-  // smoothness indicators, explicit form of Eq. (GHYZ)
-  R a1 = -(dx / 4.0) * (vm + vp) + (3.0 / 4.0) * (up - um);
-  R a2 = (dx / 4.0) * (vm - vp) + (um - 2.0 * u0 + up);
-  R a3 = (dx / 4.0) * (vm + vp) + (1.0 / 4.0) * (um - up);
-  R a4 = (dx / 4.0) * (vp - vm) - (1.0 / 2.0) * (um - 2.0 * u0 + up);
-  o.beta[0] = sq(a1 + (1.0 / 4.0) * a3) + (13.0 / 3.0) * sq(a2 + (63.0 / 130.0) * a4) + (781.0 / 20.0) * sq(a3) +
-              (1421461.0 / 2275.0) * sq(a4);
-  o.beta[1] = sq(u0 - um);
-  o.beta[2] = sq(u0 - up);
-  // Eq. (nonlinear)
-  o.tau = (1.0 / 4.0) * sq(fabs(o.beta[0] - o.beta[1]) + fabs(o.beta[0] - o.beta[2]));
-  R wbg[3], wbd[3];
-  for (int l = 0; l < 3; ++l) {
-    wbg[l] = g[l] * (1.0 + o.tau / (o.beta[l] + eps));
-    wbd[l] = d[l] * (1.0 + o.tau / (o.beta[l] + eps));
-  }
-  R sg = wbg[0] + wbg[1] + wbg[2];
-  R sd = wbd[0] + wbd[1] + wbd[2];
-  for (int l = 0; l < 3; ++l) {
-    o.wg[l] = wbg[l] / sg;
-    o.wd[l] = wbd[l] / sd;
-  }
-  // Eq. (interp)
-  o.u_half = o.wg[0] * ((1.0 / g[0]) * o.p[0] - (g[1] / g[0]) * o.p[1] - (g[2] / g[0]) * o.p[2]) + o.wg[1] * o.p[1] +
-             o.wg[2] * o.p[2];
+  face_candidates(um, u0, up, vm, vp, dx, o.p, o.dp0);
+  centre_derivatives(um, u0, up, vm, vp, dx, o.dpc);
+  indicators(um, u0, up, vm, vp, dx, o.beta, o.tau);
+  nonlinear_weights(o.beta, o.tau, g, eps, o.wg);
+  nonlinear_weights(o.beta, o.tau, d, eps, o.wd);
+  o.u_half = combine(o.wg, g, o.p);
   o.v_half = o.dp0;
   if (v_weighted) {
     // the same combination applied to the derivatives at x_{i+1/2}; p1 and p2 are linear, so
     // their derivatives there are their slopes
-    o.v_half = o.wg[0] * ((1.0 / g[0]) * o.dp0 - (g[1] / g[0]) * o.dpc[1] - (g[2] / g[0]) * o.dpc[2]) +
-               o.wg[1] * o.dpc[1] + o.wg[2] * o.dpc[2];
+    const R c[3] = {o.dp0, o.dpc[1], o.dpc[2]};
+    o.v_half = combine(o.wg, g, c);
   }
-  // Eq. (limiter)
-  o.v_mod = o.wd[0] * ((1.0 / d[0]) * o.dpc[0] - (d[1] / d[0]) * o.dpc[1] - (d[2] / d[0]) * o.dpc[2]) +
-            o.wd[1] * o.dpc[1] + o.wd[2] * o.dpc[2];
+  o.v_mod = combine(o.wd, d, o.dpc);
 }
 
-// u^-_{i+1/2}, v^-_{i+1/2} from the stencil of cell i (and v~_i as a by-product).
+// u^-_{i+1/2}, v^-_{i+1/2} from the stencil of cell i (Eqs. Pxi, P'xi, GHYZ, nonlinear, interp).
 template <class R>
 void interp_minus(const R& um, const R& u0, const R& up, const R& vm, const R& vp, double dx, const double g[3],
-                  const double d[3], double eps, R& u_half, R& v_half, R& v_mod, bool vw = false) {
-  StencilOut<R> o;
-  hweno_stencil(um, u0, up, vm, vp, dx, g, d, eps, o, vw);
-  u_half = o.u_half;
-  v_half = o.v_half;
-  v_mod = o.v_mod;
+                  double eps, R& u_half, R& v_half, bool vw = false) {
+  R beta[3], tau, w[3], p[3], dp0, c[3];
+  face_candidates(um, u0, up, vm, vp, dx, p, dp0);
+  if (vw) candidate_slopes(um, u0, up, dx, c[1], c[2]);
+  indicators(um, u0, up, vm, vp, dx, beta, tau);
+  nonlinear_weights(beta, tau, g, eps, w);
+  u_half = combine(w, g, p);
+  v_half = dp0;
+  if (vw) {
+    c[0] = dp0;
+    v_half = combine(w, g, c);
+  }
 }
 
 // u^+_{i-1/2}, v^+_{i-1/2} from the stencil of cell i: the mirror image of interp_minus.  The
 // data are reflected about x_i (x -> 2 x_i - x): values swap ends, derivatives change sign.
 template <class R>
 void interp_plus(const R& um, const R& u0, const R& up, const R& vm, const R& vp, double dx, const double g[3],
-                 const double d[3], double eps, R& u_half, R& v_half, bool vw = false) {
-  StencilOut<R> o;
+                 double eps, R& u_half, R& v_half, bool vw = false) {
   R nvp = -vp, nvm = -vm;
-  hweno_stencil(up, u0, um, nvp, nvm, dx, g, d, eps, o, vw);
-  u_half = o.u_half;
-  v_half = -o.v_half;
+  interp_minus(up, u0, um, nvp, nvm, dx, g, eps, u_half, v_half, vw);
+  v_half = -v_half;
+}
+
+// v~_i from the stencil of cell i (Eqs. limiter-p, GHYZ, nonlinear with d, limiter).
+template <class R>
+R limited_derivative(const R& um, const R& u0, const R& up, const R& vm, const R& vp, double dx, const double d[3],
+                     double eps) {
+  R beta[3], tau, w[3], dpc[3];
+  centre_derivatives(um, u0, up, vm, vp, dx, dpc);
+  indicators(um, u0, up, vm, vp, dx, beta, tau);
+  nonlinear_weights(beta, tau, d, eps, w);
+  return combine(w, d, dpc);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -566,9 +606,8 @@ struct Operator {
     double h = dir == 0 ? c.dx : c.dy;
     const bool vw = (c.flags & FLAG_V_WEIGHTED) != 0;
     if (c.system != EULER) {
-      R vmod;
-      interp_minus(Uc[0][0], Uc[1][0], Uc[2][0], Dc[0][0], Dc[2][0], h, g, d, c.eps, Um[0], Dm[0], vmod, vw);
-      interp_plus(Uc[1][0], Uc[2][0], Uc[3][0], Dc[1][0], Dc[3][0], h, g, d, c.eps, Up[0], Dp[0], vw);
+      interp_minus(Uc[0][0], Uc[1][0], Uc[2][0], Dc[0][0], Dc[2][0], h, g, c.eps, Um[0], Dm[0], vw);
+      interp_plus(Uc[1][0], Uc[2][0], Uc[3][0], Dc[1][0], Dc[3][0], h, g, c.eps, Up[0], Dp[0], vw);
       return;
     }
     // local characteristic decomposition: one basis at the face (Roe average), or with FLAG_R2
@@ -603,9 +642,8 @@ struct Operator {
     }
     R wm[4], zm[4], wp[4], zp[4];
     for (int s2 = 0; s2 < m; ++s2) {
-      R vmod;
-      interp_minus(Wm[0][s2], Wm[1][s2], Wm[2][s2], Zm[0][s2], Zm[2][s2], h, g, d, c.eps, wm[s2], zm[s2], vmod, vw);
-      interp_plus(Wp[1][s2], Wp[2][s2], Wp[3][s2], Zp[1][s2], Zp[3][s2], h, g, d, c.eps, wp[s2], zp[s2], vw);
+      interp_minus(Wm[0][s2], Wm[1][s2], Wm[2][s2], Zm[0][s2], Zm[2][s2], h, g, c.eps, wm[s2], zm[s2], vw);
+      interp_plus(Wp[1][s2], Wp[2][s2], Wp[3][s2], Zp[1][s2], Zp[3][s2], h, g, c.eps, wp[s2], zp[s2], vw);
     }
     matvec(m, Rmm, wm, Um);
     matvec(m, Rmm, zm, Dm);
@@ -617,8 +655,7 @@ struct Operator {
   void modified_derivative(int dir, R Uc[3][4], R Dc[3][4], R* Dt) const {
     double h = dir == 0 ? c.dx : c.dy;
     if (c.system != EULER) {
-      R uh, vh;
-      interp_minus(Uc[0][0], Uc[1][0], Uc[2][0], Dc[0][0], Dc[2][0], h, g, d, c.eps, uh, vh, Dt[0]);
+      Dt[0] = limited_derivative(Uc[0][0], Uc[1][0], Uc[2][0], Dc[0][0], Dc[2][0], h, d, c.eps);
       return;
     }
     EigenState<R> s = cell_state(c, Uc[1]);
@@ -631,10 +668,7 @@ struct Operator {
       matvec(m, Lm, Dc[q], Z[q]);
     }
     R zt[4];
-    for (int s2 = 0; s2 < m; ++s2) {
-      R uh, vh;
-      interp_minus(W[0][s2], W[1][s2], W[2][s2], Z[0][s2], Z[2][s2], h, g, d, c.eps, uh, vh, zt[s2]);
-    }
+    for (int s2 = 0; s2 < m; ++s2) zt[s2] = limited_derivative(W[0][s2], W[1][s2], W[2][s2], Z[0][s2], Z[2][s2], h, d, c.eps);
     matvec(m, Rm, zt, Dt);
   }
 
@@ -906,25 +940,61 @@ double cfl_dt(const Cfg& c, const R* S, double cfl, double dx_pow) {
 
 // ---------------------------------------------------------------------------------------------
 // Operation counting: the same templated code instantiated with a scalar that counts every
-// floating-point +, -, *, / and sqrt (sign changes, fabs and comparisons are not counted).  The
-// counts are data independent (the arithmetic has no data-dependent branches).
+// floating-point +, -, *, / and sqrt applied to the data.  A Counted is either a value computed
+// from the data (made by Counted::data) or a constant of the scheme (a literal or a parameter,
+// what every implicit conversion from double makes).  Not counted: sign changes, fabs and
+// comparisons; operations between constants (the constant folding any implementation does once);
+// and operations with a structural constant 0 or +-1: a product with such a factor, a quotient by
+// +-1 or of 0, a sum with a term 0.  These are the zeros and ones of the explicit Jacobian and
+// eigenvector matrices, which a plain matrix-vector product multiplies and adds like any other
+// entry, and the zero initial values of sums.  Values of the data are counted whatever they are,
+// so the counts do not depend on the data (the arithmetic has no data-dependent branches).
 struct Counted {
   double v;
-  Counted() : v(0.0) {}
-  Counted(double x) : v(x) {}
+  bool k;  // a constant of the scheme, not a value computed from the data
+  Counted() : v(0.0), k(true) {}
+  Counted(double x) : v(x), k(true) {}
+  static Counted data(double x) {
+    Counted c(x);
+    c.k = false;
+    return c;
+  }
+  static Counted make(double x, bool konst) {
+    Counted c(x);
+    c.k = konst;
+    return c;
+  }
   static long long& n() {
     static long long c = 0;
     return c;
   }
 };
-inline Counted operator+(const Counted& a, const Counted& b) { ++Counted::n(); return Counted(a.v + b.v); }
-inline Counted operator-(const Counted& a, const Counted& b) { ++Counted::n(); return Counted(a.v - b.v); }
-inline Counted operator*(const Counted& a, const Counted& b) { ++Counted::n(); return Counted(a.v * b.v); }
-inline Counted operator/(const Counted& a, const Counted& b) { ++Counted::n(); return Counted(a.v / b.v); }
-inline Counted operator-(const Counted& a) { return Counted(-a.v); }
+inline bool const0(const Counted& a) { return a.k && a.v == 0.0; }
+inline bool const1(const Counted& a) { return a.k && (a.v == 1.0 || a.v == -1.0); }
+inline Counted operator+(const Counted& a, const Counted& b) {
+  if (!(a.k && b.k) && !const0(a) && !const0(b)) ++Counted::n();
+  return Counted::make(a.v + b.v, a.k && b.k);
+}
+inline Counted operator-(const Counted& a, const Counted& b) {
+  if (!(a.k && b.k) && !const0(a) && !const0(b)) ++Counted::n();
+  return Counted::make(a.v - b.v, a.k && b.k);
+}
+inline Counted operator*(const Counted& a, const Counted& b) {
+  const bool zero = const0(a) || const0(b);
+  if (!(a.k && b.k) && !zero && !const1(a) && !const1(b)) ++Counted::n();
+  return Counted::make(a.v * b.v, (a.k && b.k) || zero);
+}
+inline Counted operator/(const Counted& a, const Counted& b) {
+  if (!(a.k && b.k) && !const0(a) && !const1(b)) ++Counted::n();
+  return Counted::make(a.v / b.v, (a.k && b.k) || const0(a));
+}
+inline Counted operator-(const Counted& a) { return Counted::make(-a.v, a.k); }
 inline bool operator>(const Counted& a, const Counted& b) { return a.v > b.v; }
-inline Counted fabs(const Counted& a) { return Counted(std::fabs(a.v)); }
-inline Counted sqrt(const Counted& a) { ++Counted::n(); return Counted(std::sqrt(a.v)); }
+inline Counted fabs(const Counted& a) { return Counted::make(std::fabs(a.v), a.k); }
+inline Counted sqrt(const Counted& a) {
+  if (!a.k) ++Counted::n();
+  return Counted::make(std::sqrt(a.v), a.k);
+}
 
 // ---------------------------------------------------------------------------------------------
 // Derivatives of the scheme for the adjoint (conventions: the step sizes and the LF coefficients
@@ -1322,20 +1392,30 @@ long long oracle_run(const oracle_cfg* c, double* S, double t_end, double cfl, d
 int oracle_count_flops(const oracle_cfg* c, long long* out) {
   if (check_cfg(c)) return -1;
   using hwo::Counted;
-  hwo::Operator<Counted> op(*c);
-  const int m = hwo::ncomp(*c);
-  const int dim = c->dim;
+  // spacings and speeds that are neither 0 nor +-1 (a parameter equal to 1 would make its products
+  // structural)
+  oracle_cfg cc = *c;
+  cc.dx = 0.0371;
+  cc.dy = 0.0293;
+  cc.ax = 0.713;
+  cc.ay = -0.537;
+  hwo::Operator<Counted> op(cc);
+  const int m = hwo::ncomp(cc);
+  const int dim = cc.dim;
   long long& n = Counted::n();
+  // four cells of a physical state (rho, momenta, E) with derivative data
   Counted Uc[4][4], Dc[4][4], Oc[4][4];
   for (int q = 0; q < 4; ++q)
     for (int k = 0; k < 4; ++k) {
-      Uc[q][k] = Counted(k == 0 ? 1.0 + 0.1 * q : (k == m - 1 ? 2.5 + 0.1 * q : 0.2 * q - 0.1));
-      Dc[q][k] = Counted(0.3 * q - 0.2 * k);
-      Oc[q][k] = Counted(0.1 * k - 0.2 * q);
+      const double qq = 0.0419 * q * q;
+      const double mom = k == 1 ? 0.2317 * q - 0.1109 - qq : -0.1931 + 0.0713 * q + qq;
+      Uc[q][k] = Counted::data(k == 0 ? 1.3127 + 0.1713 * q + qq : (k == m - 1 ? 2.7139 + 0.1327 * q - qq : mom));
+      Dc[q][k] = Counted::data(0.3137 * q - 0.2291 * k + 0.0517 + 0.0293 * q * q);
+      Oc[q][k] = Counted::data(0.1123 * k - 0.2017 * q + 0.0331 - 0.0371 * q * q);
     }
   Counted fh[4], hh[4], mx[4];
   n = 0;
-  op.face_flux(0, Uc, Dc, Oc, Counted(2.0), fh, hh, mx);
+  op.face_flux(0, Uc, Dc, Oc, Counted::data(2.0317), fh, hh, mx);  // alpha: the data's wavespeed
   long long face_all = n;
   n = 0;
   Counted fn[4], hn[4], on[4];
@@ -1357,7 +1437,7 @@ int oracle_count_flops(const oracle_cfg* c, long long* out) {
   long long ws = n;
   // conservative difference (dim differences, each a subtraction and a scaling, summed) and the
   // stage combination a B + b (M + dt L) per value
-  const long long nvals = (long long)hwo::nfield(*c) * m;
+  const long long nvals = (long long)hwo::nfield(cc) * m;
   long long upd = nvals * (dim == 2 ? 5 : 2) + nvals * 4;
   out[0] = face_all - 4 * nodal;
   out[1] = nodal;
@@ -1365,6 +1445,30 @@ int oracle_count_flops(const oracle_cfg* c, long long* out) {
   out[3] = ws;
   out[4] = upd;
   out[5] = 3 * (dim * (out[0] + out[1] + out[2] + out[3]) + upd);
+  n = 0;
+  return 0;
+}
+
+// Operation counts (the convention of oracle_count_flops) of one scalar stencil of Sec. 2.1:
+// out[0] the face part, u^- and v^- at x_{i+1/2} (Eqs. Pxi, P'xi, GHYZ, nonlinear with gamma,
+// interp); out[1] the same with the weighted derivative of the FLAG_V_WEIGHTED variant;
+// out[2] the cell part, v~_i (Eqs. limiter-p, GHYZ, nonlinear with d, limiter).
+int oracle_count_stencil(long long* out) {
+  using hwo::Counted;
+  const double g[3] = {0.95, 0.025, 0.025}, d[3] = {0.9, 0.05, 0.05};
+  const Counted um = Counted::data(1.3127), u0 = Counted::data(1.4841), up = Counted::data(1.2291);
+  const Counted vm = Counted::data(0.3137), vp = Counted::data(-0.2019);
+  long long& n = Counted::n();
+  Counted a, b;
+  n = 0;
+  hwo::interp_minus(um, u0, up, vm, vp, 0.0371, g, 1e-10, a, b, false);
+  out[0] = n;
+  n = 0;
+  hwo::interp_minus(um, u0, up, vm, vp, 0.0371, g, 1e-10, a, b, true);
+  out[1] = n;
+  n = 0;
+  a = hwo::limited_derivative(um, u0, up, vm, vp, 0.0371, d, 1e-10);
+  out[2] = n;
   n = 0;
   return 0;
 }
@@ -1443,7 +1547,7 @@ int oracle_stencil(const double* u3, const double* v2, double dx, double gamma0,
   out[17] = o.u_half;
   out[18] = o.v_half;
   out[19] = o.v_mod;
-  hwo::interp_plus(u3[0], u3[1], u3[2], v2[0], v2[1], dx, g, d, eps, out[20], out[21], vw);
+  hwo::interp_plus(u3[0], u3[1], u3[2], v2[0], v2[1], dx, g, eps, out[20], out[21], vw);
   return 0;
 }
 

@@ -421,3 +421,55 @@ def test_operation_counts_are_per_unit_and_compose():
         assert small["per_cell_step"] == 3 * (dim * per + small["update"])
     assert O.count_flops(O.make_cfg(1, O.ADVECTION, 16))["nodal_per_dir"] == 2
     assert O.count_flops(O.make_cfg(2, O.ADVECTION, 16, 16))["nodal_per_dir"] == 3
+
+
+# Hand counts of the scheme's operations, read off the formulas of Sec. 2 term by term (a constant
+# coefficient times a value is one product; sums of constants, sign changes and the zeros and ones
+# of the Euler matrices cost nothing).
+STENCIL_FACE = {
+    "Pxi, P'xi": 10 + 3 + 3 + 10,      # p0 (6 products, 4 sums), p1, p2, p0'(x_{i+1/2})
+    "GHYZ": 5 + 6 + 5 + 7 + 14 + 2 + 2,  # a1..a4, beta0 as four weighted squares, beta1, beta2
+    "tau": 5,                           # two differences, their sum, square, times 1/4
+    "nonlinear": 3 * 4 + 2 + 3,         # lin (1 + tau / (beta + eps)) each, the sum, three quotients
+    "interp": 10,                       # w0 (p0/g0 - g1/g0 p1 - g2/g0 p2) + w1 p1 + w2 p2
+}
+STENCIL_CELL = {"limiter-p": 5 + 2 + 2, "GHYZ": 41, "tau": 5, "nonlinear": 17, "limiter": 10}
+DTERMS = 7 + 11 + 7 + 11 + 3 + 3      # P2, P3, P4, P5 of Eq. (Cd-1), D(f) and D(h) of Eq. (DfDh)
+LF = 6 + 6                            # f^ and h^ of Eq. (flux-LF)
+MIXED = 7                             # Eq. (mixed): four products, three sums
+EULER2D = {                           # the characteristic and flux pieces of one 2D Euler face (x)
+    "roe": 4 + 2 * 7 + 2 * 2 + 2 + 3 * 5 + 7,  # velocities, pressures, enthalpies, sqrt rho, averages, c
+    "right": 4 + 6,                   # |q|^2/2 and the entries u -+ c, H -+ u c
+    "left": 2 + 5 + 10 + 3 + 10,      # b1, b2, rows 1..4 (the shear row is a sign change and copies)
+    "project": 7 + 7 + 2 + 7,         # L q: rows of 4, 4, 1 (-v q0 + q2) and 4 nontrivial entries
+    "back": 2 + 5 + 6 + 7,            # R w: rows (1,1,0,1), (u-c,u,0,u+c), (v,v,1,v), (H-uc,q,v,H+uc)
+    "flux": 2 + 7 + 8,                # velocities, pressure, f
+    "jvp": 26 + 19,                   # the Jacobian's nontrivial entries, then A v
+}
+
+
+def test_operation_counts_match_hand_counts():
+    """The counter against the hand counts above: one scalar stencil's face part (u^-, v^-), its
+    weighted-derivative form (the slopes p1', p2' and one more combination) and its cell part (v~);
+    a scalar face (two stencils, fluxes at U^+-, D-terms, LF fluxes, the mixed flux in 2D); the
+    2D Euler face (eight stencils, the Roe average, eigenvectors, eight projections, four back
+    projections, fluxes and Jacobian products at U^+-) and the 2D Euler modified derivative (the
+    cell's eigenvectors, six projections, four limiter stencils, one back projection)."""
+    face, cell = sum(STENCIL_FACE.values()), sum(STENCIL_CELL.values())
+    assert (face, cell) == (99, 82)
+    st = O.count_stencil()
+    assert st == {"face": face, "face_v_weighted": face + 4 + 10, "cell": cell}
+    adv1 = O.count_flops(O.make_cfg(1, O.ADVECTION, 16))
+    assert adv1["face"] == 2 * face + 2 + 2 + DTERMS + LF
+    assert adv1["modified_derivative_per_dir"] == cell and adv1["update"] == 2 * 2 + 2 * 4
+    assert O.count_flops(O.make_cfg(2, O.ADVECTION, 16, 16))["face"] == adv1["face"] + MIXED
+    assert O.count_flops(O.make_cfg(1, O.BURGERS, 16))["face"] == 2 * face + 2 * 2 + 2 + DTERMS + LF
+    e = EULER2D
+    eu = O.count_flops(O.make_cfg(2, O.EULER, 16, 16))
+    assert eu["face"] == (8 * face + 4 * (DTERMS + LF + MIXED) + e["roe"] + e["right"] + e["left"] +
+                          8 * e["project"] + 4 * e["back"] + 2 * e["flux"] + 2 * e["jvp"])
+    assert eu["nodal_per_dir"] == e["flux"] + 2 * e["jvp"]
+    cell_state = 2 + 7 + 2 + 3  # velocities, pressure, H, c
+    assert eu["modified_derivative_per_dir"] == (cell_state + e["right"] + e["left"] + 6 * e["project"] +
+                                                 4 * cell + e["back"])
+    assert eu["wavespeed_per_dir"] == 2 + 7 + 3 + 1
