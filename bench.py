@@ -8,10 +8,10 @@ the whole grid.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 4096]
 
---impl reference times the CPU oracle (plain C++ FP64, one host core) on a bounded sample of the
-same workload: a 256 x 256 periodic patch of the same smooth wave, one oracle SSP-RK3 step per
-benchmark step.  Multi-GPU (torchrun): every rank advances its own 4096^2 grid (independent
-replicas, weak scaling); the time is the maximum over ranks.
+--impl reference times the CPU oracle (plain C++ FP64 on all host cores, lines of each sweep split
+over threads) on the same workload: one oracle SSP-RK3 step of the full grid per benchmark step.
+Multi-GPU (torchrun): every rank advances its own 4096^2 grid (independent replicas, weak
+scaling); the time is the maximum over ranks.
 """
 from __future__ import annotations
 
@@ -29,11 +29,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "2D Euler HWENO-I Mcell-updates/s & HBM roofline %; batched/adjoint vs plain"
 UNIT = "Mcell-updates/s"
-# FP64 peak for the ALU roofline, from the SM count (152), the maximum SM clock (2070 MHz) and the
-# FP64 rate of GB300 (2 DFMA per SM per clock = 4 flop/clk/SM): 152 * 2.07e9 * 4.
-FP64_PEAK_FLOPS = 152 * 2.07e9 * 4
-# FP64 rate of a DFMA-chain probe on this GPU (595 G DFMA/s at ~1.96 GHz)
-FP64_PROBE_FLOPS = 1.19e12
+# FP64 peak derived from the SM count (152), the maximum SM clock (2070 MHz) and the FP64 rate of
+# GB300 (2 DFMA per SM per clock = 4 flop/clk/SM): 152 * 2.07e9 * 4, reported beside the peak the
+# benchmark measures on its own GPU (hweno_selftest_fp64_peak).
+FP64_PEAK_FLOPS_DERIVED = 152 * 2.07e9 * 4
 # algorithmic HBM bytes of one SSP-RK3 step per 2D Euler cell: the state planes each stage must
 # touch once (stage 1: read 12, write 12, write the 8-plane base; stages 2, 3: read 12, read the
 # base 12, write 12) = 104 planes of 8 bytes
@@ -128,27 +127,76 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
 
 
-def cpu_baseline(steps: int = 8, n: int = 256):
-    """The oracle (single thread) on a 256^2 periodic patch of the same smooth wave."""
+def cpu_baseline(steps: int = 2, n: int = 4096):
+    """The oracle on all host cores: `steps` SSP-RK3 steps of the benchmark's own workload (the
+    4096^2 smooth wave), outside any GPU timing."""
     import oracle as O
     import workloads as W
 
+    cores = O.set_threads(0)
     S, dx, dy = W.euler2d_smooth(n)
     cfg = O.make_cfg(2, O.EULER, n, n, dx=dx, dy=dy)
     dt = O.cfl_dt(cfg, S, 0.6)
     t0 = time.perf_counter()
     O.steps(cfg, S, dt, steps)
     sec = time.perf_counter() - t0
-    return {"value": n * n * steps / sec / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} oracle SSP-RK3 steps on a {n}x{n} periodic patch of the same smooth "
-                      f"wave (same per-cell work), one host thread, {sec:.1f} s"}
+    return {"value": n * n * steps / sec / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} oracle SSP-RK3 steps of the same {n}x{n} smooth-wave grid, lines of each sweep "
+                      f"split over {cores} host threads, {sec:.1f} s"}
 
 
-def run_batched(dev, steps: int = 3):
+def run_parity(dev, n: int, nsteps: int):
+    """The benchmark's workload advanced nsteps CFL steps on the GPU and by the oracle (all host
+    cores), compared element by element: the relative max-norm of every (field, component) plane
+    and the end times (dt of every step from each side's own state).  Outside the timed region."""
+    import numpy as np
+
+    import oracle as O
+    import workloads as W
+    from paper_2411_11229_gb300 import Solver
+
+    S, dx, dy = W.euler2d_smooth(n)
+    s = Solver(2, "euler", n, n, dx=dx, dy=dy, device=dev)
+    s.set_state(S)
+    s.set_time(0.0, 0.0)
+    s.step(0.0, nsteps)
+    _, tg = s.last_dt()
+    gpu = s.state.cpu().numpy()
+    del s
+    cores = O.set_threads(0)
+    cfg = O.make_cfg(2, O.EULER, n, n, dx=dx, dy=dy)
+    t0 = time.perf_counter()
+    ref, k, t = O.run(cfg, S, 0.0, 0.6, 1.0, max_steps=nsteps)
+    sec = time.perf_counter() - t0
+    a, b = gpu.reshape(12, -1), ref.reshape(12, -1)
+    rel = np.abs(a - b).max(axis=1) / np.maximum(np.abs(b).max(axis=1), 1e-300)
+    return {"workload": f"2D Euler {n}x{n} smooth wave, {nsteps} CFL steps", "steps": k,
+            "rel_max_per_plane": [float(x) for x in rel], "rel_max": float(rel.max()), "t_gpu": tg, "t_oracle": t,
+            "oracle_seconds": sec, "oracle_threads": cores}
+
+
+def fp64_probe(dev) -> dict:
+    """The library's FP64 issue probe on this GPU (independent register-operand DFMA chains on
+    every SM, best of 5 launches): DFMA per second and flops per second (2 per DFMA)."""
+    import ctypes
+
+    import torch
+
+    from paper_2411_11229_gb300 import _capi as C
+
+    scratch = torch.zeros(4, dtype=torch.float64, device=dev)
+    rate, per = ctypes.c_double(), ctypes.c_double()
+    C.check(C.load().hweno_selftest_fp64_peak(ctypes.c_void_p(scratch.data_ptr()), 5,
+                                              ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream),
+                                              ctypes.byref(rate), ctypes.byref(per)), "hweno_selftest_fp64_peak")
+    return {"dfma_per_s": rate.value, "flops": 2.0 * rate.value, "dfma_per_launch": per.value}
+
+
+def run_batched(dev, steps: int = 3, only_1d: bool = False):
     """The uneven batched sweep: 256 1D Euler lines (N log-uniform in [128, 16384], seeded Riemann
     data) and 32 2D Euler grids (sides in {128, 256, 512, 1024}), every instance with its own CFL
     step.  Batched path (one persistent launch per stage, CUDA graph, autotuned launch shape)
-    against one launch per instance and kernel."""
+    against one launch per instance and kernel.  only_1d: the 256 lines alone."""
     import numpy as np
     import torch
 
@@ -156,6 +204,8 @@ def run_batched(dev, steps: int = 3):
     from paper_2411_11229_gb300 import Batch
 
     pairs = W.batched_states(W.batched_instances())
+    if only_1d:
+        pairs = [(d, S) for d, S in pairs if int(d["dim"]) == 1]
     cells = sum(int(np.prod(S.shape[2:])) for _, S in pairs)
     res = {"instances": len(pairs), "cells": cells}
     times = {}
@@ -323,12 +373,15 @@ def run_rayleigh_taylor(dev, meshes=((60, 240), (120, 480), (240, 960)), t_end: 
 
 
 def run_reference(args, ws, rank):
+    """The oracle on all host cores, one SSP-RK3 step of the full benchmark grid (4096^2 smooth
+    wave) per benchmark step."""
     if rank != 0:
         return 0
     import oracle as O
     import workloads as W
 
-    n = 256
+    n = args.n
+    cores = O.set_threads(0)
     S, dx, dy = W.euler2d_smooth(n)
     cfg = O.make_cfg(2, O.EULER, n, n, dx=dx, dy=dy)
     dt = O.cfl_dt(cfg, S, 0.6)
@@ -344,10 +397,11 @@ def run_reference(args, ws, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "2D Euler HWENO-I, smooth wave, periodic [0,2]^2, SSP-RK3 CFL 0.6; "
-                               "oracle sample: 256x256 patch per step", "n": n},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"one oracle SSP-RK3 step on a {n}x{n} periodic patch per benchmark step"},
+        "config": {"workload": f"2D Euler HWENO-I {n}x{n} periodic [0,2]^2, smooth wave (0.7, 0.3), "
+                               "SSP-RK3 CFL 0.6", "n": n, "cells": n * n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"one oracle SSP-RK3 step of the full {n}x{n} grid per benchmark step, "
+                                   f"{cores} host threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -366,6 +420,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n = args.n
+    probe = fp64_probe(dev)  # the ALU roofline's peak, measured on this GPU before the workload
     S, dx, dy = W.euler2d_smooth(n)
     cells = n * n
     solver = Solver(2, "euler", n, n, dx=dx, dy=dy, device=dev)
@@ -516,16 +571,24 @@ def run_ours(args, ws, rank, local):
                         "on two streams take the steps in turn, so one handle's copies overlap the other's step",
                 "serial": {"value": serial_value, "path": "the same calls on one handle and one stream"},
                 "phases_one_step": phases},
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": probe["flops"] / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved / probe["flops"], "traffic": traffic,
                      "kernel": "k_face<2,EULER>", "flops_per_face": counts["face"],
+                     "faces_per_launch": faces, "avg_launch_ms": face_avg_ms,
+                     "frac_note": "the scheme's operations per face as the oracle writes them (+, -, *, /, sqrt "
+                                  "with nontrivial operands, counted on the oracle's own code) per second, over "
+                                  "the FP64 peak measured on this GPU",
+                     "peak_note": "measured on this GPU before the workload: register-operand DFMA issue rate "
+                                  "(hweno_selftest_fp64_peak) x 2 flops",
+                     "peak_derived": FP64_PEAK_FLOPS_DERIVED / 1e12,
+                     "peak_derived_note": "152 SMs x 2070 MHz x 2 DFMA/clk x 2 flops",
+                     "frac_of_derived": achieved / FP64_PEAK_FLOPS_DERIVED,
                      "fp64_pipe_active_ncu": None if traffic is None else FACE_FP64_PIPE_ACTIVE,
                      "fp64_instructions_per_face_ncu": None if traffic is None else FACE_FP64_INSTR_PER_FACE,
-                     "frac_note": "algorithmic flops (every +, -, *, /, sqrt of the scheme as written) per second "
-                                  "over the FP64 peak; the kernel executes fewer FP64 instructions than that "
-                                  "count, so the fraction can exceed 1; the pipe activity is the hardware's figure",
-                     "faces_per_launch": faces, "avg_launch_ms": face_avg_ms,
-                     "peak_note": "FP64 derived: 152 SMs x 2070 MHz x 4 flop/clk",
+                     "frac_executed": None if traffic is None else
+                     FACE_FP64_INSTR_PER_FACE * faces / (face_avg_ms * 1e-3) / probe["dfma_per_s"],
+                     "frac_executed_note": "FP64 instructions the kernel executes per face (ncu) x faces per second, "
+                                           "over the probe's DFMA issue rate",
                      "hbm_peak_gbs": hbm_peak},
         "hbm": {"bytes_per_cell_step_algorithmic": STEP_BYTES_PER_CELL,
                 "achieved_gbs": value * 1e6 * STEP_BYTES_PER_CELL / 1e9,
@@ -534,7 +597,7 @@ def run_ours(args, ws, rank, local):
                 "face_kernel_frac": None if traffic is None else traffic / (face_avg_ms * 1e-3) / 1e9 / hbm_peak,
                 "peak_gbs": hbm_peak, "peak_note": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback",
                 "note": "the step is bound by the FP64 pipe; HBM is reported beside it"},
-        "fp64_frac_of_probe": achieved / FP64_PROBE_FLOPS,
+        "fp64_probe": probe,
         "kernel_share": {k: v[0] / total_ms for k, v in ktimes.items()} if total_ms > 0 else None,
         "kernel_avg_ms": {k: v[0] / max(v[1], 1) for k, v in ktimes.items()},
         "flops_per_cell_step": counts["per_cell_step"],
@@ -542,17 +605,22 @@ def run_ours(args, ws, rank, local):
     if ws == 1 and not args.no_variants:
         torch.cuda.empty_cache()
         line["variants"] = run_variants(dev, n, ms_max / args.steps)
-    if ws == 1 and not args.no_rt:
+    if ws == 1 and args.rt:
         line["rayleigh_taylor"] = run_rayleigh_taylor(dev)
     if ws == 1 and not args.no_batched:
         del solver
         torch.cuda.empty_cache()
         line["batched"] = run_batched(dev)
+        torch.cuda.empty_cache()
+        line["batched"]["lines_1d_only"] = run_batched(dev, only_1d=True)
     if ws == 1 and not args.no_adjoint:
         torch.cuda.empty_cache()
         line["adjoint"] = run_adjoint(dev, args.adjoint_n, args.adjoint_steps, min(20, args.adjoint_steps))
+    if ws == 1 and args.parity_steps > 0:
+        torch.cuda.empty_cache()
+        line["parity"] = run_parity(dev, n, args.parity_steps)
     if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(n=n)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -568,7 +636,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--no-rt", action="store_true")
+    ap.add_argument("--rt", action="store_true", help="also run Example 4.11 (Rayleigh-Taylor) on its three meshes")
+    ap.add_argument("--parity-steps", type=int, default=0,
+                    help="also compare this many GPU steps of the workload with the oracle (all host cores)")
     ap.add_argument("--adjoint-n", type=int, default=1024)
     ap.add_argument("--adjoint-steps", type=int, default=200)
     args = ap.parse_args()

@@ -334,6 +334,19 @@ int hweno_rhs_static(int dim, int system, int64_t nx, int64_t ny, double dx, dou
  * r_dev[i] = 1/x_dev[i] for i < n, launched on `stream`.  Device arrays; EINVAL on NULL/n < 0. */
 int hweno_selftest_rcp(const double *x_dev, double *r_dev, int64_t n, void *stream);
 
+/* Probe of the FP64 issue rate of the current GPU, the peak of the stage kernels' ALU roofline
+ * (they are bound by the FP64 pipe, not by memory; Sec. 4's CFL-0.6 SSP-RK3 stepping of the
+ * scheme is FP64 arithmetic throughout).  Launches, on `stream`, eight resident blocks of 256
+ * threads per SM, each thread running eight independent chains of fused multiply-adds whose three
+ * operands are thread registers, once untimed and then `reps` times between CUDA events; reports
+ * the best rate in fused multiply-adds per second (2 floating-point operations each) in
+ * *dfma_per_s and the DFMAs of one launch in *dfma_per_launch (may be NULL).
+ *   scratch_dev: caller-owned device array of 4 doubles (the operands and a sink the kernel
+ *   writes only in a case that does not occur); reps in 1..100.  Synchronises the stream.
+ *   EINVAL on NULL scratch or result pointer or reps out of range, ECUDA on a CUDA error. */
+int hweno_selftest_fp64_peak(double *scratch_dev, int reps, void *stream, double *dfma_per_s,
+                             double *dfma_per_launch);
+
 #ifdef __cplusplus
 }
 #endif

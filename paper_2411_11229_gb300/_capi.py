@@ -42,6 +42,7 @@ SIGNATURES = {
     "hweno_set_profiling": (_I, [_H, _I]),
     "hweno_kernel_times": (_I, [_H, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)]),
     "hweno_selftest_rcp": (_I, [_P, _P, ctypes.c_int64, _P]),
+    "hweno_selftest_fp64_peak": (_I, [_P, _I, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "hweno_rhs_static": (_I, [_I, _I, ctypes.c_int64, ctypes.c_int64, _D, _D, _D, _I, _P, _P, _P, _P, _P]),
     "hweno_adjoint_workspace_bytes": (ctypes.c_size_t, [_H]),
     "hweno_step_record": (_I, [_H, _P]),

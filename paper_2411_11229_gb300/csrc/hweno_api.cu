@@ -9,6 +9,27 @@ __global__ void k_rcp_check(const double* __restrict__ x, double* __restrict__ r
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) r[i] = rcp(x[i]);
 }
+
+// FP64 issue probe: kDfmaChains independent chains a <- a b + c per thread, kDfmaIters times.  b
+// and c are read from a per-thread address (p[0] = p[1] = b, p[2] = p[3] = c), so they live in
+// thread registers, the operand form of the stage kernels' DFMAs.  The chains' sum is stored only
+// if it equals p[0] exactly, which the data (b just below 1, c small and positive) never give; the
+// store keeps the chains live.
+constexpr int kDfmaChains = 8, kDfmaIters = 2048, kDfmaThreads = 256, kDfmaBlocksPerSM = 8;
+__global__ void __launch_bounds__(kDfmaThreads) k_dfma_probe(double* __restrict__ p) {
+  const double b = p[threadIdx.x & 1], c = p[2 + (threadIdx.x & 1)];
+  double a[kDfmaChains];
+#pragma unroll
+  for (int k = 0; k < kDfmaChains; ++k) a[k] = 0.5 + 0.01 * k + 1e-6 * threadIdx.x;
+#pragma unroll 4
+  for (int it = 0; it < kDfmaIters; ++it)
+#pragma unroll
+    for (int k = 0; k < kDfmaChains; ++k) a[k] = fma(a[k], b, c);
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kDfmaChains; ++k) s += a[k];
+  if (s == p[0]) p[3] = s;
+}
 }  // namespace hw
 
 namespace {
@@ -415,6 +436,44 @@ int hweno_selftest_rcp(const double* x_dev, double* r_dev, int64_t n, void* stre
   return cuda_status();
 }
 
+int hweno_selftest_fp64_peak(double* scratch_dev, int reps, void* stream, double* dfma_per_s,
+                             double* dfma_per_launch) {
+  if (!scratch_dev || !dfma_per_s || reps < 1 || reps > 100) return HWENO_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    return HWENO_ECUDA;
+  // b just below 1 and c small: the chains converge to c / (1 - b) = 1e3 and stay finite
+  const double ops[4] = {0.999999, 0.999999, 1e-3, 1e-3};
+  if (cudaMemcpyAsync(scratch_dev, ops, sizeof(ops), cudaMemcpyHostToDevice, st) != cudaSuccess) return HWENO_ECUDA;
+  const unsigned blocks = (unsigned)sms * hw::kDfmaBlocksPerSM;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return HWENO_ECUDA;
+  }
+  int rc = HWENO_OK;
+  float best = 0.0f;
+  hw::k_dfma_probe<<<blocks, hw::kDfmaThreads, 0, st>>>(scratch_dev);  // untimed
+  for (int r = 0; r < reps && rc == HWENO_OK; ++r) {
+    float ms = 0.0f;
+    if (cudaEventRecord(e0, st) != cudaSuccess) rc = HWENO_ECUDA;
+    hw::k_dfma_probe<<<blocks, hw::kDfmaThreads, 0, st>>>(scratch_dev);
+    if (rc == HWENO_OK && (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1, st) != cudaSuccess ||
+                           cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      rc = HWENO_ECUDA;
+    if (rc == HWENO_OK && (best == 0.0f || ms < best)) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  const double per_launch = (double)blocks * hw::kDfmaThreads * hw::kDfmaIters * hw::kDfmaChains;
+  *dfma_per_s = best > 0.0f ? per_launch / (best * 1e-3) : 0.0;
+  if (dfma_per_launch) *dfma_per_launch = per_launch;
+  return HWENO_OK;
+}
+
 }  // extern "C"
 
 // =============================================================================================
@@ -469,7 +528,9 @@ extern "C" int hweno_rhs_static(int dim, int system, int64_t nx, int64_t ny, dou
     dy = dx;
   }
   if (nx < 5 || ny < 1 || (dim == 2 && ny < 5)) return HWENO_EINVAL;
-  if (nx > (1 << 28) || ny > (1 << 28)) return HWENO_ETOOBIG;
+  // every cell needs more than 8 bytes of scratch: a grid with more cells than the array holds
+  // doubles is refused here, before the layout's byte counts are formed (they cannot overflow)
+  if (nx > (1 << 28) || ny > (1 << 28) || nx * ny > (int64_t)(kStaticScratchBytes / 8)) return HWENO_ETOOBIG;
   if (!(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy)) return HWENO_EINVAL;
   if (system == HWENO_EULER && !(gamma > 1.0)) return HWENO_EINVAL;
   h.dim = dim;

@@ -2,6 +2,7 @@
 of the scheme runs in libhweno.so."""
 from __future__ import annotations
 
+import contextlib
 import ctypes
 
 import numpy as np
@@ -66,11 +67,14 @@ class Solver:
         self.nfield = dim + 1
         n = self.lib.hweno_state_doubles(h)
         assert n == self.nfield * self.ncomp * self.nx * self.ny
-        self.state = torch.zeros((self.nfield, self.ncomp, self.ny, self.nx), dtype=torch.float64,
-                                 device=self.device)
-        self.workspace = torch.empty(int(self.lib.hweno_workspace_bytes(h)), dtype=torch.uint8,
-                                     device=self.device)
+        # every allocation and fill of the handle's memory is ordered on the handle's stream, the
+        # stream its kernels run on (torch's caching allocator ties each block to the stream that
+        # allocated it)
         with torch.cuda.stream(self.stream):
+            self.state = torch.zeros((self.nfield, self.ncomp, self.ny, self.nx), dtype=torch.float64,
+                                     device=self.device)
+            self.workspace = torch.empty(int(self.lib.hweno_workspace_bytes(h)), dtype=torch.uint8,
+                                         device=self.device)
             C.check(self.lib.hweno_bind(h, _ptr(self.state), _ptr(self.workspace)), "hweno_bind")
 
     # ------------------------------------------------------------------------------------------
@@ -85,22 +89,46 @@ class Solver:
         except Exception:
             pass
 
+    @contextlib.contextmanager
+    def _ordered(self):
+        """Run the body on the handle's stream, ordered after the caller's current stream; on exit
+        the caller's stream waits for the handle's.  Tensors appended to the yielded list were
+        allocated inside (on the handle's stream) and are handed to the caller: they are marked as
+        used on the caller's stream, so the allocator does not hand their memory out again before
+        the caller's work on them is done."""
+        cur = torch.cuda.current_stream(self.device)
+        outs = []
+        with torch.cuda.stream(self.stream):
+            if self.stream != cur:
+                self.stream.wait_stream(cur)
+            yield outs
+        if self.stream != cur:
+            cur.wait_stream(self.stream)
+            for t in outs:
+                t.record_stream(cur)
+
     def set_state(self, S) -> None:
         S = torch.as_tensor(np.asarray(S) if not isinstance(S, torch.Tensor) else S, dtype=torch.float64)
-        with torch.cuda.stream(self.stream):
+        with self._ordered():
             self.state.copy_(S.reshape(self.state.shape).to(self.device, non_blocking=True))
 
     def rhs(self, S=None):
-        """(L(S), M(S)) of one stage as device tensors; S defaults to the bound state."""
-        Sd = self.state if S is None else torch.as_tensor(S, dtype=torch.float64).to(self.device).contiguous()
-        Sd = Sd.reshape(self.state.shape)
-        L = torch.empty_like(Sd)
-        M = torch.empty_like(Sd)
-        C.check(self.lib.hweno_rhs(self.h, _ptr(Sd), _ptr(L), _ptr(M)), "hweno_rhs")
+        """(L(S), M(S)) of one stage as device tensors; S defaults to the bound state.
+
+        S is copied and the outputs are allocated on the handle's stream, which the kernels run on;
+        the caller's current stream waits for the kernels before the outputs are handed back."""
+        with self._ordered() as outs:
+            Sd = self.state if S is None else torch.as_tensor(S, dtype=torch.float64).to(self.device).contiguous()
+            Sd = Sd.reshape(self.state.shape)
+            L = torch.empty_like(Sd)
+            M = torch.empty_like(Sd)
+            C.check(self.lib.hweno_rhs(self.h, _ptr(Sd), _ptr(L), _ptr(M)), "hweno_rhs")
+            outs += [L, M]
         return L, M
 
     def step(self, dt: float = 0.0, nsteps: int = 1) -> None:
-        C.check(self.lib.hweno_steps(self.h, float(dt), int(nsteps)), "hweno_steps")
+        with self._ordered():
+            C.check(self.lib.hweno_steps(self.h, float(dt), int(nsteps)), "hweno_steps")
 
     def set_time(self, t: float, t_end: float) -> None:
         C.check(self.lib.hweno_set_time(self.h, float(t), float(t_end)), "hweno_set_time")
@@ -150,39 +178,49 @@ class Solver:
 
     def record(self, out7: torch.Tensor) -> None:
         """Copy dt and the three stage alphas of the last step into a device tensor of 7 doubles."""
-        C.check(self.lib.hweno_step_record(self.h, ctypes.c_void_p(out7.data_ptr())), "hweno_step_record")
+        with self._ordered():
+            C.check(self.lib.hweno_step_record(self.h, ctypes.c_void_p(out7.data_ptr())), "hweno_step_record")
 
     def step_replay(self, dt: float, alpha6: torch.Tensor) -> None:
-        C.check(self.lib.hweno_step_replay(self.h, float(dt), ctypes.c_void_p(alpha6.data_ptr())),
-                "hweno_step_replay")
+        with self._ordered():
+            C.check(self.lib.hweno_step_replay(self.h, float(dt), ctypes.c_void_p(alpha6.data_ptr())),
+                    "hweno_step_replay")
 
     def adjoint_step(self, Sn: torch.Tensor, dt: float, alpha6: torch.Tensor, lam_in: torch.Tensor) -> torch.Tensor:
         """(dS^{n+1}/dS^n)^T lam_in for the step from Sn with dt and alpha6 (device tensors)."""
-        lam_out = torch.empty_like(lam_in)
-        C.check(self.lib.hweno_adjoint_step(self.h, ctypes.c_void_p(Sn.data_ptr()), float(dt),
-                                            ctypes.c_void_p(alpha6.data_ptr()), ctypes.c_void_p(lam_in.data_ptr()),
-                                            ctypes.c_void_p(lam_out.data_ptr()), ctypes.c_void_p(self._adj_ws().data_ptr())),
-                "hweno_adjoint_step")
+        with self._ordered() as outs:
+            ws = self._adj_ws()
+            lam_out = torch.empty_like(lam_in)
+            C.check(self.lib.hweno_adjoint_step(self.h, ctypes.c_void_p(Sn.data_ptr()), float(dt),
+                                                ctypes.c_void_p(alpha6.data_ptr()), ctypes.c_void_p(lam_in.data_ptr()),
+                                                ctypes.c_void_p(lam_out.data_ptr()), ctypes.c_void_p(ws.data_ptr())),
+                    "hweno_adjoint_step")
+            outs.append(lam_out)
         return lam_out
 
     def step_replay_stages(self, dt: float, alpha6: torch.Tensor, S1: torch.Tensor, S2: torch.Tensor) -> None:
         """Replay a recorded step, copying its stage inputs S1 and S2 out."""
-        C.check(self.lib.hweno_step_replay_stages(self.h, float(dt), ctypes.c_void_p(alpha6.data_ptr()),
-                                                  ctypes.c_void_p(S1.data_ptr()), ctypes.c_void_p(S2.data_ptr())),
-                "hweno_step_replay_stages")
+        with self._ordered():
+            C.check(self.lib.hweno_step_replay_stages(self.h, float(dt), ctypes.c_void_p(alpha6.data_ptr()),
+                                                      ctypes.c_void_p(S1.data_ptr()), ctypes.c_void_p(S2.data_ptr())),
+                    "hweno_step_replay_stages")
 
     def adjoint_step_stages(self, Sn, S1, S2, dt: float, alpha6: torch.Tensor, lam_in: torch.Tensor) -> torch.Tensor:
-        lam_out = torch.empty_like(lam_in)
-        C.check(self.lib.hweno_adjoint_step_stages(
-            self.h, ctypes.c_void_p(Sn.data_ptr()), ctypes.c_void_p(S1.data_ptr()), ctypes.c_void_p(S2.data_ptr()),
-            float(dt), ctypes.c_void_p(alpha6.data_ptr()), ctypes.c_void_p(lam_in.data_ptr()),
-            ctypes.c_void_p(lam_out.data_ptr()), ctypes.c_void_p(self._adj_ws().data_ptr())), "hweno_adjoint_step_stages")
+        with self._ordered() as outs:
+            ws = self._adj_ws()
+            lam_out = torch.empty_like(lam_in)
+            C.check(self.lib.hweno_adjoint_step_stages(
+                self.h, ctypes.c_void_p(Sn.data_ptr()), ctypes.c_void_p(S1.data_ptr()), ctypes.c_void_p(S2.data_ptr()),
+                float(dt), ctypes.c_void_p(alpha6.data_ptr()), ctypes.c_void_p(lam_in.data_ptr()),
+                ctypes.c_void_p(lam_out.data_ptr()), ctypes.c_void_p(ws.data_ptr())), "hweno_adjoint_step_stages")
+            outs.append(lam_out)
         return lam_out
 
     def run(self, t_end: float, max_steps: int = 10 ** 9) -> int:
         """CFL steps from t = 0 to t_end (last step clamped on the device); returns the step count."""
         n = ctypes.c_int64()
-        C.check(self.lib.hweno_run(self.h, float(t_end), int(max_steps), ctypes.byref(n)), "hweno_run")
+        with self._ordered():
+            C.check(self.lib.hweno_run(self.h, float(t_end), int(max_steps), ctypes.byref(n)), "hweno_run")
         return int(n.value)
 
 

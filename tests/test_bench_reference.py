@@ -1,6 +1,7 @@
-"""The reference arm of bench.py on the host: `--impl reference` times the oracle on a bounded
-sample of the benchmark's workload and prints one JSON line with the contract's keys (value and
-e2e equal, no host-device copies, a cpu_baseline describing the same run)."""
+"""The reference arm of bench.py on the host: `--impl reference` times the oracle on all host cores
+on the benchmark's workload and prints one JSON line with the contract's keys (value and e2e
+equal, no host-device copies, a cpu_baseline describing the same run).  Run here on a 256^2 grid
+(--n) so that the CPU suite stays short; the benchmark's default is the full 4096^2 grid."""
 import json
 import os
 import subprocess
@@ -12,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def test_reference_arm_prints_one_contract_line():
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "3"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+                          "--warmup", "3", "--n", "256"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1, out.stdout[-2000:]
@@ -23,7 +24,7 @@ def test_reference_arm_prints_one_contract_line():
     assert d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 3
     assert d["value"] > 0 and d["ms_per_step"] > 0 and d["higher_is_better"] is True
     assert d["vs_baseline"] is None and d["dtype"] == "f64" and d["data"] == "synthetic"
-    assert isinstance(d["config"], dict) and d["config"]["workload"]
+    assert isinstance(d["config"], dict) and d["config"]["workload"] and d["config"]["n"] == 256
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     e2e = d["e2e"]

@@ -35,17 +35,14 @@ def rel_planes(a, b):
     return (np.abs(a - b).max(axis=1) / den).max()
 
 
-def rel_planes_field(a, b, floor=1e-3):
-    """rel_planes where a plane far below its field's largest plane (under floor times it) is
-    measured against floor times that largest plane: such a plane holds the rounding of cancelling
-    terms (the x-momentum of a fluid at rest in x is zero exactly, and each side leaves its own
-    rounding there), which has the field's scale, not its own."""
+def rel_l1_planes(a, b):
+    """Per (field, component) plane: sum |a - b| / sum |b| (the plain sum where b's plane is zero)."""
     nf, nc = b.shape[0], b.shape[1]
-    a = a.reshape(nf, nc, -1)
-    b = b.reshape(nf, nc, -1)
-    pm = np.abs(b).max(axis=2)
-    den = np.maximum(pm, floor * pm.max(axis=1, keepdims=True))
-    return (np.abs(a - b).max(axis=2) / np.maximum(den, 1e-300)).max()
+    a = a.reshape(nf * nc, -1)
+    b = b.reshape(nf * nc, -1)
+    num = np.abs(a - b).sum(axis=1)
+    den = np.abs(b).sum(axis=1)
+    return np.where(den > 0, num / np.where(den > 0, den, 1.0), num)
 
 
 def make_state(dim, system, nx, ny, kind, seed):
@@ -177,12 +174,15 @@ def _stage_envelope(cfg, S, Lo, Mo, seeds=3):
     return eL, eM
 
 
-def _envelope(cfg, S, ref, nsteps, seeds=3):
-    env = 0.0
+def _l1_envelope(cfg, S, ref, nsteps, seeds=4):
+    """Per plane, the largest relative L1 drift of the oracle over four runs from inputs moved by one
+    ulp (a plane that holds only rounding, such as the x-momentum of a column at rest in x, drifts
+    by its own size, so it is measured against its own noise)."""
+    env = np.zeros(ref.shape[0] * ref.shape[1])
     for sd in range(seeds):
         sign = np.random.default_rng(100 + sd).choice([-1.0, 1.0], S.shape)
         out, _, _ = O.run(cfg, S * (1.0 + sign * 2.0 ** -52), 0.0, 0.6, 1.0, max_steps=nsteps)
-        env = max(env, rel_planes_field(out, ref))
+        env = np.maximum(env, rel_l1_planes(out, ref))
     return env
 
 
@@ -206,16 +206,18 @@ def test_hundred_smooth_steps(flags):
 @pytest.mark.parametrize("flags", [0, R2, AST | ALOC])
 @pytest.mark.parametrize("nsteps", [20, 100])
 def test_rayleigh_taylor_run(flags, nsteps):
-    """Example 4.11 at 16 x 64: the discontinuous interface amplifies rounding, so the bar is
-    1e-10 or ten times the oracle's one-ulp envelope, whichever is larger."""
+    """Example 4.11 at 16 x 64: the discontinuous interface amplifies rounding, so every plane is
+    compared in the relative L1 norm against ten times its largest drift over four oracle runs from
+    one-ulp perturbed inputs (or 1e-10)."""
     S, dx, dy, fixed = W.rayleigh_taylor(16)
     cfg, s = pair(2, "euler", 16, 64, S, dx, dy, flags=flags, sides=(R, R, F, F), grav=1.0, fixed=fixed,
                   gamma=5.0 / 3.0)
     out = _gpu_steps(s, nsteps)
     ref, n, _ = O.run(cfg, S, 0.0, 0.6, 1.0, max_steps=nsteps)
     assert n == nsteps
-    env = _envelope(cfg, S, ref, nsteps)
-    err = rel_planes_field(out, ref)
-    assert err <= max(1e-10, 10.0 * env), (err, env)
+    env = _l1_envelope(cfg, S, ref, nsteps)
+    err = rel_l1_planes(out, ref)
+    print("Rayleigh-Taylor", flags, nsteps, "L1 per plane", err.max(), "envelope", env.max())
+    assert np.all(err <= np.maximum(1e-10, 10.0 * env)), (err, env)
     # the total mass of both sides agrees to round-off
     assert abs(out[0, 0].sum() - ref[0, 0].sum()) <= 1e-12 * np.abs(ref[0, 0]).sum()
