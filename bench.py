@@ -145,10 +145,12 @@ def cpu_baseline(steps: int = 2, n: int = 4096):
                       f"split over {cores} host threads, {sec:.1f} s"}
 
 
-def run_parity(dev, n: int, nsteps: int):
+def run_parity(dev, n: int, nsteps: int, envelope: bool = False):
     """The benchmark's workload advanced nsteps CFL steps on the GPU and by the oracle (all host
     cores), compared element by element: the relative max-norm of every (field, component) plane
-    and the end times (dt of every step from each side's own state).  Outside the timed region."""
+    and the end times (dt of every step from each side's own state).  envelope: also the same
+    distance between the oracle's run and its run from the input moved by one ulp (random signs),
+    the rounding noise of the scheme on this workload.  Outside the timed region."""
     import numpy as np
 
     import oracle as O
@@ -168,11 +170,22 @@ def run_parity(dev, n: int, nsteps: int):
     t0 = time.perf_counter()
     ref, k, t = O.run(cfg, S, 0.0, 0.6, 1.0, max_steps=nsteps)
     sec = time.perf_counter() - t0
-    a, b = gpu.reshape(12, -1), ref.reshape(12, -1)
-    rel = np.abs(a - b).max(axis=1) / np.maximum(np.abs(b).max(axis=1), 1e-300)
-    return {"workload": f"2D Euler {n}x{n} smooth wave, {nsteps} CFL steps", "steps": k,
-            "rel_max_per_plane": [float(x) for x in rel], "rel_max": float(rel.max()), "t_gpu": tg, "t_oracle": t,
-            "oracle_seconds": sec, "oracle_threads": cores}
+    def rel_max(x):
+        a, b = x.reshape(12, -1), ref.reshape(12, -1)
+        return np.abs(a - b).max(axis=1) / np.maximum(np.abs(b).max(axis=1), 1e-300)
+
+    rel = rel_max(gpu)
+    out = {"workload": f"2D Euler {n}x{n} smooth wave, {nsteps} CFL steps", "steps": k,
+           "rel_max_per_plane": [float(x) for x in rel], "rel_max": float(rel.max()), "t_gpu": tg, "t_oracle": t,
+           "oracle_seconds": sec, "oracle_threads": cores}
+    if envelope:
+        del gpu
+        sign = np.random.default_rng(11).choice([-1.0, 1.0], S.shape)
+        pert, _, tp = O.run(cfg, S * (1.0 + sign * 2.0 ** -52), 0.0, 0.6, 1.0, max_steps=nsteps)
+        env = rel_max(pert)
+        out.update({"oracle_one_ulp_rel_max_per_plane": [float(x) for x in env],
+                    "oracle_one_ulp_rel_max": float(env.max()), "t_oracle_one_ulp": tp})
+    return out
 
 
 def fp64_probe(dev) -> dict:
@@ -618,7 +631,7 @@ def run_ours(args, ws, rank, local):
         line["adjoint"] = run_adjoint(dev, args.adjoint_n, args.adjoint_steps, min(20, args.adjoint_steps))
     if ws == 1 and args.parity_steps > 0:
         torch.cuda.empty_cache()
-        line["parity"] = run_parity(dev, n, args.parity_steps)
+        line["parity"] = run_parity(dev, n, args.parity_steps, args.parity_envelope)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n=n)
     print(json.dumps(line), flush=True)
@@ -637,8 +650,11 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--rt", action="store_true", help="also run Example 4.11 (Rayleigh-Taylor) on its three meshes")
+    ap.add_argument("--no-rt", action="store_true", help=argparse.SUPPRESS)  # the default; kept for old commands
     ap.add_argument("--parity-steps", type=int, default=0,
                     help="also compare this many GPU steps of the workload with the oracle (all host cores)")
+    ap.add_argument("--parity-envelope", action="store_true",
+                    help="with --parity-steps: also the oracle's own drift from a one-ulp perturbed input")
     ap.add_argument("--adjoint-n", type=int, default=1024)
     ap.add_argument("--adjoint-steps", type=int, default=200)
     args = ap.parse_args()
