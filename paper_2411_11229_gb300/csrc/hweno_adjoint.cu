@@ -337,14 +337,14 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
                      Hbb * fma(sl, Hl, sr * Hr);
   const double slb = iw * (ubb * pl.u + (NC == 4 ? vbb * pl.v : 0.0) + Hbb * Hl) - iwb * iw * iw;
   const double srb = iw * (ubb * prr.u + (NC == 4 ? vbb * prr.v : 0.0) + Hbb * Hr) - iwb * iw * iw;
-  // cells 1 and 2: sqrt(rho), u, v, H = (E + p) ir
+  // cells 1 and 2: sqrt(rho), u, v, H = (E + p) ir; d sqrt(rho) / d rho = sqrt(rho) ir / 2
   {
     const double Hlb = Hbb * sl * iw;
-    Uqb[1][0] += slb * 0.5 / sl;
+    Uqb[1][0] += slb * (0.5 * sl) * pl.ir;
     Uqb[1][NC - 1] += Hlb * pl.ir;
     prim_bwd<NC>(Uq[1], pl, g.gm1, Hlb * (Uq[1][NC - 1] + pl.p), ubb * sl * iw, vbb * sl * iw, Hlb * pl.ir, Uqb[1]);
     const double Hrb = Hbb * sr * iw;
-    Uqb[2][0] += srb * 0.5 / sr;
+    Uqb[2][0] += srb * (0.5 * sr) * prr.ir;
     Uqb[2][NC - 1] += Hrb * prr.ir;
     prim_bwd<NC>(Uq[2], prr, g.gm1, Hrb * (Uq[2][NC - 1] + prr.p), ubb * sr * iw, vbb * sr * iw, Hrb * prr.ir,
                  Uqb[2]);

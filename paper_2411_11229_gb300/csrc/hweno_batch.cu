@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_cells(BatchArgs a) {
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) k_batch_faces(BatchArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_batch_faces(BatchArgs a) {
   const long long span = (long long)kThreads * a.tiles_per_item;
   const int lo = DIM == 2 ? 0 : a.nfaces2, hi = DIM == 2 ? a.nfaces2 : a.nfaces;
   for (int it = lo + blockIdx.x; it < hi; it += gridDim.x) {

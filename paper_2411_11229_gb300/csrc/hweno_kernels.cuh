@@ -58,7 +58,7 @@ constexpr int kThreads = 128;
 // scal[4..7], so that the compiler can neither fold it nor keep it in a uniform register.
 __device__ __forceinline__ FU fu_of(const double* scal) {
   const double z = scal[4 + (threadIdx.x & 3)];
-  return FU{1.0 + z, -z};
+  return FU{1.0 + z, -z, __double2hiint(z)};
 }
 
 template <int NC>
@@ -107,7 +107,6 @@ template <int NC, int SYS>
 __device__ __forceinline__ void modified_derivative(const double (&U3)[3][NC], const double (&D3)[3][NC],
                                                     const Eig<NC>& e, int dir, const Grid& g, double* out,
                                                     const FU& f) {
-  const double ih = g.ih[dir];
   double dU[2][NC], Dq[2][NC], Zm[NC], Zp[NC];
 #pragma unroll
   for (int q = 0; q < 2; ++q)
@@ -125,8 +124,9 @@ __device__ __forceinline__ void modified_derivative(const double (&U3)[3][NC], c
     Zp[0] = D3[2][0];
   }
   double ht[NC];
+  const StencilK k = stencil_k(g, dir, f);
 #pragma unroll
-  for (int s = 0; s < NC; ++s) ht[s] = cell_field_d(Dq[0][s], Dq[1][s], Zm[s], Zp[s], g, dir, f) * ih;
+  for (int s = 0; s < NC; ++s) ht[s] = f.mul(cell_field_d(Dq[0][s], Dq[1][s], Zm[s], Zp[s], k, f), k.ih);
   if (SYS == SYS_EULER) {
     e.back(ht, out, f);
   } else {
@@ -183,7 +183,6 @@ __device__ __forceinline__ void load_stencil3(const Grid& g, const double* __res
 template <int NC, int SYS, bool VW>
 __device__ __forceinline__ void r2_cell_vw(const double (&U3)[3][NC], const double (&D3)[3][NC], const Eig<NC>& e,
                                            int dir, const Grid& g, double* md, double (&fs)[4][NC], const FU& f) {
-  const double ih = g.ih[dir];
   double dU[2][NC], Dq[2][NC], Zm[NC], Zp[NC];
 #pragma unroll
   for (int q = 0; q < 2; ++q)
@@ -210,11 +209,12 @@ __device__ __forceinline__ void r2_cell_vw(const double (&U3)[3][NC], const doub
     Zp[0] = D3[2][0];
   }
   const double bc = SYS == SYS_EULER ? 0.0 : U3[1][0];
+  const StencilK k = stencil_k(g, dir, f);
   double cm[NC], chm[NC], cp[NC], chp[NC], ht[NC];
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
-    cell_faces_field<VW>(Dq[0][s], Dq[1][s], Zm[s], Zp[s], bc, g, dir, cm[s], chm[s], cp[s], chp[s], ht[s], f);
-    ht[s] *= ih;
+    cell_faces_field<VW>(Dq[0][s], Dq[1][s], Zm[s], Zp[s], bc, k, g, dir, cm[s], chm[s], cp[s], chp[s], ht[s], f);
+    ht[s] = f.mul(ht[s], k.ih);
   }
   if (SYS == SYS_EULER) {
     e.back_add(cm, U3[1], fs[0], f);
@@ -427,9 +427,10 @@ __device__ __forceinline__ void r1_face_states(const double (&Uq)[4][NC], const 
   // stencil of cell k+1 (mirror image)
   const double bm = SYS == SYS_EULER ? 0.0 : Uq[1][0], bp = SYS == SYS_EULER ? 0.0 : Uq[2][0];
   double cm[NC], chm[NC], cp[NC], chp[NC];
+  const StencilK k = stencil_k(g, dir, f);
 #pragma unroll
   for (int s = 0; s < NC; ++s)
-    face_field_d<VW>(Dq[0][s], Dq[1][s], Dq[2][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], bm, bp, g, dir, cm[s],
+    face_field_d<VW>(Dq[0][s], Dq[1][s], Dq[2][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], bm, bp, k, g, dir, cm[s],
                      chm[s], cp[s], chp[s], f);
   // back to conserved variables
   if (SYS == SYS_EULER) {
@@ -634,8 +635,11 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
   }
 }
 
+// 2D: three blocks of 128 per SM, so that the stencil constants of the direction (StencilK) stay in
+// registers; 1D: four
 template <int DIM, int SYS, int VAR>
-__global__ void __launch_bounds__(kThreads, 4) k_face(Grid g, const double* __restrict__ S, Work w, int slot) {
+__global__ void __launch_bounds__(kThreads, DIM == 2 ? 3 : 4) k_face(Grid g, const double* __restrict__ S, Work w,
+                                                                    int slot) {
   const int dir = blockIdx.y;
   const int n = dir == 0 ? g.nx : g.ny;
   const int nlines = dir == 0 ? g.ny : g.nx;
@@ -661,8 +665,13 @@ __device__ __forceinline__ void update_body(const Grid& g, double* __restrict__ 
   // the stage's constants copied into thread registers (exactly: c 1 + (-0) = c), so that every
   // FP64 instruction below has register operands (see FU)
   const FU fu = fu_of(w.scal);
-  const double mix = fu.mul(-g.inv_dx, fu.one), miy = fu.mul(-g.inv_dy, fu.one);
-  const double dtr = fu.mul(dt, fu.one), akr = fu.mul(a_k, fu.one), bkr = fu.mul(b_k, fu.one);
+  const double mix = fu.reg(-g.inv_dx), miy = fu.reg(-g.inv_dy);
+  const double akr = fu.reg(a_k), bkr = fu.reg(b_k);
+  // the Runge-Kutta stage b (M + dt L) with dt L = (dt mix) dF + (dt miy) dG (+ dt source): the
+  // coefficients of the two flux differences taken as one product each, b dt (-1/h) (b = 1 at the
+  // first stage)
+  const double bdt = fu.mul(bkr, fu.reg(dt));
+  const double cx = fu.mul(bdt, mix), cy = fu.mul(bdt, miy);
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     // Eq. (euler2d-s): field f gains g (0, 0, S_f[rho], S_f[rho nu]) (read before S is overwritten)
@@ -674,20 +683,30 @@ __device__ __forceinline__ void update_body(const Grid& g, double* __restrict__ 
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
       const int fk = f * NC + k;
-      // L = -(F_{i+1/2} - F_{i-1/2}) / dx [- (G_{j+1/2} - G_{j-1/2}) / dy] [+ source]
-      double L = fu.mul(fu.sub(w.FX[fk * oplx + px + 1], w.FX[fk * oplx + px]), mix);
-      if (DIM == 2) L = fma(fu.sub(w.FY[fk * oply + p + g.nx], w.FY[fk * oply + p]), miy, L);
-      if (SRC && k == 2) L = fu.add(L, src2);
-      if (SRC && k == 3) L = fu.add(L, src3);
+      const double dF = fu.sub(w.FX[fk * oplx + px + 1], w.FX[fk * oplx + px]);
+      const double dG = DIM == 2 ? fu.sub(w.FY[fk * oply + p + g.nx], w.FY[fk * oply + p]) : 0.0;
       const double M = f == 0 ? S[fk * plane + p] : w.MD[((long long)(f - 1) * NC + k) * plane + p];
       if (mode == 1) {
+        // L = -(F_{i+1/2} - F_{i-1/2}) / dx [- (G_{j+1/2} - G_{j-1/2}) / dy] [+ source]
+        double L = fu.mul(dF, mix);
+        if (DIM == 2) L = fma(dG, miy, L);
+        if (SRC && k == 2) L = fu.add(L, src2);
+        if (SRC && k == 3) L = fu.add(L, src3);
         Lout[fk * plane + p] = L;
         Mout[fk * plane + p] = M;
-      } else if (stage == 0) {
+        continue;
+      }
+      // b M + b dt L
+      double v = stage == 0 ? M : fu.mul(bkr, M);
+      if (SRC && k == 2) v = fma(bdt, src2, v);
+      if (SRC && k == 3) v = fma(bdt, src3, v);
+      if (DIM == 2) v = fma(cy, dG, v);
+      v = fma(cx, dF, v);
+      if (stage == 0) {
         w.B[fk * plane + p] = M;
-        S[fk * plane + p] = fma(dtr, L, M);
+        S[fk * plane + p] = v;
       } else {
-        S[fk * plane + p] = fma(akr, w.B[fk * plane + p], fu.mul(bkr, fma(dtr, L, M)));
+        S[fk * plane + p] = fma(akr, w.B[fk * plane + p], v);
       }
     }
   }

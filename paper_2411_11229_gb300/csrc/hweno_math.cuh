@@ -80,14 +80,20 @@ struct Grid {
 // registers:
 // fma(a, 1, b) = a + b and fma(a, b, -0) = a b exactly (the same rounding, signed zeros included).
 // FU carries the two units; the kernels load them through memory the compiler cannot see into
-// (fu_of), and the default FU{1, -0} folds back to plain sums and products.
+// (fu_of), and the default FU{1, -0, 0} folds back to plain sums and products.  reg(c) copies a
+// constant into a thread register through the integer pipe (its bits XOR a zero the compiler cannot
+// see), so that the DFMAs reading it take register operands at no FP64 issue slot.
 struct FU {
   double one, mz;
+  int zi;  // 0
   __device__ __forceinline__ double add(double a, double b) const { return fma(a, one, b); }
   __device__ __forceinline__ double sub(double a, double b) const { return fma(a, one, -b); }
   __device__ __forceinline__ double mul(double a, double b) const { return fma(a, b, mz); }
+  __device__ __forceinline__ double reg(double c) const {
+    return __hiloint2double(__double2hiint(c) ^ zi, __double2loint(c) ^ zi);
+  }
 };
-#define HW_PLAIN_FU FU{1.0, -0.0}
+#define HW_PLAIN_FU FU{1.0, -0.0, 0}
 
 // 1/x for normal, finite x: the hardware approximation (rcp.approx.ftz.f64, relative error up to
 // about 2^-20 on this GPU) refined by one third-order step.  With e = 1 - x r the exact reciprocal
@@ -113,19 +119,55 @@ __device__ __forceinline__ double sqr(double x) { return x * x; }
 // beta1 = dm^2, beta2 = dp^2 (passed in: neighbouring stencils share them).  The kernels evaluate
 // beta0 through the completed squares below (beta0_eps; the adjoint's beta0_eps_s).
 
-// beta0 + eps with unscaled derivatives vm = v_{i-1}, vp = v_{i+1} along direction dir.  The four
-// squared forms of beta0 make one quadratic form in (h sv, du) and one in (h dv, d2); completing the
-// square in the derivative term writes them as S1 (sv + N1 du)^2 + T1 du^2 and
+// The constants of one direction's stencils (Grid fields of that direction, see Grid), copied into
+// thread registers by stencil_k: a DFMA issues faster with register operands than with a
+// constant-bank or block-uniform one (see FU), and every stencil of a face or cell reads them.
+struct StencilK {
+  double bN1, bN2, bS1, bS2, bT1, bT2, eps;  // beta0 + eps (beta0_eps)
+  double quarter, half;                      // 1/4 of tau, 1/2 of the candidate slopes
+  double G, cm[4], cp[4];                    // face: gamma0/gamma1, udm and udp of the direction
+  double cdu, mucsv, Gd, ih;                 // cell: the limiter's cdu, -ucsv, d0/d1 and 1/h
+};
+// k = the stencil constants of direction dir, copied into thread registers (FU::reg; with the
+// default units the compiler keeps them as the constants)
+__device__ __forceinline__ StencilK stencil_k(const Grid& g, int dir, const FU& f = HW_PLAIN_FU) {
+  StencilK k;
+  k.bN1 = f.reg(g.bN1[dir]);
+  k.bN2 = f.reg(g.bN2[dir]);
+  k.bS1 = f.reg(g.bS1[dir]);
+  k.bS2 = f.reg(g.bS2[dir]);
+  k.bT1 = f.reg(g.bT1);
+  k.bT2 = f.reg(g.bT2);
+  k.eps = f.reg(g.eps);
+  k.quarter = f.reg(0.25);
+  k.half = f.reg(0.5);
+  k.G = f.reg(g.G);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    k.cm[i] = f.reg(g.udm[dir][i]);
+    k.cp[i] = f.reg(g.udp[dir][i]);
+  }
+  k.cdu = f.reg(g.cdu);
+  k.mucsv = f.reg(-g.ucsv[dir]);
+  k.Gd = f.reg(g.Gd);
+  k.ih = f.reg(g.ih[dir]);
+  return k;
+}
+
+// beta0 + eps with unscaled derivatives vm = v_{i-1}, vp = v_{i+1} along the direction of k.  The
+// four squared forms of beta0 make one quadratic form in (h sv, du) and one in (h dv, d2);
+// completing the square in the derivative term writes them as S1 (sv + N1 du)^2 + T1 du^2 and
 // S2 (dv + N2 d2)^2 + T2 d2^2 (S, N per direction, T independent of h), a sum of four non-negative
 // terms, and eps enters as the first addend.  Returns beta0 + eps, du = dm + dp and sv = vm + vp.
-__device__ __forceinline__ double beta0_eps(double dm, double dp, double vm, double vp, const Grid& g, int dir,
+__device__ __forceinline__ double beta0_eps(double dm, double dp, double vm, double vp, const StencilK& k,
                                             double& du_out, double& sv_out, const FU& f = HW_PLAIN_FU) {
   const double du = f.add(dm, dp), d2 = f.sub(dp, dm);
   const double sv = f.add(vm, vp), dv = f.sub(vm, vp);
-  const double y1 = fma(g.bN1[dir], du, sv), y2 = fma(g.bN2[dir], d2, dv);
+  const double y1 = fma(k.bN1, du, sv), y2 = fma(k.bN2, d2, dv);
   du_out = du;
   sv_out = sv;
-  return fma(g.bS1[dir] * y1, y1, fma(g.bS2[dir] * y2, y2, fma(g.bT1 * du, du, fma(g.bT2 * d2, d2, g.eps))));
+  return fma(f.mul(k.bS1, y1), y1,
+             fma(f.mul(k.bS2, y2), y2, fma(f.mul(k.bT1, du), du, fma(f.mul(k.bT2, d2), d2, k.eps))));
 }
 
 // Nonlinear weights of Eq. (nonlinear) up to a common factor: with e_l = beta_l + eps,
@@ -135,10 +177,11 @@ struct Wts {
   double W0, W1, W2;
 };
 
-// Weights from e_l = beta_l + eps directly: e_l - e_k stands for beta_l - beta_k in tau.
-__device__ __forceinline__ Wts weights_e(double e0, double e1, double e2, const FU& f = HW_PLAIN_FU) {
+// Weights from e_l = beta_l + eps directly: e_l - e_k stands for beta_l - beta_k in tau.  quarter:
+// 1/4 (a register copy where the caller has one).
+__device__ __forceinline__ Wts weights_e(double e0, double e1, double e2, double quarter, const FU& f = HW_PLAIN_FU) {
   const double ts = f.add(fabs(f.sub(e0, e1)), fabs(f.sub(e0, e2)));
-  const double tau = f.mul(0.25 * ts, ts);
+  const double tau = f.mul(f.mul(quarter, ts), ts);
   const double Q0 = f.mul(e1, e2), Q1 = f.mul(e0, e2), Q2 = f.mul(e0, e1);
   const double P = f.mul(Q0, e0);
   Wts w;
@@ -146,6 +189,9 @@ __device__ __forceinline__ Wts weights_e(double e0, double e1, double e2, const 
   w.W1 = fma(tau, Q1, P);
   w.W2 = fma(tau, Q2, P);
   return w;
+}
+__device__ __forceinline__ Wts weights_e(double e0, double e1, double e2, const FU& f = HW_PLAIN_FU) {
+  return weights_e(e0, e1, e2, 0.25, f);
 }
 
 // One characteristic field at one face k+1/2: u^- from the stencil of cell k (Eqs. Pxi, P'xi,
@@ -156,28 +202,27 @@ __device__ __forceinline__ Wts weights_e(double e0, double e1, double e2, const 
 //   num / den = u_c + (W0 (r - G u_c) + W1 (p1 - u_c) + W2 (p2 - u_c)) / den,
 // with p1 - u_c and p2 - u_c half a cell difference each.  In: d01 = w1 - w0, d12 = w2 - w1,
 // d23 = w3 - w2 over the cells k-1..k+2 and their derivatives y0..y3 along direction dir
-// (unscaled).  Out: um, up = the interface values less the centre values w1, w2, added to bm, bp
-// (the centre values for a scalar law, zero where the caller adds the centre states in conserved
-// variables); with VW (the weighted-derivative option), the weighted derivatives vm, vp (the
-// unweighted ones are linear in the stencil and formed by the caller).
+// (unscaled); k: the stencil constants of dir.  Out: um, up = the interface values less the centre
+// values w1, w2, added to bm, bp (the centre values for a scalar law, zero where the caller adds the
+// centre states in conserved variables); with VW (the weighted-derivative option), the weighted
+// derivatives vm, vp (the unweighted ones are linear in the stencil and formed by the caller).
 template <bool VW>
 __device__ __forceinline__ void face_field_d(double d01, double d12, double d23, double y0, double y1, double y2,
-                                             double y3, double bm, double bp, const Grid& g, int dir, double& um,
-                                             double& vm, double& up, double& vp, const FU& f = HW_PLAIN_FU) {
-  const double e01 = fma(d01, d01, g.eps), e12 = fma(d12, d12, g.eps), e23 = fma(d23, d23, g.eps);
-  const double* cm = g.udm[dir];
-  const double* cp = g.udp[dir];
+                                             double y3, double bm, double bp, const StencilK& k, const Grid& g,
+                                             int dir, double& um, double& vm, double& up, double& vp,
+                                             const FU& f = HW_PLAIN_FU) {
+  const double e01 = fma(d01, d01, k.eps), e12 = fma(d12, d12, k.eps), e23 = fma(d23, d23, k.eps);
   const double k21 = g.uvd[dir][0], k3 = g.uvd[dir][1];
   vm = vp = 0.0;
   double du, sv;
   {
     // stencil of cell k: candidates on {i-1, i} (W1), {i, i+1} (W2)
-    const double e0 = beta0_eps(d01, d12, y0, y2, g, dir, du, sv, f);
-    const Wts wt = weights_e(e0, e01, e12, f);
-    const double r = fma(cm[0], d01, fma(cm[1], d12, fma(cm[2], y0, cm[3] * y2)));
+    const double e0 = beta0_eps(d01, d12, y0, y2, k, du, sv, f);
+    const Wts wt = weights_e(e0, e01, e12, k.quarter, f);
+    const double r = fma(k.cm[0], d01, fma(k.cm[1], d12, fma(k.cm[2], y0, f.mul(k.cm[3], y2))));
     const double sl = fma(wt.W1, d01, f.mul(wt.W2, d12));
-    const double rden = rcp(fma(g.G, wt.W0, f.add(wt.W1, wt.W2)), f);
-    um = fma(fma(wt.W0, r, 0.5 * sl), rden, bm);
+    const double rden = rcp(fma(k.G, wt.W0, f.add(wt.W1, wt.W2)), f);
+    um = fma(fma(wt.W0, r, f.mul(k.half, sl)), rden, bm);
     if (VW) {
       const double ih = g.ih[dir];
       const double v0 = fma(k21, d12, fma(-k3, d01, fma(0.0625, y0, -0.1875 * y2)));
@@ -186,12 +231,12 @@ __device__ __forceinline__ void face_field_d(double d01, double d12, double d23,
   }
   {
     // stencil of cell k+1 (mirror image): its candidate on {i, i+1} carries beta2
-    const double e0 = beta0_eps(d12, d23, y1, y3, g, dir, du, sv, f);
-    const Wts wt = weights_e(e0, e12, e23, f);
-    const double r = fma(cp[0], d12, fma(cp[1], d23, fma(cp[2], y1, cp[3] * y3)));
+    const double e0 = beta0_eps(d12, d23, y1, y3, k, du, sv, f);
+    const Wts wt = weights_e(e0, e12, e23, k.quarter, f);
+    const double r = fma(k.cp[0], d12, fma(k.cp[1], d23, fma(k.cp[2], y1, f.mul(k.cp[3], y3))));
     const double sl = fma(wt.W1, d12, f.mul(wt.W2, d23));
-    const double rden = rcp(fma(g.G, wt.W0, f.add(wt.W1, wt.W2)), f);
-    up = fma(fma(wt.W0, r, -0.5 * sl), rden, bp);
+    const double rden = rcp(fma(k.G, wt.W0, f.add(wt.W1, wt.W2)), f);
+    up = fma(fma(wt.W0, r, -f.mul(k.half, sl)), rden, bp);
     if (VW) {
       const double ih = g.ih[dir];
       const double v0 = fma(k21, d12, fma(-k3, d23, fma(-0.1875, y1, 0.0625 * y3)));
@@ -207,20 +252,18 @@ __device__ __forceinline__ void face_field_d(double d01, double d12, double d23,
 // weights; u^+/- share one reciprocal (gamma1 = gamma2 makes the mirrored weights the same numbers).
 template <bool VW>
 __device__ __forceinline__ void cell_faces_field(double d01, double d12, double y0, double y2, double bc,
-                                                 const Grid& g, int dir, double& um, double& vm, double& up,
-                                                 double& vp, double& hvt, const FU& f = HW_PLAIN_FU) {
+                                                 const StencilK& k, const Grid& g, int dir, double& um, double& vm,
+                                                 double& up, double& vp, double& hvt, const FU& f = HW_PLAIN_FU) {
   double du, sv;
-  const double e0 = beta0_eps(d01, d12, y0, y2, g, dir, du, sv, f);
-  const Wts wt = weights_e(e0, fma(d01, d01, g.eps), fma(d12, d12, g.eps), f);
-  const double rden = rcp(fma(g.G, wt.W0, f.add(wt.W1, wt.W2)), f);
+  const double e0 = beta0_eps(d01, d12, y0, y2, k, du, sv, f);
+  const Wts wt = weights_e(e0, fma(d01, d01, k.eps), fma(d12, d12, k.eps), k.quarter, f);
+  const double rden = rcp(fma(k.G, wt.W0, f.add(wt.W1, wt.W2)), f);
   // the candidates at x_{i+1/2} differ from u_i by (d01, d12)/2, those at x_{i-1/2} by
   // (-d01, -d12)/2, so both faces share W1 d01 + W2 d12
-  const double* cm = g.udm[dir];
-  const double* cp = g.udp[dir];
-  const double rm = fma(cm[0], d01, fma(cm[1], d12, fma(cm[2], y0, cm[3] * y2)));
-  const double rp = fma(cp[0], d01, fma(cp[1], d12, fma(cp[2], y0, cp[3] * y2)));
+  const double rm = fma(k.cm[0], d01, fma(k.cm[1], d12, fma(k.cm[2], y0, f.mul(k.cm[3], y2))));
+  const double rp = fma(k.cp[0], d01, fma(k.cp[1], d12, fma(k.cp[2], y0, f.mul(k.cp[3], y2))));
   const double sl = fma(wt.W1, d01, f.mul(wt.W2, d12));
-  const double hs = 0.5 * sl;
+  const double hs = f.mul(k.half, sl);
   um = fma(fma(wt.W0, rm, hs), rden, bc);
   up = fma(fma(wt.W0, rp, -hs), rden, bc);
   vm = vp = 0.0;
@@ -232,22 +275,22 @@ __device__ __forceinline__ void cell_faces_field(double d01, double d12, double 
     vm = f.mul(fma(wt.W0, fma(v0m, g.ig1, -ds), ss), rden);
     vp = f.mul(fma(wt.W0, fma(v0p, g.ig1, -ds), ss), rden);
   }
-  const double t = fma(g.cdu, du, -g.ucsv[dir] * sv);
-  hvt = f.mul(fma(wt.W0, t, sl), rcp(fma(g.Gd, wt.W0, f.add(wt.W1, wt.W2)), f));
+  const double t = fma(k.cdu, du, f.mul(k.mucsv, sv));
+  hvt = f.mul(fma(wt.W0, t, sl), rcp(fma(k.Gd, wt.W0, f.add(wt.W1, wt.W2)), f));
 }
 
 // h v~_i of one characteristic field (Eq. limiter with the derivatives of Eq. limiter-p) from the
 // differences d01 = w1 - w0, d12 = w2 - w1 of u_{i-1..i+1} and the unscaled derivatives
-// y0 = v_{i-1}, y2 = v_{i+1} along direction dir:
+// y0 = v_{i-1}, y2 = v_{i+1} along the direction of k:
 //   (h p0'(x_i) - d1 (h p1' + h p2')) / d1 = cdu du - csv h sv,  h p1' = d01, h p2' = d12.
-__device__ __forceinline__ double cell_field_d(double d01, double d12, double y0, double y2, const Grid& g, int dir,
+__device__ __forceinline__ double cell_field_d(double d01, double d12, double y0, double y2, const StencilK& k,
                                                const FU& f = HW_PLAIN_FU) {
   double du, sv;
-  const double e0 = beta0_eps(d01, d12, y0, y2, g, dir, du, sv, f);
-  const Wts wt = weights_e(e0, fma(d01, d01, g.eps), fma(d12, d12, g.eps), f);
-  const double t = fma(g.cdu, du, -g.ucsv[dir] * sv);
+  const double e0 = beta0_eps(d01, d12, y0, y2, k, du, sv, f);
+  const Wts wt = weights_e(e0, fma(d01, d01, k.eps), fma(d12, d12, k.eps), k.quarter, f);
+  const double t = fma(k.cdu, du, f.mul(k.mucsv, sv));
   const double num = fma(wt.W0, t, fma(wt.W1, d01, f.mul(wt.W2, d12)));
-  const double den = fma(g.Gd, wt.W0, f.add(wt.W1, wt.W2));
+  const double den = fma(k.Gd, wt.W0, f.add(wt.W1, wt.W2));
   return f.mul(num, rcp(den, f));
 }
 
