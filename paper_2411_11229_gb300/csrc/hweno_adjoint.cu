@@ -89,9 +89,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
   // forward intermediates of the limiter, per field, kept in this thread's shared-memory slots
   extern __shared__ double adj_cell_sm[];
   double* const svb = adj_cell_sm + threadIdx.x;
+  const AdjK ak = adj_k(g, fu);
 #pragma unroll
   for (int s = 0; s < NC; ++s)
-    ht[s] = cell_field_save(Dq[0][s], Dq[1][s], Zm[s], Zp[s], g, svb + s * kCellSaved * kThreads, kThreads, fu) * ih;
+    ht[s] = cell_field_save(Dq[0][s], Dq[1][s], Zm[s], Zp[s], ak, svb + s * kCellSaved * kThreads, kThreads, fu) * ih;
   // backward from the adjoint of the modified derivative of this cell
   double ob[NC];
 #pragma unroll
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
   for (int s = 0; s < NC; ++s) {
     double db[2] = {0.0, 0.0};
     Zmb[s] = Zpb[s] = 0.0;
-    cell_field_bwd_saved(Dq[0][s], Dq[1][s], Zm[s], Zp[s], g, htb[s] * ih, svb + s * kCellSaved * kThreads,
+    cell_field_bwd_saved(Dq[0][s], Dq[1][s], Zm[s], Zp[s], ak, htb[s] * ih, svb + s * kCellSaved * kThreads,
                          kThreads, db, Zmb[s], Zpb[s], fu);
     Dqb[0][s] = db[0];
     Dqb[1][s] = db[1];
@@ -259,9 +260,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
   // forward intermediates of the interpolation, per field, kept in this thread's shared-memory slots
   extern __shared__ double adj_face_sm[];
   double* const svb = adj_face_sm + threadIdx.x;
+  const AdjK ak = adj_k(g, fu);
 #pragma unroll
   for (int s = 0; s < NC; ++s)
-    face_field_save(Dq[0][s], Dq[1][s], Dq[2][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, cm[s], cp[s],
+    face_field_save(Dq[0][s], Dq[1][s], Dq[2][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], ak, cm[s], cp[s],
                     svb + s * kFaceSaved * kThreads, kThreads, fu);
   // interface states: centre states plus the back-projected corrections
   double Um[NC], Up[NC];
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
     double db[3] = {0.0, 0.0, 0.0}, yb[4] = {0.0, 0.0, 0.0, 0.0};
-    face_field_bwd_saved(Dq[0][s], Dq[1][s], Dq[2][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], g, cmb[s], cpb[s],
+    face_field_bwd_saved(Dq[0][s], Dq[1][s], Dq[2][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], ak, cmb[s], cpb[s],
                          svb + s * kFaceSaved * kThreads, kThreads, db, yb, fu);
 #pragma unroll
     for (int q = 0; q < 3; ++q) Dqb[q][s] = db[q];
@@ -534,15 +536,36 @@ __global__ void __launch_bounds__(kThreads, 4) k_adj_gather(Grid g, const double
     for (int k = 0; k < NC; ++k) lam[(f * NC + k) * plane + p] = lb[f][k];
 }
 
-// out = c1 x1 + c2 x2 + c3 x3 (x2, x3 may be null)
-__global__ void k_lincomb(long long n, double* __restrict__ out, double c1, const double* __restrict__ x1, double c2,
-                          const double* __restrict__ x2, double c3, const double* __restrict__ x3) {
+// The transposes of the Runge-Kutta combinations of Eq. (2Dfully-hweno), value by value, one pass
+// each (every array has n values):
+//   k_rk_seed:  muM = c1 x, muL = c2 x                       (the last stage's seeds from lam_in)
+//   k_rk_mid:   lamB = c0 y + c1 x, muM = c2 x, muL = c3 x    (x = the last stage's VJP, y = lam_in)
+//   k_rk_first: muM = x + y, muL = c3 x                       (x = the middle stage's VJP, y = lamB)
+__global__ void k_rk_seed(long long n, double* __restrict__ muM, double* __restrict__ muL, double c1, double c2,
+                          const double* __restrict__ x) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double v = c1 * x1[i];
-  if (x2) v = fma(c2, x2[i], v);
-  if (x3) v = fma(c3, x3[i], v);
-  out[i] = v;
+  const double v = x[i];
+  muM[i] = c1 * v;
+  muL[i] = c2 * v;
+}
+__global__ void k_rk_mid(long long n, double* __restrict__ lamB, double* __restrict__ muM, double* __restrict__ muL,
+                         double c0, double c1, double c2, double c3, const double* __restrict__ x,
+                         const double* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  lamB[i] = fma(c0, y[i], c1 * v);
+  muM[i] = c2 * v;
+  muL[i] = c3 * v;
+}
+__global__ void k_rk_first(long long n, double* __restrict__ muM, double* __restrict__ muL, double c3,
+                           const double* __restrict__ x, const double* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  muM[i] = v + y[i];
+  muL[i] = c3 * v;
 }
 
 }  // namespace hw
@@ -609,12 +632,9 @@ int stage_vjp(const hweno_ctx* h, const Grid& g, const double* S, const double* 
   return cudaGetLastError() == cudaSuccess ? HWENO_OK : HWENO_ECUDA;
 }
 
-int lincomb(const hweno_ctx* h, double* out, double c1, const double* x1, double c2, const double* x2, double c3,
-            const double* x3) {
-  const long long n = (long long)hweno_state_doubles(h);
-  hw::k_lincomb<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(n, out, c1, x1, c2, x2, c3, x3);
-  return cudaGetLastError() == cudaSuccess ? HWENO_OK : HWENO_ECUDA;
-}
+unsigned rk_blocks(const hweno_ctx* h) { return (unsigned)((hweno_state_doubles(h) + 255) / 256); }
+long long rk_n(const hweno_ctx* h) { return (long long)hweno_state_doubles(h); }
+int launch_status() { return cudaGetLastError() == cudaSuccess ? HWENO_OK : HWENO_ECUDA; }
 
 }  // namespace
 
@@ -631,20 +651,20 @@ int adjoint_from_stages(hweno_t* h, const AdjPtrs& a, const double* Sn, const do
     return h->dim == 1 ? stage_vjp<1>(h, g, S, alpha6 + 2 * st, muM, muL, a.aw, lam)
                        : stage_vjp<2>(h, g, S, alpha6 + 2 * st, muM, muL, a.aw, lam);
   };
-  // S^{n+1} = 1/3 B + 2/3 (M(S2) + dt L(S2))
-  if ((rc = lincomb(h, a.muM, 2.0 / 3.0, lam_in, 0.0, nullptr, 0.0, nullptr))) return rc;
-  if ((rc = lincomb(h, a.muL, 2.0 / 3.0 * dt, lam_in, 0.0, nullptr, 0.0, nullptr))) return rc;
+  // S^{n+1} = 1/3 B + 2/3 (M(S2) + dt L(S2)):  muM = 2/3 lam_in, muL = 2/3 dt lam_in
+  hw::k_rk_seed<<<rk_blocks(h), 256, 0, h->stream>>>(rk_n(h), a.muM, a.muL, 2.0 / 3.0, 2.0 / 3.0 * dt, lam_in);
+  if ((rc = launch_status())) return rc;
   if ((rc = vjp(S2, 2, a.muM, a.muL, a.lam2))) return rc;
-  // S2 = 3/4 B + 1/4 (M(S1) + dt L(S1));  lamB = 1/3 lam_in + 3/4 lam2
-  if ((rc = lincomb(h, a.lamB, 1.0 / 3.0, lam_in, 0.75, a.lam2, 0.0, nullptr))) return rc;
-  if ((rc = lincomb(h, a.muM, 0.25, a.lam2, 0.0, nullptr, 0.0, nullptr))) return rc;
-  if ((rc = lincomb(h, a.muL, 0.25 * dt, a.lam2, 0.0, nullptr, 0.0, nullptr))) return rc;
+  // S2 = 3/4 B + 1/4 (M(S1) + dt L(S1)):  lamB = 1/3 lam_in + 3/4 lam2, muM = 1/4 lam2, muL = 1/4 dt lam2
+  hw::k_rk_mid<<<rk_blocks(h), 256, 0, h->stream>>>(rk_n(h), a.lamB, a.muM, a.muL, 1.0 / 3.0, 0.75, 0.25, 0.25 * dt,
+                                                    a.lam2, lam_in);
+  if ((rc = launch_status())) return rc;
   if ((rc = vjp(S1, 1, a.muM, a.muL, a.lam1))) return rc;
-  // S1 = M(S^n) + dt L(S^n), B = M(S^n)
-  if ((rc = lincomb(h, a.muM, 1.0, a.lam1, 1.0, a.lamB, 0.0, nullptr))) return rc;
-  if ((rc = lincomb(h, a.muL, dt, a.lam1, 0.0, nullptr, 0.0, nullptr))) return rc;
+  // S1 = M(S^n) + dt L(S^n), B = M(S^n):  muM = lam1 + lamB, muL = dt lam1
+  hw::k_rk_first<<<rk_blocks(h), 256, 0, h->stream>>>(rk_n(h), a.muM, a.muL, dt, a.lam1, a.lamB);
+  if ((rc = launch_status())) return rc;
   if ((rc = vjp(Sn, 0, a.muM, a.muL, lam_out))) return rc;
-  h->launches += 9 + 8;
+  h->launches += 9 + 3;
   return HWENO_OK;
 }
 

@@ -10,32 +10,66 @@ namespace hw {
 
 __device__ __forceinline__ double sgn0(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
 
+// The stencil constants of the adjoint's h-scaled forms (Grid fields, see Grid), copied into
+// thread registers through the integer pipe (FU::reg) so that the DFMAs reading them take register
+// operands: the indicator's split (aN, aS, bT, and twice aS, bT for its backward pass), eps, G,
+// Gd, cdu, csv and the candidate coefficients dm, dp.
+struct AdjK {
+  double eps, aN1, aN2, aS1, aS2, bT1, bT2, aS1x2, aS2x2, bT1x2, bT2x2, G, Gd, cdu, csv;
+  double dm[4], dp[4];
+};
+__device__ __forceinline__ AdjK adj_k(const Grid& g, const FU& f) {
+  AdjK k;
+  k.eps = f.reg(g.eps);
+  k.aN1 = f.reg(g.aN1);
+  k.aN2 = f.reg(g.aN2);
+  k.aS1 = f.reg(g.aS1);
+  k.aS2 = f.reg(g.aS2);
+  k.bT1 = f.reg(g.bT1);
+  k.bT2 = f.reg(g.bT2);
+  k.aS1x2 = f.reg(2.0 * g.aS1);
+  k.aS2x2 = f.reg(2.0 * g.aS2);
+  k.bT1x2 = f.reg(2.0 * g.bT1);
+  k.bT2x2 = f.reg(2.0 * g.bT2);
+  k.G = f.reg(g.G);
+  k.Gd = f.reg(g.Gd);
+  k.cdu = f.reg(g.cdu);
+  k.csv = f.reg(g.csv);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    k.dm[i] = f.reg(g.dm[i]);
+    k.dp[i] = f.reg(g.dp[i]);
+  }
+  return k;
+}
+
 // e0 = beta0 + eps of the stencil {i-1, i, i+1} from the differences dm, dp and the h-scaled
 // derivatives ym = h v_{i-1}, yp = h v_{i+1} (Eq. GHYZ): the two quadratic forms of beta0 with the
 // square completed in the derivative term, S1 (sv + N1 du)^2 + T1 du^2 + S2 (dv + N2 d2)^2 + T2 d2^2
 // (du = dm + dp, d2 = dp - dm, sv = ym + yp, dv = ym - yp), eps as the first addend.  Returns e0,
 // du and sv.
-__device__ __forceinline__ double beta0_eps_s(double dm, double dp, double ym, double yp, const Grid& g, const FU& f,
+__device__ __forceinline__ double beta0_eps_s(double dm, double dp, double ym, double yp, const AdjK& k, const FU& f,
                                               double& du_out, double& sv_out) {
   const double du = f.add(dm, dp), d2 = f.sub(dp, dm);
   const double sv = f.add(ym, yp), dv = f.sub(ym, yp);
-  const double y1 = fma(g.aN1, du, sv), y2 = fma(g.aN2, d2, dv);
+  const double y1 = fma(k.aN1, du, sv), y2 = fma(k.aN2, d2, dv);
   du_out = du;
   sv_out = sv;
-  return fma(g.aS1 * y1, y1, fma(g.aS2 * y2, y2, fma(g.bT1 * du, du, fma(g.bT2 * d2, d2, g.eps))));
+  return fma(f.mul(k.aS1, y1), y1,
+             fma(f.mul(k.aS2, y2), y2, fma(f.mul(k.bT1, du), du, fma(f.mul(k.bT2, d2), d2, k.eps))));
 }
 
 // Backward of beta0_eps_s: given e0b (the adjoint of beta0 + eps), adds those of dm, dp, ym, yp.
 //   d/dsv = 2 S1 y1, d/ddu = N1 2 S1 y1 + 2 T1 du, d/ddv = 2 S2 y2, d/dd2 = N2 2 S2 y2 + 2 T2 d2.
-__device__ __forceinline__ void beta0_eps_s_bwd(double dm, double dp, double ym, double yp, const Grid& g,
+__device__ __forceinline__ void beta0_eps_s_bwd(double dm, double dp, double ym, double yp, const AdjK& k,
                                                 double e0b, double& dmb, double& dpb, double& ymb, double& ypb,
                                                 const FU& f) {
   const double du = f.add(dm, dp), d2 = f.sub(dp, dm);
   const double sv = f.add(ym, yp), dv = f.sub(ym, yp);
-  const double y1 = fma(g.aN1, du, sv), y2 = fma(g.aN2, d2, dv);
-  const double t1 = f.mul((2.0 * g.aS1) * y1, e0b), t2 = f.mul((2.0 * g.aS2) * y2, e0b);
-  const double dub = fma(g.aN1, t1, f.mul((2.0 * g.bT1) * du, e0b));
-  const double d2b = fma(g.aN2, t2, f.mul((2.0 * g.bT2) * d2, e0b));
+  const double y1 = fma(k.aN1, du, sv), y2 = fma(k.aN2, d2, dv);
+  const double t1 = f.mul(f.mul(k.aS1x2, y1), e0b), t2 = f.mul(f.mul(k.aS2x2, y2), e0b);
+  const double dub = fma(k.aN1, t1, f.mul(f.mul(k.bT1x2, du), e0b));
+  const double d2b = fma(k.aN2, t2, f.mul(f.mul(k.bT2x2, d2), e0b));
   dmb = f.add(dmb, f.sub(dub, d2b));
   dpb = f.add(dpb, f.add(dub, d2b));
   ymb = f.add(ymb, f.add(t1, t2));
@@ -75,16 +109,16 @@ constexpr int kCellSaved = 7;   // per characteristic field of a cell
 // y0..y3: um - w1 and up - w2 (the interface values less the centre values; Eqs. Pxi, interp),
 // saving the intermediates [e0, W0, W1, W2, r, X, 1/den] of the stencil of cell k, then of cell k+1.
 __device__ __forceinline__ void face_field_save(double d01, double d12, double d23, double y0, double y1,
-                                                double y2, double y3, const Grid& g, double& dum, double& dup,
+                                                double y2, double y3, const AdjK& k, double& dum, double& dup,
                                                 double* sv, int stride, const FU& f) {
-  const double e01 = fma(d01, d01, g.eps), e12 = fma(d12, d12, g.eps), e23 = fma(d23, d23, g.eps);
+  const double e01 = fma(d01, d01, k.eps), e12 = fma(d12, d12, k.eps), e23 = fma(d23, d23, k.eps);
   double du, svs;
   {
-    const double e0 = beta0_eps_s(d01, d12, y0, y2, g, f, du, svs);
+    const double e0 = beta0_eps_s(d01, d12, y0, y2, k, f, du, svs);
     const Wts wt = weights_e(e0, e01, e12, f);
-    const double r = fma(g.dm[0], d01, fma(g.dm[1], d12, fma(g.dm[2], y0, g.dm[3] * y2)));
+    const double r = fma(k.dm[0], d01, fma(k.dm[1], d12, fma(k.dm[2], y0, f.mul(k.dm[3], y2))));
     const double sl = fma(wt.W1, d01, f.mul(wt.W2, d12));
-    const double inv = rcp(fma(g.G, wt.W0, f.add(wt.W1, wt.W2)), f);
+    const double inv = rcp(fma(k.G, wt.W0, f.add(wt.W1, wt.W2)), f);
     const double X = fma(wt.W0, r, 0.5 * sl);
     dum = f.mul(X, inv);
     sv[0] = e0;
@@ -96,11 +130,11 @@ __device__ __forceinline__ void face_field_save(double d01, double d12, double d
     sv[6 * stride] = inv;
   }
   {
-    const double e0 = beta0_eps_s(d12, d23, y1, y3, g, f, du, svs);
+    const double e0 = beta0_eps_s(d12, d23, y1, y3, k, f, du, svs);
     const Wts wt = weights_e(e0, e12, e23, f);
-    const double r = fma(g.dp[0], d12, fma(g.dp[1], d23, fma(g.dp[2], y1, g.dp[3] * y3)));
+    const double r = fma(k.dp[0], d12, fma(k.dp[1], d23, fma(k.dp[2], y1, f.mul(k.dp[3], y3))));
     const double sl = fma(wt.W1, d12, f.mul(wt.W2, d23));
-    const double inv = rcp(fma(g.G, wt.W0, f.add(wt.W1, wt.W2)), f);
+    const double inv = rcp(fma(k.G, wt.W0, f.add(wt.W1, wt.W2)), f);
     const double X = fma(wt.W0, r, -0.5 * sl);
     dup = f.mul(X, inv);
     sv[7 * stride] = e0;
@@ -117,10 +151,10 @@ __device__ __forceinline__ void face_field_save(double d01, double d12, double d
 // d23 (db) and y0..y3 (yb).  um - w1 = X / den with X = W0 r + (W1 d01 + W2 d12)/2,
 // den = G W0 + W1 + W2 (up - w2 likewise with d12, d23 and -1/2).
 __device__ __forceinline__ void face_field_bwd_saved(double d01, double d12, double d23, double y0, double y1,
-                                                     double y2, double y3, const Grid& g, double umb, double upb,
+                                                     double y2, double y3, const AdjK& k, double umb, double upb,
                                                      const double* sv, int stride, double* db, double* yb,
                                                      const FU& f) {
-  const double e01 = fma(d01, d01, g.eps), e12 = fma(d12, d12, g.eps), e23 = fma(d23, d23, g.eps);
+  const double e01 = fma(d01, d01, k.eps), e12 = fma(d12, d12, k.eps), e23 = fma(d23, d23, k.eps);
   double d01b = 0.0, d12b = 0.0, d23b = 0.0, e01b = 0.0, e12b = 0.0, e23b = 0.0;
   {
     const double e0 = sv[0], W0 = sv[stride], W1 = sv[2 * stride], W2 = sv[3 * stride];
@@ -128,15 +162,15 @@ __device__ __forceinline__ void face_field_bwd_saved(double d01, double d12, dou
     const double Xb = f.mul(umb, inv);
     const double denb = f.mul(f.mul(-Xb, X), inv);
     const double hX = 0.5 * Xb;
-    const double W0b = fma(Xb, r, denb * g.G), W1b = fma(hX, d01, denb), W2b = fma(hX, d12, denb);
+    const double W0b = fma(Xb, r, f.mul(denb, k.G)), W1b = fma(hX, d01, denb), W2b = fma(hX, d12, denb);
     const double rb = f.mul(Xb, W0);
-    d01b = f.add(d01b, fma(g.dm[0], rb, f.mul(hX, W1)));
-    d12b = f.add(d12b, fma(g.dm[1], rb, f.mul(hX, W2)));
-    yb[0] += g.dm[2] * rb;
-    yb[2] += g.dm[3] * rb;
+    d01b = f.add(d01b, fma(k.dm[0], rb, f.mul(hX, W1)));
+    d12b = f.add(d12b, fma(k.dm[1], rb, f.mul(hX, W2)));
+    yb[0] += k.dm[2] * rb;
+    yb[2] += k.dm[3] * rb;
     double e0b = 0.0;
     weights_e_bwd(e0, e01, e12, W0b, W1b, W2b, e0b, e01b, e12b, f);
-    beta0_eps_s_bwd(d01, d12, y0, y2, g, e0b, d01b, d12b, yb[0], yb[2], f);
+    beta0_eps_s_bwd(d01, d12, y0, y2, k, e0b, d01b, d12b, yb[0], yb[2], f);
   }
   {
     const double e0 = sv[7 * stride], W0 = sv[8 * stride], W1 = sv[9 * stride], W2 = sv[10 * stride];
@@ -144,15 +178,15 @@ __device__ __forceinline__ void face_field_bwd_saved(double d01, double d12, dou
     const double Xb = f.mul(upb, inv);
     const double denb = f.mul(f.mul(-Xb, X), inv);
     const double hX = -0.5 * Xb;
-    const double W0b = fma(Xb, r, denb * g.G), W1b = fma(hX, d12, denb), W2b = fma(hX, d23, denb);
+    const double W0b = fma(Xb, r, f.mul(denb, k.G)), W1b = fma(hX, d12, denb), W2b = fma(hX, d23, denb);
     const double rb = f.mul(Xb, W0);
-    d12b = f.add(d12b, fma(g.dp[0], rb, f.mul(hX, W1)));
-    d23b = f.add(d23b, fma(g.dp[1], rb, f.mul(hX, W2)));
-    yb[1] += g.dp[2] * rb;
-    yb[3] += g.dp[3] * rb;
+    d12b = f.add(d12b, fma(k.dp[0], rb, f.mul(hX, W1)));
+    d23b = f.add(d23b, fma(k.dp[1], rb, f.mul(hX, W2)));
+    yb[1] += k.dp[2] * rb;
+    yb[3] += k.dp[3] * rb;
     double e0b = 0.0;
     weights_e_bwd(e0, e12, e23, W0b, W1b, W2b, e0b, e12b, e23b, f);
-    beta0_eps_s_bwd(d12, d23, y1, y3, g, e0b, d12b, d23b, yb[1], yb[3], f);
+    beta0_eps_s_bwd(d12, d23, y1, y3, k, e0b, d12b, d23b, yb[1], yb[3], f);
   }
   // e_kl = d_kl^2 + eps
   db[0] = f.add(db[0], fma(2.0 * d01, e01b, d01b));
@@ -162,14 +196,14 @@ __device__ __forceinline__ void face_field_bwd_saved(double d01, double d12, dou
 
 // The limiter (Eq. limiter) of one characteristic field from the differences d01 = w1 - w0,
 // d12 = w2 - w1 and the scaled derivatives y0, y2: h v~_i, saving [e0, W0, W1, W2, t, num, 1/den].
-__device__ __forceinline__ double cell_field_save(double d01, double d12, double y0, double y2, const Grid& g,
+__device__ __forceinline__ double cell_field_save(double d01, double d12, double y0, double y2, const AdjK& k,
                                                   double* sv, int stride, const FU& f) {
   double du, svs;
-  const double e0 = beta0_eps_s(d01, d12, y0, y2, g, f, du, svs);
-  const Wts wt = weights_e(e0, fma(d01, d01, g.eps), fma(d12, d12, g.eps), f);
-  const double t = fma(g.cdu, du, -g.csv * svs);
+  const double e0 = beta0_eps_s(d01, d12, y0, y2, k, f, du, svs);
+  const Wts wt = weights_e(e0, fma(d01, d01, k.eps), fma(d12, d12, k.eps), f);
+  const double t = fma(k.cdu, du, -f.mul(k.csv, svs));
   const double num = fma(wt.W0, t, fma(wt.W1, d01, f.mul(wt.W2, d12)));
-  const double inv = rcp(fma(g.Gd, wt.W0, f.add(wt.W1, wt.W2)), f);
+  const double inv = rcp(fma(k.Gd, wt.W0, f.add(wt.W1, wt.W2)), f);
   sv[0] = e0;
   sv[stride] = wt.W0;
   sv[2 * stride] = wt.W1;
@@ -182,25 +216,25 @@ __device__ __forceinline__ double cell_field_save(double d01, double d12, double
 
 // Backward of cell_field_save from its saved values: given the adjoint of its output, adds those
 // of d01, d12 (db) and y0, y2.
-__device__ __forceinline__ void cell_field_bwd_saved(double d01, double d12, double y0, double y2, const Grid& g,
+__device__ __forceinline__ void cell_field_bwd_saved(double d01, double d12, double y0, double y2, const AdjK& k,
                                                      double outb, const double* sv, int stride, double* db,
                                                      double& y0b, double& y2b, const FU& f) {
-  const double e1 = fma(d01, d01, g.eps), e2 = fma(d12, d12, g.eps);
+  const double e1 = fma(d01, d01, k.eps), e2 = fma(d12, d12, k.eps);
   const double e0 = sv[0], W0 = sv[stride], W1 = sv[2 * stride], W2 = sv[3 * stride];
   const double t = sv[4 * stride], num = sv[5 * stride], inv = sv[6 * stride];
   const double numb = f.mul(outb, inv);
   const double denb = f.mul(f.mul(-numb, num), inv);
-  const double W0b = fma(numb, t, denb * g.Gd), W1b = fma(numb, d01, denb), W2b = fma(numb, d12, denb);
+  const double W0b = fma(numb, t, f.mul(denb, k.Gd)), W1b = fma(numb, d01, denb), W2b = fma(numb, d12, denb);
   const double tb = f.mul(numb, W0);
   double d01b = f.mul(numb, W1), d12b = f.mul(numb, W2);
   // t = cdu (d01 + d12) - csv (y0 + y2)
-  d01b += g.cdu * tb;
-  d12b += g.cdu * tb;
-  y0b -= g.csv * tb;
-  y2b -= g.csv * tb;
+  d01b += k.cdu * tb;
+  d12b += k.cdu * tb;
+  y0b -= k.csv * tb;
+  y2b -= k.csv * tb;
   double e0b = 0.0, e1b = 0.0, e2b = 0.0;
   weights_e_bwd(e0, e1, e2, W0b, W1b, W2b, e0b, e1b, e2b, f);
-  beta0_eps_s_bwd(d01, d12, y0, y2, g, e0b, d01b, d12b, y0b, y2b, f);
+  beta0_eps_s_bwd(d01, d12, y0, y2, k, e0b, d01b, d12b, y0b, y2b, f);
   db[0] = f.add(db[0], fma(2.0 * d01, e1b, d01b));
   db[1] = f.add(db[1], fma(2.0 * d12, e2b, d12b));
 }
