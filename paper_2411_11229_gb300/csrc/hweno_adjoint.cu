@@ -280,10 +280,14 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
     Fb[k] = 0.5 * nuf[k];
     Hb2[k] = g.hih[dir] * nuh[k];
   }
-  flux_bwd<NC>(Um, g.gm1, Fb, Umb, fu);
-  flux_bwd<NC>(Up, g.gm1, Fb, Upb, fu);
-  jvp_bwd<NC>(Um, Dm, g.gm1, Hb2, Umb, Dmb, fu);
-  jvp_bwd<NC>(Up, Dp, g.gm1, Hb2, Upb, Dpb, fu);
+  {
+    // the primitives of each interface state, shared by its flux and Jacobian-product backward
+    const Prim<NC> qm = prim_of<NC>(Um, g.gm1, fu), qp = prim_of<NC>(Up, g.gm1, fu);
+    flux_bwd<NC>(Um, qm, g.gm1, Fb, Umb, fu);
+    flux_bwd<NC>(Up, qp, g.gm1, Fb, Upb, fu);
+    jvp_bwd<NC>(Um, qm, Dm, g.gm1, Hb2, Umb, Dmb, fu);
+    jvp_bwd<NC>(Up, qp, Dp, g.gm1, Hb2, Upb, Dpb, fu);
+  }
   EigBar eb = {0.0, 0.0, 0.0, 0.0, 0.0};
   double hq2b = 0.0, ucb = 0.0, hb1b = 0.0, hb2b = 0.0, hicb = 0.0;
   double cmb[NC], cpb[NC];
@@ -420,6 +424,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_adj_gather(Grid g, const double
 #pragma unroll
     for (int f = 1; f < NF; ++f) V[f - 1][k] = S[(f * NC + k) * plane + p];
   }
+  const Prim<NC> qc = prim_of<NC>(U, g.gm1, fu);  // original frame
   const long long oplx = (long long)g.ny * (g.nx + 1);
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
@@ -515,9 +520,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_adj_gather(Grid g, const double
       swap_frame<NC>(nh);
       swap_frame<NC>(no);
     }
-    flux_bwd<NC>(Un, g.gm1, nf, Ub, fu);
-    jvp_bwd<NC>(Un, Dn, g.gm1, nh, Ub, Db, fu);
-    if (DIM == 2) jvp_bwd<NC>(Un, On, g.gm1, no, Ub, Ob, fu);
+    // the cell's primitives in the direction's frame (the velocities exchanged in y), shared by
+    // the three nodal backward passes and computed once for both directions
+    Prim<NC> qn = qc;
+    if (d == 1) {
+      qn.u = qc.v;
+      qn.v = qc.u;
+    }
+    flux_bwd<NC>(Un, qn, g.gm1, nf, Ub, fu);
+    jvp_bwd<NC>(Un, qn, Dn, g.gm1, nh, Ub, Db, fu);
+    if (DIM == 2) jvp_bwd<NC>(Un, qn, On, g.gm1, no, Ub, Ob, fu);
     if (d == 1) {
       swap_frame<NC>(Ub);
       swap_frame<NC>(Db);

@@ -390,11 +390,10 @@ __device__ __forceinline__ void prim_bwd(const double* U, const Prim<NC>& q, dou
   Ub[0] = fma(-f.mul(irb, q.ir), q.ir, Ub[0]);
 }
 
-// Flux F(U) in the normal frame: given Fb, adds Ub.
+// Flux F(U) in the normal frame: given Fb, adds Ub.  q: the primitives of U (prim_of).
 template <int NC>
-__device__ __forceinline__ void flux_bwd(const double* U, double gm1, const double* Fb, double* Ub,
+__device__ __forceinline__ void flux_bwd(const double* U, const Prim<NC>& q, double gm1, const double* Fb, double* Ub,
                                          const FU& f = HW_PLAIN_FU) {
-  const Prim<NC> q = prim_of<NC>(U, gm1, f);
   double ub = 0.0, vb = 0.0, pb = 0.0;
   // F = (m, m u + p, [n u,] (E + p) u)
   Ub[1] = f.add(Ub[1], fma(Fb[1], q.u, Fb[0]));
@@ -410,11 +409,10 @@ __device__ __forceinline__ void flux_bwd(const double* U, double gm1, const doub
   prim_bwd<NC>(U, q, gm1, 0.0, ub, vb, pb, Ub, f);
 }
 
-// Jacobian product A(U) D in the normal frame: given ob, adds Ub and Db.
+// Jacobian product A(U) D in the normal frame: given ob, adds Ub and Db.  q: the primitives of U.
 template <int NC>
-__device__ __forceinline__ void jvp_bwd(const double* U, const double* D, double gm1, const double* ob, double* Ub,
-                                        double* Db, const FU& f = HW_PLAIN_FU) {
-  const Prim<NC> q = prim_of<NC>(U, gm1, f);
+__device__ __forceinline__ void jvp_bwd(const double* U, const Prim<NC>& q, const double* D, double gm1,
+                                        const double* ob, double* Ub, double* Db, const FU& f = HW_PLAIN_FU) {
   const double du = f.mul(fma(-q.u, D[0], D[1]), q.ir);
   const double dv = NC == 4 ? f.mul(fma(-q.v, D[0], D[2]), q.ir) : 0.0;
   const double dk = NC == 4 ? fma(D[1], q.u, fma(U[1], du, fma(D[2], q.v, f.mul(U[2], dv))))
