@@ -43,8 +43,8 @@ HBM_PEAK_GBS_FALLBACK = 6800.0
 FACE_TRAFFIC_BYTES_PER_FACE = 285.2  # ncu dram bytes per face, 2048^2 capture of the current face kernel
 # from the same capture: FP64 pipe activity and FP64 instructions per face (the hardware's side of
 # the roofline fraction, which counts the scheme's operations as written)
-FACE_FP64_PIPE_ACTIVE = 0.915
-FACE_FP64_INSTR_PER_FACE = 670
+FACE_FP64_PIPE_ACTIVE = 0.958
+FACE_FP64_INSTR_PER_FACE = 666
 
 
 def _dist():
