@@ -7,6 +7,8 @@ never imports the product package.
 The oracle follows the paper (Xie, Tao, Jiao, Zhang, arXiv 2411.11229) step by step in FP64:
 Sec. 2.1 (HWENO interpolation and limiter), Sec. 2.2 (central Hermite D-terms), Eqs. (flux-1d),
 (flux-LF), (fully-hweno), Sec. 3 (2D, Eq. mixed) and the characteristic-decomposition remarks.
+The ``*_ext`` functions evaluate the same formulas in long double (the exact value that the rounding
+of an FP64 evaluation is measured against).
 """
 from __future__ import annotations
 
@@ -96,6 +98,14 @@ def lib():
             L.oracle_run.argtypes = [CP, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_longlong, _P]
             L.oracle_run.restype = ctypes.c_longlong
+            L.oracle_ext_mantissa_bits.argtypes = []
+            L.oracle_ext_mantissa_bits.restype = ctypes.c_int
+            L.oracle_rhs_ext.argtypes = [CP, _P, _P, _P]
+            L.oracle_rhs_cells_ext.argtypes = [CP, _P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong),
+                                               _P, _P]
+            L.oracle_run_ext.argtypes = [CP, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_longlong, _P]
+            L.oracle_run_ext.restype = ctypes.c_longlong
             L.oracle_count_flops.argtypes = [CP, ctypes.POINTER(ctypes.c_longlong)]
             L.oracle_count_stencil.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
             L.oracle_stage_vjp.argtypes = [CP, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P]
@@ -190,6 +200,47 @@ def run(cfg: Cfg, S: np.ndarray, t_end: float, cfl: float = 0.6, dx_pow: float =
     t = np.zeros(1)
     n = lib().oracle_run(ctypes.byref(cfg), _ptr(out), float(t_end), float(cfl), float(dx_pow),
                          int(max_steps), _ptr(t))
+    if n < 0:
+        raise ValueError("oracle run failed")
+    return out, int(n), float(t[0])
+
+
+def ext_mantissa_bits() -> int:
+    """Significand bits of the extended-precision evaluation (64 on x86-64, 113 on AArch64)."""
+    return int(lib().oracle_ext_mantissa_bits())
+
+
+def rhs_ext(cfg: Cfg, S: np.ndarray):
+    """rhs() with every value computed from the data held in long double (the LF coefficients from
+    S); the scheme's coefficients are the same double constants.  Results rounded to double."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    assert S.size == state_size(cfg)
+    L = np.zeros_like(S)
+    M = np.zeros_like(S)
+    _check(lib().oracle_rhs_ext(ctypes.byref(cfg), _ptr(S), _ptr(L), _ptr(M)))
+    return L, M
+
+
+def rhs_cells_ext(cfg: Cfg, S: np.ndarray, idx):
+    """rhs_cells() in long double, with the LF coefficients of the whole of S; [ncell, field, comp]."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    nf = 2 if cfg.dim == 1 else 3
+    m = S.size // (nf * cfg.nx * cfg.ny)
+    L = np.zeros((idx.size, nf, m))
+    M = np.zeros((idx.size, nf, m))
+    _check(lib().oracle_rhs_cells_ext(ctypes.byref(cfg), _ptr(S), idx.size,
+                                      idx.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), _ptr(L), _ptr(M)))
+    return L, M
+
+
+def run_ext(cfg: Cfg, S: np.ndarray, t_end: float, cfl: float = 0.6, dx_pow: float = 1.0,
+            max_steps: int = 0):
+    """run() with the state held in long double between steps.  Returns (state, steps, t)."""
+    out = np.array(S, dtype=np.float64, copy=True, order="C")
+    t = np.zeros(1)
+    n = lib().oracle_run_ext(ctypes.byref(cfg), _ptr(out), float(t_end), float(cfl), float(dx_pow),
+                             int(max_steps), _ptr(t))
     if n < 0:
         raise ValueError("oracle run failed")
     return out, int(n), float(t[0])

@@ -5,8 +5,9 @@
 // benchmark are the only callers.  Nothing in the product library links or calls this file,
 // and this file shares no code, header or constant table with the CUDA path.
 //
-// Everything is FP64 and is meant to be compiled with -ffp-contract=off.  Every formula is
-// written in the order and notation of the paper:
+// Everything is FP64 and is meant to be compiled with -ffp-contract=off (the `_ext` entry points
+// run the same templated formulas in long double, as the reference that FP64 rounding is measured
+// against).  Every formula is written in the order and notation of the paper:
 //   Sec. 2, Eq. (EQ1)/(odeH)      augmented system and conservative semi-discretisation (1D)
 //   Sec. 2.1, Eqs. (HWEp0)-(limiter)  Hermite candidates, smoothness indicators, weights,
 //                                      interpolation and HWENO limiter
@@ -48,9 +49,11 @@
 //   FLAG_ALPHA_STEP  the LF coefficients of the first stage's input held for all three stages.
 //   FLAG_ALPHA_LOCAL local LF (Rusanov): alpha at face i+1/2 is the larger spectral radius of the
 //                    two adjacent cells i, i+1 (ghost cells through the boundary map).
+#include <cfloat>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <thread>
 #include <vector>
 #include <algorithm>
@@ -72,10 +75,11 @@ inline int threads_used() {
   if (n <= 0) n = (int)std::thread::hardware_concurrency();
   return n < 1 ? 1 : n;
 }
-// body(lo, hi) on contiguous chunks of [0, n), one chunk per thread
+// body(lo, hi) on contiguous chunks of [0, n), one chunk per thread, each chunk at least `grain`
+// long
 template <class F>
-void parallel_for(long long n, F body) {
-  const long long T = std::min<long long>(threads_used(), n);
+void parallel_for(long long n, F body, long long grain = 1) {
+  const long long T = std::min<long long>(threads_used(), n / std::max(1LL, grain));
   if (T <= 1) {
     if (n > 0) body(0LL, n);
     return;
@@ -580,7 +584,7 @@ void fill_padded(const Cfg& c, const R* S, Padded<R>& P) {
       const int j = (int)(r % P.py) - P.gy, k = (int)((r / P.py) % P.nc), f = (int)(r / ((long long)P.py * P.nc));
       for (int i = -P.gx; i < P.nx + P.gx; ++i) P.at(f, k, j, i) = boundary_value(c, S, f, k, j, i);
     }
-  });
+  }, std::max(1, (1 << 14) / P.px));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -672,16 +676,24 @@ struct Operator {
     matvec(m, Rm, zt, Dt);
   }
 
+  // the largest wavespeed over the cells (a maximum is exact, so splitting the cells over threads
+  // gives the same value)
   R max_wavespeed(int dir, const R* S) const {
     const int ny = c.dim == 2 ? c.ny : 1;
     const size_t plane = (size_t)c.nx * ny;
     R a = R(0.0);
-    for (size_t p = 0; p < plane; ++p) {
-      R U[4];
-      for (int k = 0; k < m; ++k) U[k] = S[k * plane + p];
-      R w = ph.wavespeed(dir, U);
-      if (w > a) a = w;
-    }
+    std::mutex mu;
+    parallel_for((long long)plane, [&](long long lo, long long hi) {
+      R am = R(0.0);
+      for (size_t p = (size_t)lo; p < (size_t)hi; ++p) {
+        R U[4];
+        for (int k = 0; k < m; ++k) U[k] = S[k * plane + p];
+        R w = ph.wavespeed(dir, U);
+        if (w > am) am = w;
+      }
+      std::lock_guard<std::mutex> lock(mu);
+      if (am > a) a = am;
+    }, 1 << 15);
     return a;
   }
 
@@ -800,7 +812,7 @@ struct Operator {
           Lout[((size_t)f * m + k) * plane + (size_t)j * nx + i] = val;
         }
       }
-    });
+    }, std::max(1, (1 << 14) / nx));
     if (c.grav != 0.0)
       for (int f = 0; f < nfl; ++f)
         for (size_t p = 0; p < plane; ++p) {
@@ -901,7 +913,7 @@ void rk3_combine(int st, size_t n, double dt, const R* L, const R* M, R* B, R* S
         S[p] = a_k[st] * B[p] + b_k[st] * (M[p] + dt * L[p]);
       }
     }
-  });
+  }, 1 << 15);
 }
 
 // One SSP-RK3 step with the modified derivative in the base (Eq. fully-hweno / 2Dfully-hweno).
@@ -1471,6 +1483,90 @@ int oracle_count_stencil(long long* out) {
   out[2] = n;
   n = 0;
   return 0;
+}
+
+// ---- extended precision ----
+// The same templated formulas instantiated with long double (the x87 80-bit format, 64-bit
+// significand, on x86-64; IEEE binary128, 113-bit significand, on AArch64): the state is read
+// from double once, every value computed from the data is held and rounded in long double, and
+// the results are rounded to double once at the end.  The coefficients of the scheme stay the
+// double constants written above (literals, parameters, g, d, 1/h, dt), so this is the FP64
+// oracle's arithmetic with its coefficients and with less rounding: the measure of how far an
+// FP64 evaluation (the oracle's or the GPU's) is from the exact value of the same formulas.
+
+int oracle_ext_mantissa_bits(void) { return LDBL_MANT_DIG; }
+
+static std::vector<long double> to_ext(const double* S, size_t n) {
+  std::vector<long double> v(n);
+  for (size_t p = 0; p < n; ++p) v[p] = S[p];
+  return v;
+}
+
+static size_t state_len(const oracle_cfg* c) {
+  return (size_t)hwo::nfield(*c) * hwo::ncomp(*c) * c->nx * (c->dim == 2 ? c->ny : 1);
+}
+
+// L(S) and M(S) with the LF coefficients taken from S, all in long double
+int oracle_rhs_ext(const oracle_cfg* c, const double* S, double* L, double* M) {
+  if (check_cfg(c)) return -1;
+  const size_t n = state_len(c);
+  const std::vector<long double> Se = to_ext(S, n);
+  std::vector<long double> Le(n), Me(n);
+  hwo::Operator<long double> op(*c);
+  const long double ax = op.max_wavespeed(0, Se.data());
+  const long double ay = c->dim == 2 ? op.max_wavespeed(1, Se.data()) : 0.0L;
+  op.rhs(Se.data(), Le.data(), Me.data(), ax, ay);
+  for (size_t p = 0; p < n; ++p) {
+    L[p] = (double)Le[p];
+    M[p] = (double)Me[p];
+  }
+  return 0;
+}
+
+// L and M at selected cells (flat indices j*nx+i), the LF coefficients from the whole of S, all in
+// long double.  Lout, Mout: [ncell][field][comp].
+int oracle_rhs_cells_ext(const oracle_cfg* c, const double* S, long long ncell, const long long* idx, double* Lout,
+                         double* Mout) {
+  if (check_cfg(c) || ncell < 0) return -1;
+  const size_t n = state_len(c);
+  const std::vector<long double> Se = to_ext(S, n);
+  hwo::Operator<long double> op(*c);
+  const long double ax = op.max_wavespeed(0, Se.data());
+  const long double ay = c->dim == 2 ? op.max_wavespeed(1, Se.data()) : 0.0L;
+  const size_t nout = (size_t)ncell * hwo::nfield(*c) * hwo::ncomp(*c);
+  std::vector<long double> Le(nout), Me(nout);
+  const size_t per = (size_t)hwo::nfield(*c) * hwo::ncomp(*c);
+  hwo::parallel_for(ncell, [&](long long lo, long long hi) {
+    op.rhs_cells(Se.data(), ax, ay, hi - lo, idx + lo, Le.data() + (size_t)lo * per, Me.data() + (size_t)lo * per);
+  });
+  for (size_t p = 0; p < nout; ++p) {
+    Lout[p] = (double)Le[p];
+    Mout[p] = (double)Me[p];
+  }
+  return 0;
+}
+
+// Run to t_end with CFL steps (last step clamped), or at most max_steps steps when t_end <= 0, with
+// the state held in long double between steps (each step's dt is a double, as in oracle_run).
+long long oracle_run_ext(const oracle_cfg* c, double* S, double t_end, double cfl, double dx_pow,
+                         long long max_steps, double* t_out) {
+  if (check_cfg(c)) return -1;
+  const size_t n = state_len(c);
+  std::vector<long double> Se = to_ext(S, n);
+  double t = 0.0;
+  long long k = 0;
+  while ((t_end <= 0.0 || t < t_end) && (max_steps <= 0 || k < max_steps)) {
+    double dt = hwo::cfl_dt(*c, Se.data(), cfl, dx_pow);
+    if (!(dt > 0) || !std::isfinite(dt)) return -1;
+    if (t_end > 0.0 && t + dt > t_end) dt = t_end - t;
+    hwo::rk3_step(*c, Se.data(), dt);
+    t += dt;
+    ++k;
+    if (t_end > 0.0 && t >= t_end) break;
+  }
+  for (size_t p = 0; p < n; ++p) S[p] = (double)Se[p];
+  if (t_out) *t_out = t;
+  return k;
 }
 
 // ---- derivatives (adjoint conventions: fixed dt and alpha per stage) ----

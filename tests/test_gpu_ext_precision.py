@@ -1,0 +1,148 @@
+"""The GPU path's rounding measured against the oracle's extended-precision evaluation (long
+double; IEEE binary128 on the AArch64 host of the GPU), on the 2D Euler workloads of the benchmark
+(periodic [0, 2]^2, gamma 1.4, CFL 0.6): the smooth wave and the seeded four-quadrant data.
+
+The FP64 oracle and the GPU are two FP64 evaluations of the same formulas in different orders
+(the GPU's kernels fold constants, fuse multiply-adds and form differences first).  At full size
+the operator is ill-conditioned: L of a derivative field is a difference quotient of fluxes that
+carry 1/h, so its rounding noise grows like 1/h^2, and an input moved by one ulp moves L by up to
+1e-9 (relative, 1024^2).  The bar is therefore set against the exact value of the formulas, not
+against the other FP64 evaluation: per (field, component) plane, the GPU's distance to the
+extended evaluation is at most three times the FP64 oracle's distance to it (plus 1e-14 of the
+plane's scale for planes where both are at the last bit).  Where the quantity is well conditioned
+(the state after one stage at 1024^2, the modified derivatives, the state after 100 steps), the
+GPU is also held to an absolute bar against the extended evaluation.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2411_11229_gb300 import Solver  # noqa: E402
+
+FLOOR = 1e-14
+
+
+def _rel_max(a, b, nplanes=12):
+    a, b = a.reshape(nplanes, -1), b.reshape(nplanes, -1)
+    return np.abs(a - b).max(axis=1) / np.maximum(np.abs(b).max(axis=1), 1e-300)
+
+
+def _rel_l1(a, b, nplanes=12):
+    a, b = a.reshape(nplanes, -1), b.reshape(nplanes, -1)
+    return np.abs(a - b).sum(axis=1) / np.maximum(np.abs(b).sum(axis=1), 1e-300)
+
+
+def _within(e_gpu, e_64, what):
+    print(f"  {what}: GPU {e_gpu.max():.3e}  FP64 oracle {e_64.max():.3e}")
+    assert (e_gpu <= 3.0 * e_64 + FLOOR).all(), (what, e_gpu, e_64)
+
+
+def _state(kind, n):
+    if kind == "smooth":
+        return W.euler2d_smooth(n)
+    return W.euler2d_quadrants(n, seed=2000)
+
+
+@pytest.mark.parametrize("kind", ["smooth", "quadrants"])
+def test_rhs_1024_against_extended(kind):
+    n = 1024
+    S, dx, dy = _state(kind, n)
+    cfg = O.make_cfg(2, O.EULER, n, n, dx=dx, dy=dy)
+    s = Solver(2, "euler", n, n, dx=dx, dy=dy)
+    s.set_state(S)
+    L, M = s.rhs()
+    L, M = L.cpu().numpy(), M.cpu().numpy()
+    O.set_threads(0)
+    Lo, Mo = O.rhs(cfg, S)
+    Le, Me = O.rhs_ext(cfg, S)
+    dt = O.cfl_dt(cfg, S, 0.6)
+    print(f"{kind} 1024^2, one stage")
+    _within(_rel_max(L, Le), _rel_max(Lo, Le), "L")
+    _within(_rel_max(M, Me), _rel_max(Mo, Me), "M")
+    S1, S1o, S1e = M + dt * L, Mo + dt * Lo, Me + dt * Le
+    _within(_rel_max(S1, S1e), _rel_max(S1o, S1e), "S1 = M + dt L")
+    assert _rel_max(S1, S1e).max() <= 1e-12
+    assert _rel_max(M, Me).max() <= 1e-14
+
+
+def _samples(n, rng, count=400):
+    pts = {(0, 0), (n - 1, 0), (0, n - 1), (n - 1, n - 1)}
+    for i in (0, 1, 2, n // 2 - 2, n // 2 - 1, n // 2, n // 2 + 1, n - 3, n - 2, n - 1):
+        for j in (0, 1, n // 2 - 1, n // 2, n - 2, n - 1):
+            pts.add((i, j))
+    while len(pts) < count:
+        pts.add((int(rng.integers(0, n)), int(rng.integers(0, n))))
+    return np.array(sorted(j * n + i for i, j in pts), dtype=np.int64)
+
+
+@pytest.mark.parametrize("flags", [0, O.FLAG_R2])
+@pytest.mark.parametrize("kind", ["smooth", "quadrants"])
+def test_rhs_4096_sampled_against_extended(kind, flags):
+    """The benchmark's grid: one stage at 400 cells (corners, edges, the quadrant lines, random),
+    relative to each plane's largest value over the whole grid."""
+    n = 4096
+    S, dx, dy = _state(kind, n)
+    cfg = O.make_cfg(2, O.EULER, n, n, dx=dx, dy=dy, flags=flags)
+    s = Solver(2, "euler", n, n, dx=dx, dy=dy, flags=flags)
+    s.set_state(S)
+    L, M = s.rhs()
+    idx = _samples(n, np.random.default_rng(7))
+    idx_t = torch.as_tensor(idx, device=L.device)
+    Lg = L.reshape(3, 4, -1)[:, :, idx_t].permute(2, 0, 1).cpu().numpy()
+    Mg = M.reshape(3, 4, -1)[:, :, idx_t].permute(2, 0, 1).cpu().numpy()
+    Lmax = L.reshape(12, -1).abs().amax(dim=1).cpu().numpy()
+    Mmax = M.reshape(12, -1).abs().amax(dim=1).cpu().numpy()
+    del L, M
+    O.set_threads(0)
+    Lo, Mo = O.rhs_cells(cfg, S, idx, O.max_wavespeed(cfg, S))
+    Le, Me = O.rhs_cells_ext(cfg, S, idx)
+
+    def rel(a, b, den):
+        return np.abs(a - b).reshape(len(idx), 12).max(axis=0) / np.maximum(den, 1e-300)
+
+    print(f"{kind} 4096^2 flags {flags}, one stage at {len(idx)} cells")
+    _within(rel(Lg, Le, Lmax), rel(Lo, Le, Lmax), "L")
+    _within(rel(Mg, Me, Mmax), rel(Mo, Me, Mmax), "M")
+    assert rel(Mg, Me, Mmax).max() <= 1e-14
+
+
+def _runs(kind, n, steps):
+    S, dx, dy = _state(kind, n)
+    cfg = O.make_cfg(2, O.EULER, n, n, dx=dx, dy=dy)
+    s = Solver(2, "euler", n, n, dx=dx, dy=dy)
+    s.set_state(S)
+    s.set_time(0.0, 0.0)
+    s.step(0.0, steps)
+    _, tg = s.last_dt()
+    G = s.state.cpu().numpy()
+    O.set_threads(0)
+    Oo, k, to = O.run(cfg, S, 0.0, 0.6, 1.0, max_steps=steps)
+    Oe, ke, te = O.run_ext(cfg, S, 0.0, 0.6, 1.0, max_steps=steps)
+    assert k == ke == steps
+    return G, tg, Oo, to, Oe, te
+
+
+def test_smooth_256_hundred_steps_against_extended():
+    G, tg, Oo, to, Oe, te = _runs("smooth", 256, 100)
+    print("smooth 256^2, 100 steps; end times", tg, to, te)
+    assert abs(tg - te) <= 1e-13 * te and abs(to - te) <= 1e-13 * te
+    _within(_rel_max(G, Oe), _rel_max(Oo, Oe), "state (max norm)")
+    assert _rel_max(G, Oe).max() <= 1e-10
+
+
+def test_quadrants_128_hundred_steps_against_extended():
+    """Discontinuous data: shocks steepen from the quadrant corners, and rounding moves them by a
+    fraction of a cell, so the comparison is per plane in the relative L1 norm (the step sizes
+    follow the largest wavespeed, found at a shock, so the end times differ by rounding too)."""
+    G, tg, Oo, to, Oe, te = _runs("quadrants", 128, 100)
+    print("quadrants 128^2, 100 steps; end times", tg, to, te)
+    _within(_rel_l1(G, Oe), _rel_l1(Oo, Oe), "state (L1)")
+    assert abs(tg - te) <= 3.0 * abs(to - te) + 1e-15 * te
