@@ -254,8 +254,9 @@ def run_batched(dev, steps: int = 3, only_1d: bool = False):
 def run_adjoint(dev, n: int = 1024, nsteps: int = 200, every: int = 20):
     """The adjoint workload: 2D Euler 1024^2, smooth wave plus 8 seeded Fourier modes, J = 1/2 sum
     rho(T)^2 dx dy after 200 SSP-RK3 steps, gradient through the checkpointed rollout (checkpoints
-    every 20 steps).  Reports the cost of one adjoint step relative to one forward step.  n and
-    nsteps only shrink it for a profiler capture."""
+    every 20 steps) and through the rollout that keeps every step's stage inputs.  Reports the cost
+    of one adjoint step relative to one forward step.  n and nsteps only shrink it for a profiler
+    capture."""
     import torch
 
     import workloads as W
@@ -311,6 +312,28 @@ def run_adjoint(dev, n: int = 1024, nsteps: int = 200, every: int = 20):
     res.update({"rollout_steps": nsteps, "checkpoint_every": every, "rollout_forward_s": t1 - t0,
                 "rollout_backward_s": t2 - t1, "backward_over_forward": (t2 - t1) / (t1 - t0), "J": J.item(),
                 "convention": "fixed recorded dt and per-stage alpha"})
+    g_ckpt = S0.grad.detach().clone()
+    del ST, J
+    # the same rollout keeping every step's input and stage inputs (three states per step) instead of
+    # checkpoints: no replay in the backward pass; run once first so that the timed run reuses the
+    # allocator's block for the kept states
+    kept = {}
+    for rep in range(2):
+        S0.grad = None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ST = Rollout.apply(S0, s, nsteps, every, True)
+        J = 0.5 * (ST[0, 0] ** 2).sum() * dx * dy
+        J.item()
+        t1 = time.perf_counter()
+        J.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        kept = {"forward_s": t1 - t0, "backward_s": t2 - t1, "backward_over_forward": (t2 - t1) / (t1 - t0),
+                "kept_bytes": nsteps * 3 * s.state.numel() * 8,
+                "gradient_equals_checkpointed": bool(torch.equal(S0.grad, g_ckpt))}
+        del ST, J
+    res["rollout_kept_stages"] = kept
     return res
 
 

@@ -245,6 +245,14 @@ int hweno_adjoint_step_stages(hweno_t *h, const double *S_n_dev, const double *S
                               double dt, const double *alpha6_dev, const double *lam_in_dev,
                               double *lam_out_dev, void *adj_ws_dev);
 
+/* hweno_step (dt > 0 fixed, dt <= 0 CFL on the device) that also copies the stage inputs S1 (after
+ * stage 1) and S2 (after stage 2) of the step to S1_out_dev and S2_out_dev (device arrays of
+ * hweno_state_doubles() doubles, 16-byte aligned, not the bound state): with the step's input and
+ * hweno_step_record, everything hweno_adjoint_step_stages needs, so that a rollout that keeps them
+ * needs no forward recomputation in its backward pass.  EINVAL: NULL or unaligned outputs, dt not
+ * finite; ESTATE: nothing bound. */
+int hweno_step_stages(hweno_t *h, double dt, double *S1_out_dev, double *S2_out_dev);
+
 /* hweno_step_replay that also copies the stage inputs S1 (after stage 1) and S2 (after stage 2)
  * of the step to S1_out_dev and S2_out_dev. */
 int hweno_step_replay_stages(hweno_t *h, double dt, const double *alpha6_dev, double *S1_out_dev,

@@ -51,6 +51,7 @@ SIGNATURES = {
     "hweno_stage_vjp": (_I, [_H, _P, _P, _P, _P, _P, _P]),
     "hweno_adjoint_step_stages": (_I, [_H, _P, _P, _P, _D, _P, _P, _P, _P]),
     "hweno_step_replay_stages": (_I, [_H, _D, _P, _P, _P]),
+    "hweno_step_stages": (_I, [_H, _D, _P, _P]),
     "hweno_batch_create": (_I, [_I, _P, ctypes.POINTER(_H)]),
     "hweno_batch_set_stream": (_I, [_H, _P]),
     "hweno_batch_state_doubles": (ctypes.c_size_t, [_H]),

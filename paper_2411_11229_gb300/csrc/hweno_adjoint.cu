@@ -15,6 +15,7 @@
 //                D-terms and mixed fluxes to the flux adjoints and the nodal flux VJPs, and adds
 //                the identity part of M.
 // Contributions are stored per face / per cell and gathered (no atomics: deterministic).
+#include <cmath>
 #include "hweno_adjoint.cuh"
 #include "hweno_host.cuh"
 
@@ -716,6 +717,21 @@ int hweno_step_replay_stages(hweno_t* h, double dt, const double* alpha6, double
   const size_t bytes = hweno_state_doubles(h) * 8;
   for (int st = 0; st < 3; ++st) {
     int rc = stage(h, h->state, h->state, 0, st, dt, st, nullptr, nullptr, alpha6 + 2 * st);
+    if (rc) return rc;
+    if (st < 2 && cudaMemcpyAsync(st == 0 ? S1_out : S2_out, h->state, bytes, cudaMemcpyDeviceToDevice,
+                                  h->stream) != cudaSuccess)
+      return HWENO_ECUDA;
+  }
+  return HWENO_OK;
+}
+
+int hweno_step_stages(hweno_t* h, double dt, double* S1_out, double* S2_out) {
+  if (!h || !S1_out || !S2_out || !std::isfinite(dt)) return HWENO_EINVAL;
+  if (!h->ws || !h->state) return HWENO_ESTATE;
+  if (((uintptr_t)S1_out & 15) || ((uintptr_t)S2_out & 15)) return HWENO_EINVAL;
+  const size_t bytes = hweno_state_doubles(h) * 8;
+  for (int st = 0; st < 3; ++st) {
+    int rc = stage(h, h->state, h->state, 0, st, dt, st, nullptr, nullptr);
     if (rc) return rc;
     if (st < 2 && cudaMemcpyAsync(st == 0 ? S1_out : S2_out, h->state, bytes, cudaMemcpyDeviceToDevice,
                                   h->stream) != cudaSuccess)

@@ -198,6 +198,12 @@ class Solver:
             outs.append(lam_out)
         return lam_out
 
+    def step_stages(self, S1: torch.Tensor, S2: torch.Tensor, dt: float = 0.0) -> None:
+        """One step (CFL on the device for dt <= 0), copying its stage inputs S1 and S2 out."""
+        with self._ordered():
+            C.check(self.lib.hweno_step_stages(self.h, float(dt), ctypes.c_void_p(S1.data_ptr()),
+                                               ctypes.c_void_p(S2.data_ptr())), "hweno_step_stages")
+
     def step_replay_stages(self, dt: float, alpha6: torch.Tensor, S1: torch.Tensor, S2: torch.Tensor) -> None:
         """Replay a recorded step, copying its stage inputs S1 and S2 out."""
         with self._ordered():

@@ -3,7 +3,8 @@
 steps, gradient with respect to the initial state (conserved variables and their derivatives)
 through the checkpointed autograd rollout (checkpoints every 20 steps).  Checked against central
 differences of J along 16 seeded directions (same recorded dt and alphas), against the oracle's
-adjoint at 128^2, and for independence of the checkpoint interval."""
+adjoint at 128^2, and for independence of the checkpoint interval and of keeping every step's stage
+inputs instead of checkpoints."""
 import numpy as np
 import pytest
 
@@ -20,11 +21,11 @@ from paper_2411_11229_gb300 import Solver  # noqa: E402
 from paper_2411_11229_gb300.adjoint import Rollout, replay  # noqa: E402
 
 
-def _gradient(n, nsteps, every):
+def _gradient(n, nsteps, every, keep_stages=False):
     S0n, dx, dy = W.euler2d_adjoint_init(n, seed=4000)
     s = Solver(2, "euler", n, n, dx=dx, dy=dy)
     S0 = torch.as_tensor(S0n, device="cuda").requires_grad_(True)
-    ST = Rollout.apply(S0, s, nsteps, every)
+    ST = Rollout.apply(S0, s, nsteps, every, keep_stages)
     J = 0.5 * (ST[0, 0] ** 2).sum() * dx * dy
     J.backward()
     # the recorded steps, for the replays
@@ -76,3 +77,21 @@ def test_config5_gradient_against_oracle_at_128():
 def test_checkpoint_interval_does_not_change_the_gradient():
     grads = [_gradient(64, 12, every)[4] for every in (1, 5, 12)]
     assert torch.equal(grads[0], grads[1]) and torch.equal(grads[0], grads[2])
+
+
+def test_kept_stages_give_the_checkpointed_gradient():
+    """Keeping every step's input and stage inputs in the forward pass (no replay) gives the
+    gradient of the checkpointed rollout bit for bit: the CFL step and its replay with the recorded
+    dt and alphas compute the same stage inputs."""
+    a = _gradient(64, 12, 5)
+    b = _gradient(64, 12, 5, keep_stages=True)
+    assert torch.equal(a[4], b[4])
+    assert torch.equal(a[5], b[5])
+
+
+def test_kept_stages_at_1024():
+    """The adjoint workload's size with kept stage inputs (0.3 GB per step): the gradient of 40
+    steps equals the checkpointed one bit for bit."""
+    a = _gradient(1024, 40, 20)[4]
+    b = _gradient(1024, 40, 20, keep_stages=True)[4]
+    assert torch.equal(a, b)
