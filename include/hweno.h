@@ -204,6 +204,22 @@ void hweno_destroy(hweno_t *h);
 /* Static message for a status code. */
 const char *hweno_strerror(int status);
 
+/* Bounds-checked build only (libhweno_bounds.so, compiled with -DHWENO_BOUNDS_CHECK; a debugging
+ * aid): every cell, face, ghost-line and batch-instance index the kernels form is checked against
+ * the extent of the arrays it addresses; an index out of range is counted, the source line of the
+ * first one recorded, and the access redirected to element 0 of its array.  Synchronises the
+ * device and returns the number of such indices since the previous call (then clears it); *where
+ * (may be NULL) receives the first one's source line plus 100000 x its translation unit (0: entry
+ * points and stage kernels, 1: batched, 2: adjoint).  Returns -1 in a normal build, HWENO_ECUDA if
+ * the synchronisation fails. */
+long long hweno_bounds_status(int *where);
+
+/* Bounds-checked build only: the check applied once to an index one past the end of a
+ * two-element array in a one-thread kernel (whose one write goes to element 0 whatever the check
+ * returns).  Returns what hweno_bounds_status then reports: 1 when the check works; -1 in a normal
+ * build. */
+long long hweno_bounds_selftest(void);
+
 /* Number of kernel launches issued by this handle since creation (for accounting). */
 long long hweno_launch_count(const hweno_t *h);
 

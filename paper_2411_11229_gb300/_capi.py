@@ -6,6 +6,7 @@ when the library is missing or cannot be built.
 from __future__ import annotations
 
 import ctypes
+import os
 import threading
 
 from . import _make as _build
@@ -52,6 +53,8 @@ SIGNATURES = {
     "hweno_adjoint_step_stages": (_I, [_H, _P, _P, _P, _D, _P, _P, _P, _P]),
     "hweno_step_replay_stages": (_I, [_H, _D, _P, _P, _P]),
     "hweno_step_stages": (_I, [_H, _D, _P, _P]),
+    "hweno_bounds_status": (ctypes.c_longlong, [ctypes.POINTER(ctypes.c_int)]),
+    "hweno_bounds_selftest": (ctypes.c_longlong, []),
     "hweno_batch_create": (_I, [_I, _P, ctypes.POINTER(_H)]),
     "hweno_batch_set_stream": (_I, [_H, _P]),
     "hweno_batch_state_doubles": (ctypes.c_size_t, [_H]),
@@ -87,12 +90,19 @@ _lock = threading.Lock()
 _lib = None
 
 
+def bounds_checked() -> bool:
+    """True when HWENO_BOUNDS_CHECK=1 selects the bounds-checked library (libhweno_bounds.so)."""
+    return os.environ.get("HWENO_BOUNDS_CHECK", "") == "1"
+
+
 def load(build: bool = True):
-    """Load libhweno.so (building it first if it is missing or stale)."""
+    """Load libhweno.so (building it first if it is missing or stale), or the bounds-checked
+    libhweno_bounds.so when the environment sets HWENO_BOUNDS_CHECK=1."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build() if build else _build.LIB
+            bc = bounds_checked()
+            path = _build.build(bounds_check=bc) if build else _build.lib_path(bc)
             lib = ctypes.CDLL(path)
             for name, (res, args) in SIGNATURES.items():
                 fn = getattr(lib, name)

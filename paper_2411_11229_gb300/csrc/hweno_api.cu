@@ -30,6 +30,16 @@ __global__ void __launch_bounds__(kDfmaThreads) k_dfma_probe(double* __restrict_
   for (int k = 0; k < kDfmaChains; ++k) s += a[k];
   if (s == p[0]) p[3] = s;
 }
+
+#ifdef HWENO_BOUNDS_CHECK
+// self-test of the bounds check: the check applied to an index one past the end of a two-element
+// array; the kernel then writes element 0 (a constant index), whatever the check returned
+__device__ double g_bounds_probe[2];
+__global__ void k_bounds_probe(long long n) {
+  const long long i = HW_IDX(n, n);
+  g_bounds_probe[0] = (double)i;
+}
+#endif
 }  // namespace hw
 
 namespace {
@@ -593,4 +603,29 @@ extern "C" int hweno_rhs_static(int dim, int system, int64_t nx, int64_t ny, dou
   // the array keeps the previous call's contents: clear the wavespeed slots and the status word
   if (cudaMemsetAsync(scal_begin, 0, l.alpha + l.scal + l.status, h.stream) != cudaSuccess) return HWENO_ECUDA;
   return stage(&h, S, const_cast<double*>(S), 1, 0, 0.0, 3, Lo, Mo);
+}
+
+extern "C" long long hweno_bounds_status(int* where) {
+#ifdef HWENO_BOUNDS_CHECK
+  if (cudaDeviceSynchronize() != cudaSuccess) return HWENO_ECUDA;
+  int l0 = 0, l1 = 0, l2 = 0;
+  const unsigned int c0 = hw::bounds_take(&l0), c1 = hwh::bounds_take_batch(&l1), c2 = hwh::bounds_take_adjoint(&l2);
+  if (where) *where = c0 ? l0 : (c1 ? 100000 + l1 : (c2 ? 200000 + l2 : 0));
+  return (long long)c0 + c1 + c2;
+#else
+  if (where) *where = 0;
+  return -1;
+#endif
+}
+
+extern "C" long long hweno_bounds_selftest(void) {
+#ifdef HWENO_BOUNDS_CHECK
+  const long long before = hweno_bounds_status(nullptr);
+  if (before < 0) return before;
+  hw::k_bounds_probe<<<1, 1>>>(2);
+  if (cudaGetLastError() != cudaSuccess) return HWENO_ECUDA;
+  return hweno_bounds_status(nullptr);
+#else
+  return -1;
+#endif
 }

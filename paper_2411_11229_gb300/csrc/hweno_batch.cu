@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_stage(BatchArgs a) {
   const long long span = (long long)kThreads * a.tiles_per_item;
   for (int it = blockIdx.x; it < a.ncells; it += gridDim.x) {
     const int2 c = a.cells[it];
-    const BatchInst& I = a.inst[c.x];
+    const BatchInst& I = a.inst[HW_IDX(c.x, a.ninst)];
     if (I.dim == 1)
       batch_cells<1>(I, c.y * span, a.tiles_per_item, a.slot);
     else
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_stage(BatchArgs a) {
   grid.sync();
   for (int it = blockIdx.x; it < a.nfaces; it += gridDim.x) {
     const int4 f = a.faces[it];
-    const BatchInst& I = a.inst[f.x];
+    const BatchInst& I = a.inst[HW_IDX(f.x, a.ninst)];
     if (I.dim == 1)
       batch_faces<1>(I, 0, f.z * span, a.tiles_per_item, a.slot);
     else
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_stage(BatchArgs a) {
   grid.sync();
   for (int it = blockIdx.x; it < a.ncells; it += gridDim.x) {
     const int2 c = a.cells[it];
-    const BatchInst& I = a.inst[c.x];
+    const BatchInst& I = a.inst[HW_IDX(c.x, a.ninst)];
     if (I.dim == 1)
       batch_update<1>(I, c.y * span, a.tiles_per_item, a);
     else
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_cells(BatchArgs a) {
   const int lo = DIM == 2 ? 0 : a.ncells2, hi = DIM == 2 ? a.ncells2 : a.ncells;
   for (int it = lo + blockIdx.x; it < hi; it += gridDim.x) {
     const int2 c = a.cells[it];
-    batch_cells<DIM>(a.inst[c.x], c.y * span, a.tiles_per_item, a.slot);
+    batch_cells<DIM>(a.inst[HW_IDX(c.x, a.ninst)], c.y * span, a.tiles_per_item, a.slot);
   }
 }
 
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_batch_faces(BatchArgs a) {
   const int lo = DIM == 2 ? 0 : a.nfaces2, hi = DIM == 2 ? a.nfaces2 : a.nfaces;
   for (int it = lo + blockIdx.x; it < hi; it += gridDim.x) {
     const int4 f = a.faces[it];
-    batch_faces<DIM>(a.inst[f.x], DIM == 2 ? f.y : 0, f.z * span, a.tiles_per_item, a.slot);
+    batch_faces<DIM>(a.inst[HW_IDX(f.x, a.ninst)], DIM == 2 ? f.y : 0, f.z * span, a.tiles_per_item, a.slot);
   }
 }
 
@@ -143,11 +143,22 @@ __global__ void __launch_bounds__(kThreads) k_batch_update(BatchArgs a) {
   const int lo = DIM == 2 ? 0 : a.ncells2, hi = DIM == 2 ? a.ncells2 : a.ncells;
   for (int it = lo + blockIdx.x; it < hi; it += gridDim.x) {
     const int2 c = a.cells[it];
-    batch_update<DIM>(a.inst[c.x], c.y * span, a.tiles_per_item, a);
+    batch_update<DIM>(a.inst[HW_IDX(c.x, a.ninst)], c.y * span, a.tiles_per_item, a);
   }
 }
 
 }  // namespace hw
+
+namespace hwh {
+unsigned int bounds_take_batch(int* line) {
+#ifdef HWENO_BOUNDS_CHECK
+  return hw::bounds_take(line);
+#else
+  if (line) *line = 0;
+  return 0;
+#endif
+}
+}  // namespace hwh
 
 struct hweno_batch {
   int n;

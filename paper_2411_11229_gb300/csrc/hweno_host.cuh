@@ -319,6 +319,11 @@ inline int stage(hweno_ctx* h, const double* S_in, double* S_out, int mode, int 
 }
 
 // one forward stage in place with fixed dt and the given LF coefficients
+// bounds-checked build: the out-of-range index records of the batched and adjoint translation
+// units (count since the last call, first source line; 0 in a normal build)
+unsigned int bounds_take_batch(int* line);
+unsigned int bounds_take_adjoint(int* line);
+
 inline int stage_replay(hweno_ctx* h, double* S, int st, double dt, const double* alpha2_dev) {
   return stage(h, S, S, 0, st, dt, st, nullptr, nullptr, alpha2_dev);
 }

@@ -158,7 +158,7 @@ __device__ __forceinline__ void load_stencil3(const Grid& g, const double* __res
     bool refl, fixed = false;
     const int ac = VAR ? bc_map_ext(a0 - 1 + q, n, g.side[2 * d], g.side[2 * d + 1], refl, fixed)
                        : bc_map(a0 - 1 + q, n, g.bc, refl);
-    const long long pc = d == 0 ? (long long)j * g.nx + ac : (long long)ac * g.nx + i;
+    const long long pc = HW_IDX(d == 0 ? (long long)j * g.nx + ac : (long long)ac * g.nx + i, plane);
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
       U3[q][k] = (q == 1 && Uc) ? Uc[k] : S[k * plane + pc];
@@ -249,11 +249,12 @@ __device__ __forceinline__ void r2_cell(const double (&U3)[3][NC], const double 
 // Cell work of one stage at cell p: primitives and wavespeeds (returned in wsx, wsy), nodal
 // values per direction, modified derivatives (and, for R2, the face states of the cell).
 template <int DIM, int SYS, int VAR = 0>
-__device__ __forceinline__ void cell_body(const Grid& g, const double* __restrict__ S, const Work& w, long long p,
+__device__ __forceinline__ void cell_body(const Grid& g, const double* __restrict__ S, const Work& w, long long p_in,
                                           double& wsx, double& wsy) {
   using T = Traits<DIM, SYS>;
   constexpr int NC = T::NC, NG = T::NG;
   const long long plane = g.plane;
+  const long long p = HW_IDX(p_in, plane);
   const FU f = fu_of(w.scal);
   {
     const int i = (int)(p % g.nx), j = (int)(p / g.nx);
@@ -480,7 +481,7 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
     fside[q] = 2 * dir + (fa - 2 + q < 0 ? 0 : 1);
     const int a = VAR ? bc_map_ext(fa - 2 + q, n, g.side[2 * dir], g.side[2 * dir + 1], refl[q], fixed[q])
                       : bc_map(fa - 2 + q, n, g.bc, refl[q]);
-    pc[q] = dir == 0 ? (long long)line * g.nx + a : (long long)a * g.nx + line;
+    pc[q] = HW_IDX(dir == 0 ? (long long)line * g.nx + a : (long long)a * g.nx + line, plane);
   }
   const int fown = dir == 0 ? 1 : 2, foth = dir == 0 ? 2 : 1;
   double Um[NC], Up[NC], Dm[NC], Dp[NC];
@@ -490,12 +491,13 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
     const long long gs = w.gstride;
     const double* Glo = w.GFS + (long long)(dir * 2 + 0) * 2 * NC * gs;
     const double* Ghi = w.GFS + (long long)(dir * 2 + 1) * 2 * NC * gs;
+    const long long gl = HW_IDX(line, gs);
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-      Um[k] = fa >= 1 ? FSd[(0 * NC + k) * plane + pc[1]] : Glo[(0 * NC + k) * gs + line];
-      Dm[k] = fa >= 1 ? FSd[(1 * NC + k) * plane + pc[1]] : Glo[(1 * NC + k) * gs + line];
-      Up[k] = fa < n ? FSd[(2 * NC + k) * plane + pc[2]] : Ghi[(0 * NC + k) * gs + line];
-      Dp[k] = fa < n ? FSd[(3 * NC + k) * plane + pc[2]] : Ghi[(1 * NC + k) * gs + line];
+      Um[k] = fa >= 1 ? FSd[(0 * NC + k) * plane + pc[1]] : Glo[(0 * NC + k) * gs + gl];
+      Dm[k] = fa >= 1 ? FSd[(1 * NC + k) * plane + pc[1]] : Glo[(1 * NC + k) * gs + gl];
+      Up[k] = fa < n ? FSd[(2 * NC + k) * plane + pc[2]] : Ghi[(0 * NC + k) * gs + gl];
+      Dp[k] = fa < n ? FSd[(3 * NC + k) * plane + pc[2]] : Ghi[(1 * NC + k) * gs + gl];
     }
   } else {
     double Uq[4][NC], Zq[4][NC];
@@ -572,7 +574,7 @@ __device__ __forceinline__ void face_body(const Grid& g, const double* __restric
   const double* nod = w.NOD + (long long)dir * NG * NC * plane;
   double* out = dir == 0 ? w.FX : w.FY;
   const long long oplane = dir == 0 ? (long long)g.ny * (g.nx + 1) : (long long)(g.ny + 1) * g.nx;
-  const long long fo = dir == 0 ? (long long)line * (g.nx + 1) + fa : (long long)fa * g.nx + line;
+  const long long fo = HW_IDX(dir == 0 ? (long long)line * (g.nx + 1) + fa : (long long)fa * g.nx + line, oplane);
   const bool cd2 = VAR && (g.flags & FLAG_CD2) != 0;
   double fh[NC], hh[NC], mh[NC];
 #pragma unroll
@@ -653,15 +655,16 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 ? 3 : 4) k_face(Grid g, con
 // B := M, S = M + dt L).  mode 1: write L and M to Lout, Mout.
 template <int DIM, int SYS, int VAR = 0>
 __device__ __forceinline__ void update_body(const Grid& g, double* __restrict__ S, const Work& w, int mode, int stage,
-                                            double a_k, double b_k, double dt, long long p,
+                                            double a_k, double b_k, double dt, long long p_in,
                                             double* __restrict__ Lout, double* __restrict__ Mout) {
   using T = Traits<DIM, SYS>;
   constexpr int NC = T::NC, NF = T::NF;
   constexpr bool SRC = VAR != 0 && DIM == 2 && SYS == SYS_EULER;  // gravity source possible
   const long long plane = g.plane;
+  const long long p = HW_IDX(p_in, plane);
   const int i = (int)(p % g.nx), j = (int)(p / g.nx);
-  const long long px = (long long)j * (g.nx + 1) + i;
   const long long oplx = (long long)g.ny * (g.nx + 1), oply = (long long)(g.ny + 1) * g.nx;
+  const long long px = HW_IDX((long long)j * (g.nx + 1) + i, oplx - 1);  // faces px and px + 1
   // the stage's constants copied into thread registers (exactly: c 1 + (-0) = c), so that every
   // FP64 instruction below has register operands (see FU)
   const FU fu = fu_of(w.scal);
@@ -787,10 +790,11 @@ __global__ void __launch_bounds__(kThreads) k_r2_ghost(Grid g, const double* __r
   r2_cell<NC, SYS_EULER>(U3, D3, e, dir, g, md, fs, fu_of(w.scal));
   double* G = w.GFS + (long long)(dir * 2 + end) * 2 * NC * gs;
   const int q0 = end == 0 ? 0 : 2;
+  const long long gl = HW_IDX(line, gs);
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
-    G[(0 * NC + k) * gs + line] = fs[q0][k];
-    G[(1 * NC + k) * gs + line] = fs[q0 + 1][k];
+    G[(0 * NC + k) * gs + gl] = fs[q0][k];
+    G[(1 * NC + k) * gs + gl] = fs[q0 + 1][k];
   }
 }
 

@@ -521,6 +521,39 @@ struct Eig {
 };
 
 // ---------------------------------------------------------------------------------------------
+// Bounds-checked build (-DHWENO_BOUNDS_CHECK: libhweno_bounds.so, a debugging aid in place of a
+// memory checker).  Every array access of the kernels is base + (field NC + comp) extent + index,
+// with field and comp bounded by compile-time constants and each base and extent fixed by the host
+// layout, so checking each cell, face and ghost-line index where a kernel forms it covers the
+// accesses.  HW_IDX(i, n) is i when 0 <= i < n; otherwise it counts the event, records the source
+// line of the first one, and gives 0, so that the access stays inside its array.  The host reads
+// and clears the record with bounds_take (one record per translation unit; hweno_bounds_status).
+// In the normal build HW_IDX(i, n) is i.
+#ifdef HWENO_BOUNDS_CHECK
+static __device__ unsigned int g_bounds_count;
+static __device__ int g_bounds_line;
+__device__ __forceinline__ long long bounds_idx(long long i, long long n, int line) {
+  if (i >= 0 && i < n) return i;
+  if (atomicAdd(&g_bounds_count, 1u) == 0u) g_bounds_line = line;
+  return 0;
+}
+#define HW_IDX(i, n) ::hw::bounds_idx((long long)(i), (long long)(n), __LINE__)
+// this translation unit's count of out-of-range indices since the last call, and the source line
+// of the first (synchronous copies; clears the count)
+[[maybe_unused]] static unsigned int bounds_take(int* line) {
+  unsigned int c = 0, z = 0;
+  int l = 0;
+  cudaMemcpyFromSymbol(&c, g_bounds_count, sizeof c);
+  cudaMemcpyFromSymbol(&l, g_bounds_line, sizeof l);
+  cudaMemcpyToSymbol(g_bounds_count, &z, sizeof z);
+  if (line) *line = l;
+  return c;
+}
+#else
+#define HW_IDX(i, n) (i)
+#endif
+
+// ---------------------------------------------------------------------------------------------
 // Boundary index maps.  Periodic wraps, transmissive clamps (zero-order extrapolation),
 // reflective mirrors about the wall (cell -1-k for k < 0, 2n-1-k for k >= n) and sets refl.
 __device__ __forceinline__ int bc_map(int k, int n, int bc, bool& refl) {
