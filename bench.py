@@ -41,8 +41,8 @@ HBM_PEAK_GBS_FALLBACK = 6800.0
 # DRAM bytes per face of the 2D Euler face kernel from an ncu capture at 2048^2 (profiles/); the
 # traffic grows in proportion to the faces, so a 4096^2 launch moves this times its faces.
 FACE_TRAFFIC_BYTES_PER_FACE = 285.2  # ncu dram bytes per face, 2048^2 capture of the current face kernel
-# handles (each with its state, workspace and stream) that take the end-to-end steps in turn
-E2E_HANDLES = 3
+# device slots (each with its state, workspace and stream) of the end-to-end pipeline
+E2E_DEPTH = 3
 # from the same capture: FP64 pipe activity and FP64 instructions per face (the hardware's side of
 # the roofline fraction, which counts the scheme's operations as written)
 FACE_FP64_PIPE_ACTIVE = 0.958
@@ -505,10 +505,11 @@ def run_ours(args, ws, rank, local):
 
     # end to end through the C ABI with host buffers: upload, step, download every step.  Each step
     # takes its input from pinned host memory and returns its result there, so consecutive steps are
-    # independent problems; three handles on three streams take them in turn, and the copies of two
-    # run on the copy engines while the third steps (with two, a handle's next upload waits for its
-    # own download, which the other handle's step does not cover when the host link is slow).  The
-    # serial form (one handle, one stream) is reported beside it.
+    # independent problems: one hweno_pipeline call takes them, on three device slots in turn, so that
+    # the copies of two run on the copy engines while the third steps (with two, a slot's next upload
+    # waits for its own download, which the other slot's step does not cover when the host link is
+    # slow).  The serial form (upload, step, download on one handle and one stream) is reported
+    # beside it.
     host_in = torch.from_numpy(np.ascontiguousarray(solver.state.cpu().numpy())).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     nbytes = host_in.numel() * 8
@@ -531,45 +532,28 @@ def run_ours(args, ws, rank, local):
     barrier()
     ms_serial = max_over_ranks(f0.elapsed_time(f1), ws, dev)
     serial_value = job_throughput(ws, cells, ke2e, ms_serial)
-    nring = E2E_HANDLES
-    streams = [torch.cuda.Stream(dev) for _ in range(nring)]
-    ring = []
-    for st in streams:
-        sv = Solver(2, "euler", n, n, dx=dx, dy=dy, device=dev, stream=st)
-        sv.set_state(S)
-        sv.set_time(0.0, 0.0)
-        ring.append(sv)
-    ins = [host_in] + [torch.empty_like(host_in).pin_memory() for _ in range(nring - 1)]
+    depth = E2E_DEPTH
+    ins = [host_in] + [torch.empty_like(host_in).pin_memory() for _ in range(depth - 1)]
     for h in ins[1:]:
         h.copy_(host_in)
-    outs = [host_out] + [torch.empty_like(host_in).pin_memory() for _ in range(nring - 1)]
-    for i, sv in enumerate(ring):
-        sv.upload(ins[i])
-        sv.step(0.0)
-        sv.download(outs[i])
-        sv.sync()
+    outs = [host_out] + [torch.empty_like(host_in).pin_memory() for _ in range(depth - 1)]
+    seq_in = [ins[k % depth] for k in range(ke2e)]
+    seq_out = [outs[k % depth] for k in range(ke2e)]
+    solver.pipeline(ins, outs, 1, depth)  # allocates the slots' device memory outside the timed region
     barrier()
     torch.cuda.synchronize()
     p0 = torch.cuda.Event(enable_timing=True)
     p1 = torch.cuda.Event(enable_timing=True)
-    p0.record(streams[0])
-    for st in streams[1:]:
-        st.wait_event(p0)
-    for k in range(ke2e):
-        sv = ring[k % nring]
-        sv.upload(ins[k % nring])
-        sv.step(0.0)
-        sv.download(outs[k % nring])
-    for st in streams[1:]:
-        pb = torch.cuda.Event()
-        pb.record(st)
-        streams[0].wait_event(pb)
-    p1.record(streams[0])
+    p0.record(stream)
+    w0 = time.perf_counter()
+    solver.pipeline(seq_in, seq_out, 1, depth)
+    wall_ms = (time.perf_counter() - w0) * 1e3
+    p1.record(stream)
     torch.cuda.synchronize()
     barrier()
     ms_e2e = max_over_ranks(p0.elapsed_time(p1), ws, dev)
     e2e_value = job_throughput(ws, cells, ke2e, ms_e2e)
-    del ring
+    e2e_wall_value = job_throughput(ws, cells, ke2e, max_over_ranks(wall_ms, ws, dev))
     # one more end-to-end step outside the timed region, with an event between its phases: where
     # the end-to-end time goes (the copies run at the host link's rate, which varies between boxes)
     g = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -610,10 +594,13 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                 "steps": ke2e,
-                "path": f"hweno_upload + hweno_step + hweno_download per step, pinned host buffers; {nring} "
-                        "handles on as many streams take the steps in turn, so the copies of the others overlap "
-                        "each handle's step",
-                "serial": {"value": serial_value, "path": "the same calls on one handle and one stream"},
+                "path": f"one hweno_pipeline call: upload, one SSP-RK3 step and download per problem, pinned "
+                        f"host buffers, {depth} device slots on their own streams in turn, so the copies of the "
+                        "others overlap each slot's step (CUDA events on the handle's stream around the call)",
+                "wall_value": e2e_wall_value,
+                "serial": {"value": serial_value,
+                           "path": "hweno_upload + hweno_step + hweno_download per step on one handle and one "
+                                   "stream"},
                 "phases_one_step": phases},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": probe["flops"] / 1e12,
                      "unit": "TFLOP/s", "frac": achieved / probe["flops"], "traffic": traffic,

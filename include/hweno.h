@@ -191,6 +191,26 @@ int hweno_sync(hweno_t *h);
 int hweno_upload(hweno_t *h, const double *host_state);
 int hweno_download(hweno_t *h, double *host_state);
 
+/* Bytes of device memory one slot of hweno_pipeline needs: a state and a workspace (each 256-byte
+ * aligned within the slot). */
+size_t hweno_pipeline_slot_bytes(const hweno_t *h);
+
+/* Independent problems of this handle's grid and scheme, host memory to host memory: problem i is
+ * uploaded from host_in[i], advanced by nsteps SSP-RK3 steps with the CFL dt computed on the
+ * device (no end time), and downloaded to host_out[i] (host arrays of hweno_state_doubles()
+ * doubles; pinned memory lets the copies overlap the steps; host_out[i] may equal host_in[i], the
+ * arrays of different problems must not overlap unless i and j share a slot, i = j mod depth).
+ * depth slots (1..8) in slot_mem (caller-owned device memory of depth * hweno_pipeline_slot_bytes()
+ * bytes, 256-byte aligned), each with its own state, workspace and stream, take the problems in
+ * turn (problem i on slot i mod depth), so that the uploads and downloads of some slots run on the
+ * copy engines while another slot steps.  The slots start after the work queued on the handle's
+ * stream and the handle's stream is ordered after them; the call returns when every result is in
+ * host memory, with HWENO_ENONPHYS if any problem met a non-physical state.  The handle's own bound
+ * state and workspace are not used.  EINVAL: NULL or unaligned pointers, count or nsteps < 0, depth
+ * outside 1..8. */
+int hweno_pipeline(hweno_t *h, int count, const double *const *host_in, double *const *host_out, int nsteps,
+                   int depth, void *slot_mem);
+
 /* Per-kernel timing (tracing aid).  When on, every stage records CUDA events on the handle's
  * stream around its three launches (cell, face, update kernels).  hweno_kernel_times()
  * synchronises, returns the summed milliseconds and launch counts per kernel kind in

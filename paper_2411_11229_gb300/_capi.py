@@ -53,6 +53,8 @@ SIGNATURES = {
     "hweno_adjoint_step_stages": (_I, [_H, _P, _P, _P, _D, _P, _P, _P, _P]),
     "hweno_step_replay_stages": (_I, [_H, _D, _P, _P, _P]),
     "hweno_step_stages": (_I, [_H, _D, _P, _P]),
+    "hweno_pipeline_slot_bytes": (ctypes.c_size_t, [_H]),
+    "hweno_pipeline": (_I, [_H, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _I, _P]),
     "hweno_bounds_status": (ctypes.c_longlong, [ctypes.POINTER(ctypes.c_int)]),
     "hweno_bounds_selftest": (ctypes.c_longlong, []),
     "hweno_batch_create": (_I, [_I, _P, ctypes.POINTER(_H)]),

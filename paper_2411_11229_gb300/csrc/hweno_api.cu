@@ -418,6 +418,71 @@ int hweno_kernel_times(hweno_t* h, double* ms3, long long* n3) {
   return HWENO_OK;
 }
 
+size_t hweno_pipeline_slot_bytes(const hweno_t* h) {
+  if (!h) return 0;
+  return align_up(hweno_state_doubles(h) * 8) + hweno_workspace_bytes(h);
+}
+
+int hweno_pipeline(hweno_t* h, int count, const double* const* host_in, double* const* host_out, int nsteps,
+                   int depth, void* slot_mem) {
+  if (!h || count < 0 || nsteps < 0 || depth < 1 || depth > 8 || !slot_mem) return HWENO_EINVAL;
+  if ((uintptr_t)slot_mem & 255) return HWENO_EINVAL;
+  if (count > 0 && (!host_in || !host_out)) return HWENO_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (!host_in[i] || !host_out[i]) return HWENO_EINVAL;
+  const size_t bytes = hweno_state_doubles(h) * 8, sb = align_up(bytes), per = hweno_pipeline_slot_bytes(h);
+  unsigned char* base = static_cast<unsigned char*>(slot_mem);
+  // the slots: copies of the handle's scheme, each bound to its own state and workspace and
+  // launching on its own stream, ordered after the work already queued on the handle's stream
+  std::vector<hweno_ctx> slot(depth, *h);
+  std::vector<cudaStream_t> st(depth, nullptr);
+  cudaEvent_t start = nullptr;
+  int rc = cudaEventCreateWithFlags(&start, cudaEventDisableTiming) == cudaSuccess &&
+                   cudaEventRecord(start, h->stream) == cudaSuccess
+               ? HWENO_OK
+               : HWENO_ECUDA;
+  for (int d = 0; d < depth && !rc; ++d) {
+    hweno_ctx& s = slot[d];
+    s.events.clear();
+    s.profiling = false;
+    s.launches = 0;
+    if (cudaStreamCreateWithFlags(&st[d], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamWaitEvent(st[d], start, 0) != cudaSuccess) {
+      rc = HWENO_ECUDA;
+      break;
+    }
+    s.stream = st[d];
+    rc = hweno_bind(&s, reinterpret_cast<double*>(base + d * per), base + d * per + sb);
+  }
+  // problem i on slot i mod depth: upload, nsteps CFL steps, download, in that slot's stream order
+  for (int i = 0; i < count && !rc; ++i) {
+    hweno_ctx& s = slot[i % depth];
+    if (cudaMemcpyAsync(s.state, host_in[i], bytes, cudaMemcpyHostToDevice, s.stream) != cudaSuccess) {
+      rc = HWENO_ECUDA;
+      break;
+    }
+    for (int k = 0; k < nsteps && !rc; ++k) rc = hweno_step(&s, 0.0);
+    if (!rc && cudaMemcpyAsync(host_out[i], s.state, bytes, cudaMemcpyDeviceToHost, s.stream) != cudaSuccess)
+      rc = HWENO_ECUDA;
+  }
+  // wait for every slot; the handle's stream is ordered after them
+  for (int d = 0; d < depth; ++d) {
+    if (!st[d]) continue;
+    const int sr = read_status(&slot[d]);  // synchronises the slot's stream
+    if (!rc) rc = sr;
+    h->launches += slot[d].launches;
+    cudaEvent_t done = nullptr;
+    if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess) {
+      cudaEventRecord(done, st[d]);
+      cudaStreamWaitEvent(h->stream, done, 0);
+      cudaEventDestroy(done);
+    }
+    cudaStreamDestroy(st[d]);
+  }
+  if (start) cudaEventDestroy(start);
+  return rc;
+}
+
 void hweno_destroy(hweno_t* h) {
   if (!h) return;
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);

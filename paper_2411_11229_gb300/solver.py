@@ -169,6 +169,30 @@ class Solver:
     def launch_count(self) -> int:
         return int(self.lib.hweno_launch_count(self.h))
 
+    def pipeline(self, host_in, host_out, nsteps: int = 1, depth: int = 3) -> None:
+        """Independent problems of this grid and scheme, host to host (hweno_pipeline): problem i is
+        uploaded from the host tensor host_in[i], advanced by nsteps CFL steps and downloaded to
+        host_out[i] (float64, contiguous, the state's size; pinned memory lets the copies overlap
+        the steps), on `depth` device slots in turn.  Returns when every result is in host memory."""
+        n = len(host_in)
+        if len(host_out) != n:
+            raise ValueError("host_in and host_out differ in length")
+        size = self.state.numel()
+        for t in list(host_in) + list(host_out):
+            if t.device.type != "cpu" or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != size:
+                raise ValueError("pipeline arrays: contiguous float64 host tensors of the state's size")
+        need = int(depth) * int(self.lib.hweno_pipeline_slot_bytes(self.h))
+        mem = getattr(self, "pipeline_memory", None)
+        if mem is None or mem.numel() < need:
+            self.pipeline_memory = None
+            with torch.cuda.stream(self.stream):
+                self.pipeline_memory = torch.empty(need, dtype=torch.uint8, device=self.device)
+        ins = (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() for t in host_in])
+        outs = (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() for t in host_out])
+        with self._ordered():
+            C.check(self.lib.hweno_pipeline(self.h, n, ins, outs, int(nsteps), int(depth),
+                                            _ptr(self.pipeline_memory)), "hweno_pipeline")
+
     # ---- adjoint support (fixed dt and per-stage LF coefficients) ----------------------------
     def _adj_ws(self):
         if getattr(self, "adj_workspace", None) is None:
