@@ -648,7 +648,9 @@ int stage_vjp(const hweno_ctx* h, const Grid& g, const double* S, const double* 
   constexpr size_t cell_sm = (size_t)hw::kCellSaved * NC * hw::kThreads * sizeof(double);
   constexpr size_t face_sm = (size_t)hw::kFaceSaved * NC * hw::kThreads * sizeof(double);
   if (cudaFuncSetAttribute(hw::k_adj_face<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)face_sm) !=
-      cudaSuccess)
+          cudaSuccess ||
+      cudaFuncSetAttribute(hw::k_adj_cell<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_sm) !=
+          cudaSuccess)
     return HWENO_ECUDA;
   hw::k_adj_cell<DIM><<<dim3(bc, DIM), hw::kThreads, cell_sm, st>>>(g, S, muM, aw);
   const long long nfx = (long long)(g.nx + 1) * g.ny;

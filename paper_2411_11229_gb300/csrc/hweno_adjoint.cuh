@@ -12,10 +12,10 @@ __device__ __forceinline__ double sgn0(double x) { return x > 0.0 ? 1.0 : (x < 0
 
 // The stencil constants of the adjoint's h-scaled forms (Grid fields, see Grid), copied into
 // thread registers through the integer pipe (FU::reg) so that the DFMAs reading them take register
-// operands: the indicator's split (aN, aS, bT, and twice aS, bT for its backward pass), eps, G,
-// Gd, cdu, csv and the candidate coefficients dm, dp.
+// operands: the indicator's split (aN, aS, bT), eps, G, Gd, cdu, csv and the candidate
+// coefficients dm, dp.
 struct AdjK {
-  double eps, aN1, aN2, aS1, aS2, bT1, bT2, aS1x2, aS2x2, bT1x2, bT2x2, G, Gd, cdu, csv;
+  double eps, aN1, aN2, aS1, aS2, bT1, bT2, G, Gd, cdu, csv;
   double dm[4], dp[4];
 };
 __device__ __forceinline__ AdjK adj_k(const Grid& g, const FU& f) {
@@ -27,10 +27,6 @@ __device__ __forceinline__ AdjK adj_k(const Grid& g, const FU& f) {
   k.aS2 = f.reg(g.aS2);
   k.bT1 = f.reg(g.bT1);
   k.bT2 = f.reg(g.bT2);
-  k.aS1x2 = f.reg(2.0 * g.aS1);
-  k.aS2x2 = f.reg(2.0 * g.aS2);
-  k.bT1x2 = f.reg(2.0 * g.bT1);
-  k.bT2x2 = f.reg(2.0 * g.bT2);
   k.G = f.reg(g.G);
   k.Gd = f.reg(g.Gd);
   k.cdu = f.reg(g.cdu);
@@ -47,74 +43,103 @@ __device__ __forceinline__ AdjK adj_k(const Grid& g, const FU& f) {
 // derivatives ym = h v_{i-1}, yp = h v_{i+1} (Eq. GHYZ): the two quadratic forms of beta0 with the
 // square completed in the derivative term, S1 (sv + N1 du)^2 + T1 du^2 + S2 (dv + N2 d2)^2 + T2 d2^2
 // (du = dm + dp, d2 = dp - dm, sv = ym + yp, dv = ym - yp), eps as the first addend.  Returns e0,
-// du and sv.
+// du and sv, and in bt the four products S1 y1, S2 y2, T1 du, T2 d2 (its backward pass reads them).
+struct BetaTerms {
+  double s1y1, s2y2, t1du, t2d2;
+};
 __device__ __forceinline__ double beta0_eps_s(double dm, double dp, double ym, double yp, const AdjK& k, const FU& f,
-                                              double& du_out, double& sv_out) {
+                                              double& du_out, double& sv_out, BetaTerms& bt) {
   const double du = f.add(dm, dp), d2 = f.sub(dp, dm);
   const double sv = f.add(ym, yp), dv = f.sub(ym, yp);
   const double y1 = fma(k.aN1, du, sv), y2 = fma(k.aN2, d2, dv);
   du_out = du;
   sv_out = sv;
-  return fma(f.mul(k.aS1, y1), y1,
-             fma(f.mul(k.aS2, y2), y2, fma(f.mul(k.bT1, du), du, fma(f.mul(k.bT2, d2), d2, k.eps))));
+  bt.s1y1 = f.mul(k.aS1, y1);
+  bt.s2y2 = f.mul(k.aS2, y2);
+  bt.t1du = f.mul(k.bT1, du);
+  bt.t2d2 = f.mul(k.bT2, d2);
+  return fma(bt.s1y1, y1, fma(bt.s2y2, y2, fma(bt.t1du, du, fma(bt.t2d2, d2, k.eps))));
 }
 
-// Backward of beta0_eps_s: given e0b (the adjoint of beta0 + eps), adds those of dm, dp, ym, yp.
+// Backward of beta0_eps_s from its saved products: given e0b (the adjoint of beta0 + eps), adds
+// those of dm, dp, ym, yp.
 //   d/dsv = 2 S1 y1, d/ddu = N1 2 S1 y1 + 2 T1 du, d/ddv = 2 S2 y2, d/dd2 = N2 2 S2 y2 + 2 T2 d2.
-__device__ __forceinline__ void beta0_eps_s_bwd(double dm, double dp, double ym, double yp, const AdjK& k,
-                                                double e0b, double& dmb, double& dpb, double& ymb, double& ypb,
-                                                const FU& f) {
-  const double du = f.add(dm, dp), d2 = f.sub(dp, dm);
-  const double sv = f.add(ym, yp), dv = f.sub(ym, yp);
-  const double y1 = fma(k.aN1, du, sv), y2 = fma(k.aN2, d2, dv);
-  const double t1 = f.mul(f.mul(k.aS1x2, y1), e0b), t2 = f.mul(f.mul(k.aS2x2, y2), e0b);
-  const double dub = fma(k.aN1, t1, f.mul(f.mul(k.bT1x2, du), e0b));
-  const double d2b = fma(k.aN2, t2, f.mul(f.mul(k.bT2x2, d2), e0b));
+__device__ __forceinline__ void beta0_eps_s_bwd(const BetaTerms& bt, const AdjK& k, double e0b, double& dmb,
+                                                double& dpb, double& ymb, double& ypb, const FU& f) {
+  const double e0b2 = f.add(e0b, e0b);  // 2 e0b, exactly
+  const double t1 = f.mul(bt.s1y1, e0b2), t2 = f.mul(bt.s2y2, e0b2);
+  const double dub = fma(k.aN1, t1, f.mul(bt.t1du, e0b2));
+  const double d2b = fma(k.aN2, t2, f.mul(bt.t2d2, e0b2));
   dmb = f.add(dmb, f.sub(dub, d2b));
   dpb = f.add(dpb, f.add(dub, d2b));
   ymb = f.add(ymb, f.add(t1, t2));
   ypb = f.add(ypb, f.sub(t1, t2));
 }
 
-// Backward of weights_e (W_l = P + tau Q_l from e_l = beta_l + eps, tau from e_0 - e_l): given
-// W0b..W2b, adds the adjoints of e0, e1, e2.
-__device__ __forceinline__ void weights_e_bwd(double e0, double e1, double e2, double W0b, double W1b, double W2b,
-                                              double& e0b, double& e1b, double& e2b, const FU& f) {
-  const double ts = f.add(fabs(f.sub(e0, e1)), fabs(f.sub(e0, e2)));
-  const double tau = f.mul(0.25 * ts, ts);
+// x sgn(s) with sgn(0) = 0, in the integer pipe: the sign bit of s flips that of x, and a zero s
+// (either sign) gives +0
+__device__ __forceinline__ double mul_sgn(double x, double s) {
+  const int sh = __double2hiint(s), sl = __double2loint(s);
+  const bool zero = ((sh & 0x7fffffff) | sl) == 0;
+  const double y = __hiloint2double(__double2hiint(x) ^ (sh & (int)0x80000000), __double2loint(x));
+  return zero ? 0.0 : y;
+}
+
+// Backward of weights_e (W_l = P + tau Q_l from e_l = beta_l + eps, tau = (|e0 - e1| + |e0 - e2|)^2
+// / 4) with tau saved by the forward pass: given W0b..W2b, adds the adjoints of e0, e1, e2.
+__device__ __forceinline__ void weights_e_bwd(double e0, double e1, double e2, double tau, double W0b, double W1b,
+                                              double W2b, double& e0b, double& e1b, double& e2b, const FU& f) {
+  const double a = f.sub(e0, e1), b = f.sub(e0, e2);
+  const double ts = f.add(fabs(a), fabs(b));
   const double Q0 = f.mul(e1, e2), Q1 = f.mul(e0, e2), Q2 = f.mul(e0, e1);
   const double Pb = f.add(f.add(W0b, W1b), W2b);
   const double taub = fma(W0b, Q0, fma(W1b, Q1, f.mul(W2b, Q2)));
   const double Q0b = fma(W0b, tau, f.mul(Pb, e0)), Q1b = f.mul(W1b, tau), Q2b = f.mul(W2b, tau);
   const double tsb = f.mul(0.5 * ts, taub);
-  const double s1 = sgn0(e0 - e1), s2 = sgn0(e0 - e2);
-  e0b = f.add(e0b, fma(tsb, f.add(s1, s2), fma(Pb, Q0, fma(Q1b, e2, f.mul(Q2b, e1)))));
-  e1b = f.add(e1b, fma(-tsb, s1, fma(Q0b, e2, f.mul(Q2b, e0))));
-  e2b = f.add(e2b, fma(-tsb, s2, fma(Q0b, e1, f.mul(Q1b, e0))));
+  // the adjoint of ts reaches e0 - e1 and e0 - e2 times their signs
+  const double ta = mul_sgn(tsb, a), tb = mul_sgn(tsb, b);
+  e0b = f.add(e0b, f.add(f.add(ta, tb), fma(Pb, Q0, fma(Q1b, e2, f.mul(Q2b, e1)))));
+  e1b = f.add(e1b, f.sub(fma(Q0b, e2, f.mul(Q2b, e0)), ta));
+  e2b = f.add(e2b, f.sub(fma(Q0b, e1, f.mul(Q1b, e0)), tb));
 }
 
 // ---------------------------------------------------------------------------------------------
 // Backward passes from saved forward values.  The adjoint kernels run the forward interpolation
 // once, keep each stencil's intermediates (beta0 + eps, the three weights, the candidate
-// combination, the weighted sum and 1/den) in shared memory, and the backward pass reads them
-// instead of recomputing them.  The forward map is taken in difference form, as the forward kernels
+// combination, the weighted sum, 1/den, tau and the four products of the indicator) in shared
+// memory, and the backward pass reads them instead of recomputing them.  The forward map is taken in difference form, as the forward kernels
 // take it: the characteristic fields enter only through differences of neighbouring cells.  sv
 // points at this thread's first slot; consecutive values are `stride` doubles apart (one slot per
 // thread of the block).
-constexpr int kFaceSaved = 14;  // per characteristic field of a face: 7 per stencil
-constexpr int kCellSaved = 7;   // per characteristic field of a cell
+constexpr int kStencilSaved = 12;                 // per stencil
+constexpr int kFaceSaved = 2 * kStencilSaved;     // per characteristic field of a face (two stencils)
+constexpr int kCellSaved = kStencilSaved;         // per characteristic field of a cell
+
+// slots 7..11 of a stencil: tau and the indicator's products
+__device__ __forceinline__ void save_tail(double* sv, int stride, double tau, const BetaTerms& bt) {
+  sv[7 * stride] = tau;
+  sv[8 * stride] = bt.s1y1;
+  sv[9 * stride] = bt.s2y2;
+  sv[10 * stride] = bt.t1du;
+  sv[11 * stride] = bt.t2d2;
+}
+__device__ __forceinline__ BetaTerms load_terms(const double* sv, int stride) {
+  return BetaTerms{sv[8 * stride], sv[9 * stride], sv[10 * stride], sv[11 * stride]};
+}
 
 // One characteristic field at one face k+1/2 (h-scaled derivatives) from the differences
 // d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2 of the cells k-1..k+2 and their scaled derivatives
 // y0..y3: um - w1 and up - w2 (the interface values less the centre values; Eqs. Pxi, interp),
-// saving the intermediates [e0, W0, W1, W2, r, X, 1/den] of the stencil of cell k, then of cell k+1.
+// saving the intermediates [e0, W0, W1, W2, r, X, 1/den, tau, S1 y1, S2 y2, T1 du, T2 d2] of the
+// stencil of cell k, then of cell k+1.
 __device__ __forceinline__ void face_field_save(double d01, double d12, double d23, double y0, double y1,
                                                 double y2, double y3, const AdjK& k, double& dum, double& dup,
                                                 double* sv, int stride, const FU& f) {
   const double e01 = fma(d01, d01, k.eps), e12 = fma(d12, d12, k.eps), e23 = fma(d23, d23, k.eps);
   double du, svs;
+  BetaTerms bt;
   {
-    const double e0 = beta0_eps_s(d01, d12, y0, y2, k, f, du, svs);
+    const double e0 = beta0_eps_s(d01, d12, y0, y2, k, f, du, svs, bt);
     const Wts wt = weights_e(e0, e01, e12, f);
     const double r = fma(k.dm[0], d01, fma(k.dm[1], d12, fma(k.dm[2], y0, f.mul(k.dm[3], y2))));
     const double sl = fma(wt.W1, d01, f.mul(wt.W2, d12));
@@ -128,22 +153,25 @@ __device__ __forceinline__ void face_field_save(double d01, double d12, double d
     sv[4 * stride] = r;
     sv[5 * stride] = X;
     sv[6 * stride] = inv;
+    save_tail(sv, stride, wt.tau, bt);
   }
   {
-    const double e0 = beta0_eps_s(d12, d23, y1, y3, k, f, du, svs);
+    double* const s2 = sv + kStencilSaved * stride;
+    const double e0 = beta0_eps_s(d12, d23, y1, y3, k, f, du, svs, bt);
     const Wts wt = weights_e(e0, e12, e23, f);
     const double r = fma(k.dp[0], d12, fma(k.dp[1], d23, fma(k.dp[2], y1, f.mul(k.dp[3], y3))));
     const double sl = fma(wt.W1, d12, f.mul(wt.W2, d23));
     const double inv = rcp(fma(k.G, wt.W0, f.add(wt.W1, wt.W2)), f);
     const double X = fma(wt.W0, r, -0.5 * sl);
     dup = f.mul(X, inv);
-    sv[7 * stride] = e0;
-    sv[8 * stride] = wt.W0;
-    sv[9 * stride] = wt.W1;
-    sv[10 * stride] = wt.W2;
-    sv[11 * stride] = r;
-    sv[12 * stride] = X;
-    sv[13 * stride] = inv;
+    s2[0] = e0;
+    s2[stride] = wt.W0;
+    s2[2 * stride] = wt.W1;
+    s2[3 * stride] = wt.W2;
+    s2[4 * stride] = r;
+    s2[5 * stride] = X;
+    s2[6 * stride] = inv;
+    save_tail(s2, stride, wt.tau, bt);
   }
 }
 
@@ -169,12 +197,13 @@ __device__ __forceinline__ void face_field_bwd_saved(double d01, double d12, dou
     yb[0] += k.dm[2] * rb;
     yb[2] += k.dm[3] * rb;
     double e0b = 0.0;
-    weights_e_bwd(e0, e01, e12, W0b, W1b, W2b, e0b, e01b, e12b, f);
-    beta0_eps_s_bwd(d01, d12, y0, y2, k, e0b, d01b, d12b, yb[0], yb[2], f);
+    weights_e_bwd(e0, e01, e12, sv[7 * stride], W0b, W1b, W2b, e0b, e01b, e12b, f);
+    beta0_eps_s_bwd(load_terms(sv, stride), k, e0b, d01b, d12b, yb[0], yb[2], f);
   }
   {
-    const double e0 = sv[7 * stride], W0 = sv[8 * stride], W1 = sv[9 * stride], W2 = sv[10 * stride];
-    const double r = sv[11 * stride], X = sv[12 * stride], inv = sv[13 * stride];
+    const double* const s2 = sv + kStencilSaved * stride;
+    const double e0 = s2[0], W0 = s2[stride], W1 = s2[2 * stride], W2 = s2[3 * stride];
+    const double r = s2[4 * stride], X = s2[5 * stride], inv = s2[6 * stride];
     const double Xb = f.mul(upb, inv);
     const double denb = f.mul(f.mul(-Xb, X), inv);
     const double hX = -0.5 * Xb;
@@ -185,8 +214,8 @@ __device__ __forceinline__ void face_field_bwd_saved(double d01, double d12, dou
     yb[1] += k.dp[2] * rb;
     yb[3] += k.dp[3] * rb;
     double e0b = 0.0;
-    weights_e_bwd(e0, e12, e23, W0b, W1b, W2b, e0b, e12b, e23b, f);
-    beta0_eps_s_bwd(d12, d23, y1, y3, k, e0b, d12b, d23b, yb[1], yb[3], f);
+    weights_e_bwd(e0, e12, e23, s2[7 * stride], W0b, W1b, W2b, e0b, e12b, e23b, f);
+    beta0_eps_s_bwd(load_terms(s2, stride), k, e0b, d12b, d23b, yb[1], yb[3], f);
   }
   // e_kl = d_kl^2 + eps
   db[0] = f.add(db[0], fma(2.0 * d01, e01b, d01b));
@@ -195,11 +224,13 @@ __device__ __forceinline__ void face_field_bwd_saved(double d01, double d12, dou
 }
 
 // The limiter (Eq. limiter) of one characteristic field from the differences d01 = w1 - w0,
-// d12 = w2 - w1 and the scaled derivatives y0, y2: h v~_i, saving [e0, W0, W1, W2, t, num, 1/den].
+// d12 = w2 - w1 and the scaled derivatives y0, y2: h v~_i, saving [e0, W0, W1, W2, t, num, 1/den,
+// tau, S1 y1, S2 y2, T1 du, T2 d2].
 __device__ __forceinline__ double cell_field_save(double d01, double d12, double y0, double y2, const AdjK& k,
                                                   double* sv, int stride, const FU& f) {
   double du, svs;
-  const double e0 = beta0_eps_s(d01, d12, y0, y2, k, f, du, svs);
+  BetaTerms bt;
+  const double e0 = beta0_eps_s(d01, d12, y0, y2, k, f, du, svs, bt);
   const Wts wt = weights_e(e0, fma(d01, d01, k.eps), fma(d12, d12, k.eps), f);
   const double t = fma(k.cdu, du, -f.mul(k.csv, svs));
   const double num = fma(wt.W0, t, fma(wt.W1, d01, f.mul(wt.W2, d12)));
@@ -211,6 +242,7 @@ __device__ __forceinline__ double cell_field_save(double d01, double d12, double
   sv[4 * stride] = t;
   sv[5 * stride] = num;
   sv[6 * stride] = inv;
+  save_tail(sv, stride, wt.tau, bt);
   return f.mul(num, inv);
 }
 
@@ -233,8 +265,8 @@ __device__ __forceinline__ void cell_field_bwd_saved(double d01, double d12, dou
   y0b -= k.csv * tb;
   y2b -= k.csv * tb;
   double e0b = 0.0, e1b = 0.0, e2b = 0.0;
-  weights_e_bwd(e0, e1, e2, W0b, W1b, W2b, e0b, e1b, e2b, f);
-  beta0_eps_s_bwd(d01, d12, y0, y2, k, e0b, d01b, d12b, y0b, y2b, f);
+  weights_e_bwd(e0, e1, e2, sv[7 * stride], W0b, W1b, W2b, e0b, e1b, e2b, f);
+  beta0_eps_s_bwd(load_terms(sv, stride), k, e0b, d01b, d12b, y0b, y2b, f);
   db[0] = f.add(db[0], fma(2.0 * d01, e1b, d01b));
   db[1] = f.add(db[1], fma(2.0 * d12, e2b, d12b));
 }

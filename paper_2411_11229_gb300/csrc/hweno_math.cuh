@@ -175,6 +175,7 @@ __device__ __forceinline__ double beta0_eps(double dm, double dp, double vm, dou
 // W_l = e0 e1 e2 + tau * prod_{k != l} e_k.  One reciprocal normalises them later.
 struct Wts {
   double W0, W1, W2;
+  double tau;  // tau of Eq. (nonlinear) (read by the adjoint's saved forward pass)
 };
 
 // Weights from e_l = beta_l + eps directly: e_l - e_k stands for beta_l - beta_k in tau.  quarter:
@@ -188,6 +189,7 @@ __device__ __forceinline__ Wts weights_e(double e0, double e1, double e2, double
   w.W0 = fma(tau, Q0, P);
   w.W1 = fma(tau, Q1, P);
   w.W2 = fma(tau, Q2, P);
+  w.tau = tau;
   return w;
 }
 __device__ __forceinline__ Wts weights_e(double e0, double e1, double e2, const FU& f = HW_PLAIN_FU) {
