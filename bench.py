@@ -568,6 +568,8 @@ def run_ours(args, ws, rank, local):
     phases = {"upload_ms": g[0].elapsed_time(g[1]), "step_ms": g[1].elapsed_time(g[2]),
               "download_ms": g[2].elapsed_time(g[3])}
     phases["copy_gbs"] = 2 * nbytes / ((phases["upload_ms"] + phases["download_ms"]) * 1e-3) / 1e9
+    phases["h2d_gbs"] = nbytes / (phases["upload_ms"] * 1e-3) / 1e9
+    phases["d2h_gbs"] = nbytes / (phases["download_ms"] * 1e-3) / 1e9
 
     if rank != 0:
         return 0
