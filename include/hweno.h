@@ -191,7 +191,8 @@ int hweno_sync(hweno_t *h);
 int hweno_upload(hweno_t *h, const double *host_state);
 int hweno_download(hweno_t *h, double *host_state);
 
-/* Bytes of device memory one slot of hweno_pipeline needs: a state and a workspace (each 256-byte
+/* Host-to-host pipeline (not in the paper: for callers whose inputs and results live in host
+ * memory).  Bytes of device memory one slot of hweno_pipeline needs: a state and a workspace (each 256-byte
  * aligned within the slot). */
 size_t hweno_pipeline_slot_bytes(const hweno_t *h);
 
@@ -225,7 +226,7 @@ void hweno_destroy(hweno_t *h);
 const char *hweno_strerror(int status);
 
 /* Bounds-checked build only (libhweno_bounds.so, compiled with -DHWENO_BOUNDS_CHECK; a debugging
- * aid): every cell, face, ghost-line and batch-instance index the kernels form is checked against
+ * aid, not in the paper): every cell, face, ghost-line and batch-instance index the kernels form is checked against
  * the extent of the arrays it addresses; an index out of range is counted, the source line of the
  * first one recorded, and the access redirected to element 0 of its array.  Synchronises the
  * device and returns the number of such indices since the previous call (then clears it); *where
@@ -281,12 +282,12 @@ int hweno_adjoint_step_stages(hweno_t *h, const double *S_n_dev, const double *S
                               double dt, const double *alpha6_dev, const double *lam_in_dev,
                               double *lam_out_dev, void *adj_ws_dev);
 
-/* hweno_step (dt > 0 fixed, dt <= 0 CFL on the device) that also copies the stage inputs S1 (after
- * stage 1) and S2 (after stage 2) of the step to S1_out_dev and S2_out_dev (device arrays of
- * hweno_state_doubles() doubles, 16-byte aligned, not the bound state): with the step's input and
- * hweno_step_record, everything hweno_adjoint_step_stages needs, so that a rollout that keeps them
- * needs no forward recomputation in its backward pass.  EINVAL: NULL or unaligned outputs, dt not
- * finite; ESTATE: nothing bound. */
+/* hweno_step (Eq. fully-hweno / 2Dfully-hweno; dt > 0 fixed, dt <= 0 CFL on the device) that also
+ * copies the stage inputs S1 (after stage 1) and S2 (after stage 2) of the step to S1_out_dev and
+ * S2_out_dev (device arrays of hweno_state_doubles() doubles, 16-byte aligned, not the bound
+ * state): with the step's input and hweno_step_record, everything hweno_adjoint_step_stages needs,
+ * so that a rollout that keeps them needs no forward recomputation in its backward pass.  EINVAL:
+ * NULL or unaligned outputs, dt not finite; ESTATE: nothing bound. */
 int hweno_step_stages(hweno_t *h, double dt, double *S1_out_dev, double *S2_out_dev);
 
 /* hweno_step_replay that also copies the stage inputs S1 (after stage 1) and S2 (after stage 2)
