@@ -1,6 +1,7 @@
 """The GPU path's rounding measured against the oracle's extended-precision evaluation (long
 double; IEEE binary128 on the AArch64 host of the GPU), on the 2D Euler workloads of the benchmark
-(periodic [0, 2]^2, gamma 1.4, CFL 0.6): the smooth wave and the seeded four-quadrant data.
+(periodic [0, 2]^2, gamma 1.4, CFL 0.6): the smooth wave and the seeded four-quadrant data; also
+the 1D Euler Riemann workload at its largest size and the two scalar laws at 1024^2.
 
 The FP64 oracle and the GPU are two FP64 evaluations of the same formulas in different orders
 (the GPU's kernels fold constants, fuse multiply-adds and form differences first).  At full size
@@ -146,3 +147,48 @@ def test_quadrants_128_hundred_steps_against_extended():
     print("quadrants 128^2, 100 steps; end times", tg, to, te)
     _within(_rel_l1(G, Oe), _rel_l1(Oo, Oe), "state (L1)")
     assert abs(tg - te) <= 3.0 * abs(to - te) + 1e-15 * te
+
+
+def test_euler1d_riemann_16384_against_extended():
+    """The 1D Euler Riemann workload at its largest size (transmissive walls): one stage full
+    field, and ten CFL steps (relative L1 per plane: a shock cell's derivative value moves with
+    rounding)."""
+    n = 16384
+    S, dx, _ = W.euler1d_riemann(n, seed=1000)
+    cfg = O.make_cfg(1, O.EULER, n, dx=dx, bc=O.BC_TRANSMISSIVE)
+    s = Solver(1, "euler", n, dx=dx, bc="transmissive")
+    s.set_state(S)
+    L, M = s.rhs()
+    L, M = L.cpu().numpy(), M.cpu().numpy()
+    O.set_threads(0)
+    Lo, Mo = O.rhs(cfg, S)
+    Le, Me = O.rhs_ext(cfg, S)
+    print("1D Euler Riemann 16384, one stage")
+    _within(_rel_max(L, Le, 6), _rel_max(Lo, Le, 6), "L")
+    _within(_rel_max(M, Me, 6), _rel_max(Mo, Me, 6), "M")
+    s.set_time(0.0, 0.0)
+    s.step(0.0, 10)
+    G = s.state.cpu().numpy()
+    Oo, k, _ = O.run(cfg, S, 0.0, 0.6, 1.0, max_steps=10)
+    Oe, ke, _ = O.run_ext(cfg, S, 0.0, 0.6, 1.0, max_steps=10)
+    assert k == ke == 10
+    _within(_rel_l1(G, Oe, 6), _rel_l1(Oo, Oe, 6), "state after 10 steps (L1)")
+
+
+@pytest.mark.parametrize("system", ["burgers", "advection"])
+def test_scalar_1024_against_extended(system):
+    """The scalar laws (no characteristic decomposition) at 1024^2, one stage, full field."""
+    n = 1024
+    S, dx, dy = W.scalar_random(2, n, n, 31, "smooth")
+    sysn = {"burgers": O.BURGERS, "advection": O.ADVECTION}[system]
+    cfg = O.make_cfg(2, sysn, n, n, dx=dx, dy=dy, ax=0.8, ay=-0.6)
+    s = Solver(2, system, n, n, dx=dx, dy=dy, ax=0.8, ay=-0.6)
+    s.set_state(S)
+    L, M = s.rhs()
+    L, M = L.cpu().numpy(), M.cpu().numpy()
+    O.set_threads(0)
+    Lo, Mo = O.rhs(cfg, S)
+    Le, Me = O.rhs_ext(cfg, S)
+    print(f"2D {system} 1024^2, one stage")
+    _within(_rel_max(L, Le, 3), _rel_max(Lo, Le, 3), "L")
+    _within(_rel_max(M, Me, 3), _rel_max(Mo, Me, 3), "M")
