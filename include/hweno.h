@@ -237,8 +237,8 @@ long long hweno_bounds_status(int *where);
 
 /* Bounds-checked build only: the check applied once to an index one past the end of a
  * two-element array in a one-thread kernel (whose one write goes to element 0 whatever the check
- * returns).  Returns what hweno_bounds_status then reports: 1 when the check works; -1 in a normal
- * build. */
+ * returns).  Reads and drops the record of earlier launches first, then returns what
+ * hweno_bounds_status reports for the probe: 1 when the check works; -1 in a normal build. */
 long long hweno_bounds_selftest(void);
 
 /* Number of kernel launches issued by this handle since creation (for accounting). */

@@ -1,14 +1,12 @@
 // Reverse-mode derivatives (hand-written) of the device arithmetic in hweno_math.cuh, for the
 // adjoint of one Runge-Kutta stage.  Conventions: the LF coefficient alpha of every stage and the
-// step size are held fixed; d|x|/dx = sign(x) with sign(0) = 0.  Every backward routine
-// recomputes the forward values it needs from the same inputs and ADDS the adjoints of its
-// inputs to the bar arrays.
+// step size are held fixed; d|x|/dx = sign(x) with sign(0) = 0 (mul_sgn).  Every backward routine
+// reads the forward values it needs (saved by the forward pass or recomputed from the same inputs)
+// and ADDS the adjoints of its inputs to the bar arrays.
 #pragma once
 #include "hweno_kernels.cuh"
 
 namespace hw {
-
-__device__ __forceinline__ double sgn0(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
 
 // The stencil constants of the adjoint's h-scaled forms (Grid fields, see Grid), copied into
 // thread registers through the integer pipe (FU::reg) so that the DFMAs reading them take register
