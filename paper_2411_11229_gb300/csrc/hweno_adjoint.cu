@@ -48,9 +48,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
   const int n = d == 0 ? g.nx : g.ny;
   const int a0 = d == 0 ? i : j;
   const int fld = d == 0 ? 1 : 2;
-  const double h = g.h[d], ih = g.ih[d];
+  const double ih = g.ih[d];
   const FU fu = fu_of(aw.scal);
-  double U3[3][NC], hD3[3][NC];
+  // the derivatives enter unscaled, as in the forward cell kernel (h folded into the constants)
+  double U3[3][NC], D3[3][NC];
   long long pc[3];
   bool refl[3];
 #pragma unroll
@@ -60,14 +61,14 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
       U3[q][k] = S[k * plane + pc[q]];
-      hD3[q][k] = h * S[(fld * NC + k) * plane + pc[q]];
+      D3[q][k] = S[(fld * NC + k) * plane + pc[q]];
     }
     if (d == 1) {
       swap_frame<NC>(U3[q]);
-      swap_frame<NC>(hD3[q]);
+      swap_frame<NC>(D3[q]);
     }
     mirror_U<NC>(U3[q], refl[q]);
-    mirror_D<NC>(hD3[q], refl[q]);
+    mirror_D<NC>(D3[q], refl[q]);
   }
   // forward: eigenvectors of the cell's own state
   const Prim<NC> pr = prim_of<NC>(U3[1], g.gm1, fu);
@@ -85,12 +86,12 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
     for (int k = 0; k < NC; ++k) dU[q][k] = fu.sub(U3[q + 1][k], U3[q][k]);
   e.project(dU[0], Dq[0], fu);
   e.project(dU[1], Dq[1], fu);
-  e.project(hD3[0], Zm, fu);
-  e.project(hD3[2], Zp, fu);
+  e.project(D3[0], Zm, fu);
+  e.project(D3[2], Zp, fu);
   // forward intermediates of the limiter, per field, kept in this thread's shared-memory slots
   extern __shared__ double adj_cell_sm[];
   double* const svb = adj_cell_sm + threadIdx.x;
-  const AdjK ak = adj_k(g, fu);
+  const AdjK ak = adj_k(g, d, fu);
 #pragma unroll
   for (int s = 0; s < NC; ++s)
     ht[s] = cell_field_save(Dq[0][s], Dq[1][s], Zm[s], Zp[s], ak, svb + s * kCellSaved * kThreads, kThreads, fu) * ih;
@@ -115,16 +116,16 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
     Dqb[0][s] = db[0];
     Dqb[1][s] = db[1];
   }
-  double dUb[2][NC], Ub[3][NC], hDmb[NC], hDpb[NC];
+  double dUb[2][NC], Ub[3][NC], Dmb[NC], Dpb[NC];
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
     dUb[0][k] = dUb[1][k] = 0.0;
-    hDmb[k] = hDpb[k] = 0.0;
+    Dmb[k] = Dpb[k] = 0.0;
   }
 #pragma unroll
   for (int q = 0; q < 2; ++q) project_bwd<NC>(e, dU[q], Dqb[q], dUb[q], hb1b, hb2b, hicb, eb, fu);
-  project_bwd<NC>(e, hD3[0], Zmb, hDmb, hb1b, hb2b, hicb, eb, fu);
-  project_bwd<NC>(e, hD3[2], Zpb, hDpb, hb1b, hb2b, hicb, eb, fu);
+  project_bwd<NC>(e, D3[0], Zmb, Dmb, hb1b, hb2b, hicb, eb, fu);
+  project_bwd<NC>(e, D3[2], Zpb, Dpb, hb1b, hb2b, hicb, eb, fu);
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
     Ub[0][k] = -dUb[0][k];
@@ -142,9 +143,9 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
   // (the table is its own transpose)
 #pragma unroll
   for (int q = 0; q < 3; ++q) mirror_U<NC>(Ub[q], refl[q]);
-  mirror_D<NC>(hDmb, refl[0]);
-  mirror_D<NC>(hDpb, refl[2]);
-  // store (original frame): 3 U contributions, then h * (derivative adjoints) of cells i-1, i+1
+  mirror_D<NC>(Dmb, refl[0]);
+  mirror_D<NC>(Dpb, refl[2]);
+  // store (original frame): 3 U contributions, then the derivative adjoints of cells i-1, i+1
   double* out = aw.CM + ((long long)d * plane + p) * 5 * NC;
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
@@ -153,13 +154,13 @@ __global__ void __launch_bounds__(kThreads) k_adj_cell(Grid g, const double* __r
     for (int k = 0; k < NC; ++k) out[q * NC + k] = Ub[q][k];
   }
   if (d == 1) {
-    swap_frame<NC>(hDmb);
-    swap_frame<NC>(hDpb);
+    swap_frame<NC>(Dmb);
+    swap_frame<NC>(Dpb);
   }
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
-    out[3 * NC + k] = h * hDmb[k];
-    out[4 * NC + k] = h * hDpb[k];
+    out[3 * NC + k] = Dmb[k];
+    out[4 * NC + k] = Dpb[k];
   }
 }
 
@@ -190,7 +191,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
     pc[q] = HW_IDX(dir == 0 ? (long long)line * g.nx + a : (long long)a * g.nx + line, plane);
   }
   const int fown = dir == 0 ? 1 : 2;
-  const double h = g.h[dir], ih = g.ih[dir];
+  // 1/(2h): the flux adjoints below are differences (mu_L[right] - mu_L[left]) without their 1/h,
+  // which this coefficient carries together with the 1/2 of the LF fluxes
+  const double hih = g.hih[dir];
+  const double k21 = g.uvd[dir][0], k3 = g.uvd[dir][1];
   const double alpha = alpha2[dir];
   const FU fu = fu_of(aw.scal);
   double Uq[4][NC], Zq[4][NC];
@@ -199,7 +203,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
       Uq[q][k] = S[k * plane + pc[q]];
-      Zq[q][k] = h * S[(fown * NC + k) * plane + pc[q]];
+      Zq[q][k] = S[(fown * NC + k) * plane + pc[q]];  // unscaled, as in the forward face kernel
     }
     if (dir == 1) {
       swap_frame<NC>(Uq[q]);
@@ -220,8 +224,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
       const double lf = hasL ? muL[k * plane + HW_IDX(cL, plane)] : 0.0;
       const double rh = hasR ? muL[(fown * NC + k) * plane + HW_IDX(cR, plane)] : 0.0;
       const double lh = hasL ? muL[(fown * NC + k) * plane + HW_IDX(cL, plane)] : 0.0;
-      nuf[k] = fu.sub(rf, lf) * ih;
-      nuh[k] = fu.sub(rh, lh) * ih;
+      nuf[k] = fu.sub(rf, lf);
+      nuh[k] = fu.sub(rh, lh);
     }
     if (dir == 1) {
       swap_frame<NC>(nuf);
@@ -241,8 +245,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
   Eig<NC> e;
   e.setup(ub, vb, Hb, c2 * ic, ic, g.gm1);
   // the interpolation sees the characteristic fields only through differences of neighbouring
-  // cells; the interface derivatives (h-scaled, Eq. P'xi) are linear in the stencil and formed in
-  // conserved variables
+  // cells; the interface derivatives (Eq. P'xi) are linear in the stencil and formed in conserved
+  // variables (k21 = 21/(16 h), k3 = 3/(16 h))
   double dU[3][NC], Dm[NC], Dp[NC];
 #pragma unroll
   for (int q = 0; q < 3; ++q)
@@ -250,8 +254,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
     for (int k = 0; k < NC; ++k) dU[q][k] = fu.sub(Uq[q + 1][k], Uq[q][k]);
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
-    Dm[k] = fma(1.3125, dU[1][k], fma(-0.1875, dU[0][k], fma(0.0625, Zq[0][k], -0.1875 * Zq[2][k])));
-    Dp[k] = fma(1.3125, dU[1][k], fma(-0.1875, dU[2][k], fma(-0.1875, Zq[1][k], 0.0625 * Zq[3][k])));
+    Dm[k] = fma(k21, dU[1][k], fma(-k3, dU[0][k], fma(0.0625, Zq[0][k], -0.1875 * Zq[2][k])));
+    Dp[k] = fma(k21, dU[1][k], fma(-k3, dU[2][k], fma(-0.1875, Zq[1][k], 0.0625 * Zq[3][k])));
   }
   double Dq[3][NC], Yq[4][NC];
 #pragma unroll
@@ -262,7 +266,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
   // forward intermediates of the interpolation, per field, kept in this thread's shared-memory slots
   extern __shared__ double adj_face_sm[];
   double* const svb = adj_face_sm + threadIdx.x;
-  const AdjK ak = adj_k(g, fu);
+  const AdjK ak = adj_k(g, dir, fu);
 #pragma unroll
   for (int s = 0; s < NC; ++s)
     face_field_save(Dq[0][s], Dq[1][s], Dq[2][s], Yq[0][s], Yq[1][s], Yq[2][s], Yq[3][s], ak, cm[s], cp[s],
@@ -271,16 +275,18 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
   double Um[NC], Up[NC];
   e.back_add(cm, Uq[1], Um, fu);
   e.back_add(cp, Uq[2], Up, fu);
-  // ---- backward: fh = (FUm + FUp - alpha (Up - Um)) / 2 + Df, hh = hih (HDm + HDp - alpha (Dp - Dm)) + Dh
+  // ---- backward: fh = (FUm + FUp - alpha (Up - Um)) / 2 + Df, hh = (HDm + HDp - alpha (Dp - Dm)) / 2
+  // + Dh, with the flux adjoints nuf / h and nuh / h
   double Umb[NC], Upb[NC], Dmb[NC], Dpb[NC], Fb[NC], Hb2[NC];
+  const double ha = hih * alpha;
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
-    Umb[k] = 0.5 * alpha * nuf[k];
-    Upb[k] = -0.5 * alpha * nuf[k];
-    Dmb[k] = g.hih[dir] * alpha * nuh[k];
-    Dpb[k] = -g.hih[dir] * alpha * nuh[k];
-    Fb[k] = 0.5 * nuf[k];
-    Hb2[k] = g.hih[dir] * nuh[k];
+    Umb[k] = ha * nuf[k];
+    Upb[k] = -Umb[k];
+    Dmb[k] = ha * nuh[k];
+    Dpb[k] = -Dmb[k];
+    Fb[k] = hih * nuf[k];
+    Hb2[k] = hih * nuh[k];
   }
   {
     // the primitives of each interface state, shared by its flux and Jacobian-product backward
@@ -304,9 +310,9 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
     Uqb[0][k] = Uqb[3][k] = 0.0;
     Uqb[1][k] = Umb[k];
     Uqb[2][k] = Upb[k];
-    dUb[0][k] = -0.1875 * Dmb[k];
-    dUb[1][k] = 1.3125 * fu.add(Dmb[k], Dpb[k]);
-    dUb[2][k] = -0.1875 * Dpb[k];
+    dUb[0][k] = -k3 * Dmb[k];
+    dUb[1][k] = k21 * fu.add(Dmb[k], Dpb[k]);
+    dUb[2][k] = -k3 * Dpb[k];
     Zqb[0][k] = 0.0625 * Dmb[k];
     Zqb[1][k] = -0.1875 * Dpb[k];
     Zqb[2][k] = -0.1875 * Dmb[k];
@@ -357,7 +363,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
     prim_bwd<NC>(Uq[2], prr, g.gm1, Hrb * (Uq[2][NC - 1] + prr.p), ubb * sr * iw, vbb * sr * iw, Hrb * prr.ir,
                  Uqb[2]);
   }
-  // store (original frame); the derivative contributions carry the factor h of Z = h D
+  // store (original frame): the contributions to U and to the unscaled derivative of the direction
   const long long fo = HW_IDX(dir == 0 ? (long long)line * (g.nx + 1) + fa : (long long)fa * g.nx + line,
                               dir == 0 ? (long long)(g.nx + 1) * g.ny : (long long)(g.ny + 1) * g.nx);
   const long long base = ((dir == 0 ? 0 : (long long)(g.nx + 1) * g.ny) + fo) * 4 * NC;
@@ -372,7 +378,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_face(Grid g, const double* __r
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
       aw.CU[base + q * NC + k] = Uqb[q][k];
-      aw.CD[base + q * NC + k] = h * Zqb[q][k];
+      aw.CD[base + q * NC + k] = Zqb[q][k];
     }
   }
 }

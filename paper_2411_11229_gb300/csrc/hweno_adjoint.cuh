@@ -8,38 +8,39 @@
 
 namespace hw {
 
-// The stencil constants of the adjoint's h-scaled forms (Grid fields, see Grid), copied into
-// thread registers through the integer pipe (FU::reg) so that the DFMAs reading them take register
-// operands: the indicator's split (aN, aS, bT), eps, G, Gd, cdu, csv and the candidate
-// coefficients dm, dp.
+// The stencil constants of one direction, those of the forward kernels (StencilK): derivatives
+// enter unscaled, the h of every derivative term folded into its coefficient (see Grid).  Copied
+// into thread registers through the integer pipe (FU::reg) so that the DFMAs reading them take
+// register operands: the indicator's split (aN = bN[dir], aS = bS[dir], bT), eps, G, Gd, cdu,
+// csv = ucsv[dir] and the candidate coefficients dm = udm[dir], dp = udp[dir].
 struct AdjK {
   double eps, aN1, aN2, aS1, aS2, bT1, bT2, G, Gd, cdu, csv;
   double dm[4], dp[4];
 };
-__device__ __forceinline__ AdjK adj_k(const Grid& g, const FU& f) {
+__device__ __forceinline__ AdjK adj_k(const Grid& g, int dir, const FU& f) {
   AdjK k;
   k.eps = f.reg(g.eps);
-  k.aN1 = f.reg(g.aN1);
-  k.aN2 = f.reg(g.aN2);
-  k.aS1 = f.reg(g.aS1);
-  k.aS2 = f.reg(g.aS2);
+  k.aN1 = f.reg(g.bN1[dir]);
+  k.aN2 = f.reg(g.bN2[dir]);
+  k.aS1 = f.reg(g.bS1[dir]);
+  k.aS2 = f.reg(g.bS2[dir]);
   k.bT1 = f.reg(g.bT1);
   k.bT2 = f.reg(g.bT2);
   k.G = f.reg(g.G);
   k.Gd = f.reg(g.Gd);
   k.cdu = f.reg(g.cdu);
-  k.csv = f.reg(g.csv);
+  k.csv = f.reg(g.ucsv[dir]);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    k.dm[i] = f.reg(g.dm[i]);
-    k.dp[i] = f.reg(g.dp[i]);
+    k.dm[i] = f.reg(g.udm[dir][i]);
+    k.dp[i] = f.reg(g.udp[dir][i]);
   }
   return k;
 }
 
-// e0 = beta0 + eps of the stencil {i-1, i, i+1} from the differences dm, dp and the h-scaled
-// derivatives ym = h v_{i-1}, yp = h v_{i+1} (Eq. GHYZ): the two quadratic forms of beta0 with the
-// square completed in the derivative term, S1 (sv + N1 du)^2 + T1 du^2 + S2 (dv + N2 d2)^2 + T2 d2^2
+// e0 = beta0 + eps of the stencil {i-1, i, i+1} from the differences dm, dp and the unscaled
+// derivatives ym = v_{i-1}, yp = v_{i+1} along the direction of k (Eq. GHYZ; the forward kernels'
+// beta0_eps): the two quadratic forms of beta0 with the square completed in the derivative term, S1 (sv + N1 du)^2 + T1 du^2 + S2 (dv + N2 d2)^2 + T2 d2^2
 // (du = dm + dp, d2 = dp - dm, sv = ym + yp, dv = ym - yp), eps as the first addend.  Returns e0,
 // du and sv, and in bt the four products S1 y1, S2 y2, T1 du, T2 d2 (its backward pass reads them).
 struct BetaTerms {
@@ -125,11 +126,11 @@ __device__ __forceinline__ BetaTerms load_terms(const double* sv, int stride) {
   return BetaTerms{sv[8 * stride], sv[9 * stride], sv[10 * stride], sv[11 * stride]};
 }
 
-// One characteristic field at one face k+1/2 (h-scaled derivatives) from the differences
-// d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2 of the cells k-1..k+2 and their scaled derivatives
-// y0..y3: um - w1 and up - w2 (the interface values less the centre values; Eqs. Pxi, interp),
-// saving the intermediates [e0, W0, W1, W2, r, X, 1/den, tau, S1 y1, S2 y2, T1 du, T2 d2] of the
-// stencil of cell k, then of cell k+1.
+// One characteristic field at one face k+1/2 (the forward kernels' face_field_d) from the
+// differences d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2 of the cells k-1..k+2 and their
+// unscaled derivatives y0..y3 along the direction of k: um - w1 and up - w2 (the interface values
+// less the centre values; Eqs. Pxi, interp), saving the intermediates [e0, W0, W1, W2, r, X,
+// 1/den, tau, S1 y1, S2 y2, T1 du, T2 d2] of the stencil of cell k, then of cell k+1.
 __device__ __forceinline__ void face_field_save(double d01, double d12, double d23, double y0, double y1,
                                                 double y2, double y3, const AdjK& k, double& dum, double& dup,
                                                 double* sv, int stride, const FU& f) {
@@ -222,8 +223,8 @@ __device__ __forceinline__ void face_field_bwd_saved(double d01, double d12, dou
 }
 
 // The limiter (Eq. limiter) of one characteristic field from the differences d01 = w1 - w0,
-// d12 = w2 - w1 and the scaled derivatives y0, y2: h v~_i, saving [e0, W0, W1, W2, t, num, 1/den,
-// tau, S1 y1, S2 y2, T1 du, T2 d2].
+// d12 = w2 - w1 and the unscaled derivatives y0, y2 (the forward kernels' cell_field_d): h v~_i,
+// saving [e0, W0, W1, W2, t, num, 1/den, tau, S1 y1, S2 y2, T1 du, T2 d2].
 __device__ __forceinline__ double cell_field_save(double d01, double d12, double y0, double y2, const AdjK& k,
                                                   double* sv, int stride, const FU& f) {
   double du, svs;
@@ -257,7 +258,7 @@ __device__ __forceinline__ void cell_field_bwd_saved(double d01, double d12, dou
   const double W0b = fma(numb, t, f.mul(denb, k.Gd)), W1b = fma(numb, d01, denb), W2b = fma(numb, d12, denb);
   const double tb = f.mul(numb, W0);
   double d01b = f.mul(numb, W1), d12b = f.mul(numb, W2);
-  // t = cdu (d01 + d12) - csv (y0 + y2)
+  // t = cdu (d01 + d12) - csv (y0 + y2), csv = ucsv of the direction
   d01b += k.cdu * tb;
   d12b += k.cdu * tb;
   y0b -= k.csv * tb;

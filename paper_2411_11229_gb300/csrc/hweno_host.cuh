@@ -163,13 +163,9 @@ inline Grid grid_of(const hweno_ctx* h) {
   // left face (mirror) on (d_{i,i+1} of its own stencil's first pair, second pair, h v_{i-1}, h v_{i+1})
   const double dm[4] = {-cr[0], cr[2], cr[3], cr[4]};
   const double dp[4] = {-cl[0], cl[2], cl[3], cl[4]};
-  for (int k = 0; k < 4; ++k) {
-    g.dm[k] = dm[k];
-    g.dp[k] = dp[k];
-  }
   g.G = g.g0 / g1;
   g.cdu = (0.75 - g.d1) / g.d1;
-  g.csv = 0.25 / g.d1;
+  const double csv = 0.25 / g.d1;
   g.Gd = g.d0 / g.d1;
   // The smoothness indicator beta0 of Eq. (GHYZ) as two quadratic forms.  Its linear forms
   // (coefficients on (h sv, du) and on (h dv, d2)) with their weights:
@@ -193,10 +189,6 @@ inline Grid grid_of(const hweno_ctx* h) {
   const Pair p1 = pair(fA, 1.0, fC, 781.0 / 20.0), p2 = pair(fB, 13.0 / 3.0, fD, 1421461.0 / 2275.0);
   g.bT1 = p1.T;
   g.bT2 = p2.T;
-  g.aS1 = p1.s;
-  g.aN1 = p1.q / p1.s;
-  g.aS2 = p2.s;
-  g.aN2 = p2.q / p2.s;
   const double hs[2] = {h->dx, h->dy};
   for (int d = 0; d < 2; ++d) {
     g.h[d] = hs[d];
@@ -221,7 +213,7 @@ inline Grid grid_of(const hweno_ctx* h) {
     g.udp[d][3] = dp[3] * hs[d];
     g.uvd[d][0] = 1.3125 / hs[d];
     g.uvd[d][1] = 0.1875 / hs[d];
-    g.ucsv[d] = g.csv * hs[d];
+    g.ucsv[d] = csv * hs[d];
     g.e2fih[d] = hw::DCoef2::ef / hs[d];
     g.e2gih[d] = hw::DCoef2::eg / hs[d];
   }

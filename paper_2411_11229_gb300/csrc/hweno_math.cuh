@@ -42,22 +42,19 @@ struct Grid {
   // Folded constants (computed on the host from the linear weights and the spacings):
   //   cr, cl: coefficients of (p0 - gamma1 (p1 + p2)) / gamma1 on (um, u0, up, hvm, hvp) at the
   //           right face x_{i+1/2} and, mirrored, at the left face x_{i-1/2};
-  //   G = gamma0 / gamma1;  limiter: cdu = (3/4 - d1)/d1, csv = (1/4)/d1, Gd = d0 / d1;
+  //   G = gamma0 / gamma1;  limiter: cdu = (3/4 - d1)/d1, Gd = d0 / d1;
   //   per direction: h, 1/h, ch*h, ef/h, eg/h (D-terms), 1/(2h).
   double cr[5], cl[5], G;
-  //   dm, dp: the same combinations with the centre value taken out (their value coefficients
-  //           sum to G): (p0 - gamma1 (p1 + p2))/gamma1 - G u_i on (d01, d12, hvm, hvp) at the
-  //           right face and, mirrored, on (d_{i-1,i}, d_{i,i+1}, ...) at the left face;
-  double dm[4], dp[4];
-  double cdu, csv, Gd;
-  // The same arithmetic with the derivatives entering unscaled (v, not h v), per direction: the h
-  // of every derivative term folded into its coefficient.  bS1, bN1, bS2, bN2 (per direction) and
-  // bT1, bT2: the smoothness indicator as S1 (sv + N1 du)^2 + T1 du^2 + S2 (dv + N2 d2)^2 + T2 d2^2
-  // (see beta0_eps); udm, udp: dm, dp with their derivative coefficients times h;
-  // uvd = (21/16, 3/16)/h: the cell differences in the derivative at the face; ucsv = csv h.
+  double cdu, Gd;
+  // The arithmetic with the derivatives entering unscaled (v, not h v), per direction: the h of
+  // every derivative term folded into its coefficient (the forward and the adjoint kernels).
+  // bS1, bN1, bS2, bN2 (per direction) and bT1, bT2: the smoothness indicator as
+  // S1 (sv + N1 du)^2 + T1 du^2 + S2 (dv + N2 d2)^2 + T2 d2^2 (see beta0_eps); udm, udp: the
+  // combinations (p0 - gamma1 (p1 + p2))/gamma1 - G u_i with the centre value taken out (their value
+  // coefficients sum to G) on (d01, d12, vm, vp) at the right face and, mirrored, on
+  // (d_{i-1,i}, d_{i,i+1}, ...) at the left face; uvd = (21/16, 3/16)/h: the cell differences in
+  // the derivative at the face; ucsv = h/(4 d1), the limiter's derivative coefficient.
   double bS1[2], bN1[2], bS2[2], bN2[2], bT1, bT2;
-  // the same split for h-scaled derivatives (h = 1 in S and N; the adjoint's form)
-  double aS1, aN1, aS2, aN2;
   double udm[2][4], udp[2][4], uvd[2][2], ucsv[2];
   double h[2], ih[2], chh[2], efih[2], egih[2], hih[2];
   // Extended scheme (read only by the kernels instantiated with VAR != 0):
