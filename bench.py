@@ -211,7 +211,9 @@ def run_batched(dev, steps: int = 3, only_1d: bool = False):
     """The uneven batched sweep: 256 1D Euler lines (N log-uniform in [128, 16384], seeded Riemann
     data) and 32 2D Euler grids (sides in {128, 256, 512, 1024}), every instance with its own CFL
     step.  Batched path (one persistent launch per stage, CUDA graph, autotuned launch shape)
-    against one launch per instance and kernel.  only_1d: the 256 lines alone."""
+    against one launch per instance and kernel.  only_1d: the 256 lines alone.  The timed batched
+    steps of the full sweep run between cudaProfilerStart and cudaProfilerStop (no effect without a
+    profiler; `ncu --profile-from-start off` records just those launches)."""
     import numpy as np
     import torch
 
@@ -237,10 +239,15 @@ def run_batched(dev, steps: int = 3, only_1d: bool = False):
         l0 = b.launch_count()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        window = mode == "batched" and not only_1d
+        if window:
+            torch.cuda.profiler.start()
         e0.record(b.stream)
         run(steps)
         e1.record(b.stream)
         b.sync()
+        if window:
+            torch.cuda.profiler.stop()
         times[mode] = e0.elapsed_time(e1) / steps
         res[f"launches_per_step_{mode}"] = (b.launch_count() - l0) // steps
         b.dts()
