@@ -126,3 +126,37 @@ def test_create_ex_sizes_and_adjoint_refusal():
     finally:
         for h in (h0, h1, h2, h3):
             lib.hweno_destroy(h)
+
+
+def test_pipeline_and_stage_copy_refuse_invalid_arguments_on_the_host():
+    """hweno_pipeline and hweno_step_stages check their arguments before any device work; the
+    bounds-check entry points report -1 in the normal build."""
+    lib = C.load()
+    rc, h = _create(2, C.HWENO_EULER, 40, 30, 0.05, 0.05, 1.4, C.HWENO_BC_PERIODIC)
+    assert rc == 0
+    try:
+        state = lib.hweno_state_doubles(h) * 8
+        assert lib.hweno_pipeline_slot_bytes(h) == ((state + 255) // 256) * 256 + lib.hweno_workspace_bytes(h)
+        assert lib.hweno_pipeline_slot_bytes(None) == 0
+        fake = ctypes.c_void_p(1 << 20)  # never dereferenced: every call below fails validation
+        one = (ctypes.c_void_p * 1)(1 << 21)
+        nul = (ctypes.c_void_p * 1)(None)
+        P = lib.hweno_pipeline
+        assert P(None, 1, one, one, 1, 2, fake) == C.HWENO_EINVAL
+        assert P(h, -1, one, one, 1, 2, fake) == C.HWENO_EINVAL
+        assert P(h, 1, one, one, -1, 2, fake) == C.HWENO_EINVAL
+        assert P(h, 1, one, one, 1, 0, fake) == C.HWENO_EINVAL
+        assert P(h, 1, one, one, 1, 9, fake) == C.HWENO_EINVAL
+        assert P(h, 1, one, one, 1, 2, None) == C.HWENO_EINVAL
+        assert P(h, 1, one, one, 1, 2, ctypes.c_void_p((1 << 20) + 8)) == C.HWENO_EINVAL
+        assert P(h, 1, None, one, 1, 2, fake) == C.HWENO_EINVAL
+        assert P(h, 1, one, nul, 1, 2, fake) == C.HWENO_EINVAL
+        S = lib.hweno_step_stages
+        assert S(h, 0.0, None, fake) == C.HWENO_EINVAL
+        assert S(h, float("nan"), fake, fake) == C.HWENO_EINVAL
+        assert S(h, 0.0, fake, fake) == C.HWENO_ESTATE  # nothing bound
+        where = ctypes.c_int(7)
+        assert lib.hweno_bounds_status(ctypes.byref(where)) == -1 and where.value == 0
+        assert lib.hweno_bounds_selftest() == -1
+    finally:
+        lib.hweno_destroy(h)
