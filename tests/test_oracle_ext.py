@@ -1,8 +1,8 @@
 """Pins of the oracle's extended-precision evaluation (long double: 64-bit significand on x86-64,
 113-bit on AArch64), the reference the GPU path's rounding is measured against at full size.
 
-  * it computes the same scheme: the HWENO-I accuracy tables of Sec. 4 to the printed digits, and
-    the FP64 oracle within that oracle's own rounding envelope;
+  * it computes the same scheme: the HWENO-I accuracy tables of Sec. 4 (1D and 2D Euler, 1D and 2D
+    Burgers) to the printed digits, and the FP64 oracle within that oracle's own rounding envelope;
   * it carries the extra precision through the whole operator: for linear advection the scheme is
     invariant under u -> u + C in exact arithmetic (the candidates of Eqs. (Pxi) and the
     combination of Eq. (interp) reproduce constants, the indicators, slopes, D-terms of Eq. (Cd-1)
@@ -126,3 +126,26 @@ def test_ext_against_fp64_within_rounding():
     err, env = _rel_planes(out, oute, 12), _rel_planes(outp, out, 12)
     print("10 steps: FP64 against extended", err.max(), "one-ulp drift", env.max())
     assert (err <= np.maximum(2 * env, 1e-15)).all(), (err, env)
+
+
+def test_ext_paper_table_burgers():
+    """The scalar code paths in extended precision: the HWENO-I columns of the 1D and 2D Burgers
+    tables of Sec. 4 (first rows) to the printed digits."""
+    with open(GOLD) as f:
+        tables = json.load(f)
+    for n, l1, linf in tables["burgers1d"]["rows"][:2]:
+        S, dx = W.burgers_1d(n)
+        cfg = O.make_cfg(1, O.BURGERS, n, dx=dx)
+        out, _, _ = O.run_ext(cfg, S, 0.5, 0.6, 5.0 / 3.0)
+        ex, _ = W.burgers_1d(n, t=0.5)
+        e = np.abs(out[0, 0] - ex[0, 0])
+        assert _close_to_printed(e.mean() / (2 * np.pi), l1), (n, e.mean(), l1)
+        assert _close_to_printed(e.max(), linf), (n, e.max(), linf)
+    n, l1, linf = tables["burgers2d"]["rows"][0]
+    S, dx = W.burgers_2d(n)
+    cfg = O.make_cfg(2, O.BURGERS, n, n, dx=dx, dy=dx)
+    out, _, _ = O.run_ext(cfg, S, 0.5, 0.6, 5.0 / 3.0)
+    ex, _ = W.burgers_2d(n, t=0.5)
+    e = np.abs(out[0, 0] - ex[0, 0])
+    assert _close_to_printed(e.mean(), l1), (n, e.mean(), l1)
+    assert _close_to_printed(e.max(), linf), (n, e.max(), linf)
